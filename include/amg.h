@@ -1,0 +1,203 @@
+/*
+ * amg.h -- C ABI of the GB300 (sm_103a) auxiliary-grid algebraic multigrid library
+ * (libamg_gb300.so).
+ *
+ * The method is that of Wang, Hu, Cohen and Xu, "A Parallel Auxiliary Grid AMG Method for
+ * GPU": unsmoothed aggregation from a region quadtree over a uniform auxiliary grid laid on
+ * the finest mesh, Galerkin coarse operators, a quadtree-coloured Gauss-Seidel smoother and
+ * the nonlinear AMLI-cycle (K-cycle) preconditioning a Krylov iteration. All of the work
+ * runs in the library's CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: an AMG_* status (0 = AMG_OK). No C++ exception crosses this interface.
+ *  - Pointers marked "device or host" may point to device memory or to host memory (pageable
+ *    or pinned); the library detects which and stages host data through device buffers
+ *    inside the call. All other array pointers are host pointers unless stated.
+ *  - Ownership: input arrays are borrowed for the duration of the call only; setup copies
+ *    what it keeps. A hierarchy is owned by the library until amg_free.
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream). All device work
+ *    of a call is ordered on it. Calls return after their results are complete (the status,
+ *    iteration counts and residuals are host values).
+ *  - Threads: a hierarchy may be used by one thread / one stream at a time; different
+ *    hierarchies are independent.
+ *  - Indices are 32-bit: n < 2^31 and nnz < 2^31.
+ */
+#ifndef AMG_GB300_AMG_H
+#define AMG_GB300_AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    AMG_OK = 0,
+    AMG_ERR_INVALID_ARG = 1,   /* NULL pointer, n <= 0, bad option, non-finite coordinate */
+    AMG_ERR_BAD_MATRIX = 2,    /* not square CSR with sorted unique in-range columns and a
+                                  positive diagonal, non-finite value, or a coarsest matrix
+                                  that is not positive definite */
+    AMG_ERR_OOM = 3,           /* device allocation failed */
+    AMG_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    AMG_ERR_NOT_CONVERGED = 5, /* max_iters reached; x, iters, relres are valid */
+    AMG_ERR_BREAKDOWN = 6,     /* (p, Ap) <= 0 or non-finite in the outer Krylov iteration */
+    AMG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+    AMG_ERR_UNSUPPORTED = 8    /* outside the library's limits (see amg_options) */
+};
+
+/* Outer Krylov iteration. */
+enum { AMG_OUTER_FCG = 0, AMG_OUTER_FGMRES = 1 };
+/* Arithmetic of the AMLI-cycle (the preconditioner). */
+enum { AMG_FP64 = 0, AMG_FP32 = 1 };
+
+/*
+ * Sparse SPD matrix A of the linear system A x = b (paper Sec. 1), in CSR:
+ * rowptr[n+1], col[nnz], val[nnz]; columns ascending and unique within each row, the
+ * diagonal present and positive. Arrays are device or host memory, borrowed.
+ */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const double *val;
+} amg_csr;
+
+/* Options; amg_options_default fills the defaults given in brackets. */
+typedef struct {
+    int aux_level;      /* depth L of the quadtree / auxiliary grid 2^L x 2^L (Sec. 3.1);
+                           0 = automatic, the largest L with 4^L <= n [0]; at most 14 */
+    int coarsest_max;   /* coarsen until a level has at most this many unknowns; that level
+                           is solved exactly (Alg. 2, B_1 = A_1^{-1}) [64]; 1..256 */
+    int kcycle_n;       /* steps n of Alg. 1 on each coarse level of the AMLI-cycle [2];
+                           1..4 */
+    int max_iters;      /* outer iterations [200] */
+    int outer;          /* AMG_OUTER_FCG: Alg. 1 on the finest level (flexible CG with full
+                           A-orthogonalisation) [default]; AMG_OUTER_FGMRES: restarted
+                           flexible GMRES (requires cycle_prec = AMG_FP32 or FP64) */
+    int cycle_prec;     /* AMG_FP64 [default] or AMG_FP32 (cycle in single precision, outer
+                           residuals, updates and inner products in double) */
+    int fgmres_restart; /* restart length of FGMRES [30] */
+    int has_bbox;       /* 1: use bbox as the auxiliary box Omega_0^0 instead of the
+                           coordinates' min/max (eq. ab12) [0] */
+    double bbox[4];     /* a1, b1, a2, b2 */
+} amg_options;
+
+typedef struct amg_hierarchy amg_hierarchy;
+
+/* Fill *opt with the defaults. */
+void amg_options_default(amg_options *opt);
+
+/*
+ * Setup phase (paper Sec. 3 and Sec. 4.2-4.5): auxiliary box (eq. ab12), level-L aggregates
+ * by binning the unknowns' coordinates into the 2^L x 2^L auxiliary cells (Sec. 4.2), coarse
+ * aggregates from the quadtree parents (eq. agg_k), Galerkin operators A_{k-1} = P^t A_k P
+ * (eq. acsum) on every level down to the first with at most coarsest_max unknowns, the
+ * quadtree colouring of every level (Sec. 4.5), and the exact coarsest solve.
+ *   A      : the fine matrix (device or host, borrowed).
+ *   x, y   : coordinates (x_j, y_j) of unknown j, arrays of A->n doubles (device or host).
+ *   opt    : options (host); NULL = defaults.
+ *   stream : cudaStream_t for the device work.
+ *   out    : receives the new hierarchy (owned by the library until amg_free).
+ * Errors: AMG_ERR_INVALID_ARG, AMG_ERR_BAD_MATRIX (checked on the device),
+ * AMG_ERR_UNSUPPORTED, AMG_ERR_OOM, AMG_ERR_CUDA. On error *out is NULL.
+ */
+int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_options *opt,
+              void *stream, amg_hierarchy **out);
+
+/*
+ * Solve phase: x = A^{-1} b by the outer Krylov iteration preconditioned with the nonlinear
+ * AMLI-cycle (Alg. 2 with Alg. 1 on the coarse levels), from x_0 = 0, until
+ * ||b - A x||_2 / ||b||_2 <= tol.
+ *   b      : right-hand side, n doubles (device or host, borrowed).
+ *   tol    : relative residual target (>= 0).
+ *   x      : output, n doubles (device or host, caller-allocated; initial content ignored).
+ *   iters  : receives the number of outer iterations (preconditioner applications); may be
+ *            NULL.
+ *   relres : receives ||b - A x||_2 / ||b||_2 of the returned x; may be NULL.
+ * Returns AMG_OK, or AMG_ERR_NOT_CONVERGED / AMG_ERR_BREAKDOWN with x, iters and relres
+ * still valid, or another error.
+ */
+int amg_solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
+              double *relres, void *stream);
+
+/* Device memory held by the hierarchy, in bytes (for admission against a memory budget). */
+int amg_hierarchy_bytes(const amg_hierarchy *h, size_t *bytes);
+
+/* Release a hierarchy and its device memory (NULL is ignored). */
+void amg_free(amg_hierarchy *h);
+
+/* Static, human-readable text of a status code. */
+const char *amg_status_string(int status);
+
+/* Detail of the last failing call on the calling thread (valid until its next call). */
+const char *amg_last_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Inspection (host copies of what setup built), for checking and diagnostics.
+ * Levels are numbered 0 = the given fine matrix, 1 = the auxiliary level L, 2 = level L-1,
+ * ..., num_levels-1 = the coarsest. Rows of level l >= 1 are aggregates numbered in
+ * ascending lexicographic cell order t1 + 2^k t2 (the numbering of Sec. 3.1), empty cells
+ * skipped.
+ * ------------------------------------------------------------------------------------- */
+
+/* Number of levels and the depth L actually used. */
+int amg_num_levels(const amg_hierarchy *h, int *num_levels, int *aux_level);
+
+/* The auxiliary box a1, b1, a2, b2 actually used (eq. ab12). */
+int amg_get_bbox(const amg_hierarchy *h, double bbox[4]);
+
+/*
+ * info[0] = n (unknowns), info[1] = stored entries of A_l (without padding),
+ * info[2] = cells per side of the grid the rows live on (level 0: the level-L grid),
+ * info[3] = span s (largest cell offset over the stored entries),
+ * info[4] = colour modulus m = max(2, s+1) (m*m colours),
+ * info[5] = padded entries in the on-device sliced-ELL layout,
+ * info[6] = 1 if this is the coarsest level (solved exactly).
+ */
+int amg_level_info(const amg_hierarchy *h, int level, int64_t info[8]);
+
+/*
+ * Host copies of level `level` in natural row order (fine: the caller's unknown order;
+ * coarse: aggregate number). Any pointer may be NULL to skip it. Sizes: n for agg, color,
+ * t1, t2; n+1 for rowptr; info[1] for col and val (CSR, columns ascending).
+ *   agg    : row of the next coarser level containing each row (-1 on the coarsest).
+ *   color  : colour (t1 mod m) + m (t2 mod m) of each row's cell.
+ *   t1, t2 : cell coordinates of each row.
+ */
+int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *color,
+                     int32_t *t1, int32_t *t2, int32_t *rowptr, int32_t *col, double *val);
+
+/*
+ * One application of the AMLI-cycle preconditioner z = B^_level[f] (Alg. 2) on level
+ * `level` (0 = finest), in FP64, vectors in that level's natural row order.
+ * f, z: device or host arrays of n doubles (z caller-allocated).
+ */
+int amg_apply_cycle(amg_hierarchy *h, int level, const double *f, double *z, void *stream);
+
+/*
+ * One Gauss-Seidel sweep of the quadtree-coloured smoother on level `level` (Sec. 4.5):
+ * backward = 0: forward sweep R_k (colours ascending); 1: backward sweep R_k^t. Starts from
+ * the given u (updated in place). f, u: device or host, natural row order.
+ */
+int amg_smooth(amg_hierarchy *h, int level, int backward, const double *f, double *u,
+               void *stream);
+
+/*
+ * The ELL format of paper Sec. 4.1 (Fig. ellform): a CSR matrix of `rows` rows with at most
+ * K = width entries per row stored as two rows x K arrays Aj (columns, -1 padding) and Ax
+ * (values, 0 padding), written here column-major (entry (i, k) at [k * rows + i]).
+ * diag_first = 1 moves each row's diagonal entry to slot 0 (as the paper's solver stores
+ * it); 0 keeps the CSR order. Device kernel; all arrays are device or host memory.
+ * Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries.
+ */
+int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, const double *val,
+                   int32_t width, int diag_first, int32_t *Aj, double *Ax, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_GB300_AMG_H */

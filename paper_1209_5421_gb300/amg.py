@@ -1,0 +1,259 @@
+"""Python binding of libamg_gb300.so (include/amg.h): argument marshalling only.
+
+Every step of setup and solve runs in the library's CUDA kernels. Arrays may be numpy
+arrays (host memory; the library stages them to the device) or torch tensors (device or
+host memory). There is no CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamg_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "amg.h")
+
+OK = 0
+ERR_INVALID_ARG, ERR_BAD_MATRIX, ERR_OOM, ERR_CUDA = 1, 2, 3, 4
+ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT, ERR_UNSUPPORTED = 5, 6, 7, 8
+OUTER_FCG, OUTER_FGMRES = 0, 1
+FP64, FP32 = 0, 1
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status}")
+        self.status = status
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("aux_level", C.c_int), ("coarsest_max", C.c_int), ("kcycle_n", C.c_int),
+                ("max_iters", C.c_int), ("outer", C.c_int), ("cycle_prec", C.c_int),
+                ("fgmres_restart", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4)]
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/amg.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(amg_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libamg_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1209_5421_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.amg_options_default.argtypes = [C.POINTER(Options)]
+        L.amg_options_default.restype = None
+        L.amg_setup.argtypes = [C.POINTER(Csr), P, P, C.POINTER(Options), P, C.POINTER(P)]
+        L.amg_solve.argtypes = [P, P, C.c_double, P, C.POINTER(C.c_int), C.POINTER(C.c_double), P]
+        L.amg_hierarchy_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+        L.amg_free.argtypes = [P]
+        L.amg_free.restype = None
+        L.amg_status_string.argtypes = [C.c_int]
+        L.amg_status_string.restype = C.c_char_p
+        L.amg_last_error.argtypes = []
+        L.amg_last_error.restype = C.c_char_p
+        L.amg_num_levels.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.amg_get_bbox.argtypes = [P, P]
+        L.amg_level_info.argtypes = [P, C.c_int, P]
+        L.amg_level_export.argtypes = [P, C.c_int] + [P] * 7
+        L.amg_apply_cycle.argtypes = [P, C.c_int, P, P, P]
+        L.amg_smooth.argtypes = [P, C.c_int, C.c_int, P, P, P]
+        L.amg_csr_to_ell.argtypes = [C.c_int32, P, P, P, C.c_int32, C.c_int, P, P, P]
+        for f in ("amg_setup", "amg_solve", "amg_hierarchy_bytes", "amg_num_levels",
+                  "amg_get_bbox", "amg_level_info", "amg_level_export", "amg_apply_cycle",
+                  "amg_smooth", "amg_csr_to_ell"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise AmgError(status, f"{what}: {lib().amg_last_error().decode()}")
+
+
+def _as(a, dtype):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def status_string(s: int) -> str:
+    return lib().amg_status_string(s).decode()
+
+
+class Hierarchy:
+    """amg_setup / amg_solve on one matrix with node coordinates (paper Sec. 3-4)."""
+
+    def __init__(self, rowptr, col, val, x, y, aux_level=0, coarsest_max=64, kcycle_n=2,
+                 max_iters=200, cycle_prec=FP64, outer=OUTER_FCG, fgmres_restart=30,
+                 bbox=None, stream=None):
+        L = lib()
+        self._keep = (_as(rowptr, np.int32), _as(col, np.int32), _as(val, np.float64),
+                      _as(x, np.float64), _as(y, np.float64))
+        rp, cl, vl, xx, yy = self._keep
+        n = len(rp) - 1
+        nnz = len(cl)
+        A = Csr(n, nnz, _ptr(rp), _ptr(cl), _ptr(vl))
+        o = Options()
+        L.amg_options_default(C.byref(o))
+        o.aux_level, o.coarsest_max, o.kcycle_n, o.max_iters = aux_level, coarsest_max, kcycle_n, max_iters
+        o.cycle_prec, o.outer, o.fgmres_restart = cycle_prec, outer, fgmres_restart
+        if bbox is not None:
+            o.has_bbox = 1
+            for k in range(4):
+                o.bbox[k] = bbox[k]
+        h = C.c_void_p()
+        st = L.amg_setup(C.byref(A), _ptr(xx), _ptr(yy), C.byref(o), _stream(stream), C.byref(h))
+        self._keep = None
+        _check(st, "amg_setup")
+        self.h = h
+        self.n = n
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob.rowptr, prob.col, prob.val, prob.x, prob.y, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().amg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, tol=1e-8, x=None, stream=None, check=False):
+        """x = A^{-1} b. Returns (x, iters, relres, status). x: numpy if b is numpy."""
+        b = _as(b, np.float64)
+        if x is None:
+            x = np.empty(self.n) if isinstance(b, np.ndarray) else b.new_empty(self.n)
+        it = C.c_int()
+        rr = C.c_double()
+        st = lib().amg_solve(self.h, _ptr(b), tol, _ptr(x), C.byref(it), C.byref(rr),
+                             _stream(stream))
+        if check or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st, "amg_solve")
+        return x, it.value, rr.value, st
+
+    @property
+    def nbytes(self) -> int:
+        v = C.c_size_t()
+        _check(lib().amg_hierarchy_bytes(self.h, C.byref(v)), "amg_hierarchy_bytes")
+        return v.value
+
+    @property
+    def nlev(self) -> int:
+        n = C.c_int()
+        a = C.c_int()
+        _check(lib().amg_num_levels(self.h, C.byref(n), C.byref(a)), "amg_num_levels")
+        return n.value
+
+    @property
+    def L(self) -> int:
+        n = C.c_int()
+        a = C.c_int()
+        _check(lib().amg_num_levels(self.h, C.byref(n), C.byref(a)), "amg_num_levels")
+        return a.value
+
+    @property
+    def bbox(self) -> np.ndarray:
+        b = np.empty(4)
+        _check(lib().amg_get_bbox(self.h, _ptr(b)), "amg_get_bbox")
+        return b
+
+    def level_info(self, l: int) -> dict:
+        info = np.zeros(8, np.int64)
+        _check(lib().amg_level_info(self.h, l, _ptr(info)), "amg_level_info")
+        keys = ("n", "stored", "cellw", "span", "m", "padded", "coarsest", "nblocks")
+        return dict(zip(keys, (int(v) for v in info)))
+
+    def level(self, l: int) -> dict:
+        """Natural-order host copies of level l: agg, color, t1, t2 and the CSR operator."""
+        inf = self.level_info(l)
+        n, nnz = inf["n"], inf["stored"]
+        out = {k: np.empty(n, np.int32) for k in ("agg", "color", "t1", "t2")}
+        out["rowptr"] = np.empty(n + 1, np.int32)
+        out["col"] = np.empty(nnz, np.int32)
+        out["val"] = np.empty(nnz)
+        _check(lib().amg_level_export(self.h, l, _ptr(out["agg"]), _ptr(out["color"]),
+                                      _ptr(out["t1"]), _ptr(out["t2"]), _ptr(out["rowptr"]),
+                                      _ptr(out["col"]), _ptr(out["val"])), "amg_level_export")
+        out.update(inf)
+        return out
+
+    def apply_cycle(self, level: int, f, stream=None):
+        f = _as(f, np.float64)
+        z = np.empty(len(f)) if isinstance(f, np.ndarray) else f.new_empty(len(f))
+        _check(lib().amg_apply_cycle(self.h, level, _ptr(f), _ptr(z), _stream(stream)),
+               "amg_apply_cycle")
+        return z
+
+    def smooth(self, level: int, f, u, backward=False, stream=None):
+        f = _as(f, np.float64)
+        u = _as(u, np.float64).copy()
+        _check(lib().amg_smooth(self.h, level, int(backward), _ptr(f), _ptr(u), _stream(stream)),
+               "amg_smooth")
+        return u
+
+
+def csr_to_ell(rowptr, col, val, width, diag_first=True, stream=None):
+    """The paper's ELL format (Sec. 4.1): column-major Aj (cols, -1 pad), Ax (vals, 0 pad)."""
+    rowptr, col, val = _as(rowptr, np.int32), _as(col, np.int32), _as(val, np.float64)
+    rows = len(rowptr) - 1
+    Aj = np.empty(rows * width, np.int32)
+    Ax = np.empty(rows * width)
+    _check(lib().amg_csr_to_ell(rows, _ptr(rowptr), _ptr(col), _ptr(val), width,
+                                int(diag_first), _ptr(Aj), _ptr(Ax), _stream(stream)),
+           "amg_csr_to_ell")
+    return Aj, Ax

@@ -1,0 +1,210 @@
+// Internal structures of the GB300 auxiliary-grid AMG library.
+//
+// Data layout in HBM (every level, "pi order"):
+//   Rows of each level are stored permuted into the smoother's sweep order pi (colour
+//   ascending, then aggregate, then -- on the finest level -- unknown ascending inside the
+//   aggregate; paper Sec. 4.5). Every colour is therefore one contiguous row range, every
+//   finest-level block (aggregate) a contiguous row range, and restriction from the finest
+//   level is a contiguous segmented sum.
+//   Matrices are sliced ELL with slices of 32 rows (one warp): inside a slice, entry k of row
+//   r sits at sl_ptr[r/32] + 32*k + r%32, so a warp reading slot k of its 32 rows touches one
+//   contiguous 256-byte (FP64) segment. Slot 0 holds the diagonal (paper Sec. 4.1 keeps the
+//   diagonal first); padding has col = -1, val = 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+constexpr int kSliceH = 32;        // sliced-ELL slice height (one warp)
+constexpr int kMaxKcycle = 4;      // largest supported kcycle_n
+constexpr int kMaxLevels = 20;
+constexpr int kRedBlocks = 608;    // blocks of the deterministic reductions (4 x 152 SMs)
+constexpr int kRedThreads = 256;
+constexpr int kMaxCoarsest = 256;  // largest exact coarsest level
+
+// scalar slots of a level's device scalar array
+// (one slot per Alg. 1 step where a kernel reads the previous step's value while writing its
+// own, so no grid-wide kernel reads a slot it also writes)
+enum : int {
+    SC_PQ0 = 0,       // (p_i, A p_i) for i = 0..kMaxKcycle-1
+    SC_RP0 = 4,       // (r_i, p_i)
+    SC_ZQ0 = 8,       // (z, A p_j) for j = 0..kMaxKcycle-1 (current step)
+    SC_RR0 = 12,      // (r_{i+1}, r_{i+1}) written by step i
+    SC_STOP0 = 16,    // 1.0 if Alg. 1 stopped at or before step i
+    SC_N = 24
+};
+
+struct Sell {
+    int n = 0;
+    int nslices = 0;
+    int *sl_ptr = nullptr;   // [nslices+1]
+    int *col = nullptr;      // [padded]
+    double *val = nullptr;   // [padded]
+    float *val32 = nullptr;  // FP32 copy of val (FP32 cycle only)
+    int64_t padded = 0;
+    int64_t stored = 0;
+};
+
+template <class T>
+struct Vecs {
+    T *rhs = nullptr, *e = nullptr, *r = nullptr, *z = nullptr;
+    T *p[kMaxKcycle] = {}, *q[kMaxKcycle] = {};
+};
+
+struct Level {
+    int n = 0;
+    int cellw = 0;          // cells per side of the grid the rows live on
+    int span = 0, m = 2, ncolors = 4;
+    bool coarsest = false;
+    Sell A;
+    std::vector<int> color_rows;    // host [ncolors+1]: pi-row range of each colour
+    std::vector<int> color_blocks;  // host [ncolors+1] (finest level): block range per colour
+    int nblocks = 0;
+    int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block
+    int *parent = nullptr;  // [n] pi-row of the next coarser level
+    int4 *children = nullptr;  // level >= 2: [n] children pi-rows in level-1 by quadrant
+    int *nat = nullptr;     // [n] natural index of pi-row p
+    int *inv = nullptr;     // [n] pi-row of natural index
+    int *cell = nullptr;    // [n] cell index t1 + cellw * t2 of pi-row p
+    int *agg_nat = nullptr; // [n] natural aggregate (next level) of natural row
+    double *Ainv = nullptr; // coarsest: dense inverse, pi order, row-major
+    float *Ainv32 = nullptr;
+    Vecs<double> v64;
+    Vecs<float> v32;
+    double *sc = nullptr;   // [SC_N] device scalars of Alg. 1 on this level
+};
+
+}  // namespace amg
+
+struct amg_hierarchy {
+    amg_options opt{};
+    int L = 0;
+    double bbox[4] = {0, 0, 0, 0};
+    int nlev = 0;
+    int64_t N = 0;
+    std::vector<amg::Level> lev;
+    cudaStream_t stream = nullptr;      // private non-blocking stream of the hierarchy
+    cudaEvent_t order_ev = nullptr;     // orders it after the caller's stream
+    int device = 0;
+    // allocations owned by the hierarchy
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    // deterministic reduction scratch
+    double *red_partials = nullptr;   // [kRedBlocks * kMaxRed]
+    unsigned int *red_counter = nullptr;
+    int *err_flag = nullptr;
+    // outer Krylov state
+    double *xo = nullptr, *ro = nullptr, *zo = nullptr, *to = nullptr;  // pi order
+    double *bo = nullptr;
+    int outer_cap = 0;
+    std::vector<double *> P, Q;        // directions p_j, A p_j
+    double **dP = nullptr, **dQ = nullptr;
+    double *osc = nullptr;             // outer scalars
+    int *oit = nullptr;                // device iteration counter
+    double *h_pinned = nullptr;        // pinned host scalars
+    // FGMRES state (FP64 basis)
+    double *gm_V = nullptr, *gm_Z = nullptr, *gm_H = nullptr;
+    int gm_cap = 0;
+    // FP32 cycle buffers for outer<->cycle conversion
+    float *r32 = nullptr, *z32 = nullptr;
+    // captured preconditioner application
+    cudaGraphExec_t cycle_graph = nullptr;
+    int cycle_graph_prec = -1;
+    // host staging for host-memory arguments
+    double *stage_b = nullptr, *stage_x = nullptr;
+    // natural-order cells and colours of every level (inspection)
+    std::vector<int *> cell_nat, color_nat;
+    // per-level device tables and the single-CTA tail program (solve.cu)
+    void *lev_tab64 = nullptr, *lev_tab32 = nullptr;
+    void *tail_prog64 = nullptr, *tail_prog32 = nullptr;
+    int tail_nops64 = 0, tail_nops32 = 0;
+    int tail_level = -1;
+    bool fp32_ready = false;
+};
+
+namespace amg {
+
+// ---- error handling -------------------------------------------------------------------
+struct Error {
+    int status;
+    std::string what;
+};
+
+#define AMG_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            throw ::amg::Error{e_ == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+        }                                                                                \
+    } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CUDA(cudaGetLastError())
+
+inline int nblocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// ---- allocation (stream-ordered, tracked by the hierarchy) ----------------------------
+template <class T>
+T *halloc(amg_hierarchy *h, size_t count) {
+    void *p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    AMG_CUDA(cudaMallocAsync(&p, bytes, h->stream));
+    h->allocs.push_back(p);
+    h->bytes += bytes;
+    return (T *)p;
+}
+
+// scratch allocation freed by the owner (RAII)
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s_) : s(s_) {}
+    template <class T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        AMG_CUDA(cudaMallocAsync(&p, bytes, s));
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    ~Scratch() {
+        for (void *p : ptrs) cudaFreeAsync(p, s);
+    }
+};
+
+// ---- primitives (scan_sort.cu) --------------------------------------------------------
+// Exclusive prefix sum of in[0..n) into out (may alias in); the total goes to *d_total
+// (device int) if non-null. Deterministic.
+void exclusive_scan(const int *in, int *out, int n, int *d_total, cudaStream_t s);
+// Stable sort of (key, val) pairs by key, keys in [0, 2^key_bits). Results replace the
+// inputs. Deterministic (LSD radix sort, 8-bit digits).
+void stable_sort_pairs(int *keys, int *vals, int n, int key_bits, cudaStream_t s);
+
+// ---- setup (setup.cu) and solve (solve.cu) --------------------------------------------
+// make the hierarchy's stream wait for all work already queued on the caller's stream
+inline void bind_stream(amg_hierarchy *h, void *user_stream) {
+    AMG_CUDA(cudaEventRecord(h->order_ev, (cudaStream_t)user_stream));
+    AMG_CUDA(cudaStreamWaitEvent(h->stream, h->order_ev, 0));
+}
+
+void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y);
+void allocate_solve_workspace(amg_hierarchy *h);
+int solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
+          double *relres);
+void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double *z_nat);
+void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
+                  double *u_nat);
+
+}  // namespace amg

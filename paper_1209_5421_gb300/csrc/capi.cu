@@ -1,0 +1,415 @@
+// C ABI of the library (include/amg.h): argument checks, host/device staging, ownership,
+// status codes; no exception crosses the interface.
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "amg_internal.cuh"
+
+using amg::Error;
+using amg::Scratch;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string &what) {
+    g_last_error = what;
+    return status;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a device-or-host array (host data is copied into scratch)
+template <class T>
+const T *to_device(const T *p, size_t count, Scratch &tmp) {
+    if (!p || count == 0 || is_device_ptr(p)) return p;
+    T *d = tmp.get<T>(count);
+    AMG_CUDA(cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, tmp.s));
+    return d;
+}
+
+void init_pool_once(int dev) {
+    static std::mutex m;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> g(m);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;  // keep freed blocks in this process's pool for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done.push_back(dev);
+}
+
+void destroy(amg_hierarchy *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->cycle_graph) cudaGraphExecDestroy(h->cycle_graph);
+    for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->order_ev) cudaEventDestroy(h->order_ev);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+#define AMG_CATCH                                                 \
+    catch (const Error &e) {                                      \
+        return fail(e.status, e.what);                            \
+    }                                                             \
+    catch (const std::bad_alloc &) {                              \
+        return fail(AMG_ERR_OOM, "host allocation failed");       \
+    }                                                             \
+    catch (...) {                                                 \
+        return fail(AMG_ERR_CUDA, "unexpected internal exception"); \
+    }
+
+__global__ void k_csr_to_ell(int rows, const int *__restrict__ rowptr, const int *__restrict__ col,
+                             const double *__restrict__ val, int width, int diag_first,
+                             int *__restrict__ Aj, double *__restrict__ Ax, int *err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    int b = rowptr[i], e = rowptr[i + 1];
+    if (e - b > width) {
+        atomicOr(err, 1);
+        return;
+    }
+    int k = 0;
+    int dpos = -1;
+    if (diag_first)
+        for (int p = b; p < e; p++)
+            if (col[p] == i) dpos = p;
+    if (dpos >= 0) {
+        Aj[i] = i;
+        Ax[i] = val[dpos];
+        k = 1;
+    }
+    for (int p = b; p < e; p++) {
+        if (p == dpos) continue;
+        Aj[(size_t)k * rows + i] = col[p];
+        Ax[(size_t)k * rows + i] = val[p];
+        k++;
+    }
+    for (; k < width; k++) {
+        Aj[(size_t)k * rows + i] = -1;
+        Ax[(size_t)k * rows + i] = 0.0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *amg_last_error(void) { return g_last_error.c_str(); }
+
+void amg_options_default(amg_options *o) {
+    if (!o) return;
+    o->aux_level = 0;
+    o->coarsest_max = 64;
+    o->kcycle_n = 2;
+    o->max_iters = 200;
+    o->outer = AMG_OUTER_FCG;
+    o->cycle_prec = AMG_FP64;
+    o->fgmres_restart = 30;
+    o->has_bbox = 0;
+    o->bbox[0] = o->bbox[1] = o->bbox[2] = o->bbox[3] = 0.0;
+}
+
+const char *amg_status_string(int s) {
+    switch (s) {
+        case AMG_OK: return "ok";
+        case AMG_ERR_INVALID_ARG: return "invalid argument";
+        case AMG_ERR_BAD_MATRIX: return "matrix is not valid SPD CSR input";
+        case AMG_ERR_OOM: return "out of device memory";
+        case AMG_ERR_CUDA: return "CUDA error";
+        case AMG_ERR_NOT_CONVERGED: return "not converged within max_iters";
+        case AMG_ERR_BREAKDOWN: return "Krylov breakdown";
+        case AMG_ERR_TIMEOUT: return "device wait timed out";
+        case AMG_ERR_UNSUPPORTED: return "outside the library's limits";
+        default: return "unknown status";
+    }
+}
+
+int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_options *opt,
+              void *stream, amg_hierarchy **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A || !x || !y || !A->rowptr || !A->col || !A->val)
+        return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (A->n <= 0) return fail(AMG_ERR_INVALID_ARG, "n must be positive");
+    if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
+        return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
+    if (A->nnz < A->n) return fail(AMG_ERR_BAD_MATRIX, "every row needs its diagonal");
+    amg_options o;
+    if (opt) o = *opt;
+    else amg_options_default(&o);
+    if (o.aux_level < 0 || o.aux_level > 14) return fail(AMG_ERR_UNSUPPORTED, "aux_level must be 0..14");
+    if (o.coarsest_max < 1 || o.coarsest_max > amg::kMaxCoarsest)
+        return fail(AMG_ERR_UNSUPPORTED, "coarsest_max must be 1..256");
+    if (o.kcycle_n < 1 || o.kcycle_n > amg::kMaxKcycle)
+        return fail(AMG_ERR_UNSUPPORTED, "kcycle_n must be 1..4");
+    if (o.max_iters < 1 || o.max_iters > 100000) return fail(AMG_ERR_INVALID_ARG, "max_iters");
+    if (o.cycle_prec != AMG_FP64 && o.cycle_prec != AMG_FP32)
+        return fail(AMG_ERR_INVALID_ARG, "cycle_prec");
+    if (o.outer != AMG_OUTER_FCG && o.outer != AMG_OUTER_FGMRES)
+        return fail(AMG_ERR_INVALID_ARG, "outer");
+    if (o.outer == AMG_OUTER_FGMRES && (o.fgmres_restart < 1 || o.fgmres_restart > 1000))
+        return fail(AMG_ERR_INVALID_ARG, "fgmres_restart");
+    if (o.has_bbox && !(o.bbox[1] > o.bbox[0] && o.bbox[3] > o.bbox[2]))
+        return fail(AMG_ERR_INVALID_ARG, "bbox must have b1 > a1 and b2 > a2");
+    amg_hierarchy *h = nullptr;
+    try {
+        h = new amg_hierarchy();
+        h->opt = o;
+        h->N = A->n;
+        AMG_CUDA(cudaGetDevice(&h->device));
+        init_pool_once(h->device);
+        AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        AMG_CUDA(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
+        amg::bind_stream(h, stream);
+        const int n = (int)A->n;
+        Scratch tmp(h->stream);
+        amg_csr Ad = *A;
+        Ad.rowptr = to_device(A->rowptr, (size_t)n + 1, tmp);
+        Ad.col = to_device(A->col, (size_t)A->nnz, tmp);
+        Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
+        const double *xd = to_device(x, (size_t)n, tmp);
+        const double *yd = to_device(y, (size_t)n, tmp);
+        h->err_flag = amg::halloc<int>(h, 1);
+        amg::build_hierarchy(h, Ad, xd, yd);
+        amg::allocate_solve_workspace(h);
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        *out = h;
+        return AMG_OK;
+    } catch (const Error &e) {
+        destroy(h);
+        return fail(e.status, e.what);
+    } catch (const std::bad_alloc &) {
+        destroy(h);
+        return fail(AMG_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        destroy(h);
+        return fail(AMG_ERR_CUDA, "unexpected internal exception");
+    }
+}
+
+int amg_solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
+              double *relres, void *stream) {
+    if (!h || !b || !x) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol >= 0.0)) return fail(AMG_ERR_INVALID_ARG, "tol must be >= 0");
+    if (h->opt.outer == AMG_OUTER_FGMRES)
+        return fail(AMG_ERR_UNSUPPORTED, "FGMRES outer iteration is not available");
+    try {
+        amg::bind_stream(h, stream);
+        const size_t n = (size_t)h->N;
+        Scratch tmp(h->stream);
+        const double *bd = to_device(b, n, tmp);
+        bool xhost = !is_device_ptr(x);
+        double *xd = xhost ? tmp.get<double>(n) : x;
+        int st = amg::solve(h, bd, tol, xd, iters, relres);
+        if (xhost) {
+            AMG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        if (st != AMG_OK) g_last_error = amg_status_string(st);
+        return st;
+    }
+    AMG_CATCH
+}
+
+int amg_hierarchy_bytes(const amg_hierarchy *h, size_t *bytes) {
+    if (!h || !bytes) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    *bytes = h->bytes;
+    return AMG_OK;
+}
+
+void amg_free(amg_hierarchy *h) { destroy(h); }
+
+int amg_num_levels(const amg_hierarchy *h, int *num_levels, int *aux_level) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    if (num_levels) *num_levels = h->nlev;
+    if (aux_level) *aux_level = h->L;
+    return AMG_OK;
+}
+
+int amg_get_bbox(const amg_hierarchy *h, double bbox[4]) {
+    if (!h || !bbox) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 4; k++) bbox[k] = h->bbox[k];
+    return AMG_OK;
+}
+
+int amg_level_info(const amg_hierarchy *h, int level, int64_t info[8]) {
+    if (!h || !info) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level >= h->nlev) return fail(AMG_ERR_INVALID_ARG, "level out of range");
+    const amg::Level &lv = h->lev[level];
+    info[0] = lv.n;
+    info[1] = lv.A.stored;
+    info[2] = lv.cellw;
+    info[3] = lv.span;
+    info[4] = lv.m;
+    info[5] = lv.A.padded;
+    info[6] = lv.coarsest ? 1 : 0;
+    info[7] = (level == 0) ? lv.nblocks : 0;
+    return AMG_OK;
+}
+
+int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *color,
+                     int32_t *t1, int32_t *t2, int32_t *rowptr, int32_t *col, double *val) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    if (level < 0 || level >= h->nlev) return fail(AMG_ERR_INVALID_ARG, "level out of range");
+    try {
+        const amg::Level &lv = h->lev[level];
+        cudaStream_t s = h->stream;
+        const int n = lv.n;
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (agg) {
+            if (lv.agg_nat) AMG_CUDA(cudaMemcpy(agg, lv.agg_nat, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            else std::fill(agg, agg + n, -1);
+        }
+        if (color) AMG_CUDA(cudaMemcpy(color, h->color_nat[level], sizeof(int) * n, cudaMemcpyDeviceToHost));
+        if (t1 || t2) {
+            std::vector<int> c(n);
+            AMG_CUDA(cudaMemcpy(c.data(), h->cell_nat[level], sizeof(int) * n, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n; i++) {
+                if (t1) t1[i] = c[i] % lv.cellw;
+                if (t2) t2[i] = c[i] / lv.cellw;
+            }
+        }
+        if (rowptr || col || val) {
+            std::vector<int> nat(n), sl(lv.A.nslices + 1), ac(lv.A.padded);
+            std::vector<double> av(lv.A.padded);
+            AMG_CUDA(cudaMemcpy(nat.data(), lv.nat, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            AMG_CUDA(cudaMemcpy(sl.data(), lv.A.sl_ptr, sizeof(int) * sl.size(), cudaMemcpyDeviceToHost));
+            AMG_CUDA(cudaMemcpy(ac.data(), lv.A.col, sizeof(int) * ac.size(), cudaMemcpyDeviceToHost));
+            AMG_CUDA(cudaMemcpy(av.data(), lv.A.val, sizeof(double) * av.size(), cudaMemcpyDeviceToHost));
+            std::vector<int> inv(n);
+            for (int p = 0; p < n; p++) inv[nat[p]] = p;
+            std::vector<std::pair<int, double>> row;
+            int64_t pos = 0;
+            if (rowptr) rowptr[0] = 0;
+            for (int R = 0; R < n; R++) {
+                int p = inv[R];
+                int sidx = p >> 5, lane = p & 31;
+                int width = (sl[sidx + 1] - sl[sidx]) >> 5;
+                row.clear();
+                for (int k = 0; k < width; k++) {
+                    int c = ac[sl[sidx] + 32 * k + lane];
+                    if (c >= 0) row.push_back({nat[c], av[sl[sidx] + 32 * k + lane]});
+                }
+                std::sort(row.begin(), row.end(),
+                          [](const std::pair<int, double> &a, const std::pair<int, double> &b) {
+                              return a.first < b.first;
+                          });
+                for (auto &e : row) {
+                    if (col) col[pos] = e.first;
+                    if (val) val[pos] = e.second;
+                    pos++;
+                }
+                if (rowptr) rowptr[R + 1] = (int32_t)pos;
+            }
+        }
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_apply_cycle(amg_hierarchy *h, int level, const double *f, double *z, void *stream) {
+    if (!h || !f || !z) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level >= h->nlev) return fail(AMG_ERR_INVALID_ARG, "level out of range");
+    try {
+        amg::bind_stream(h, stream);
+        const size_t n = (size_t)h->lev[level].n;
+        Scratch tmp(h->stream);
+        const double *fd = to_device(f, n, tmp);
+        bool zhost = !is_device_ptr(z);
+        double *zd = zhost ? tmp.get<double>(n) : z;
+        amg::apply_cycle_level(h, level, fd, zd);
+        if (zhost) {
+            AMG_CUDA(cudaMemcpyAsync(z, zd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_smooth(amg_hierarchy *h, int level, int backward, const double *f, double *u,
+               void *stream) {
+    if (!h || !f || !u) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level >= h->nlev) return fail(AMG_ERR_INVALID_ARG, "level out of range");
+    if (h->lev[level].coarsest) return fail(AMG_ERR_INVALID_ARG, "the coarsest level is not smoothed");
+    try {
+        amg::bind_stream(h, stream);
+        const size_t n = (size_t)h->lev[level].n;
+        Scratch tmp(h->stream);
+        const double *fd = to_device(f, n, tmp);
+        bool uhost = !is_device_ptr(u);
+        double *ud = u;
+        if (uhost) {
+            ud = tmp.get<double>(n);
+            AMG_CUDA(cudaMemcpyAsync(ud, u, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+        }
+        amg::smooth_level(h, level, backward ? 1 : 0, fd, ud);
+        if (uhost) {
+            AMG_CUDA(cudaMemcpyAsync(u, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+            AMG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, const double *val,
+                   int32_t width, int diag_first, int32_t *Aj, double *Ax, void *stream) {
+    if (rows <= 0 || width < 0 || !rowptr || !col || !val || !Aj || !Ax)
+        return fail(AMG_ERR_INVALID_ARG, "bad argument");
+    try {
+        cudaStream_t s = (cudaStream_t)stream;
+        Scratch tmp(s);
+        std::vector<int32_t> hrp;
+        const int32_t *rp = rowptr;
+        int nnz;
+        if (is_device_ptr(rowptr)) {
+            AMG_CUDA(cudaMemcpyAsync(&nnz, rowptr + rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA(cudaStreamSynchronize(s));
+        } else {
+            nnz = rowptr[rows];
+        }
+        rp = to_device(rowptr, (size_t)rows + 1, tmp);
+        const int32_t *cd = to_device(col, (size_t)nnz, tmp);
+        const double *vd = to_device(val, (size_t)nnz, tmp);
+        bool host_out = !is_device_ptr(Aj) || !is_device_ptr(Ax);
+        const size_t cells = (size_t)rows * width;
+        int32_t *Ajd = host_out ? tmp.get<int32_t>(cells) : Aj;
+        double *Axd = host_out ? tmp.get<double>(cells) : Ax;
+        int *err = tmp.get<int>(1);
+        AMG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        k_csr_to_ell<<<amg::nblocks_for(rows, 256), 256, 0, s>>>(rows, rp, cd, vd, width, diag_first,
+                                                                  Ajd, Axd, err);
+        AMG_LAUNCH_CHECK();
+        int herr = 0;
+        AMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (host_out) {
+            AMG_CUDA(cudaMemcpyAsync(Aj, Ajd, sizeof(int32_t) * cells, cudaMemcpyDeviceToHost, s));
+            AMG_CUDA(cudaMemcpyAsync(Ax, Axd, sizeof(double) * cells, cudaMemcpyDeviceToHost, s));
+        }
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (herr) return fail(AMG_ERR_INVALID_ARG, "a row has more entries than width");
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+}  // extern "C"

@@ -1,0 +1,803 @@
+// Setup phase on the GPU (paper Sec. 3 and Sec. 4.2-4.5):
+//   validation -> auxiliary box (eq. ab12) -> level-L cell of every unknown (Sec. 4.2 index
+//   formula) -> aggregates of every level by occupancy scan over the quadtree cells
+//   (eqs. agg_L, agg_k; empty cells skipped) -> span and quadtree colouring (Sec. 4.5) ->
+//   sweep-order permutation -> sliced-ELL operators -> Galerkin operators by per-row
+//   segmented reduction into stencil slots (eq. acsum / c-sum) -> coarsest exact inverse.
+#include <algorithm>
+#include <cmath>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+namespace {
+
+constexpr int kT = 256;
+
+// ---------------------------------------------------------------------------------------
+// validation: square CSR, sorted unique in-range columns, positive finite diagonal, finite
+// values and coordinates. Bit 1 = bad matrix, bit 2 = bad coordinate.
+__global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rowptr,
+                           const int *__restrict__ col, const double *__restrict__ val,
+                           const double *__restrict__ x, const double *__restrict__ y,
+                           int *err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int flags = 0;
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    if (i == 0 && b != 0) flags |= 1;
+    if (i == n - 1 && e != nnz) flags |= 1;
+    if (b < 0 || e < b || e > nnz) {
+        flags |= 1;
+    } else {
+        bool diag = false;
+        int prev = -1;
+        for (int64_t p = b; p < e; p++) {
+            int c = col[p];
+            double v = val[p];
+            if (c < 0 || c >= n || c <= prev) flags |= 1;
+            prev = c;
+            if (!isfinite(v)) flags |= 1;
+            if (c == i) {
+                diag = true;
+                if (!(v > 0.0)) flags |= 1;
+            }
+        }
+        if (!diag) flags |= 1;
+    }
+    if (!isfinite(x[i]) || !isfinite(y[i])) flags |= 2;
+    if (flags) atomicOr(err, flags);
+}
+
+// ---------------------------------------------------------------------------------------
+// eq. ab12: a1 = min x, b1 = max x, a2 = min y, b2 = max y (exact, order-independent)
+__global__ void k_minmax_partial(int n, const double *__restrict__ x,
+                                 const double *__restrict__ y, double *part) {
+    __shared__ double s[4][kT];
+    double a1 = INFINITY, b1 = -INFINITY, a2 = INFINITY, b2 = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double xv = x[i], yv = y[i];
+        a1 = fmin(a1, xv);
+        b1 = fmax(b1, xv);
+        a2 = fmin(a2, yv);
+        b2 = fmax(b2, yv);
+    }
+    s[0][threadIdx.x] = a1;
+    s[1][threadIdx.x] = b1;
+    s[2][threadIdx.x] = a2;
+    s[3][threadIdx.x] = b2;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] = fmin(s[0][threadIdx.x], s[0][threadIdx.x + o]);
+            s[1][threadIdx.x] = fmax(s[1][threadIdx.x], s[1][threadIdx.x + o]);
+            s[2][threadIdx.x] = fmin(s[2][threadIdx.x], s[2][threadIdx.x + o]);
+            s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_minmax_final(int nb, const double *part, double *bbox) {
+    if (threadIdx.x != 0) return;
+    double a1 = INFINITY, b1 = -INFINITY, a2 = INFINITY, b2 = -INFINITY;
+    for (int b = 0; b < nb; b++) {
+        a1 = fmin(a1, part[4 * b]);
+        b1 = fmax(b1, part[4 * b + 1]);
+        a2 = fmin(a2, part[4 * b + 2]);
+        b2 = fmax(b2, part[4 * b + 3]);
+    }
+    bbox[0] = a1;
+    bbox[1] = b1;
+    bbox[2] = a2;
+    bbox[3] = b2;
+}
+
+// ---------------------------------------------------------------------------------------
+// Sec. 4.2 index formula, one coordinate: floor((v - lo) / (hi - lo) * 2^L). Operation order
+// subtract, IEEE round-to-nearest divide, exact multiply by 2^L, floor; the closed upper
+// edge of the box belongs to the last cell and points outside are clamped into it.
+__device__ __forceinline__ int cell_1d(double v, double lo, double hi, int L) {
+    const int w = 1 << L;
+    if (!(hi > lo)) return 0;
+    double q = __ddiv_rn(__dsub_rn(v, lo), __dsub_rn(hi, lo));
+    double s = __dmul_rn(q, (double)w);
+    if (!(s >= 0.0)) return 0;
+    if (s >= (double)w) return w - 1;
+    return (int)floor(s);
+}
+
+// level-L aggregate label of every unknown (eq. agg_L): i = ty * 2^L + tx
+__global__ void k_bin(int n, const double *__restrict__ x, const double *__restrict__ y,
+                      const double *__restrict__ bbox, int L, int *__restrict__ cell) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int tx = cell_1d(x[j], bbox[0], bbox[1], L);
+    int ty = cell_1d(y[j], bbox[2], bbox[3], L);
+    cell[j] = ty * (1 << L) + tx;
+}
+
+// parent cell of a cell of a grid of width w (Sec. 4.2 coarse-level form):
+// ((t2 / 2) * (w / 2) + t1 / 2)
+__global__ void k_parent_cell(int n, const int *__restrict__ cell, int w, int *__restrict__ pc) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell[i];
+    pc[i] = ((c / w) >> 1) * (w >> 1) + ((c % w) >> 1);
+}
+
+__global__ void k_mark(int n, const int *__restrict__ cid, int *__restrict__ occ) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) occ[cid[i]] = 1;
+}
+
+__global__ void k_lookup(int n, const int *__restrict__ idx, const int *__restrict__ table,
+                         int *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = table[idx[i]];
+}
+
+__global__ void k_cells_of_aggs(int64_t ncell, const int *__restrict__ occ,
+                                const int *__restrict__ num, int *__restrict__ cellof) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell && occ[c]) cellof[num[c]] = (int)c;
+}
+
+__global__ void k_iota(int n, int *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = i;
+}
+
+__global__ void k_scatter_inv(int n, const int *__restrict__ nat, int *__restrict__ inv) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) inv[nat[p]] = p;
+}
+
+// ---------------------------------------------------------------------------------------
+// span s: the largest |dt1|, |dt2| between the cells of the row and column of an entry
+__device__ __forceinline__ int cell_dist(int a, int b, int w) {
+    int d1 = abs(a % w - b % w), d2 = abs(a / w - b / w);
+    return d1 > d2 ? d1 : d2;
+}
+
+__device__ __forceinline__ void block_max_atomic(int v, int *out) {
+    __shared__ int sm[kT / 32];
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = sm[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = max(m, sm[w]);
+        atomicMax(out, m);
+    }
+}
+
+// fine level: cells = level-L cells of the unknowns (CSR input order)
+__global__ void k_span_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                           const int *__restrict__ cell, int w, int *span) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = 0;
+    if (i < n) {
+        int ci = cell[i];
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) s = max(s, cell_dist(ci, cell[col[p]], w));
+    }
+    block_max_atomic(s, span);
+}
+
+// span of the next coarser operator: offsets between the parent cells (width w/2) of the
+// row and column of every entry of this level (sliced ELL, pi order)
+__global__ void k_span_parent(int n, const int *__restrict__ sl, const int *__restrict__ col,
+                              const int *__restrict__ cell, int w, int *span) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = 0;
+    if (i < n) {
+        const int base = sl[i >> 5] + (i & 31), width = (sl[(i >> 5) + 1] - sl[i >> 5]) >> 5;
+        int ci = cell[i];
+        int pi = ((ci / w) >> 1) * (w >> 1) + ((ci % w) >> 1);
+        for (int k = 0; k < width; k++) {
+            int c = col[base + 32 * k];
+            if (c < 0) continue;
+            int cc = cell[c];
+            int pc = ((cc / w) >> 1) * (w >> 1) + ((cc % w) >> 1);
+            s = max(s, cell_dist(pi, pc, w >> 1));
+        }
+    }
+    block_max_atomic(s, span);
+}
+
+// colour of a cell (Sec. 4.5, modulus m = max(2, s+1)): (t1 mod m) + m (t2 mod m)
+__global__ void k_colors(int n, const int *__restrict__ cell, int w, int m,
+                         int *__restrict__ color) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell[i];
+    color[i] = (c % w) % m + m * ((c / w) % m);
+}
+
+__global__ void k_count(int n, const int *__restrict__ key, int *__restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[key[i]], 1);
+}
+
+// block pointers from sorted block keys (every block non-empty)
+__global__ void k_bptr(int n, int nb, const int *__restrict__ key, int *__restrict__ bptr) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n && (p == 0 || key[p] != key[p - 1])) bptr[key[p]] = p;
+    if (p == 0) bptr[nb] = n;
+}
+
+__global__ void k_gather_idx(int m, const int *__restrict__ idx, const int *__restrict__ src,
+                             int *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) out[i] = src[idx[i]];
+}
+
+// ---------------------------------------------------------------------------------------
+// sliced ELL construction
+__global__ void k_rowlen_csr(int n, const int *__restrict__ nat, const int *__restrict__ rowptr,
+                             int *__restrict__ len) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) {
+        int j = nat ? nat[p] : p;
+        len[p] = rowptr[j + 1] - rowptr[j];
+    }
+}
+
+// one warp per slice: 32 * (longest row of the slice)
+__global__ void k_slice_width(int n, int nslices, const int *__restrict__ len, int *__restrict__ sw) {
+    int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    int r = s * 32 + lane;
+    int v = r < n ? len[r] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sw[s] = 32 * v;
+}
+
+// fine operator in pi order: row p <- input row nat[p], diagonal in slot 0, then the other
+// entries in CSR order, columns renumbered to pi order
+__global__ void k_fill_csr(int n, const int *__restrict__ nat, const int *__restrict__ inv,
+                           const int *__restrict__ rowptr, const int *__restrict__ col,
+                           const double *__restrict__ val, const int *__restrict__ sl,
+                           int *__restrict__ ocol, double *__restrict__ oval) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int j = nat ? nat[p] : p;
+    const int base = sl[p >> 5] + (p & 31), width = (sl[(p >> 5) + 1] - sl[p >> 5]) >> 5;
+    int k = 1;
+    for (int q = rowptr[j]; q < rowptr[j + 1]; q++) {
+        int c = col[q];
+        if (c == j) {
+            ocol[base] = p;
+            oval[base] = val[q];
+        } else {
+            ocol[base + 32 * k] = inv ? inv[c] : c;
+            oval[base + 32 * k] = val[q];
+            k++;
+        }
+    }
+    for (; k < width; k++) {
+        ocol[base + 32 * k] = -1;
+        oval[base + 32 * k] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Galerkin operator by segmented reduction (eq. acsum, ELL form eq. c-sum): coarse row P
+// gathers the rows of its aggregate (finest level: the contiguous block bptr[P]..bptr[P+1];
+// coarser levels: up to four children by quadrant), maps every column to its coarse row C
+// and adds the value into the stencil slot of the cell offset C - P (|offset| <= s). Fixed
+// summation order (members ascending, slots ascending): deterministic, no atomics.
+// COUNT pass writes the row lengths; FILL pass writes diagonal slot first, then the touched
+// slots in ascending offset order (= ascending coarse aggregate number).
+template <int SMAX, bool FINE, bool FILL>
+__global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restrict__ children,
+                      const int *__restrict__ fsl, const int *__restrict__ fcol,
+                      const double *__restrict__ fval, const int *__restrict__ fparent,
+                      const int *__restrict__ ccell, int cw, int s, const int *__restrict__ csl,
+                      int *__restrict__ clen, int *__restrict__ ccol,
+                      double *__restrict__ cval, int *err) {
+    constexpr int WMAX = 2 * SMAX + 1;
+    constexpr int NS = WMAX * WMAX;
+    int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const int W = 2 * s + 1;
+    double acc[FILL ? NS : 1];
+    int cof[FILL ? NS : 1];
+    unsigned long long bits[(NS + 63) / 64];
+#pragma unroll
+    for (int t = 0; t < (NS + 63) / 64; t++) bits[t] = 0ull;
+    if (FILL) {
+        for (int t = 0; t < NS; t++) acc[t] = 0.0;
+    }
+    const int cP = ccell[P];
+    const int p1 = cP % cw, p2 = cP / cw;
+    int rbeg, rend;
+    int kids[4];
+    if (FINE) {
+        rbeg = bptr[P];
+        rend = bptr[P + 1];
+    } else {
+        int4 ch = children[P];
+        kids[0] = ch.x;
+        kids[1] = ch.y;
+        kids[2] = ch.z;
+        kids[3] = ch.w;
+        rbeg = 0;
+        rend = 4;
+    }
+    for (int it = rbeg; it < rend; it++) {
+        int i = FINE ? it : kids[it];
+        if (i < 0) continue;
+        const int base = fsl[i >> 5] + (i & 31), width = (fsl[(i >> 5) + 1] - fsl[i >> 5]) >> 5;
+        for (int k = 0; k < width; k++) {
+            int c = fcol[base + 32 * k];
+            if (c < 0) continue;
+            int C = fparent[c];
+            int cC = ccell[C];
+            int d1 = cC % cw - p1, d2 = cC / cw - p2;
+            if (d1 < -s || d1 > s || d2 < -s || d2 > s) {
+                atomicOr(err, 4);
+                continue;
+            }
+            int t = (d2 + s) * W + (d1 + s);
+            bits[t >> 6] |= 1ull << (t & 63);
+            if (FILL) {
+                acc[t] += fval[base + 32 * k];
+                cof[t] = C;
+            }
+        }
+    }
+    const int center = s * W + s;
+    if (!FILL) {
+        int cnt = 0;
+#pragma unroll
+        for (int t = 0; t < (NS + 63) / 64; t++) cnt += __popcll(bits[t]);
+        if (!((bits[center >> 6] >> (center & 63)) & 1ull)) cnt++;  // diagonal always stored
+        clen[P] = cnt;
+        return;
+    }
+    const int base = csl[P >> 5] + (P & 31), width = (csl[(P >> 5) + 1] - csl[P >> 5]) >> 5;
+    ccol[base] = P;
+    cval[base] = acc[center];
+    int k = 1;
+    for (int t = 0; t < W * W; t++) {
+        if (t == center || !((bits[t >> 6] >> (t & 63)) & 1ull)) continue;
+        ccol[base + 32 * k] = cof[t];
+        cval[base + 32 * k] = acc[t];
+        k++;
+    }
+    for (; k < width; k++) {
+        ccol[base + 32 * k] = -1;
+        cval[base + 32 * k] = 0.0;
+    }
+}
+
+// parent pi-row of every pi-row: inv_next[agg_nat[nat[p]]]
+__global__ void k_parent_pi(int n, const int *__restrict__ nat, const int *__restrict__ agg_nat,
+                            const int *__restrict__ inv_next, int *__restrict__ parent) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) parent[p] = inv_next[agg_nat[nat[p]]];
+}
+
+// children of every coarse pi-row by quadrant q = (t1 & 1) + 2 (t2 & 1) of the child cell
+__global__ void k_children(int n, const int *__restrict__ parent, const int *__restrict__ cell,
+                           int cw, int4 *__restrict__ children) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int c = cell[p];
+    int q = ((c % cw) & 1) + 2 * ((c / cw) & 1);
+    reinterpret_cast<int *>(children + parent[p])[q] = p;
+}
+
+// ---------------------------------------------------------------------------------------
+// exact coarsest solve: dense A (pi order) -> Cholesky A = L L^t -> A^{-1} = L^{-t} L^{-1}.
+// One CTA; n <= kMaxCoarsest. Bit 8 of err: not positive definite.
+__global__ void k_dense_from_sell(int n, const int *__restrict__ sl, const int *__restrict__ col,
+                                  const double *__restrict__ val, double *__restrict__ a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int base = sl[i >> 5] + (i & 31), width = (sl[(i >> 5) + 1] - sl[i >> 5]) >> 5;
+    for (int k = 0; k < width; k++) {
+        int c = col[base + 32 * k];
+        if (c >= 0) a[(size_t)i * n + c] += val[base + 32 * k];
+    }
+}
+
+__global__ void k_chol_inverse(int n, double *a, double *w, double *ainv, float *ainv32,
+                               int *err) {
+    __shared__ int bad;
+    const int t = threadIdx.x, T = blockDim.x;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        if (t == 0) {
+            double d = a[(size_t)j * n + j];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            a[(size_t)j * n + j] = sqrt(fabs(d));
+        }
+        __syncthreads();
+        if (bad) break;
+        double djj = a[(size_t)j * n + j];
+        for (int i = j + 1 + t; i < n; i += T) a[(size_t)i * n + j] /= djj;
+        __syncthreads();
+        for (int i = j + 1 + t; i < n; i += T) {
+            double lij = a[(size_t)i * n + j];
+            for (int k = j + 1; k <= i; k++) a[(size_t)i * n + k] -= lij * a[(size_t)k * n + j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (t == 0) atomicOr(err, 8);
+        return;
+    }
+    // W = L^{-1} (lower), one column per thread
+    for (int c = t; c < n; c += T) {
+        for (int i = 0; i < c; i++) w[(size_t)i * n + c] = 0.0;
+        for (int i = c; i < n; i++) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; k++) s -= a[(size_t)i * n + k] * w[(size_t)k * n + c];
+            w[(size_t)i * n + c] = s / a[(size_t)i * n + i];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < n * n; e += T) {
+        int i = e / n, j = e % n;
+        double s = 0.0;
+        for (int k = max(i, j); k < n; k++) s += w[(size_t)k * n + i] * w[(size_t)k * n + j];
+        ainv[e] = s;
+        if (ainv32) ainv32[e] = (float)s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+int read_int(const int *d, cudaStream_t s) {
+    int v = 0;
+    AMG_CUDA(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+
+std::vector<int> read_ints(const int *d, int n, cudaStream_t s) {
+    std::vector<int> v(n);
+    if (n) {
+        AMG_CUDA(cudaMemcpyAsync(v.data(), d, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+    }
+    return v;
+}
+
+int bits_for(int64_t maxval) {  // bits to hold values in [0, maxval]
+    int b = 1;
+    while (b < 31 && (1ll << b) <= maxval) b++;
+    return b;
+}
+
+// sliced-ELL slice pointers from row lengths; returns padded size
+int64_t slice_pointers(amg_hierarchy *h, Sell &A, int n, const int *len) {
+    cudaStream_t s = h->stream;
+    A.n = n;
+    A.nslices = (n + 31) / 32;
+    A.sl_ptr = halloc<int>(h, A.nslices + 1);
+    Scratch tmp(s);
+    int *sw = tmp.get<int>(A.nslices);
+    k_slice_width<<<nblocks_for((int64_t)A.nslices * 32, kT), kT, 0, s>>>(n, A.nslices, len, sw);
+    AMG_LAUNCH_CHECK();
+    exclusive_scan(sw, A.sl_ptr, A.nslices, A.sl_ptr + A.nslices, s);
+    A.padded = read_int(A.sl_ptr + A.nslices, s);
+    A.col = halloc<int>(h, A.padded);
+    A.val = halloc<double>(h, A.padded);
+    return A.padded;
+}
+
+// colours + stable colour sort of a level given natural cells (width w): fills nat, inv,
+// color_rows; returns natural colours (device, kept for export)
+void order_level(amg_hierarchy *h, Level &lv, const int *cell_nat, int *color_nat) {
+    cudaStream_t s = h->stream;
+    int n = lv.n;
+    lv.m = std::max(2, lv.span + 1);
+    lv.ncolors = lv.m * lv.m;
+    k_colors<<<nblocks_for(n, kT), kT, 0, s>>>(n, cell_nat, lv.cellw, lv.m, color_nat);
+    AMG_LAUNCH_CHECK();
+    Scratch tmp(s);
+    int *keys = tmp.get<int>(n);
+    int *cnt = tmp.get<int>(lv.ncolors);
+    AMG_CUDA(cudaMemcpyAsync(keys, color_nat, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    lv.nat = halloc<int>(h, n);
+    lv.inv = halloc<int>(h, n);
+    k_iota<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.nat);
+    AMG_LAUNCH_CHECK();
+    stable_sort_pairs(keys, lv.nat, n, bits_for(lv.ncolors - 1), s);
+    k_scatter_inv<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.nat, lv.inv);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * lv.ncolors, s));
+    k_count<<<nblocks_for(n, kT), kT, 0, s>>>(n, color_nat, cnt);
+    AMG_LAUNCH_CHECK();
+    std::vector<int> c = read_ints(cnt, lv.ncolors, s);
+    lv.color_rows.assign(lv.ncolors + 1, 0);
+    for (int k = 0; k < lv.ncolors; k++) lv.color_rows[k + 1] = lv.color_rows[k] + c[k];
+    lv.cell = halloc<int>(h, n);
+    k_gather_idx<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.nat, cell_nat, lv.cell);
+    AMG_LAUNCH_CHECK();
+}
+
+template <bool FINE>
+void launch_rap(amg_hierarchy *h, Level &f, Level &c, bool fill, int *len) {
+    cudaStream_t s = h->stream;
+    int span = c.span;
+    int nb = nblocks_for(c.n, 128);
+#define AMG_RAP_CASE(SM)                                                                    \
+    if (fill)                                                                               \
+        k_rap<SM, FINE, true><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, f.A.sl_ptr,       \
+                                                 f.A.col, f.A.val, f.parent, c.cell,       \
+                                                 c.cellw, span, c.A.sl_ptr, nullptr,       \
+                                                 c.A.col, c.A.val, h->err_flag);           \
+    else                                                                                    \
+        k_rap<SM, FINE, false><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, f.A.sl_ptr,      \
+                                                  f.A.col, f.A.val, f.parent, c.cell,      \
+                                                  c.cellw, span, nullptr, len, nullptr,    \
+                                                  nullptr, h->err_flag);
+    if (span <= 1) {
+        AMG_RAP_CASE(1)
+    } else if (span <= 2) {
+        AMG_RAP_CASE(2)
+    } else if (span <= 4) {
+        AMG_RAP_CASE(4)
+    } else {
+        AMG_RAP_CASE(8)
+    }
+#undef AMG_RAP_CASE
+    AMG_LAUNCH_CHECK();
+}
+
+void galerkin(amg_hierarchy *h, Level &f, Level &c, bool fine) {
+    cudaStream_t s = h->stream;
+    Scratch tmp(s);
+    int *len = tmp.get<int>(c.n);
+    if (fine) launch_rap<true>(h, f, c, false, len);
+    else launch_rap<false>(h, f, c, false, len);
+    int *d_tot = tmp.get<int>(1);
+    int *scanned = tmp.get<int>(c.n);
+    exclusive_scan(len, scanned, c.n, d_tot, s);
+    c.A.stored = read_int(d_tot, s);
+    slice_pointers(h, c.A, c.n, len);
+    if (fine) launch_rap<true>(h, f, c, true, nullptr);
+    else launch_rap<false>(h, f, c, true, nullptr);
+}
+
+void coarsest_inverse(amg_hierarchy *h, Level &lv) {
+    cudaStream_t s = h->stream;
+    int n = lv.n;
+    Scratch tmp(s);
+    double *a = tmp.get<double>((size_t)n * n);
+    double *w = tmp.get<double>((size_t)n * n);
+    AMG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * n * n, s));
+    k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val, a);
+    AMG_LAUNCH_CHECK();
+    lv.Ainv = halloc<double>(h, (size_t)n * n);
+    lv.Ainv32 = halloc<float>(h, (size_t)n * n);
+    k_chol_inverse<<<1, 256, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
+    AMG_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+// =======================================================================================
+void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, const double *y) {
+    cudaStream_t s = h->stream;
+    const int n = (int)Ain.n;
+    const amg_options &o = h->opt;
+
+    // ---- validation
+    AMG_CUDA(cudaMemsetAsync(h->err_flag, 0, sizeof(int), s));
+    k_validate<<<nblocks_for(n, kT), kT, 0, s>>>(n, Ain.nnz, Ain.rowptr, Ain.col, Ain.val, x, y,
+                                                h->err_flag);
+    AMG_LAUNCH_CHECK();
+    int err = read_int(h->err_flag, s);
+    if (err & 1) throw Error{AMG_ERR_BAD_MATRIX, "matrix is not valid SPD CSR input"};
+    if (err & 2) throw Error{AMG_ERR_INVALID_ARG, "non-finite coordinate"};
+
+    Scratch tmp(s);
+    // ---- auxiliary box (eq. ab12)
+    double *d_bbox = tmp.get<double>(4);
+    if (o.has_bbox) {
+        for (int k = 0; k < 4; k++) h->bbox[k] = o.bbox[k];
+        AMG_CUDA(cudaMemcpyAsync(d_bbox, h->bbox, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
+    } else {
+        int nb = std::min(nblocks_for(n, kT), 1024);
+        double *part = tmp.get<double>(4 * nb);
+        k_minmax_partial<<<nb, kT, 0, s>>>(n, x, y, part);
+        AMG_LAUNCH_CHECK();
+        k_minmax_final<<<1, 32, 0, s>>>(nb, part, d_bbox);
+        AMG_LAUNCH_CHECK();
+        AMG_CUDA(cudaMemcpyAsync(h->bbox, d_bbox, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    }
+    // ---- depth L (Sec. 3.1): largest L with 4^L <= n
+    int L = o.aux_level;
+    if (L == 0)
+        while ((int64_t)1 << (2 * (L + 1)) <= (int64_t)n) L++;
+    h->L = L;
+
+    // ---- level-L cells of the unknowns
+    int *cellL = tmp.get<int>(n);
+    k_bin<<<nblocks_for(n, kT), kT, 0, s>>>(n, x, y, d_bbox, L, cellL);
+    AMG_LAUNCH_CHECK();
+
+    // ---- aggregates of every level, natural numbering (ascending cell index)
+    struct Nat {
+        int n;
+        int w;       // width of the grid `cell` refers to
+        int *cell;   // natural cells
+        int *agg;    // natural aggregate in the next level
+    };
+    std::vector<Nat> nat;
+    nat.push_back({n, 1 << L, cellL, nullptr});
+    int k = L;
+    while (nat.back().n > o.coarsest_max) {
+        Nat &cur = nat.back();
+        const int w = 1 << k;
+        const int64_t ncell = (int64_t)w * w;
+        int *cid;
+        if (nat.size() == 1) {
+            cid = cur.cell;
+        } else {
+            cid = tmp.get<int>(cur.n);
+            k_parent_cell<<<nblocks_for(cur.n, kT), kT, 0, s>>>(cur.n, cur.cell, cur.w, cid);
+            AMG_LAUNCH_CHECK();
+        }
+        int *occ = tmp.get<int>(ncell);
+        int *num = tmp.get<int>(ncell + 1);
+        AMG_CUDA(cudaMemsetAsync(occ, 0, sizeof(int) * ncell, s));
+        k_mark<<<nblocks_for(cur.n, kT), kT, 0, s>>>(cur.n, cid, occ);
+        AMG_LAUNCH_CHECK();
+        exclusive_scan(occ, num, (int)ncell, num + ncell, s);
+        int nc = read_int(num + ncell, s);
+        cur.agg = halloc<int>(h, cur.n);
+        k_lookup<<<nblocks_for(cur.n, kT), kT, 0, s>>>(cur.n, cid, num, cur.agg);
+        AMG_LAUNCH_CHECK();
+        int *cellof = halloc<int>(h, nc);
+        k_cells_of_aggs<<<nblocks_for(ncell, kT), kT, 0, s>>>(ncell, occ, num, cellof);
+        AMG_LAUNCH_CHECK();
+        nat.push_back({nc, w, cellof, nullptr});
+        if (k == 0) break;
+        k--;
+    }
+    const int nlev = (int)nat.size();
+    h->nlev = nlev;
+    h->lev.assign(nlev, Level());
+    for (int l = 0; l < nlev; l++) {
+        h->lev[l].n = nat[l].n;
+        h->lev[l].cellw = nat[l].w;
+        h->lev[l].agg_nat = nat[l].agg;
+    }
+    h->lev[nlev - 1].coarsest = true;
+
+    // keep natural cells and colours of every level for inspection
+    // (level 0's cells are the level-L cells of the unknowns)
+    std::vector<int *> cell_nat(nlev), color_nat(nlev);
+    cell_nat[0] = halloc<int>(h, n);
+    AMG_CUDA(cudaMemcpyAsync(cell_nat[0], cellL, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    for (int l = 1; l < nlev; l++) cell_nat[l] = nat[l].cell;
+    for (int l = 0; l < nlev; l++) color_nat[l] = halloc<int>(h, nat[l].n);
+
+    // ---- span of the fine operator in level-L cells
+    int *d_span = tmp.get<int>(1);
+    AMG_CUDA(cudaMemsetAsync(d_span, 0, sizeof(int), s));
+    k_span_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, Ain.rowptr, Ain.col, cellL, 1 << L, d_span);
+    AMG_LAUNCH_CHECK();
+    int span0 = read_int(d_span, s);
+    if (span0 > 8) throw Error{AMG_ERR_UNSUPPORTED, "fine couplings span more than 8 auxiliary cells"};
+
+    Level &F = h->lev[0];
+    F.span = span0;
+    if (nlev == 1) {
+        // the fine level is the coarsest: natural order, exact inverse only
+        F.m = std::max(2, span0 + 1);
+        F.ncolors = F.m * F.m;
+        k_colors<<<nblocks_for(n, kT), kT, 0, s>>>(n, cellL, 1 << L, F.m, color_nat[0]);
+        AMG_LAUNCH_CHECK();
+        F.nat = halloc<int>(h, n);
+        F.inv = halloc<int>(h, n);
+        k_iota<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat);
+        k_iota<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.inv);
+        AMG_LAUNCH_CHECK();
+        F.cell = cell_nat[0];
+        int *len = tmp.get<int>(n);
+        k_rowlen_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, nullptr, Ain.rowptr, len);
+        AMG_LAUNCH_CHECK();
+        slice_pointers(h, F.A, n, len);
+        k_fill_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, nullptr, nullptr, Ain.rowptr, Ain.col,
+                                                     Ain.val, F.A.sl_ptr, F.A.col, F.A.val);
+        AMG_LAUNCH_CHECK();
+        F.A.stored = Ain.nnz;
+        F.color_rows = {0, n};
+        coarsest_inverse(h, F);
+    } else {
+        // ---- level 1 (auxiliary level L): colours with the fine span, pi order
+        Level &C1 = h->lev[1];
+        C1.span = span0;  // pattern of P^t A P = cell pairs of the fine couplings
+        order_level(h, C1, cell_nat[1], color_nat[1]);
+        F.m = C1.m;
+        F.ncolors = C1.ncolors;
+        k_colors<<<nblocks_for(n, kT), kT, 0, s>>>(n, cellL, 1 << L, F.m, color_nat[0]);
+        AMG_LAUNCH_CHECK();
+
+        // ---- fine pi order: blocks = level-1 pi rows, stable in the unknown index
+        int *keys = tmp.get<int>(n);
+        k_lookup<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.agg_nat, C1.inv, keys);
+        AMG_LAUNCH_CHECK();
+        F.nat = halloc<int>(h, n);
+        F.inv = halloc<int>(h, n);
+        k_iota<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat);
+        AMG_LAUNCH_CHECK();
+        stable_sort_pairs(keys, F.nat, n, bits_for(C1.n - 1), s);
+        k_scatter_inv<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, F.inv);
+        AMG_LAUNCH_CHECK();
+        F.parent = halloc<int>(h, n);
+        AMG_CUDA(cudaMemcpyAsync(F.parent, keys, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+        F.nblocks = C1.n;
+        F.bptr = halloc<int>(h, C1.n + 1);
+        k_bptr<<<nblocks_for(n, kT), kT, 0, s>>>(n, C1.n, keys, F.bptr);
+        AMG_LAUNCH_CHECK();
+        F.cell = halloc<int>(h, n);
+        k_gather_idx<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, cellL, F.cell);
+        AMG_LAUNCH_CHECK();
+        F.color_blocks = C1.color_rows;
+        {
+            int *idx = tmp.get<int>(C1.ncolors + 1);
+            int *out = tmp.get<int>(C1.ncolors + 1);
+            AMG_CUDA(cudaMemcpyAsync(idx, C1.color_rows.data(), sizeof(int) * (C1.ncolors + 1),
+                                     cudaMemcpyHostToDevice, s));
+            k_gather_idx<<<1, 256, 0, s>>>(C1.ncolors + 1, idx, F.bptr, out);
+            AMG_LAUNCH_CHECK();
+            F.color_rows = read_ints(out, C1.ncolors + 1, s);
+        }
+
+        // ---- fine operator in pi order
+        int *len = tmp.get<int>(n);
+        k_rowlen_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, Ain.rowptr, len);
+        AMG_LAUNCH_CHECK();
+        slice_pointers(h, F.A, n, len);
+        k_fill_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, F.inv, Ain.rowptr, Ain.col, Ain.val,
+                                                     F.A.sl_ptr, F.A.col, F.A.val);
+        AMG_LAUNCH_CHECK();
+        F.A.stored = Ain.nnz;
+
+        // ---- A_1 = P^t A P
+        galerkin(h, F, C1, true);
+
+        // ---- coarser levels
+        for (int l = 2; l < nlev; l++) {
+            Level &f = h->lev[l - 1];
+            Level &c = h->lev[l];
+            AMG_CUDA(cudaMemsetAsync(d_span, 0, sizeof(int), s));
+            k_span_parent<<<nblocks_for(f.n, kT), kT, 0, s>>>(f.n, f.A.sl_ptr, f.A.col, f.cell,
+                                                              f.cellw, d_span);
+            AMG_LAUNCH_CHECK();
+            c.span = read_int(d_span, s);
+            order_level(h, c, cell_nat[l], color_nat[l]);
+            f.parent = halloc<int>(h, f.n);
+            k_parent_pi<<<nblocks_for(f.n, kT), kT, 0, s>>>(f.n, f.nat, f.agg_nat, c.inv, f.parent);
+            AMG_LAUNCH_CHECK();
+            c.children = halloc<int4>(h, c.n);
+            AMG_CUDA(cudaMemsetAsync(c.children, 0xff, sizeof(int4) * c.n, s));
+            k_children<<<nblocks_for(f.n, kT), kT, 0, s>>>(f.n, f.parent, f.cell, f.cellw,
+                                                           c.children);
+            AMG_LAUNCH_CHECK();
+            galerkin(h, f, c, false);
+        }
+        coarsest_inverse(h, h->lev[nlev - 1]);
+    }
+    err = read_int(h->err_flag, s);
+    if (err & 8) throw Error{AMG_ERR_BAD_MATRIX, "coarsest operator is not positive definite"};
+    if (err & 4) throw Error{AMG_ERR_CUDA, "internal error: stencil offset beyond the span"};
+    // natural cells / colours for inspection live as long as the hierarchy
+    for (int l = 0; l < nlev; l++) {
+        h->lev[l].sc = halloc<double>(h, SC_N);
+    }
+    h->cell_nat = cell_nat;
+    h->color_nat = color_nat;
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace amg
