@@ -1,0 +1,369 @@
+"""Benchmark: solves/s (and p50/p99 latency) of the auxiliary-grid AMG on one GB300.
+
+One step = one whole pass of the method over one synthetic system: amg_setup (binning,
+aggregation, Galerkin operators, colouring, coarsest factorisation) + amg_solve to a 1e-8
+relative residual + amg_free. Inputs (CSR, coordinates, rhs) are resident in HBM when the
+timed region starts; L2 is flushed (a 256 MiB write) before every timed step, outside the
+step's CUDA events.
+
+  value : solves/s of the whole job (N ranks x steps / max-over-ranks time)
+  e2e   : the same, through the C ABI with pinned HOST buffers (copies inside the step)
+  roofline : the dominant kernel's algorithmic bytes / its CUDA-event duration, from a
+             profiling pass of the same workload and launch configuration
+  cpu_baseline : the FP64 CPU oracle on this machine's host cores
+
+--impl reference times the FP64 CPU oracle (the only reference implementation of this path)
+on the same workload. Multi-GPU: independent replicas per rank (the method is one problem
+per GPU; ranks do not exchange data), scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "solves/s at 1e-8 rel. residual (setup+solve)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="quasi_uniform_1025")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        try:
+            import torch
+
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except ImportError:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_baseline(prob, aux, tol, budget_s=30.0):
+    """The FP64 CPU oracle, as it stands, on this machine's host cores (one thread)."""
+    from oracle import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    O = oracle.Hierarchy.from_problem(prob, aux_level=aux)
+    t1 = time.perf_counter()
+    x, it, rr, st = O.solve(prob.b, tol)
+    t2 = time.perf_counter()
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": it, "relres": rr, "status": st}
+
+
+# ---------------------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 CPU oracle on the host cores, same workload and metric."""
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_1209_5421_gb300.meshes import workload
+
+    oracle.build()
+    prob, aux = workload(args.workload)
+    times = []
+    its = None
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O = oracle.Hierarchy.from_problem(prob, aux_level=aux)
+        x, its, rr, st = O.solve(prob.b, args.tol)
+        del O
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+        if sum(times) > 150.0 and len(times) >= 1:  # bounded: a few minutes at most
+            break
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "unknowns": prob.n, "nnz": prob.nnz,
+                   "aux_level": aux, "tol": args.tol, "iters": its},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full oracle setup+solve(s) of {args.workload}"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1209_5421_gb300 import amg
+    from paper_1209_5421_gb300.meshes import workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, aux = workload(args.workload)
+    prec = amg.FP32 if args.prec == "fp32" else amg.FP64
+    opts = dict(aux_level=aux, cycle_prec=prec)
+    td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
+    A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
+    b = td(prob.b)
+    x = torch.empty_like(b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = amg.Hierarchy(*A, **opts)
+        _, it, rr, st = h.solve(b, args.tol, x=x)
+        h.close()
+        if st != amg.OK:
+            raise RuntimeError(f"solve failed: status {st}, relres {rr}")
+        return it, rr
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            it, rr = step()
+            ends[k].record(stream)
+            iters.append(it)
+        torch.cuda.synchronize()
+    barrier(world)
+    lat = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    total_ms = max_over_ranks(world, sum(lat))
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- e2e: the C ABI with pinned host buffers (H2D of inputs, D2H of x inside the step)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
+        Ah = [pin(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
+        bh = pin(prob.b)
+        xh = torch.empty_like(bh).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in Ah) + bh.numel() * bh.element_size()
+        d2h = xh.numel() * xh.element_size()
+
+        def step_host():
+            h = amg.Hierarchy(*Ah, **opts)
+            _, it, rr, st = h.solve(bh, args.tol, x=xh)
+            h.close()
+            if st != amg.OK:
+                raise RuntimeError(f"solve failed: status {st}")
+
+        for _ in range(max(1, args.warmup)):
+            step_host()
+        torch.cuda.synchronize()
+        barrier(world)
+        el = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_host()
+            el += time.perf_counter() - t0
+        barrier(world)
+        el = max_over_ranks(world, el)
+        e2e = {"value": world * args.steps / el, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # ---- profiling pass: per-kernel CUDA-event durations and algorithmic bytes
+    roofline = None
+    kernels = None
+    launches = None
+    if not args.no_profile:
+        h = amg.Hierarchy(*A, **opts)
+        h.profile(True)
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        h.solve(b, args.tol, x=x)
+        kernels = h.profile_read()
+        h.close()
+        launches = sum(k["launches"] for k in kernels)
+        peak, peak_kind = measured_peak_hbm()
+        dom = max(kernels, key=lambda k: k["ms"])
+        ach = dom["bytes"] / dom["launches"] / (dom["ms"] / dom["launches"] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "traffic": None,
+                    "kernel": dom["name"], "peak_source": peak_kind,
+                    "bytes_per_launch": dom["bytes"] / dom["launches"],
+                    "ms_per_launch": dom["ms"] / dom["launches"]}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu and world == 1:
+            c = cpu_oracle_baseline(prob, aux, args.tol)
+            tot = c["setup_s"] + c["solve_s"]
+            cpu = {"value": 1.0 / tot, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one full oracle setup+solve of {args.workload} "
+                             f"({c['iters']} iterations, {tot:.1f} s)"}
+        lat_sorted = sorted(lat)
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == amg.FP64 else "f32-cycle/f64-outer",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "unknowns": prob.n, "nnz": prob.nnz,
+                       "aux_level": aux, "tol": args.tol, "iters": iters[-1],
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"replicas{world}"},
+            "latency_ms": {"p50": round(float(np.percentile(lat_sorted, 50)), 3),
+                           "p99": round(float(np.percentile(lat_sorted, 99)), 3)},
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        if kernels:
+            out["kernels"] = sorted(
+                [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 4),
+                  "GBps": round(k["bytes"] / (k["ms"] / 1e3) / 1e9, 1) if k["ms"] > 0 else None}
+                 for k in kernels], key=lambda d: -d["ms"])[:12]
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

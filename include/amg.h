@@ -196,6 +196,34 @@ int amg_smooth(amg_hierarchy *h, int level, int backward, const double *f, doubl
 int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, const double *val,
                    int32_t width, int diag_first, int32_t *Aj, double *Ax, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics.
+ * ------------------------------------------------------------------------------------- */
+
+/* Kernel launches made by the last amg_setup and the last amg_solve on h (graph replays
+ * count every kernel node of the graph). */
+int amg_launch_counts(const amg_hierarchy *h, int64_t *setup_launches, int64_t *solve_launches);
+
+/*
+ * Per-kernel timing: with enable = 1, every kernel of the following solves is bracketed by
+ * CUDA events on the hierarchy's stream (also inside the captured cycle graph), and its
+ * duration is accumulated per (kernel kind, level) together with its algorithmic bytes: the
+ * bytes of every array it must read or write once at its width (4-byte indices, value width
+ * of the cycle precision; no padding). Enabling or disabling resets the totals. Timing adds
+ * event nodes between kernels; measure throughput with profiling off.
+ */
+int amg_profile_enable(amg_hierarchy *h, int enable);
+
+/*
+ * Copies up to `capacity` accumulated records: kind (see amg_kernel_name), level, launches,
+ * total milliseconds and total algorithmic bytes. *count receives the number of records.
+ */
+int amg_profile_read(const amg_hierarchy *h, int capacity, int32_t *kind, int32_t *level,
+                     int64_t *launches, double *ms, double *bytes, int *count);
+
+/* Static name of a kernel kind reported by amg_profile_read. */
+const char *amg_kernel_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,9 +77,15 @@ def lib():
         L.amg_apply_cycle.argtypes = [P, C.c_int, P, P, P]
         L.amg_smooth.argtypes = [P, C.c_int, C.c_int, P, P, P]
         L.amg_csr_to_ell.argtypes = [C.c_int32, P, P, P, C.c_int32, C.c_int, P, P, P]
+        L.amg_launch_counts.argtypes = [P, P, P]
+        L.amg_profile_enable.argtypes = [P, C.c_int]
+        L.amg_profile_read.argtypes = [P, C.c_int, P, P, P, P, P, C.POINTER(C.c_int)]
+        L.amg_kernel_name.argtypes = [C.c_int]
+        L.amg_kernel_name.restype = C.c_char_p
         for f in ("amg_setup", "amg_solve", "amg_hierarchy_bytes", "amg_num_levels",
                   "amg_get_bbox", "amg_level_info", "amg_level_export", "amg_apply_cycle",
-                  "amg_smooth", "amg_csr_to_ell"):
+                  "amg_smooth", "amg_csr_to_ell", "amg_launch_counts", "amg_profile_enable",
+                  "amg_profile_read"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -230,6 +236,32 @@ class Hierarchy:
                                       _ptr(out["t1"]), _ptr(out["t2"]), _ptr(out["rowptr"]),
                                       _ptr(out["col"]), _ptr(out["val"])), "amg_level_export")
         out.update(inf)
+        return out
+
+    def launch_counts(self) -> tuple[int, int]:
+        s = np.zeros(1, np.int64)
+        v = np.zeros(1, np.int64)
+        _check(lib().amg_launch_counts(self.h, _ptr(s), _ptr(v)), "amg_launch_counts")
+        return int(s[0]), int(v[0])
+
+    def profile(self, enable: bool = True):
+        _check(lib().amg_profile_enable(self.h, int(enable)), "amg_profile_enable")
+
+    def profile_read(self) -> list[dict]:
+        cap = 256
+        kind = np.zeros(cap, np.int32)
+        level = np.zeros(cap, np.int32)
+        launches = np.zeros(cap, np.int64)
+        ms = np.zeros(cap)
+        by = np.zeros(cap)
+        cnt = C.c_int()
+        _check(lib().amg_profile_read(self.h, cap, _ptr(kind), _ptr(level), _ptr(launches),
+                                      _ptr(ms), _ptr(by), C.byref(cnt)), "amg_profile_read")
+        out = []
+        for k in range(min(cnt.value, cap)):
+            nm = lib().amg_kernel_name(int(kind[k])).decode()
+            out.append({"name": f"{nm}@L{int(level[k])}", "kind": nm, "level": int(level[k]),
+                        "launches": int(launches[k]), "ms": float(ms[k]), "bytes": float(by[k])})
         return out
 
     def apply_cycle(self, level: int, f, stream=None):

@@ -65,6 +65,7 @@ struct Level {
     bool coarsest = false;
     Sell A;
     std::vector<int> color_rows;    // host [ncolors+1]: pi-row range of each colour
+    std::vector<int64_t> color_nnz; // host [ncolors]: stored entries of each colour's rows
     std::vector<int> color_blocks;  // host [ncolors+1] (finest level): block range per colour
     int nblocks = 0;
     int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block
@@ -80,6 +81,8 @@ struct Level {
     Vecs<float> v32;
     double *sc = nullptr;   // [SC_N] device scalars of Alg. 1 on this level
 };
+
+struct Profiler;
 
 }  // namespace amg
 
@@ -125,8 +128,13 @@ struct amg_hierarchy {
     void *lev_tab64 = nullptr, *lev_tab32 = nullptr;
     void *tail_prog64 = nullptr, *tail_prog32 = nullptr;
     int tail_nops64 = 0, tail_nops32 = 0;
+    double tail_bytes64 = 0, tail_bytes32 = 0;
     int tail_level = -1;
     bool fp32_ready = false;
+    // diagnostics: per-op CUDA-event profiling and launch counts (solve.cu)
+    amg::Profiler *prof = nullptr;
+    int64_t graph_nodes = 0;
+    int64_t setup_launches = 0, solve_launches = 0;
 };
 
 namespace amg {
@@ -146,7 +154,13 @@ struct Error {
         }                                                                                \
     } while (0)
 
-#define AMG_LAUNCH_CHECK() AMG_CUDA(cudaGetLastError())
+// every kernel launch is followed by AMG_LAUNCH_CHECK, which also counts it
+extern thread_local int64_t g_launches;
+#define AMG_LAUNCH_CHECK()            \
+    do {                              \
+        ++::amg::g_launches;          \
+        AMG_CUDA(cudaGetLastError()); \
+    } while (0)
 
 inline int nblocks_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
@@ -200,6 +214,11 @@ inline void bind_stream(amg_hierarchy *h, void *user_stream) {
 }
 
 void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y);
+void profiler_enable(amg_hierarchy *h, bool on);
+void profiler_free(amg_hierarchy *h);
+int profiler_read(const amg_hierarchy *h, int cap, int32_t *kind, int32_t *level,
+                  int64_t *launches, double *ms, double *bytes);
+const char *kernel_name(int kind);
 void allocate_solve_workspace(amg_hierarchy *h);
 int solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
           double *relres);

@@ -57,6 +57,7 @@ void destroy(amg_hierarchy *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     if (h->cycle_graph) cudaGraphExecDestroy(h->cycle_graph);
+    amg::profiler_free(h);
     for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -187,10 +188,12 @@ int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_opti
         Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
         const double *xd = to_device(x, (size_t)n, tmp);
         const double *yd = to_device(y, (size_t)n, tmp);
+        const int64_t l0 = amg::g_launches;
         h->err_flag = amg::halloc<int>(h, 1);
         amg::build_hierarchy(h, Ad, xd, yd);
         amg::allocate_solve_workspace(h);
         AMG_CUDA(cudaStreamSynchronize(h->stream));
+        h->setup_launches = amg::g_launches - l0;
         *out = h;
         return AMG_OK;
     } catch (const Error &e) {
@@ -218,7 +221,9 @@ int amg_solve(amg_hierarchy *h, const double *b, double tol, double *x, int *ite
         const double *bd = to_device(b, n, tmp);
         bool xhost = !is_device_ptr(x);
         double *xd = xhost ? tmp.get<double>(n) : x;
+        const int64_t l0 = amg::g_launches;
         int st = amg::solve(h, bd, tol, xd, iters, relres);
+        h->solve_launches = amg::g_launches - l0;
         if (xhost) {
             AMG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
             AMG_CUDA(cudaStreamSynchronize(h->stream));
@@ -411,5 +416,31 @@ int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, cons
     }
     AMG_CATCH
 }
+
+int amg_launch_counts(const amg_hierarchy *h, int64_t *setup_launches, int64_t *solve_launches) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    if (setup_launches) *setup_launches = h->setup_launches;
+    if (solve_launches) *solve_launches = h->solve_launches;
+    return AMG_OK;
+}
+
+int amg_profile_enable(amg_hierarchy *h, int enable) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    try {
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        amg::profiler_enable(h, enable != 0);
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_profile_read(const amg_hierarchy *h, int capacity, int32_t *kind, int32_t *level,
+                     int64_t *launches, double *ms, double *bytes, int *count) {
+    if (!h || !count || capacity < 0) return fail(AMG_ERR_INVALID_ARG, "bad argument");
+    *count = amg::profiler_read(h, capacity, kind, level, launches, ms, bytes);
+    return AMG_OK;
+}
+
+const char *amg_kernel_name(int kind) { return amg::kernel_name(kind); }
 
 }  // extern "C"

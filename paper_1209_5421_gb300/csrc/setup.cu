@@ -373,6 +373,20 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
     }
 }
 
+// stored entries per colour (rows of colour c are the range [cr[c], cr[c+1]))
+__global__ void k_color_nnz(int n, const int *__restrict__ len, const int *__restrict__ cr,
+                            int ncol, unsigned long long *__restrict__ out) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int lo = 0, hi = ncol;  // largest c with cr[c] <= p
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (cr[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    atomicAdd(&out[lo], (unsigned long long)len[p]);
+}
+
 // parent pi-row of every pi-row: inv_next[agg_nat[nat[p]]]
 __global__ void k_parent_pi(int n, const int *__restrict__ nat, const int *__restrict__ agg_nat,
                             const int *__restrict__ inv_next, int *__restrict__ parent) {
@@ -465,6 +479,23 @@ std::vector<int> read_ints(const int *d, int n, cudaStream_t s) {
         AMG_CUDA(cudaStreamSynchronize(s));
     }
     return v;
+}
+
+void color_nnz(amg_hierarchy *h, Level &lv, const int *len) {
+    cudaStream_t s = h->stream;
+    const int nc = (int)lv.color_rows.size() - 1;
+    Scratch tmp(s);
+    int *cr = tmp.get<int>(nc + 1);
+    unsigned long long *out = tmp.get<unsigned long long>(nc);
+    AMG_CUDA(cudaMemcpyAsync(cr, lv.color_rows.data(), sizeof(int) * (nc + 1),
+                             cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nc, s));
+    k_color_nnz<<<nblocks_for(lv.n, kT), kT, 0, s>>>(lv.n, len, cr, nc, out);
+    AMG_LAUNCH_CHECK();
+    std::vector<unsigned long long> v(nc);
+    AMG_CUDA(cudaMemcpyAsync(v.data(), out, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    lv.color_nnz.assign(v.begin(), v.end());
 }
 
 int bits_for(int64_t maxval) {  // bits to hold values in [0, maxval]
@@ -561,6 +592,7 @@ void galerkin(amg_hierarchy *h, Level &f, Level &c, bool fine) {
     exclusive_scan(len, scanned, c.n, d_tot, s);
     c.A.stored = read_int(d_tot, s);
     slice_pointers(h, c.A, c.n, len);
+    color_nnz(h, c, len);
     if (fine) launch_rap<true>(h, f, c, true, nullptr);
     else launch_rap<false>(h, f, c, true, nullptr);
 }
@@ -762,6 +794,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
                                                      F.A.sl_ptr, F.A.col, F.A.val);
         AMG_LAUNCH_CHECK();
         F.A.stored = Ain.nnz;
+        color_nnz(h, F, len);
 
         // ---- A_1 = P^t A P
         galerkin(h, F, C1, true);

@@ -564,6 +564,164 @@ __global__ void k_bump(int *it_ptr) {
 }
 
 // =======================================================================================
+// diagnostics: CUDA-event timing of every op and its algorithmic bytes
+thread_local int64_t g_launches = 0;
+
+enum : int { K_TAIL = 9, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
+             K_TRUE_RESIDUAL, K_NUM };
+
+const char *kernel_name(int kind) {
+    static const char *names[K_NUM] = {"zero", "gs_colour", "resid_restrict", "prolong_correct",
+                                       "coarse_solve", "alg1_multidot", "alg1_orth",
+                                       "alg1_spmv_dot", "alg1_update", "tail_cta",
+                                       "outer_multidot", "outer_orth", "outer_spmv_dot",
+                                       "outer_update", "true_residual"};
+    return (kind >= 0 && kind < K_NUM) ? names[kind] : "unknown";
+}
+
+struct Profiler {
+    struct Rec {
+        int kind, level;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<Rec> graph_recs;  // event nodes inside the captured cycle graph
+    std::vector<Rec> pending;     // direct launches not yet harvested
+    std::vector<Rec> graph_old;   // records of superseded graphs (events freed at the end)
+    struct Acc {
+        int64_t launches = 0;
+        double ms = 0, bytes = 0;
+    };
+    std::vector<std::pair<std::pair<int, int>, Acc>> acc;
+
+    Acc &slot(int kind, int level) {
+        for (auto &e : acc)
+            if (e.first.first == kind && e.first.second == level) return e.second;
+        acc.push_back({{kind, level}, Acc()});
+        return acc.back().second;
+    }
+    Rec begin(int kind, int level, double bytes, cudaStream_t s) {
+        Rec r{kind, level, bytes, nullptr, nullptr};
+        AMG_CUDA(cudaEventCreate(&r.a));
+        AMG_CUDA(cudaEventCreate(&r.b));
+        // external event nodes inside a stream capture, plain records otherwise
+        if (is_capturing(s)) AMG_CUDA(cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal));
+        else AMG_CUDA(cudaEventRecord(r.a, s));
+        return r;
+    }
+    void end(Rec &r, cudaStream_t s, bool capturing) {
+        if (capturing) AMG_CUDA(cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal));
+        else AMG_CUDA(cudaEventRecord(r.b, s));
+        (capturing ? graph_recs : pending).push_back(r);
+    }
+    static bool is_capturing(cudaStream_t s) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+        return st == cudaStreamCaptureStatusActive;
+    }
+    void add(const Rec &r) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        Acc &a = slot(r.kind, r.level);
+        a.launches++;
+        a.ms += ms;
+        a.bytes += r.bytes;
+    }
+    void harvest_graph() {
+        for (auto &r : graph_recs) add(r);
+    }
+    void harvest_pending() {
+        for (auto &r : pending) {
+            add(r);
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        pending.clear();
+    }
+    ~Profiler() {
+        for (auto *v : {&graph_recs, &pending, &graph_old})
+            for (auto &r : *v) {
+                cudaEventDestroy(r.a);
+                cudaEventDestroy(r.b);
+            }
+    }
+};
+
+void profiler_enable(amg_hierarchy *h, bool on) {
+    if (!h->prof) h->prof = new Profiler();
+    h->prof->on = on;
+    if (h->cycle_graph) {  // recapture so the graph carries (or drops) the event nodes
+        cudaGraphExecDestroy(h->cycle_graph);
+        h->cycle_graph = nullptr;
+        for (auto &r : h->prof->graph_recs) h->prof->graph_old.push_back(r);
+        h->prof->graph_recs.clear();
+    }
+    h->prof->acc.clear();
+}
+
+void profiler_free(amg_hierarchy *h) {
+    delete h->prof;
+    h->prof = nullptr;
+}
+
+int profiler_read(const amg_hierarchy *h, int cap, int32_t *kind, int32_t *level,
+                  int64_t *launches, double *ms, double *bytes) {
+    if (!h->prof) return 0;
+    int k = 0;
+    for (auto &e : h->prof->acc) {
+        if (k >= cap) break;
+        if (kind) kind[k] = e.first.first;
+        if (level) level[k] = e.first.second;
+        if (launches) launches[k] = e.second.launches;
+        if (ms) ms[k] = e.second.ms;
+        if (bytes) bytes[k] = e.second.bytes;
+        k++;
+    }
+    return (int)h->prof->acc.size();
+}
+
+static bool profiling(const amg_hierarchy *h) { return h->prof && h->prof->on; }
+
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st == cudaStreamCaptureStatusActive;
+}
+
+// algorithmic bytes of one op: every array the op must touch, once, at its width
+// (w = value width, 4-byte column indices; padding of the sliced ELL is not counted)
+static double op_bytes(const amg_hierarchy *h, const Op &op, int w) {
+    const Level &lv = h->lev[op.level];
+    const double n = lv.n, nnz = (double)lv.A.stored;
+    const double nn = op.level + 1 < h->nlev ? h->lev[op.level + 1].n : 0;
+    switch (op.kind) {
+        case OP_ZERO: return w * n;
+        case OP_GS: {
+            const std::vector<int> &ranges = op.level == 0 ? lv.color_blocks : lv.color_rows;
+            int c = 0;
+            while (c + 1 < (int)ranges.size() && ranges[c] != op.i0) c++;
+            double rows = lv.color_rows[c + 1] - lv.color_rows[c];
+            double e = c < (int)lv.color_nnz.size() ? (double)lv.color_nnz[c] : 0;
+            double blocks = op.i1 - op.i0;
+            return e * (4 + w) + rows * 3.0 * w + (op.level == 0 ? 4.0 * blocks : 0.0);
+        }
+        case OP_RESTRICT:
+            return nnz * (4 + w) + 2.0 * w * n + w * nn + (op.level == 0 ? 4.0 * nn : 16.0 * nn);
+        case OP_PROLONG: return 2.0 * w * n + 4.0 * n + w * nn;
+        case OP_COARSE: return w * n * n + 2.0 * w * n;
+        case OP_MULTIDOT: return w * n * (1 + op.step);
+        case OP_ORTH: return w * n * (2 + op.step);
+        case OP_SPMV_DOT: return nnz * (4 + w) + 3.0 * w * n;
+        case OP_UPDATE: return (op.step == 0 ? 2.0 : 3.0) * w * n + (op.last ? 0.0 : 3.0 * w * n);
+    }
+    return 0;
+}
+
+// =======================================================================================
 // host side
 namespace {
 
@@ -586,11 +744,15 @@ struct Emitter {
     int tail_level;                // levels >= tail_level are recorded into the tail program
     const Op *tail_prog = nullptr; // device program of the tail
     int tail_nops = 0;
+    double tail_bytes = 0;
     RedCtx rc;
 
     void launch(const Op &op) {
         cudaStream_t s = h->stream;
         const Level &lv = h->lev[op.level];
+        Profiler::Rec rec{};
+        const bool prof = profiling(h);
+        if (prof) rec = h->prof->begin(op.kind, op.level, op_bytes(h, op, sizeof(T)), s);
         switch (op.kind) {
             case OP_ZERO: k_zero<T><<<ew_grid(lv.n), 256, 0, s>>>(tab, op); break;
             case OP_GS: k_gs<T><<<ew_grid(op.i1 - op.i0), 256, 0, s>>>(tab, op); break;
@@ -603,11 +765,16 @@ struct Emitter {
             case OP_UPDATE: k_update<T><<<red_grid(lv.n), kRedThreads, 0, s>>>(tab, op, rc); break;
         }
         AMG_LAUNCH_CHECK();
+        if (prof) h->prof->end(rec, s, capturing(s));
     }
 
     void emit(const Op &op) {
-        if (record) record->push_back(op);
-        else launch(op);
+        if (record) {
+            record->push_back(op);
+            tail_bytes += op_bytes(h, op, sizeof(T));
+        } else {
+            launch(op);
+        }
     }
 
     Op mk(int kind, int level) {
@@ -658,10 +825,14 @@ struct Emitter {
 
     // e = B~_l [rhs] (Alg. 1 with kcycle_n steps; exact on the coarsest level)
     void btilde(int l) {
-        if (!record && l >= tail_level) {
-            // the whole recursion from here runs in one CTA
+        if (!record && l == tail_level) {
+            // the whole recursion from here runs in one CTA (the program is B~ of this level)
+            Profiler::Rec rec{};
+            const bool prof = profiling(h);
+            if (prof) rec = h->prof->begin(K_TAIL, l, tail_bytes, h->stream);
             k_tail<T><<<1, kTailThreads, 0, h->stream>>>(tab, tail_prog, tail_nops);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, h->stream, capturing(h->stream));
             return;
         }
         Level &lv = h->lev[l];
@@ -754,9 +925,11 @@ void build_tail(amg_hierarchy *h) {
     if (sizeof(T) == 8) {
         h->tail_prog64 = d;
         h->tail_nops64 = (int)prog.size();
+        h->tail_bytes64 = em.tail_bytes;
     } else {
         h->tail_prog32 = d;
         h->tail_nops32 = (int)prog.size();
+        h->tail_bytes32 = em.tail_bytes;
     }
 }
 
@@ -786,6 +959,7 @@ Emitter<T> make_emitter(amg_hierarchy *h) {
                   nullptr, h->tail_level};
     em.tail_prog = (const Op *)((sizeof(T) == 8) ? h->tail_prog64 : h->tail_prog32);
     em.tail_nops = (sizeof(T) == 8) ? h->tail_nops64 : h->tail_nops32;
+    em.tail_bytes = (sizeof(T) == 8) ? h->tail_bytes64 : h->tail_bytes32;
     em.rc = RedCtx{h->red_partials, h->red_counter};
     return em;
 }
@@ -828,6 +1002,7 @@ static void ensure_cycle_graph(amg_hierarchy *h, int prec) {
     cudaStream_t s = h->stream;
     AMG_CUDA(cudaStreamSynchronize(s));
     cudaGraph_t g;
+    const int64_t launches_before = g_launches;
     AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
         if (prec == AMG_FP32) record_cycle<float>(h);
@@ -839,6 +1014,8 @@ static void ensure_cycle_graph(amg_hierarchy *h, int prec) {
         throw;
     }
     AMG_CUDA(cudaStreamEndCapture(s, &g));
+    h->graph_nodes = g_launches - launches_before;  // captured, not yet executed
+    g_launches = launches_before;
     cudaError_t e = cudaGraphInstantiate(&h->cycle_graph, g, 0);
     cudaGraphDestroy(g);
     AMG_CUDA(e);
@@ -916,6 +1093,7 @@ static void apply_preconditioner(amg_hierarchy *h) {
         AMG_LAUNCH_CHECK();
     }
     AMG_CUDA(cudaGraphLaunch(h->cycle_graph, s));
+    g_launches += h->graph_nodes;
     if (prec == AMG_FP32) {
         k_convert<float, double><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->z32, h->zo);
         AMG_LAUNCH_CHECK();
@@ -939,6 +1117,7 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
     const int maxit = h->opt.max_iters;
     Level &F = h->lev[0];
     RedCtx rc{h->red_partials, h->red_counter};
+    const bool prof = profiling(h);
     prepare_precision(h);
     // x = 0, r = b (pi order)
     k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, b_nat, h->bo);
@@ -967,21 +1146,35 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
         for (it = 0; it < maxit;) {
             ensure_directions(h, it + 1);
             apply_preconditioner(h);  // zo = B^[ro]
+            const double nd = n, nnz = (double)F.A.stored;
+            Profiler::Rec rec{};
+            if (prof) rec = h->prof->begin(K_OUTER_MULTIDOT, 0, 8.0 * nd * (1 + it), s);
             k_outer_multidot<<<red_grid(n), kRedThreads, 0, s>>>(n, h->zo, h->dQ, h->oit, h->osc, rc);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s, false);
+            if (prof) rec = h->prof->begin(K_OUTER_ORTH, 0, 8.0 * nd * (2 + it), s);
             k_outer_orth<<<ew_grid(n), 256, 0, s>>>(n, h->zo, h->dP, h->oit, h->osc, opq);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s, false);
+            if (prof) rec = h->prof->begin(K_OUTER_SPMV_DOT, 0, 12.0 * nnz + 24.0 * nd, s);
             k_outer_spmv_dot<<<red_grid(n), kRedThreads, 0, s>>>(Lf, h->dP, h->dQ, h->oit, h->ro,
                                                                  h->osc, opq, rc);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s, false);
+            if (prof) rec = h->prof->begin(K_OUTER_UPDATE, 0, 48.0 * nd, s);
             k_outer_update<<<red_grid(n), kRedThreads, 0, s>>>(n, h->dP, h->dQ, h->oit, h->xo,
                                                                h->ro, h->osc, opq, rc);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s, false);
             k_bump<<<1, 32, 0, s>>>(h->oit);
             AMG_LAUNCH_CHECK();
             AMG_CUDA(cudaMemcpyAsync(h->h_pinned, h->osc, sizeof(double) * 8,
                                      cudaMemcpyDeviceToHost, s));
             AMG_CUDA(cudaStreamSynchronize(s));
+            if (prof) {
+                h->prof->harvest_graph();
+                h->prof->harvest_pending();
+            }
             it++;
             if (h->h_pinned[OS_STOP] != 0.0) {
                 status = AMG_ERR_BREAKDOWN;
