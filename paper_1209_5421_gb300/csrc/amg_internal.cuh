@@ -75,6 +75,8 @@ struct Level {
     int *inv = nullptr;     // [n] pi-row of natural index
     int *cell = nullptr;    // [n] cell index t1 + cellw * t2 of pi-row p
     int *agg_nat = nullptr; // [n] natural aggregate (next level) of natural row
+    double *dinv64 = nullptr;  // 1 / a_ii (smoother), FP64 and FP32
+    float *dinv32 = nullptr;
     double *Ainv = nullptr; // coarsest: dense inverse, pi order, row-major
     float *Ainv32 = nullptr;
     Vecs<double> v64;
@@ -83,6 +85,7 @@ struct Level {
 };
 
 struct Profiler;
+struct EngineBase;
 
 }  // namespace amg
 
@@ -117,23 +120,20 @@ struct amg_hierarchy {
     int gm_cap = 0;
     // FP32 cycle buffers for outer<->cycle conversion
     float *r32 = nullptr, *z32 = nullptr;
-    // captured preconditioner application
-    cudaGraphExec_t cycle_graph = nullptr;
-    int cycle_graph_prec = -1;
+    // persistent cycle engines (FP64 / FP32 cycle), their reduction buffer and grid barrier
+    amg::EngineBase *eng64 = nullptr, *eng32 = nullptr;
+    double *cyc_partials = nullptr;    // [2][4][grid]
+    unsigned long long *bar = nullptr; // grid-barrier arrival counter
     // host staging for host-memory arguments
     double *stage_b = nullptr, *stage_x = nullptr;
     // natural-order cells and colours of every level (inspection)
     std::vector<int *> cell_nat, color_nat;
-    // per-level device tables and the single-CTA tail program (solve.cu)
+    // per-level device tables (solve.cu)
     void *lev_tab64 = nullptr, *lev_tab32 = nullptr;
-    void *tail_prog64 = nullptr, *tail_prog32 = nullptr;
-    int tail_nops64 = 0, tail_nops32 = 0;
-    double tail_bytes64 = 0, tail_bytes32 = 0;
     int tail_level = -1;
     bool fp32_ready = false;
     // diagnostics: per-op CUDA-event profiling and launch counts (solve.cu)
     amg::Profiler *prof = nullptr;
-    int64_t graph_nodes = 0;
     int64_t setup_launches = 0, solve_launches = 0;
 };
 
@@ -214,6 +214,7 @@ inline void bind_stream(amg_hierarchy *h, void *user_stream) {
 }
 
 void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y);
+void free_engines(amg_hierarchy *h);
 void profiler_enable(amg_hierarchy *h, bool on);
 void profiler_free(amg_hierarchy *h);
 int profiler_read(const amg_hierarchy *h, int cap, int32_t *kind, int32_t *level,

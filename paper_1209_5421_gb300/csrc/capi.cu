@@ -56,7 +56,7 @@ void init_pool_once(int dev) {
 void destroy(amg_hierarchy *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
-    if (h->cycle_graph) cudaGraphExecDestroy(h->cycle_graph);
+    amg::free_engines(h);
     amg::profiler_free(h);
     for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);

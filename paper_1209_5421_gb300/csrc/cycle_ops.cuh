@@ -1,0 +1,484 @@
+// Device building blocks of the AMLI-cycle (paper Alg. 1, Alg. 2, Sec. 4.3, Sec. 4.5): the
+// operation descriptors, level views, deterministic reductions, the bounded grid barrier
+// and every cycle operation as a row-parallel device function ("thread tid of nth").
+// The same functions run in three executors (solve.cu): one multi-CTA kernel per op, a
+// persistent cooperative kernel that runs a whole program of ops with grid barriers, and a
+// single-CTA interpreter over levels staged in shared memory.
+#pragma once
+
+#include <stdint.h>
+
+#include "amg_internal.cuh"
+
+namespace amg {
+
+enum OpKind : int {
+    OP_ZERO = 0,      // u = 0
+    OP_GS,            // one colour of a Gauss-Seidel sweep: rows/blocks [i0, i1)
+    OP_RESTRICT,      // next.rhs = P^t (f - A u)
+    OP_PROLONG,       // u += P next.e
+    OP_COARSE,        // e = A^{-1} rhs (coarsest level)
+    OP_MULTIDOT,      // sc[ZQ_j] = (p_i, q_j), j < i
+    OP_ORTH,          // p_i += sum_j beta_ij p_j, beta_ij = -sc[ZQ_j] / sc[PQ_j]
+    OP_SPMV_DOT,      // q_i = A p_i, sc[PQ_i] = (p_i, q_i), sc[RP_i] = (r_i, p_i)
+    OP_UPDATE,        // alpha_i; e (+)= alpha_i p_i; r = r_i - alpha_i q_i; sc[RR_i] = (r, r)
+    OP_TAIL,          // persistent program: CTA 0 runs the tail program in shared memory
+    OP_NOP,           // persistent program: only the prologue (finalise a reduction)
+};
+
+struct Op {
+    int kind;
+    int level;
+    int i0, i1;       // GS range (blocks on the finest level, rows elsewhere)
+    int backward;     // GS direction
+    int step;         // Alg. 1 step index i
+    int last;         // Alg. 1: last step
+    int fsel, usel;   // vector selectors (vec_of)
+    // persistent executor: reductions leave per-CTA partials in buffer red_pb; the next op
+    // sums them (every CTA, same order) into sc of fin_level at fin_dst[0..fin_n)
+    int red_pb;
+    int fin_pb, fin_level, fin_n;
+    int fin_dst[4];
+};
+
+enum : int { V_RHS = 0, V_E, V_R, V_P0 };  // V_P0 + i = p_i
+
+// view of one level; I = column index type (int in HBM, uint16 in the shared-memory tail)
+template <class T, class I>
+struct LevelDev {
+    using val_t = T;
+    using idx_t = I;
+    int n;
+    int fine;                       // 1 on the finest level (block smoother, bptr)
+    const int *sl;
+    const I *col;
+    const T *val;
+    const T *dinv;                  // 1 / a_ii (smoother)
+    const int *bptr;
+    const int *parent;
+    const int4 *children;           // children of the NEXT coarser level's rows
+    const double *Ainv;             // coarsest: dense inverse (FP64 in both cycles)
+    T *rhs, *e, *r;
+    T *p[kMaxKcycle], *q[kMaxKcycle];
+    double *sc;
+    int nnext;
+};
+
+__device__ __forceinline__ bool col_ok(int c) { return c >= 0; }
+__device__ __forceinline__ bool col_ok(unsigned short c) { return c != (unsigned short)0xFFFF; }
+
+template <class LV>
+__device__ __forceinline__ typename LV::val_t *vec_of(const LV &L, int sel) {
+    return sel == V_RHS ? L.rhs : sel == V_E ? L.e : sel == V_R ? L.r : L.p[sel - V_P0];
+}
+
+// ---------------------------------------------------------------------------------------
+// reductions: fixed-order trees, no floating-point atomics (bitwise reproducible)
+enum : int { RM_LASTBLOCK = 0, RM_BLOCK = 1, RM_PARTIAL = 2 };
+
+// GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, so reductions keep
+// FP64 work low: FP32 partials (FP32 cycle) are summed by a warp tree in FP32 and only the
+// per-warp sums are combined in FP64; FP64 partials go through shared memory and one warp
+// sums them (32 values per lane in fixed order, then a 5-level shuffle tree), about one
+// FP64 add per partial instead of five for a shuffle tree over every warp.
+__device__ __forceinline__ double *red_scratch() {
+    __shared__ double s[1024];  // >= blockDim.x (1024 at most)
+    return s;
+}
+
+__device__ __forceinline__ double warp_sum(double y) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+    return y;
+}
+
+// r[k] (valid in thread 0) = block sum of v[k]; every thread must call it
+template <int NV, class A>
+__device__ __forceinline__ void block_sum(const A (&v)[NV], double (&r)[NV]) {
+    double *s = red_scratch();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if constexpr (sizeof(A) == 4) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            float x = v[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) s[k * 32 + w] = (double)x;
+        }
+        __syncthreads();
+        if (w == 0)
+#pragma unroll
+            for (int k = 0; k < NV; k++) r[k] = warp_sum(lane < nw ? s[k * 32 + lane] : 0.0);
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            s[threadIdx.x] = (double)v[k];
+            __syncthreads();
+            if (w == 0) {
+                double y = 0.0;
+                for (int j = lane; j < (int)blockDim.x; j += 32) y += s[j];
+                r[k] = warp_sum(y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+struct RedCtx {
+    double *partials;        // LASTBLOCK: [NV][gridDim]; PARTIAL: [2][4][gridDim]
+    unsigned int *counter;   // LASTBLOCK only
+};
+
+// RM_LASTBLOCK: per-block partial; the last block to finish sums them in block order.
+// RM_BLOCK (one CTA): the block sum. RM_PARTIAL (persistent kernel): per-block partials
+// into buffer pb; the next op sums them. Final values are stored by thread 0 into out[k].
+template <int NV, int RM, class A>
+__device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&out)[NV],
+                                             const RedCtx &rc, int pb) {
+    double r[NV];
+    block_sum<NV, A>(v, r);
+    if (RM == RM_BLOCK) {
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; k++)
+                if (out[k]) *out[k] = r[k];
+        __syncthreads();
+        return;
+    }
+    if (RM == RM_PARTIAL) {
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; k++)
+                rc.partials[((size_t)pb * 4 + k) * gridDim.x + blockIdx.x] = r[k];
+        return;
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) rc.partials[k * gridDim.x + blockIdx.x] = r[k];
+        __threadfence();
+        unsigned t = atomicAdd(rc.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x < 32) {
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double y = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+                y += __ldcg(&rc.partials[k * gridDim.x + b]);
+            y = warp_sum(y);
+            if (threadIdx.x == 0 && out[k]) *out[k] = y;
+        }
+        if (threadIdx.x == 0) *rc.counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// grid barrier of the persistent cooperative kernel (all CTAs co-resident by construction).
+// Every wait is bounded (kBarrierLimitNs); on expiry the CTA raises bit 16 of *err and every
+// CTA leaves its op loop at its next barrier.
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
+constexpr int kErrTimeout = 1 << 16;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_volatile_int(const int *p) {
+    return *reinterpret_cast<const volatile int *>(p);
+}
+
+// Monotonic counter barrier: every CTA adds 1 with a release reduction and waits (relaxed
+// polling, then an acquire fence) until the counter reaches (k+1) * gridDim.x for its k-th
+// barrier. The counter is zeroed before every launch. Returns false if the kernel must stop.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err,
+                                             unsigned long long &target, int &abort_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += gridDim.x;
+        red_release_add_u64(count, 1ull);
+        unsigned long long t0 = 0;
+        int spins = 0;
+        while (ld_relaxed_u64(count) < target) {
+            if ((++spins & 1023) == 0) {
+                if (t0 == 0) {
+                    t0 = global_ns();
+                } else if (global_ns() - t0 > kBarrierLimitNs || (ld_volatile_int(err) & kErrTimeout)) {
+                    atomicOr(err, kErrTimeout);
+                    abort_flag = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return abort_flag == 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// row kernels (sliced ELL: entry k of row i at sl[i/32] + 32 k + i%32, slot 0 = diagonal).
+// The small levels are pure latency, so a row's slots are read in batches of 8: all column
+// indices and values of a batch are loaded before any gathered x[c], which turns a chain of
+// two dependent loads per slot into about three round trips per row.
+constexpr int kRowBatch = 8;
+
+// sum over slots k0 <= k < width of a_ik x[c_ik] (padding contributes nothing)
+template <class LV>
+__device__ __forceinline__ typename LV::val_t row_dot(const LV &L, int base, int k0, int width,
+                                                      const typename LV::val_t *x) {
+    using T = typename LV::val_t;
+    using I = typename LV::idx_t;
+    T acc = 0;
+    for (int kb = k0; kb < width; kb += kRowBatch) {
+        I c[kRowBatch];
+        T a[kRowBatch];
+#pragma unroll
+        for (int j = 0; j < kRowBatch; j++) {
+            const int k = kb + j;
+            c[j] = k < width ? L.col[base + 32 * k] : (I)-1;
+            a[j] = k < width ? L.val[base + 32 * k] : T(0);
+        }
+        T xv[kRowBatch];
+#pragma unroll
+        for (int j = 0; j < kRowBatch; j++) xv[j] = col_ok(c[j]) ? x[c[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < kRowBatch; j++) acc += a[j] * xv[j];
+    }
+    return acc;
+}
+
+template <class LV>
+__device__ __forceinline__ typename LV::val_t row_residual(const LV &L, int i,
+                                                           const typename LV::val_t *f,
+                                                           const typename LV::val_t *u) {
+    const int s = i >> 5;
+    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+    return f[i] - row_dot(L, base, 0, width, u);
+}
+
+// Gauss-Seidel update of row i: u_i = (f_i - sum_{j != i} a_ij u_j) / a_ii, the division
+// taken as a product with the reciprocal diagonal stored at setup
+template <class LV>
+__device__ __forceinline__ void gs_row(const LV &L, int i, const typename LV::val_t *f,
+                                       typename LV::val_t *u) {
+    const int s = i >> 5;
+    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+    u[i] = (f[i] - row_dot(L, base, 1, width, u)) * L.dinv[i];
+}
+
+// ---------------------------------------------------------------------------------------
+// the ops
+template <class LV>
+__device__ void op_zero(const LV &L, typename LV::val_t *u, int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) u[i] = 0;
+}
+
+// one colour: independent blocks (finest level, rows of a block in sweep order) or rows
+template <class LV>
+__device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
+                      typename LV::val_t *u, int tid, int nth) {
+    for (int b = op.i0 + tid; b < op.i1; b += nth) {
+        if (L.fine) {
+            const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
+            if (!op.backward)
+                for (int i = r0; i < r1; i++) gs_row(L, i, f, u);
+            else
+                for (int i = r1 - 1; i >= r0; i--) gs_row(L, i, f, u);
+        } else {
+            gs_row(L, b, f, u);
+        }
+    }
+}
+
+// fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
+// coarser levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form)
+template <class LV>
+__device__ void op_restrict(const LV &L, const typename LV::val_t *f,
+                            const typename LV::val_t *u, typename LV::val_t *fc, int tid,
+                            int nth) {
+    using T = typename LV::val_t;
+    for (int R = tid; R < L.nnext; R += nth) {
+        T acc = 0;
+        if (L.fine) {
+            for (int i = L.bptr[R]; i < L.bptr[R + 1]; i++) acc += row_residual(L, i, f, u);
+        } else {
+            const int4 ch = L.children[R];
+            if (ch.x >= 0) acc += row_residual(L, ch.x, f, u);
+            if (ch.y >= 0) acc += row_residual(L, ch.y, f, u);
+            if (ch.z >= 0) acc += row_residual(L, ch.z, f, u);
+            if (ch.w >= 0) acc += row_residual(L, ch.w, f, u);
+        }
+        fc[R] = acc;
+    }
+}
+
+// u_i += e_{agg(i)} (Sec. 4.3 prolongation)
+template <class LV>
+__device__ void op_prolong(const LV &L, const typename LV::val_t *e, typename LV::val_t *u,
+                           int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) u[i] += e[L.parent[i]];
+}
+
+// e = A^{-1} rhs with the dense inverse of the coarsest level, accumulated in FP64 by g
+// lanes per row (g = largest power of two <= 32 with g * n <= nth) and a shuffle tree
+template <class LV>
+__device__ void op_coarse(const LV &L, int tid, int nth) {
+    using T = typename LV::val_t;
+    const int n = L.n;
+    int g = 1;
+    while (g < 32 && 2 * g * n <= nth) g *= 2;
+    const int sub = tid & (g - 1), rows_per_pass = nth / g;
+    for (int base = 0; base < n; base += rows_per_pass) {
+        const int i = base + tid / g;
+        double s = 0.0;
+        if (i < n) {
+            const double *a = L.Ainv + (size_t)i * n;
+            for (int j = sub; j < n; j += g) s += a[j] * (double)L.rhs[j];
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+        if (i < n && sub == 0) L.e[i] = (T)s;
+    }
+}
+
+template <class LV, int RM>
+__device__ void op_multidot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+    using T = typename LV::val_t;
+    const int i = op.step;
+    T v[kMaxKcycle] = {};
+    const T *z = L.p[i];
+    for (int r = tid; r < L.n; r += nth) {
+        T zr = z[r];
+#pragma unroll
+        for (int j = 0; j < kMaxKcycle; j++)
+            if (j < i) v[j] += zr * L.q[j][r];
+    }
+    double *out[kMaxKcycle];
+#pragma unroll
+    for (int j = 0; j < kMaxKcycle; j++) out[j] = j < i ? &L.sc[SC_ZQ0 + j] : nullptr;
+    reduce_store<kMaxKcycle, RM, T>(v, out, rc, op.red_pb);
+}
+
+// p_i = z + sum_j beta_ij p_j, beta_ij = -(z, p_j)_A / (p_j, p_j)_A  (Alg. 1, step 2).
+// The coefficients are computed once per CTA (FP64 division is scarce on this GPU) and
+// broadcast through shared memory.
+template <class LV>
+__device__ void op_orth(const LV &L, const Op &op, int tid, int nth) {
+    using T = typename LV::val_t;
+    __shared__ double beta_s[kMaxKcycle];
+    const int i = op.step;
+    if (threadIdx.x < kMaxKcycle) {
+        const int j = threadIdx.x;
+        double pq = L.sc[SC_PQ0 + j];
+        beta_s[j] = (j < i && pq > 0.0) ? -L.sc[SC_ZQ0 + j] / pq : 0.0;
+    }
+    __syncthreads();
+    T beta[kMaxKcycle];
+#pragma unroll
+    for (int j = 0; j < kMaxKcycle; j++) beta[j] = (T)beta_s[j];
+    T *p = L.p[i];
+    for (int r = tid; r < L.n; r += nth) {
+        T acc = p[r];
+#pragma unroll
+        for (int j = 0; j < kMaxKcycle; j++)
+            if (j < i) acc += beta[j] * L.p[j][r];
+        p[r] = acc;
+    }
+}
+
+// q_i = A p_i; (p_i, q_i); (r_i, p_i) with r_0 = rhs
+template <class LV, int RM>
+__device__ void op_spmv_dot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+    using T = typename LV::val_t;
+    const int i = op.step;
+    const T *p = L.p[i];
+    T *q = L.q[i];
+    const T *r = i == 0 ? L.rhs : L.r;
+    T v[2] = {0, 0};
+    for (int row = tid; row < L.n; row += nth) {
+        const int s = row >> 5;
+        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+        const T acc = row_dot(L, base, 0, width, p);
+        q[row] = acc;
+        T pr = p[row];
+        v[0] += pr * acc;
+        v[1] += r[row] * pr;
+    }
+    double *out[2] = {&L.sc[SC_PQ0 + i], &L.sc[SC_RP0 + i]};
+    reduce_store<2, RM, T>(v, out, rc, op.red_pb);
+}
+
+// alpha_i = (r_i, p_i) / (p_i, p_i)_A; u_{i+1} = u_i + alpha_i p_i; r_{i+1} = r_i - alpha_i q_i.
+// Alg. 1 stops (alpha = 0 from then on) once (p_i, p_i)_A <= 0 or a residual is exactly zero.
+template <class LV, int RM>
+__device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+    using T = typename LV::val_t;
+    __shared__ double coef[2];  // alpha, stopped: computed once per CTA
+    const int i = op.step, last = op.last;
+    if (threadIdx.x == 0) {
+        const double pq = L.sc[SC_PQ0 + i];
+        const bool prev_stop =
+            i > 0 && (L.sc[SC_STOP0 + i - 1] != 0.0 || L.sc[SC_RR0 + i - 1] == 0.0);
+        const bool stopped = prev_stop || !(pq > 0.0) || !isfinite(pq);
+        coef[0] = stopped ? 0.0 : L.sc[SC_RP0 + i] / pq;
+        coef[1] = stopped ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const T a = (T)coef[0];
+    const bool stopped = coef[1] != 0.0;
+    const T *p = L.p[i];
+    const T *q = L.q[i];
+    const T *r_in = i == 0 ? L.rhs : L.r;
+    T *e = L.e;
+    T v[1] = {0};
+    for (int row = tid; row < L.n; row += nth) {
+        e[row] = (i == 0) ? a * p[row] : e[row] + a * p[row];
+        if (!last) {
+            T rn = r_in[row] - a * q[row];
+            L.r[row] = rn;
+            v[0] += rn * rn;
+        }
+    }
+    if (!last) {
+        double *out[1] = {&L.sc[SC_RR0 + i]};
+        reduce_store<1, RM, T>(v, out, rc, op.red_pb);
+    }
+    if ((RM == RM_BLOCK || blockIdx.x == 0) && threadIdx.x == 0)
+        L.sc[SC_STOP0 + i] = stopped ? 1.0 : 0.0;
+}
+
+// run one op (everything except OP_TAIL / OP_NOP)
+template <class LV, int RM>
+__device__ __forceinline__ void run_op(const LV *tab, const Op &op, const RedCtx &rc, int tid,
+                                       int nth) {
+    const LV &L = tab[op.level];
+    switch (op.kind) {
+        case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
+        case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
+        case OP_RESTRICT:
+            op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), tab[op.level + 1].rhs, tid, nth);
+            break;
+        case OP_PROLONG: op_prolong(L, tab[op.level + 1].e, vec_of(L, op.usel), tid, nth); break;
+        case OP_COARSE: op_coarse(L, tid, nth); break;
+        case OP_MULTIDOT: op_multidot<LV, RM>(L, op, rc, tid, nth); break;
+        case OP_ORTH: op_orth(L, op, tid, nth); break;
+        case OP_SPMV_DOT: op_spmv_dot<LV, RM>(L, op, rc, tid, nth); break;
+        case OP_UPDATE: op_update<LV, RM>(L, op, rc, tid, nth); break;
+        default: break;
+    }
+}
+
+}  // namespace amg

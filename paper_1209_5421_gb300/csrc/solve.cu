@@ -1,414 +1,209 @@
-// Solve phase on the GPU: the nonlinear AMLI-cycle (paper Alg. 2) with nonlinear PCG on
-// the coarse levels (Alg. 1), the quadtree-coloured Gauss-Seidel smoother (Sec. 4.5),
-// implicit prolongation / restriction (Sec. 4.3), and the outer Krylov iteration.
+// Solve phase on the GPU: the nonlinear AMLI-cycle (paper Alg. 2) with nonlinear PCG on the
+// coarse levels (Alg. 1), the quadtree-coloured Gauss-Seidel smoother (Sec. 4.5), implicit
+// prolongation / restriction (Sec. 4.3), and the outer Krylov iteration (Alg. 1 on the
+// finest level, flexible CG with full A-orthogonalisation).
 //
-// Execution model. The cycle is a fixed sequence of operations ("ops") on device-resident
-// data: a Gauss-Seidel sweep over one colour, a fused residual+restriction, a fused
-// prolongation+correction, the exact coarsest solve, and the Alg. 1 pieces (A-orthogonal
-// direction, SpMV with its two inner products, the update). Every scalar (alpha, beta, inner
-// products) stays in device memory. The host walks the recursion once and either
-//   * launches one multi-CTA kernel per op (large levels), or
-//   * appends the op to a program that one CTA interprets with __syncthreads() between ops
-//     (all levels from the "tail" level down: small levels are latency-bound, and one CTA
-//     runs their whole recursive Alg. 1 / Alg. 2 without a kernel launch per op).
-// The whole preconditioner application is captured once into a CUDA graph and replayed.
+// Execution. One application of the preconditioner B^_fine is a fixed program of ops (see
+// cycle_ops.cuh) over device-resident data; every scalar stays on the device. It runs as ONE
+// persistent cooperative kernel (one CTA per SM): the CTAs execute each op row-parallel and
+// meet at a bounded grid barrier before the next. The coarse levels from the "tail" level
+// down (a few thousand rows or less: pure latency) are staged in shared memory by CTA 0 at
+// kernel start, and CTA 0 alone runs their whole recursive Alg. 1 / Alg. 2 there with
+// __syncthreads() between ops while the other CTAs wait at the barrier. The outer Krylov
+// update is four small kernels per iteration; the host reads one residual per iteration.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 
-#include "amg_internal.cuh"
+#include "cycle_ops.cuh"
 
 namespace amg {
 
-enum OpKind : int {
-    OP_ZERO = 0,      // u = 0
-    OP_GS,            // one colour of a Gauss-Seidel sweep: rows/blocks [i0, i1)
-    OP_RESTRICT,      // next.rhs = P^t (f - A u)
-    OP_PROLONG,       // u += P next.e
-    OP_COARSE,        // e = A^{-1} rhs (coarsest level)
-    OP_MULTIDOT,      // sc[ZQ_j] = (p_i, q_j), j < i
-    OP_ORTH,          // p_i -= sum_j (sc[ZQ_j] / sc[PQ_j]) p_j
-    OP_SPMV_DOT,      // q_i = A p_i, sc[PQ_i] = (p_i, q_i), sc[RP_i] = (r_i, p_i)
-    OP_UPDATE,        // alpha_i; e (+)= alpha_i p_i; r = r_i - alpha_i q_i; sc[RR] = (r, r)
-};
-
-struct Op {
-    int kind;
-    int level;
-    int i0, i1;       // GS range
-    int backward;     // GS direction
-    int step;         // Alg. 1 step index i
-    int last;         // Alg. 1: is this the last step
-    int fsel, usel;   // vector selectors (see vec_of)
-};
-
-// vector selectors of a level
-enum : int { V_RHS = 0, V_E, V_R, V_P0 };  // V_P0 + i = p_i
-
 template <class T>
-struct LevelDev {
-    int n;
-    int fine;                       // 1 on the finest level (block smoother, bptr)
-    const int *sl, *col;
-    const T *val;
-    const int *bptr;
-    const int *parent;
-    const int4 *children;           // of the NEXT coarser level
-    const T *Ainv;
-    T *rhs, *e, *r;
-    T *p[kMaxKcycle], *q[kMaxKcycle];
-    double *sc;
-    int nnext;                      // rows of the next coarser level
+using GLev = LevelDev<T, int>;                 // level in HBM
+template <class T>
+using SLev = LevelDev<T, unsigned short>;      // level staged in shared memory
+
+constexpr int kPThreads = 1024;     // persistent kernel CTA size (one CTA per SM)
+constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
+
+// shared-memory image of the tail levels (byte offsets into the dynamic shared memory)
+struct TailLevelLayout {
+    int n, nslices, padded;
+    int sl, col, val, dinv, parent, children, Ainv, rhs, e, r;
+    int p[kMaxKcycle], q[kMaxKcycle];
+};
+struct TailLayout {
+    int tl;      // first staged level (nlev = none)
+    int nlev;
+    int bytes;
+    int prog;    // the tail program (ops)
+    int sc;      // the tail levels' Alg. 1 scalars, SC_N doubles per level
+    TailLevelLayout lv[kMaxLevels];
 };
 
 template <class T>
-__device__ __forceinline__ T *vec_of(const LevelDev<T> &L, int sel) {
-    return sel == V_RHS ? L.rhs : sel == V_E ? L.e : sel == V_R ? L.r : L.p[sel - V_P0];
-}
-
-// ---------------------------------------------------------------------------------------
-// reductions: fixed-order trees, no floating-point atomics (bitwise reproducible)
-template <int NV>
-__device__ __forceinline__ void block_reduce(double (&v)[NV]) {
-    __shared__ double sm[NV][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; k++)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; k++) sm[k][w] = v[k];
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            v[k] = lane < nw ? sm[k][lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        }
-    }
-    __syncthreads();
-}
-
-struct RedCtx {
-    double *partials;       // [NV * gridDim.x]
-    unsigned int *counter;
+struct CycleArgs {
+    const GLev<T> *tab;
+    const Op *prog;
+    int nops;
+    const Op *tail_prog;
+    int tail_nops;
+    TailLayout lay;
+    double *partials;            // [2][4][gridDim]
+    unsigned long long *bar;     // barrier counter (zeroed before every launch)
+    int *err;
+    unsigned long long *ts;      // per-op end timestamps (profiling) or null
+    unsigned long long *tprof;   // tail: [kind] cycles, [16 + kind] count (profiling) or null
 };
 
-// GRID: per-block partial, the last block to finish sums the partials in block order.
-// !GRID (one CTA): the block sum. Thread 0 stores the results into out[k].
-template <int NV, bool GRID>
-__device__ __forceinline__ void reduce_store(double (&v)[NV], double *const (&out)[NV],
-                                             const RedCtx &rc) {
-    block_reduce<NV>(v);
-    if (!GRID) {
-        if (threadIdx.x == 0)
-#pragma unroll
-            for (int k = 0; k < NV; k++)
-                if (out[k]) *out[k] = v[k];
-        __syncthreads();
-        return;
-    }
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) rc.partials[k * gridDim.x + blockIdx.x] = v[k];
-        __threadfence();
-        unsigned t = atomicAdd(rc.counter, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        double w[NV];
-#pragma unroll
-        for (int k = 0; k < NV; k++) {
-            w[k] = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-                w[k] += __ldcg(&rc.partials[k * gridDim.x + b]);
-        }
-        block_reduce<NV>(w);
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int k = 0; k < NV; k++)
-                if (out[k]) *out[k] = w[k];
-            *rc.counter = 0u;
-        }
-    }
+// ---------------------------------------------------------------------------------------
+// standalone executor (diagnostic path: amg_apply_cycle on coarse levels, amg_smooth)
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_op(const GLev<T> *__restrict__ tab, Op op,
+                                                    RedCtx rc) {
+    run_op<GLev<T>, RM_LASTBLOCK>(tab, op, rc, blockIdx.x * blockDim.x + threadIdx.x,
+                                  gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------------------
-// row kernels (sliced ELL, slot 0 = diagonal)
+// persistent cycle kernel
 template <class T>
-__device__ __forceinline__ T row_residual(const LevelDev<T> &L, int i, const T *f, const T *u) {
-    const int s = i >> 5;
-    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
-    T acc = f[i];
-    for (int k = 0; k < width; k++) {
-        int c = L.col[base + 32 * k];
-        if (c >= 0) acc -= L.val[base + 32 * k] * u[c];
-    }
-    return acc;
-}
-
-// Gauss-Seidel update of row i: u_i = (f_i - sum_{j != i} a_ij u_j) / a_ii
-template <class T>
-__device__ __forceinline__ void gs_row(const LevelDev<T> &L, int i, const T *f, T *u) {
-    const int s = i >> 5;
-    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
-    T acc = f[i];
-    const T d = L.val[base];
-    for (int k = 1; k < width; k++) {
-        int c = L.col[base + 32 * k];
-        if (c >= 0) acc -= L.val[base + 32 * k] * u[c];
-    }
-    u[i] = acc / d;
-}
-
-// ---------------------------------------------------------------------------------------
-// ops as row-parallel device functions: thread `tid` of `nth` (a grid or one CTA)
-template <class T>
-__device__ void op_zero(const LevelDev<T> &L, T *u, int tid, int nth) {
-    for (int i = tid; i < L.n; i += nth) u[i] = T(0);
-}
-
-// one colour: independent blocks (finest level, rows of a block in sweep order) or rows
-template <class T>
-__device__ void op_gs(const LevelDev<T> &L, const Op &op, const T *f, T *u, int tid, int nth) {
-    for (int b = op.i0 + tid; b < op.i1; b += nth) {
-        if (L.fine) {
-            const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
-            if (!op.backward)
-                for (int i = r0; i < r1; i++) gs_row(L, i, f, u);
-            else
-                for (int i = r1 - 1; i >= r0; i--) gs_row(L, i, f, u);
-        } else {
-            gs_row(L, b, f, u);
-        }
-    }
-}
-
-// fc = P^t (f - A u): finest level sums the contiguous block of each aggregate; coarser
-// levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form)
-template <class T>
-__device__ void op_restrict(const LevelDev<T> &L, const T *f, const T *u, T *fc, int tid,
-                            int nth) {
-    for (int R = tid; R < L.nnext; R += nth) {
-        T acc = T(0);
-        if (L.fine) {
-            for (int i = L.bptr[R]; i < L.bptr[R + 1]; i++) acc += row_residual(L, i, f, u);
-        } else {
-            const int4 ch = L.children[R];
-            if (ch.x >= 0) acc += row_residual(L, ch.x, f, u);
-            if (ch.y >= 0) acc += row_residual(L, ch.y, f, u);
-            if (ch.z >= 0) acc += row_residual(L, ch.z, f, u);
-            if (ch.w >= 0) acc += row_residual(L, ch.w, f, u);
-        }
-        fc[R] = acc;
-    }
-}
-
-// u_i += e_{agg(i)} (Sec. 4.3 prolongation)
-template <class T>
-__device__ void op_prolong(const LevelDev<T> &L, const T *e, T *u, int tid, int nth) {
-    for (int i = tid; i < L.n; i += nth) u[i] += e[L.parent[i]];
-}
-
-// e = A^{-1} rhs with the dense inverse of the coarsest level
-template <class T>
-__device__ void op_coarse(const LevelDev<T> &L, const T *f, T *e, int tid, int nth) {
-    const int n = L.n;
-    for (int i = tid; i < n; i += nth) {
-        double s = 0.0;
-        const T *a = L.Ainv + (size_t)i * n;
-        for (int j = 0; j < n; j++) s += (double)a[j] * (double)f[j];
-        e[i] = (T)s;
-    }
-}
-
-template <class T, bool GRID>
-__device__ void op_multidot(const LevelDev<T> &L, int i, const RedCtx &rc, int tid, int nth) {
-    double v[kMaxKcycle] = {};
-    const T *z = L.p[i];
-    for (int r = tid; r < L.n; r += nth) {
-        double zr = z[r];
-#pragma unroll
-        for (int j = 0; j < kMaxKcycle; j++)
-            if (j < i) v[j] += zr * (double)L.q[j][r];
-    }
-    double *out[kMaxKcycle];
-#pragma unroll
-    for (int j = 0; j < kMaxKcycle; j++) out[j] = j < i ? &L.sc[SC_ZQ0 + j] : nullptr;
-    reduce_store<kMaxKcycle, GRID>(v, out, rc);
-}
-
-// p_i = z + sum_j beta_ij p_j, beta_ij = -(z, p_j)_A / (p_j, p_j)_A  (Alg. 1, step 2)
-template <class T>
-__device__ void op_orth(const LevelDev<T> &L, int i, int tid, int nth) {
-    double beta[kMaxKcycle];
-#pragma unroll
-    for (int j = 0; j < kMaxKcycle; j++) {
-        double pq = L.sc[SC_PQ0 + j];
-        beta[j] = (j < i && pq > 0.0) ? -L.sc[SC_ZQ0 + j] / pq : 0.0;
-    }
-    T *p = L.p[i];
-    for (int r = tid; r < L.n; r += nth) {
-        T acc = p[r];
-#pragma unroll
-        for (int j = 0; j < kMaxKcycle; j++)
-            if (j < i) acc += (T)beta[j] * L.p[j][r];
-        p[r] = acc;
-    }
-}
-
-// q_i = A p_i; (p_i, q_i); (r_i, p_i) with r_0 = rhs
-template <class T, bool GRID>
-__device__ void op_spmv_dot(const LevelDev<T> &L, int i, const RedCtx &rc, int tid, int nth) {
-    const T *p = L.p[i];
-    T *q = L.q[i];
-    const T *r = i == 0 ? L.rhs : L.r;
-    double v[2] = {0.0, 0.0};
-    for (int row = tid; row < L.n; row += nth) {
-        const int s = row >> 5;
-        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
-        T acc = T(0);
-        for (int k = 0; k < width; k++) {
-            int c = L.col[base + 32 * k];
-            if (c >= 0) acc += L.val[base + 32 * k] * p[c];
-        }
-        q[row] = acc;
-        double pr = p[row];
-        v[0] += pr * (double)acc;
-        v[1] += (double)r[row] * pr;
-    }
-    double *out[2] = {&L.sc[SC_PQ0 + i], &L.sc[SC_RP0 + i]};
-    reduce_store<2, GRID>(v, out, rc);
-}
-
-// alpha_i = (r_i, p_i) / (p_i, p_i)_A; u_{i+1} = u_i + alpha_i p_i; r_{i+1} = r_i - alpha_i q_i.
-// Alg. 1 stops (alpha = 0 from then on) once (p_i, p_i)_A <= 0 or a residual is exactly zero.
-template <class T, bool GRID>
-__device__ void op_update(const LevelDev<T> &L, int i, int last, const RedCtx &rc, int tid,
-                          int nth) {
-    const double pq = L.sc[SC_PQ0 + i];
-    const bool prev_stop =
-        i > 0 && (L.sc[SC_STOP0 + i - 1] != 0.0 || L.sc[SC_RR0 + i - 1] == 0.0);
-    const bool stopped = prev_stop || !(pq > 0.0) || !isfinite(pq);
-    const double alpha = stopped ? 0.0 : L.sc[SC_RP0 + i] / pq;
-    const T a = (T)alpha;
-    const T *p = L.p[i];
-    const T *q = L.q[i];
-    const T *r_in = i == 0 ? L.rhs : L.r;
-    T *e = L.e;
-    double v[1] = {0.0};
-    for (int row = tid; row < L.n; row += nth) {
-        e[row] = (i == 0) ? a * p[row] : e[row] + a * p[row];
-        if (!last) {
-            T rn = r_in[row] - a * q[row];
-            L.r[row] = rn;
-            v[0] += (double)rn * (double)rn;
-        }
-    }
-    if (!last) {
-        double *out[1] = {&L.sc[SC_RR0 + i]};
-        reduce_store<1, GRID>(v, out, rc);
-    }
-    if ((!GRID || blockIdx.x == 0) && threadIdx.x == 0) L.sc[SC_STOP0 + i] = stopped ? 1.0 : 0.0;
-}
-
-// ---------------------------------------------------------------------------------------
-// multi-CTA kernels (one op per launch)
-template <class T>
-__global__ void k_zero(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> &L = tab[op.level];
-    op_zero(L, vec_of(L, op.usel), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void k_gs(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> L = tab[op.level];
-    op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), blockIdx.x * blockDim.x + threadIdx.x,
-          gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void k_restrict(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> L = tab[op.level];
-    op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), tab[op.level + 1].rhs,
-                blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void k_prolong(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> L = tab[op.level];
-    op_prolong(L, tab[op.level + 1].e, vec_of(L, op.usel), blockIdx.x * blockDim.x + threadIdx.x,
-               gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void k_coarse(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> L = tab[op.level];
-    op_coarse(L, L.rhs, L.e, threadIdx.x, blockDim.x);
-}
-
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_multidot(const LevelDev<T> *__restrict__ tab,
-                                                          Op op, RedCtx rc) {
-    const LevelDev<T> L = tab[op.level];
-    op_multidot<T, true>(L, op.step, rc, blockIdx.x * blockDim.x + threadIdx.x,
-                         gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void k_orth(const LevelDev<T> *__restrict__ tab, Op op) {
-    const LevelDev<T> L = tab[op.level];
-    op_orth(L, op.step, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_spmv_dot(const LevelDev<T> *__restrict__ tab,
-                                                          Op op, RedCtx rc) {
-    const LevelDev<T> L = tab[op.level];
-    op_spmv_dot<T, true>(L, op.step, rc, blockIdx.x * blockDim.x + threadIdx.x,
-                         gridDim.x * blockDim.x);
-}
-
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) k_update(const LevelDev<T> *__restrict__ tab,
-                                                        Op op, RedCtx rc) {
-    const LevelDev<T> L = tab[op.level];
-    op_update<T, true>(L, op.step, op.last, rc, blockIdx.x * blockDim.x + threadIdx.x,
-                       gridDim.x * blockDim.x);
-}
-
-// ---------------------------------------------------------------------------------------
-// single-CTA interpreter of a program of ops (levels from the tail level down)
-constexpr int kTailThreads = 512;
-
-template <class T>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const LevelDev<T> *__restrict__ tab,
-                                                       const Op *__restrict__ prog, int nops) {
+__device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *stab) {
+    const TailLayout &Y = a.lay;
     const int tid = threadIdx.x, nth = blockDim.x;
-    RedCtx rc{nullptr, nullptr};
-    for (int k = 0; k < nops; k++) {
-        const Op op = prog[k];
-        const LevelDev<T> &L = tab[op.level];
-        switch (op.kind) {
-            case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
-            case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
-            case OP_RESTRICT:
-                op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), tab[op.level + 1].rhs, tid, nth);
-                break;
-            case OP_PROLONG: op_prolong(L, tab[op.level + 1].e, vec_of(L, op.usel), tid, nth); break;
-            case OP_COARSE: op_coarse(L, L.rhs, L.e, tid, nth); break;
-            case OP_MULTIDOT: op_multidot<T, false>(L, op.step, rc, tid, nth); break;
-            case OP_ORTH: op_orth(L, op.step, tid, nth); break;
-            case OP_SPMV_DOT: op_spmv_dot<T, false>(L, op.step, rc, tid, nth); break;
-            case OP_UPDATE: op_update<T, false>(L, op.step, op.last, rc, tid, nth); break;
+    for (int l = Y.tl; l < Y.nlev; l++) {
+        const TailLevelLayout &y = Y.lv[l];
+        const GLev<T> &G = a.tab[l];
+        int *sl = (int *)(sm + y.sl);
+        unsigned short *col = (unsigned short *)(sm + y.col);
+        T *val = (T *)(sm + y.val);
+        for (int i = tid; i <= y.nslices; i += nth) sl[i] = G.sl[i];
+        for (int i = tid; i < y.padded; i += nth) {
+            int c = G.col[i];
+            col[i] = c >= 0 ? (unsigned short)c : (unsigned short)0xFFFF;
+            val[i] = G.val[i];
         }
+        if (y.dinv >= 0)
+            for (int i = tid; i < y.n; i += nth) ((T *)(sm + y.dinv))[i] = G.dinv[i];
+        if (y.parent >= 0)
+            for (int i = tid; i < y.n; i += nth) ((int *)(sm + y.parent))[i] = G.parent[i];
+        if (y.children >= 0)  // children of this level's rows (in level l-1)
+            for (int i = tid; i < y.n; i += nth)
+                ((int4 *)(sm + y.children))[i] = a.tab[l - 1].children[i];
+        if (y.Ainv >= 0)
+            for (int i = tid; i < y.n * y.n; i += nth) ((double *)(sm + y.Ainv))[i] = G.Ainv[i];
+        if (tid == 0) {
+            SLev<T> &S = stab[l];
+            S.n = y.n;
+            S.fine = 0;
+            S.sl = sl;
+            S.col = col;
+            S.val = val;
+            S.dinv = y.dinv >= 0 ? (const T *)(sm + y.dinv) : nullptr;
+            S.bptr = nullptr;
+            S.parent = y.parent >= 0 ? (const int *)(sm + y.parent) : nullptr;
+            S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
+                             ? (const int4 *)(sm + Y.lv[l + 1].children) : nullptr;
+            S.Ainv = y.Ainv >= 0 ? (const double *)(sm + y.Ainv) : nullptr;
+            S.rhs = (T *)(sm + y.rhs);
+            S.e = (T *)(sm + y.e);
+            S.r = y.r >= 0 ? (T *)(sm + y.r) : nullptr;
+            for (int k = 0; k < kMaxKcycle; k++) {
+                S.p[k] = y.p[k] >= 0 ? (T *)(sm + y.p[k]) : nullptr;
+                S.q[k] = y.q[k] >= 0 ? (T *)(sm + y.q[k]) : nullptr;
+            }
+            S.sc = (double *)(sm + Y.sc) + (size_t)(l - Y.tl) * SC_N;
+            S.nnext = l + 1 < Y.nlev ? Y.lv[l + 1].n : 0;
+        }
+    }
+    const int words = a.tail_nops * (int)(sizeof(Op) / sizeof(int));
+    for (int i = tid; i < words; i += nth)
+        ((int *)(sm + Y.prog))[i] = ((const int *)a.tail_prog)[i];
+}
+
+template <class T>
+__device__ void run_tail(const CycleArgs<T> &a, const SLev<T> *stab, unsigned char *sm) {
+    const int tl = a.lay.tl, n = a.lay.lv[tl].n;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const T *grhs = a.tab[tl].rhs;
+    T *srhs = stab[tl].rhs;
+    for (int i = tid; i < n; i += nth) srhs[i] = grhs[i];
+    __syncthreads();
+    RedCtx rc{nullptr, nullptr};
+    const Op *prog = (const Op *)(sm + a.lay.prog);
+    long long t0 = clock64();
+    for (int k = 0; k < a.tail_nops; k++) {
+        const Op &op = prog[k];  // read in place: a local copy would go through the stack
+        run_op<SLev<T>, RM_BLOCK>(stab, op, rc, tid, nth);
         __syncthreads();
+        if (a.tprof && tid == 0) {
+            long long t1 = clock64();
+            atomicAdd(&a.tprof[op.kind & 15], (unsigned long long)(t1 - t0));
+            atomicAdd(&a.tprof[16 + (op.kind & 15)], 1ull);
+            t0 = t1;
+        }
+    }
+    T *ge = a.tab[tl].e;
+    const T *se = stab[tl].e;
+    for (int i = tid; i < n; i += nth) ge[i] = se[i];
+}
+
+// sum the per-CTA partials of the previous op (every CTA, identical order) into sc; one
+// warp does it in FP64
+template <class T>
+__device__ __forceinline__ void finalize(const CycleArgs<T> &a, const GLev<T> *tab, const Op &op) {
+    if (threadIdx.x < 32) {
+        const int G = gridDim.x;
+        double *sc = tab[op.fin_level].sc;
+        for (int k = 0; k < op.fin_n; k++) {
+            double y = 0.0;
+            for (int b = threadIdx.x; b < G; b += 32)
+                y += __ldcg(&a.partials[((size_t)op.fin_pb * 4 + k) * G + b]);
+            y = warp_sum(y);
+            if (threadIdx.x == 0 && op.fin_dst[k] >= 0) sc[op.fin_dst[k]] = y;
+        }
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ SLev<T> stab[kMaxLevels];
+    __shared__ GLev<T> gtab[kMaxLevels];
+    __shared__ unsigned long long target;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        target = 0;
+        abort_flag = 0;
+    }
+    {  // the level table, read by every op, lives in shared memory
+        const int words = a.lay.nlev * (int)(sizeof(GLev<T>) / sizeof(int));
+        for (int i = threadIdx.x; i < words; i += blockDim.x)
+            ((int *)gtab)[i] = ((const int *)a.tab)[i];
+    }
+    if (blockIdx.x == 0 && a.lay.tl < a.lay.nlev) stage_tail(a, sm, stab);
+    __syncthreads();
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnth = gridDim.x * blockDim.x;
+    const RedCtx rc{a.partials, nullptr};
+    Op op = a.prog[0];
+    for (int k = 0; k < a.nops; k++) {
+        if (op.fin_pb >= 0) finalize(a, gtab, op);
+        if (op.kind == OP_TAIL) {
+            if (blockIdx.x == 0) run_tail(a, stab, sm);
+        } else if (op.kind != OP_NOP) {
+            run_op<GLev<T>, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
+        }
+        const Op next = a.prog[k + 1 < a.nops ? k + 1 : k];  // fetched while waiting
+        if (!grid_barrier(a.bar, a.err, target, abort_flag)) break;
+        if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
+        op = next;
     }
 }
+
+__global__ void k_timestamp(unsigned long long *t) { *t = global_ns(); }
 
 // ---------------------------------------------------------------------------------------
 // outer Krylov kernels (FP64, pi order)
@@ -424,6 +219,14 @@ __global__ void k_scatter(int n, const int *__restrict__ idx, const double *__re
     if (p < n) dst[idx[p]] = src[p];
 }
 
+// 1 / a_ii of every row (slot 0 of the sliced ELL holds the diagonal)
+template <class T>
+__global__ void k_inv_diag(int n, const int *__restrict__ sl, const double *__restrict__ val,
+                           T *__restrict__ dinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = (T)(1.0 / val[sl[i >> 5] + (i & 31)]);
+}
+
 template <class A, class B>
 __global__ void k_convert(int n, const A *__restrict__ src, B *__restrict__ dst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -437,11 +240,11 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(int n, const double *__re
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         a[0] += v[i] * v[i];
     double *o[1] = {out};
-    reduce_store<1, true>(a, o, rc);
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
 }
 
 // t = b - A x, (t, t) -> out
-__global__ void __launch_bounds__(kRedThreads) k_true_residual(LevelDev<double> L,
+__global__ void __launch_bounds__(kRedThreads) k_true_residual(GLev<double> L,
                                                                const double *__restrict__ b,
                                                                const double *__restrict__ x,
                                                                double *__restrict__ t,
@@ -453,12 +256,12 @@ __global__ void __launch_bounds__(kRedThreads) k_true_residual(LevelDev<double> 
         a[0] += ri * ri;
     }
     double *o[1] = {out};
-    reduce_store<1, true>(a, o, rc);
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
 }
 
-// outer scalars: osc[0] = (b,b), osc[1] = (r,r), osc[2] = stop flag, osc[3] = (p_i, A p_i),
-// osc[4] = (r, p_i), osc[8 + j] = (z, A p_j), osc[8 + max_iters + j] = (p_j, A p_j)
-enum : int { OS_BB = 0, OS_RR = 1, OS_STOP = 2, OS_PQ = 3, OS_RP = 4, OS_TT = 5, OS_ZQ = 8 };
+// outer scalars: osc[OS_BB] = (b,b), osc[OS_RR] = (r,r), osc[OS_STOP] = breakdown flag,
+// osc[OS_RP] = (r, p_i), osc[OS_TT] = (t, t), osc[OS_ZQ + j] = (z, A p_j); (p_j, A p_j) in opq
+enum : int { OS_BB = 0, OS_RR = 1, OS_STOP = 2, OS_RP = 4, OS_TT = 5, OS_ZQ = 8 };
 
 // (z, q_j) for all j < it: each block loops over j; the last block reduces every j
 __global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const double *__restrict__ z,
@@ -469,11 +272,11 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const dou
     __shared__ bool last;
     for (int j = 0; j < it; j++) {
         const double *q = Q[j];
-        double a[1] = {0.0};
+        double a[1] = {0.0}, r[1];
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
             a[0] += z[i] * q[i];
-        block_reduce<1>(a);
-        if (threadIdx.x == 0) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = a[0];
+        block_sum<1, double>(a, r);
+        if (threadIdx.x == 0) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = r[0];
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -483,12 +286,14 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const dou
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int j = 0; j < it; j++) {
-        double w[1] = {0.0};
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-            w[0] += __ldcg(&rc.partials[(size_t)j * gridDim.x + b]);
-        block_reduce<1>(w);
-        if (threadIdx.x == 0) osc[OS_ZQ + j] = w[0];
+    if (threadIdx.x < 32) {
+        for (int j = 0; j < it; j++) {
+            double y = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+                y += __ldcg(&rc.partials[(size_t)j * gridDim.x + b]);
+            y = warp_sum(y);
+            if (threadIdx.x == 0) osc[OS_ZQ + j] = y;
+        }
     }
     if (threadIdx.x == 0) *rc.counter = 0u;
 }
@@ -506,8 +311,8 @@ __global__ void k_outer_orth(int n, const double *__restrict__ z, double *const 
     }
 }
 
-// q = A p, (p, q) -> osc[PQ] and opq[it], (r, p) -> osc[RP]
-__global__ void __launch_bounds__(kRedThreads) k_outer_spmv_dot(LevelDev<double> L,
+// q = A p, (p, q) -> opq[it], (r, p) -> osc[RP]
+__global__ void __launch_bounds__(kRedThreads) k_outer_spmv_dot(GLev<double> L,
                                                                 double *const *__restrict__ P,
                                                                 double *const *__restrict__ Q,
                                                                 const int *__restrict__ it_ptr,
@@ -521,20 +326,16 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_spmv_dot(LevelDev<double>
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < L.n; row += gridDim.x * blockDim.x) {
         const int s = row >> 5;
         const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
-        double acc = 0.0;
-        for (int k = 0; k < width; k++) {
-            int c = L.col[base + 32 * k];
-            if (c >= 0) acc += L.val[base + 32 * k] * p[c];
-        }
+        const double acc = row_dot(L, base, 0, width, p);
         q[row] = acc;
         v[0] += p[row] * acc;
         v[1] += r[row] * p[row];
     }
     double *out[2] = {&opq[it], &osc[OS_RP]};
-    reduce_store<2, true>(v, out, rc);
+    reduce_store<2, RM_LASTBLOCK, double>(v, out, rc, 0);
 }
 
-// alpha = (r, p) / (p, Ap); x += alpha p; r -= alpha q; (r, r); it++
+// alpha = (r, p) / (p, Ap); x += alpha p; r -= alpha q; (r, r)
 __global__ void __launch_bounds__(kRedThreads) k_outer_update(int n, double *const *__restrict__ P,
                                                               double *const *__restrict__ Q,
                                                               int *it_ptr, double *__restrict__ x,
@@ -555,7 +356,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_update(int n, double *con
         v[0] += rn * rn;
     }
     double *out[1] = {&osc[OS_RR]};
-    reduce_store<1, true>(v, out, rc);
+    reduce_store<1, RM_LASTBLOCK, double>(v, out, rc, 0);
     if (blockIdx.x == 0 && threadIdx.x == 0 && bad) osc[OS_STOP] = 1.0;
 }
 
@@ -564,18 +365,33 @@ __global__ void k_bump(int *it_ptr) {
 }
 
 // =======================================================================================
-// diagnostics: CUDA-event timing of every op and its algorithmic bytes
+// diagnostics: per-kernel timing and algorithmic bytes
 thread_local int64_t g_launches = 0;
 
-enum : int { K_TAIL = 9, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
+enum : int { K_CYCLE = 11, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
              K_TRUE_RESIDUAL, K_NUM };
+constexpr int K_IN_CYCLE = 100;  // + op kind: an op timed inside the persistent kernel
+constexpr int K_IN_TAIL = 200;   // + op kind: an op timed inside the shared-memory tail
 
 const char *kernel_name(int kind) {
     static const char *names[K_NUM] = {"zero", "gs_colour", "resid_restrict", "prolong_correct",
                                        "coarse_solve", "alg1_multidot", "alg1_orth",
-                                       "alg1_spmv_dot", "alg1_update", "tail_cta",
-                                       "outer_multidot", "outer_orth", "outer_spmv_dot",
-                                       "outer_update", "true_residual"};
+                                       "alg1_spmv_dot", "alg1_update", "tail_cta", "barrier_only",
+                                       "cycle_persistent", "outer_multidot", "outer_orth",
+                                       "outer_spmv_dot", "outer_update", "true_residual"};
+    static const char *incycle[K_NUM] = {"in_cycle:zero", "in_cycle:gs_colour",
+                                         "in_cycle:resid_restrict", "in_cycle:prolong_correct",
+                                         "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
+                                         "in_cycle:alg1_orth", "in_cycle:alg1_spmv_dot",
+                                         "in_cycle:alg1_update", "in_cycle:tail_cta",
+                                         "in_cycle:barrier_only"};
+    static const char *intail[11] = {"in_tail:zero", "in_tail:gs_colour", "in_tail:resid_restrict",
+                                     "in_tail:prolong_correct", "in_tail:coarse_solve",
+                                     "in_tail:alg1_multidot", "in_tail:alg1_orth",
+                                     "in_tail:alg1_spmv_dot", "in_tail:alg1_update", "in_tail:?",
+                                     "in_tail:?"};
+    if (kind >= K_IN_CYCLE && kind < K_IN_CYCLE + 11) return incycle[kind - K_IN_CYCLE];
+    if (kind >= K_IN_TAIL && kind < K_IN_TAIL + 11) return intail[kind - K_IN_TAIL];
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "unknown";
 }
 
@@ -586,9 +402,7 @@ struct Profiler {
         cudaEvent_t a, b;
     };
     bool on = false;
-    std::vector<Rec> graph_recs;  // event nodes inside the captured cycle graph
-    std::vector<Rec> pending;     // direct launches not yet harvested
-    std::vector<Rec> graph_old;   // records of superseded graphs (events freed at the end)
+    std::vector<Rec> pending;
     struct Acc {
         int64_t launches = 0;
         double ms = 0, bytes = 0;
@@ -601,65 +415,44 @@ struct Profiler {
         acc.push_back({{kind, level}, Acc()});
         return acc.back().second;
     }
+    void add(int kind, int level, double ms, double bytes, int64_t launches = 1) {
+        Acc &a = slot(kind, level);
+        a.launches += launches;
+        a.ms += ms;
+        a.bytes += bytes;
+    }
     Rec begin(int kind, int level, double bytes, cudaStream_t s) {
         Rec r{kind, level, bytes, nullptr, nullptr};
         AMG_CUDA(cudaEventCreate(&r.a));
         AMG_CUDA(cudaEventCreate(&r.b));
-        // external event nodes inside a stream capture, plain records otherwise
-        if (is_capturing(s)) AMG_CUDA(cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal));
-        else AMG_CUDA(cudaEventRecord(r.a, s));
+        AMG_CUDA(cudaEventRecord(r.a, s));
         return r;
     }
-    void end(Rec &r, cudaStream_t s, bool capturing) {
-        if (capturing) AMG_CUDA(cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal));
-        else AMG_CUDA(cudaEventRecord(r.b, s));
-        (capturing ? graph_recs : pending).push_back(r);
+    void end(Rec &r, cudaStream_t s) {
+        AMG_CUDA(cudaEventRecord(r.b, s));
+        pending.push_back(r);
     }
-    static bool is_capturing(cudaStream_t s) {
-        cudaStreamCaptureStatus st;
-        if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
-        return st == cudaStreamCaptureStatusActive;
-    }
-    void add(const Rec &r) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-        Acc &a = slot(r.kind, r.level);
-        a.launches++;
-        a.ms += ms;
-        a.bytes += r.bytes;
-    }
-    void harvest_graph() {
-        for (auto &r : graph_recs) add(r);
-    }
-    void harvest_pending() {
+    void harvest() {
         for (auto &r : pending) {
-            add(r);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) add(r.kind, r.level, ms, r.bytes);
+            else cudaGetLastError();
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
         }
         pending.clear();
     }
     ~Profiler() {
-        for (auto *v : {&graph_recs, &pending, &graph_old})
-            for (auto &r : *v) {
-                cudaEventDestroy(r.a);
-                cudaEventDestroy(r.b);
-            }
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
     }
 };
 
 void profiler_enable(amg_hierarchy *h, bool on) {
     if (!h->prof) h->prof = new Profiler();
     h->prof->on = on;
-    if (h->cycle_graph) {  // recapture so the graph carries (or drops) the event nodes
-        cudaGraphExecDestroy(h->cycle_graph);
-        h->cycle_graph = nullptr;
-        for (auto &r : h->prof->graph_recs) h->prof->graph_old.push_back(r);
-        h->prof->graph_recs.clear();
-    }
     h->prof->acc.clear();
 }
 
@@ -685,12 +478,6 @@ int profiler_read(const amg_hierarchy *h, int cap, int32_t *kind, int32_t *level
 }
 
 static bool profiling(const amg_hierarchy *h) { return h->prof && h->prof->on; }
-
-static bool capturing(cudaStream_t s) {
-    cudaStreamCaptureStatus st;
-    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
-    return st == cudaStreamCaptureStatusActive;
-}
 
 // algorithmic bytes of one op: every array the op must touch, once, at its width
 // (w = value width, 4-byte column indices; padding of the sliced ELL is not counted)
@@ -723,6 +510,20 @@ static double op_bytes(const amg_hierarchy *h, const Op &op, int w) {
 
 // =======================================================================================
 // host side
+struct EngineBase {
+    Op *prog = nullptr;
+    int nops = 0;
+    Op *tail_prog = nullptr;
+    int tail_nops = 0;
+    TailLayout lay{};
+    size_t smem = 0;
+    int grid = 0;
+    std::vector<Op> hprog, htail;
+    double tail_bytes = 0, cycle_bytes = 0;
+    unsigned long long *ts = nullptr;
+    unsigned long long *tprof = nullptr;
+};
+
 namespace {
 
 template <class T>
@@ -732,58 +533,35 @@ Vecs<double> &vecs<double>(Level &lv) { return lv.v64; }
 template <>
 Vecs<float> &vecs<float>(Level &lv) { return lv.v32; }
 
-int red_grid(int64_t n) { return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads)); }
-int ew_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+int red_grid(int64_t n) {
+    return (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+}
 
-// Walks Alg. 1 / Alg. 2 and either launches or records each op.
-template <class T>
-struct Emitter {
+size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+bool is_reduction(const Op &op) {
+    return op.kind == OP_MULTIDOT || op.kind == OP_SPMV_DOT || (op.kind == OP_UPDATE && !op.last);
+}
+
+// Walks Alg. 2 / Alg. 1 from a level and appends the ops to a program. The recursion stops
+// at `stop_level`, where one OP_TAIL stands for B~ of that level (persistent program), or
+// continues to the coarsest level (tail program, standalone execution).
+struct Builder {
     amg_hierarchy *h;
-    const LevelDev<T> *tab;        // device table
-    std::vector<Op> *record;       // non-null: record ops (tail program)
-    int tail_level;                // levels >= tail_level are recorded into the tail program
-    const Op *tail_prog = nullptr; // device program of the tail
-    int tail_nops = 0;
-    double tail_bytes = 0;
-    RedCtx rc;
+    std::vector<Op> *out;
+    int stop_level;  // >= nlev: never stop
 
-    void launch(const Op &op) {
-        cudaStream_t s = h->stream;
-        const Level &lv = h->lev[op.level];
-        Profiler::Rec rec{};
-        const bool prof = profiling(h);
-        if (prof) rec = h->prof->begin(op.kind, op.level, op_bytes(h, op, sizeof(T)), s);
-        switch (op.kind) {
-            case OP_ZERO: k_zero<T><<<ew_grid(lv.n), 256, 0, s>>>(tab, op); break;
-            case OP_GS: k_gs<T><<<ew_grid(op.i1 - op.i0), 256, 0, s>>>(tab, op); break;
-            case OP_RESTRICT: k_restrict<T><<<ew_grid(h->lev[op.level + 1].n), 256, 0, s>>>(tab, op); break;
-            case OP_PROLONG: k_prolong<T><<<ew_grid(lv.n), 256, 0, s>>>(tab, op); break;
-            case OP_COARSE: k_coarse<T><<<1, 256, 0, s>>>(tab, op); break;
-            case OP_MULTIDOT: k_multidot<T><<<red_grid(lv.n), kRedThreads, 0, s>>>(tab, op, rc); break;
-            case OP_ORTH: k_orth<T><<<ew_grid(lv.n), 256, 0, s>>>(tab, op); break;
-            case OP_SPMV_DOT: k_spmv_dot<T><<<red_grid(lv.n), kRedThreads, 0, s>>>(tab, op, rc); break;
-            case OP_UPDATE: k_update<T><<<red_grid(lv.n), kRedThreads, 0, s>>>(tab, op, rc); break;
-        }
-        AMG_LAUNCH_CHECK();
-        if (prof) h->prof->end(rec, s, capturing(s));
-    }
-
-    void emit(const Op &op) {
-        if (record) {
-            record->push_back(op);
-            tail_bytes += op_bytes(h, op, sizeof(T));
-        } else {
-            launch(op);
-        }
-    }
-
-    Op mk(int kind, int level) {
+    static Op mk(int kind, int level) {
         Op o;
         std::memset(&o, 0, sizeof o);
         o.kind = kind;
         o.level = level;
+        o.red_pb = -1;
+        o.fin_pb = -1;
+        for (int k = 0; k < 4; k++) o.fin_dst[k] = -1;
         return o;
     }
+    void emit(const Op &o) { out->push_back(o); }
 
     // z = B^_l [f] (Alg. 2)
     void bhat(int l, int fsel, int zsel) {
@@ -798,7 +576,6 @@ struct Emitter {
             Op g = mk(OP_GS, l);
             g.i0 = ranges[c];
             g.i1 = ranges[c + 1];
-            g.backward = 0;
             g.fsel = fsel;
             g.usel = zsel;
             emit(g);
@@ -825,14 +602,8 @@ struct Emitter {
 
     // e = B~_l [rhs] (Alg. 1 with kcycle_n steps; exact on the coarsest level)
     void btilde(int l) {
-        if (!record && l == tail_level) {
-            // the whole recursion from here runs in one CTA (the program is B~ of this level)
-            Profiler::Rec rec{};
-            const bool prof = profiling(h);
-            if (prof) rec = h->prof->begin(K_TAIL, l, tail_bytes, h->stream);
-            k_tail<T><<<1, kTailThreads, 0, h->stream>>>(tab, tail_prog, tail_nops);
-            AMG_LAUNCH_CHECK();
-            if (prof) h->prof->end(rec, h->stream, capturing(h->stream));
+        if (l == stop_level) {
+            emit(mk(OP_TAIL, l));
             return;
         }
         Level &lv = h->lev[l];
@@ -862,12 +633,55 @@ struct Emitter {
     }
 };
 
+// persistent program: reductions leave partials in alternating buffers; the next op sums
+// them into the level's scalars
+void annotate_reductions(std::vector<Op> &prog) {
+    std::vector<Op> out;
+    int pb = 0;
+    bool pending = false;
+    Op pend{};
+    auto attach = [&](Op &op) {
+        op.fin_pb = pend.red_pb;
+        op.fin_level = pend.level;
+        if (pend.kind == OP_MULTIDOT) {
+            op.fin_n = pend.step;
+            for (int j = 0; j < pend.step; j++) op.fin_dst[j] = SC_ZQ0 + j;
+        } else if (pend.kind == OP_SPMV_DOT) {
+            op.fin_n = 2;
+            op.fin_dst[0] = SC_PQ0 + pend.step;
+            op.fin_dst[1] = SC_RP0 + pend.step;
+        } else {
+            op.fin_n = 1;
+            op.fin_dst[0] = SC_RR0 + pend.step;
+        }
+    };
+    for (Op op : prog) {
+        if (pending) {
+            attach(op);
+            pending = false;
+        }
+        if (is_reduction(op)) {
+            op.red_pb = pb;
+            pb ^= 1;
+            pending = true;
+            pend = op;
+        }
+        out.push_back(op);
+    }
+    if (pending) {
+        Op nop = Builder::mk(OP_NOP, pend.level);
+        attach(nop);
+        out.push_back(nop);
+    }
+    prog.swap(out);
+}
+
 template <class T>
 void fill_tables(amg_hierarchy *h) {
-    std::vector<LevelDev<T>> tab(h->nlev);
+    std::vector<GLev<T>> tab(h->nlev);
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
-        LevelDev<T> &d = tab[l];
+        GLev<T> &d = tab[l];
         std::memset(&d, 0, sizeof d);
         d.n = lv.n;
         d.fine = (l == 0) ? 1 : 0;
@@ -875,11 +689,12 @@ void fill_tables(amg_hierarchy *h) {
         d.col = lv.A.col;
         if constexpr (sizeof(T) == 8) d.val = (const T *)lv.A.val;
         else d.val = (const T *)lv.A.val32;
+        if constexpr (sizeof(T) == 8) d.dinv = (const T *)lv.dinv64;
+        else d.dinv = (const T *)lv.dinv32;
         d.bptr = lv.bptr;
         d.parent = lv.parent;
         d.children = (l + 1 < h->nlev) ? h->lev[l + 1].children : nullptr;
-        if constexpr (sizeof(T) == 8) d.Ainv = (const T *)lv.Ainv;
-        else d.Ainv = (const T *)lv.Ainv32;
+        d.Ainv = lv.Ainv;
         Vecs<T> &v = vecs<T>(lv);
         d.rhs = v.rhs;
         d.e = v.e;
@@ -892,45 +707,136 @@ void fill_tables(amg_hierarchy *h) {
         d.nnext = (l + 1 < h->nlev) ? h->lev[l + 1].n : 0;
     }
     void *&dst = (sizeof(T) == 8) ? h->lev_tab64 : h->lev_tab32;
-    if (!dst) dst = halloc<LevelDev<T>>(h, h->nlev);
-    AMG_CUDA(cudaMemcpyAsync(dst, tab.data(), sizeof(LevelDev<T>) * h->nlev,
-                             cudaMemcpyHostToDevice, h->stream));
+    if (!dst) dst = halloc<GLev<T>>(h, h->nlev);
+    AMG_CUDA(cudaMemcpyAsync(dst, tab.data(), sizeof(GLev<T>) * h->nlev, cudaMemcpyHostToDevice,
+                             h->stream));
 }
 
-int tail_rows() {
+template <class T>
+const GLev<T> *dtab(amg_hierarchy *h) {
+    return (const GLev<T> *)((sizeof(T) == 8) ? h->lev_tab64 : h->lev_tab32);
+}
+
+// shared-memory image of levels l0..nlev-1; returns false if a level is too large
+bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, TailLayout &Y) {
+    std::memset(&Y, 0, sizeof Y);
+    Y.tl = l0;
+    Y.nlev = h->nlev;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        int o = (int)off;
+        off += align16(bytes);
+        return o;
+    };
+    const int kc = h->opt.kcycle_n;
+    for (int l = l0; l < h->nlev; l++) {
+        const Level &lv = h->lev[l];
+        if (lv.n > kTailRowsMax) return false;
+        TailLevelLayout &y = Y.lv[l];
+        y.n = lv.n;
+        y.nslices = lv.A.nslices;
+        y.padded = (int)lv.A.padded;
+        y.sl = take(sizeof(int) * (size_t)(lv.A.nslices + 1));
+        y.col = take(2 * (size_t)lv.A.padded);
+        y.val = take((size_t)w * lv.A.padded);
+        y.dinv = lv.coarsest ? -1 : take((size_t)w * lv.n);
+        y.parent = lv.coarsest ? -1 : take(sizeof(int) * (size_t)lv.n);
+        y.children = (l > l0) ? take(sizeof(int4) * (size_t)lv.n) : -1;
+        y.Ainv = lv.coarsest ? take(sizeof(double) * lv.n * lv.n) : -1;
+        y.rhs = take((size_t)w * lv.n);
+        y.e = take((size_t)w * lv.n);
+        y.r = lv.coarsest ? -1 : take((size_t)w * lv.n);
+        for (int k = 0; k < kMaxKcycle; k++) {
+            y.p[k] = (!lv.coarsest && k < kc) ? take((size_t)w * lv.n) : -1;
+            y.q[k] = (!lv.coarsest && k < kc) ? take((size_t)w * lv.n) : -1;
+        }
+        if (off > (size_t)INT32_MAX) return false;
+    }
+    Y.sc = take(sizeof(double) * SC_N * (size_t)(h->nlev - l0));
+    Y.prog = take(sizeof(Op) * (size_t)tail_ops);
+    Y.bytes = (int)off;
+    return true;
+}
+
+template <class T>
+EngineBase *&engine_slot(amg_hierarchy *h) {
+    return (sizeof(T) == 8) ? h->eng64 : h->eng32;
+}
+
+int max_tail_bytes() {
     static int v = [] {
-        const char *e = getenv("AMG_TAIL_ROWS");
-        return e ? atoi(e) : 4096;
+        const char *e = getenv("AMG_TAIL_SMEM");  // tuning knob: cap on the staged tail
+        return e ? atoi(e) : INT32_MAX;
     }();
     return v;
 }
 
 template <class T>
-void build_tail(amg_hierarchy *h) {
-    // the tail starts at the first coarse level (>= 1) with at most tail_rows() rows
+void build_engine(amg_hierarchy *h) {
+    EngineBase *&E = engine_slot<T>(h);
+    if (!E) E = new EngineBase();
+    cudaStream_t s = h->stream;
+    int dev = h->device, optin = 0, nsm = 0;
+    AMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    AMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaFuncAttributes fa;
+    AMG_CUDA(cudaFuncGetAttributes(&fa, k_cycle<T>));
+    const long budget = std::min<long>((long)optin - (long)fa.sharedSizeBytes - 1024,
+                                       (long)max_tail_bytes());
+    // the tail: the finest coarse level from which every level fits in shared memory
     int tl = h->nlev;
-    for (int l = 1; l < h->nlev; l++)
-        if (h->lev[l].n <= tail_rows()) {
+    for (int l = 1; l < h->nlev; l++) {
+        TailLayout Y;
+        std::vector<Op> tp;
+        Builder bt{h, &tp, h->nlev + 1};
+        bt.btilde(l);
+        if (tail_layout(h, l, sizeof(T), (int)tp.size(), Y) && Y.bytes <= budget) {
             tl = l;
+            E->lay = Y;
             break;
         }
-    h->tail_level = tl;
-    if (tl >= h->nlev) return;
-    std::vector<Op> prog;
-    Emitter<T> em{h, nullptr, &prog, tl};
-    em.btilde(tl);
-    Op *d = halloc<Op>(h, prog.size());
-    AMG_CUDA(cudaMemcpyAsync(d, prog.data(), sizeof(Op) * prog.size(), cudaMemcpyHostToDevice,
-                             h->stream));
-    if (sizeof(T) == 8) {
-        h->tail_prog64 = d;
-        h->tail_nops64 = (int)prog.size();
-        h->tail_bytes64 = em.tail_bytes;
-    } else {
-        h->tail_prog32 = d;
-        h->tail_nops32 = (int)prog.size();
-        h->tail_bytes32 = em.tail_bytes;
     }
+    if (tl == h->nlev) {
+        std::memset(&E->lay, 0, sizeof E->lay);
+        E->lay.tl = h->nlev;
+        E->lay.nlev = h->nlev;
+    }
+    h->tail_level = tl;
+    E->hprog.clear();
+    E->htail.clear();
+    Builder b{h, &E->hprog, tl};
+    b.bhat(0, V_RHS, V_E);
+    annotate_reductions(E->hprog);
+    if (tl < h->nlev) {
+        Builder bt{h, &E->htail, h->nlev + 1};
+        bt.btilde(tl);
+    }
+    E->tail_bytes = 0;
+    for (const Op &op : E->htail) E->tail_bytes += op_bytes(h, op, sizeof(T));
+    E->cycle_bytes = E->tail_bytes * 0;
+    for (const Op &op : E->hprog)
+        E->cycle_bytes += (op.kind == OP_TAIL) ? E->tail_bytes
+                          : (op.kind == OP_NOP) ? 0.0 : op_bytes(h, op, sizeof(T));
+    E->nops = (int)E->hprog.size();
+    E->tail_nops = (int)E->htail.size();
+    E->prog = halloc<Op>(h, E->hprog.size());
+    AMG_CUDA(cudaMemcpyAsync(E->prog, E->hprog.data(), sizeof(Op) * E->hprog.size(),
+                             cudaMemcpyHostToDevice, s));
+    if (E->tail_nops) {
+        E->tail_prog = halloc<Op>(h, E->htail.size());
+        AMG_CUDA(cudaMemcpyAsync(E->tail_prog, E->htail.data(), sizeof(Op) * E->htail.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    E->smem = tl < h->nlev ? (size_t)E->lay.bytes : 0;
+    AMG_CUDA(cudaFuncSetAttribute(k_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)E->smem));
+    int per_sm = 0;
+    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle<T>, kPThreads, E->smem));
+    if (per_sm < 1) throw Error{AMG_ERR_CUDA, "persistent cycle kernel cannot be resident"};
+    E->grid = nsm;  // one CTA per SM (co-resident: cooperative launch)
+    E->ts = halloc<unsigned long long>(h, E->hprog.size() + 1);
+    E->tprof = halloc<unsigned long long>(h, 32);
+    AMG_CUDA(cudaMemsetAsync(E->tprof, 0, 32 * sizeof(unsigned long long), s));
 }
 
 template <class T>
@@ -953,17 +859,6 @@ void alloc_vecs(amg_hierarchy *h) {
     }
 }
 
-template <class T>
-Emitter<T> make_emitter(amg_hierarchy *h) {
-    Emitter<T> em{h, (const LevelDev<T> *)((sizeof(T) == 8) ? h->lev_tab64 : h->lev_tab32),
-                  nullptr, h->tail_level};
-    em.tail_prog = (const Op *)((sizeof(T) == 8) ? h->tail_prog64 : h->tail_prog32);
-    em.tail_nops = (sizeof(T) == 8) ? h->tail_nops64 : h->tail_nops32;
-    em.tail_bytes = (sizeof(T) == 8) ? h->tail_bytes64 : h->tail_bytes32;
-    em.rc = RedCtx{h->red_partials, h->red_counter};
-    return em;
-}
-
 void ensure_fp32(amg_hierarchy *h) {
     if (h->fp32_ready) return;
     cudaStream_t s = h->stream;
@@ -974,61 +869,116 @@ void ensure_fp32(amg_hierarchy *h) {
             (int)lv.A.padded, lv.A.val, lv.A.val32);
         AMG_LAUNCH_CHECK();
     }
+    for (int l = 0; l < h->nlev; l++) {
+        Level &lv = h->lev[l];
+        lv.dinv32 = halloc<float>(h, lv.n);
+        k_inv_diag<float><<<nblocks_for(lv.n, 256), 256, 0, s>>>(lv.n, lv.A.sl_ptr, lv.A.val, lv.dinv32);
+        AMG_LAUNCH_CHECK();
+    }
     alloc_vecs<float>(h);
     h->r32 = halloc<float>(h, h->N);
     h->z32 = halloc<float>(h, h->N);
-    // the fine level's cycle vectors
+    h->lev[0].v32.rhs = h->r32;
+    h->lev[0].v32.e = h->z32;
     fill_tables<float>(h);
-    build_tail<float>(h);
+    build_engine<float>(h);
     h->fp32_ready = true;
 }
 
-// z (FP64, pi order) = B^_0 [r]; level-0 input/output buffers are set in the table
+// one launch of the persistent kernel: z = B^_0 [r] on level 0's table buffers
 template <class T>
-void record_cycle(amg_hierarchy *h) {
-    Emitter<T> em = make_emitter<T>(h);
-    em.bhat(0, V_RHS, V_E);
+void launch_cycle(amg_hierarchy *h) {
+    EngineBase *E = engine_slot<T>(h);
+    cudaStream_t s = h->stream;
+    const bool prof = profiling(h);
+    CycleArgs<T> a;
+    a.tab = dtab<T>(h);
+    a.prog = E->prog;
+    a.nops = E->nops;
+    a.tail_prog = E->tail_prog;
+    a.tail_nops = E->tail_nops;
+    a.lay = E->lay;
+    a.partials = h->cyc_partials;
+    a.bar = h->bar;
+    a.err = h->err_flag;
+    AMG_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), s));
+    a.ts = prof ? E->ts + 1 : nullptr;
+    a.tprof = prof ? E->tprof : nullptr;
+    Profiler::Rec rec{};
+    if (prof) {
+        k_timestamp<<<1, 1, 0, s>>>(E->ts);
+        AMG_LAUNCH_CHECK();
+        rec = h->prof->begin(K_CYCLE, 0, E->cycle_bytes, s);
+    }
+    void *args[] = {&a};
+    AMG_CUDA(cudaLaunchCooperativeKernel((void *)k_cycle<T>, dim3(E->grid), dim3(kPThreads), args,
+                                         E->smem, s));
+    AMG_LAUNCH_CHECK();
+    if (prof) h->prof->end(rec, s);
+}
+
+// per-op durations of the last profiled launch, from the in-kernel timestamps (each op's
+// time includes the grid barrier that ends it)
+template <class T>
+void harvest_cycle_timestamps(amg_hierarchy *h) {
+    EngineBase *E = engine_slot<T>(h);
+    std::vector<unsigned long long> t(E->hprog.size() + 1);
+    AMG_CUDA(cudaMemcpy(t.data(), E->ts, sizeof(unsigned long long) * t.size(),
+                        cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < E->hprog.size(); k++) {
+        const Op &op = E->hprog[k];
+        double ms = (double)(t[k + 1] - t[k]) * 1e-6;
+        double bytes = (op.kind == OP_TAIL) ? E->tail_bytes
+                       : (op.kind == OP_NOP) ? 0.0 : op_bytes(h, op, sizeof(T));
+        h->prof->add(K_IN_CYCLE + op.kind, op.level, ms, bytes);
+    }
+    // inside the tail: SM cycles per op kind, reported at the nominal clock of this device
+    unsigned long long tp[32];
+    AMG_CUDA(cudaMemcpy(tp, E->tprof, sizeof tp, cudaMemcpyDeviceToHost));
+    AMG_CUDA(cudaMemset(E->tprof, 0, sizeof tp));
+    int khz = 0;
+    AMG_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device));
+    for (int k = 0; k < 16; k++)
+        if (tp[16 + k]) h->prof->add(K_IN_TAIL + k, E->lay.tl, (double)tp[k] / khz, 0.0, (int64_t)tp[16 + k]);
+}
+
+// standalone execution of B^_l (diagnostic path): one kernel per op, every level in HBM
+template <class T>
+void run_standalone(amg_hierarchy *h, int l, int fsel, int zsel) {
+    cudaStream_t s = h->stream;
+    std::vector<Op> prog;
+    Builder b{h, &prog, h->nlev + 1};
+    b.bhat(l, fsel, zsel);
+    RedCtx rc{h->red_partials, h->red_counter};
+    for (const Op &op : prog) {
+        const Level &lv = h->lev[op.level];
+        int grid;
+        switch (op.kind) {
+            case OP_GS: grid = nblocks_for(op.i1 - op.i0, kRedThreads); break;
+            case OP_RESTRICT: grid = nblocks_for(h->lev[op.level + 1].n, kRedThreads); break;
+            case OP_COARSE: grid = 1; break;
+            case OP_MULTIDOT:
+            case OP_SPMV_DOT:
+            case OP_UPDATE: grid = red_grid(lv.n); break;
+            default: grid = nblocks_for(lv.n, kRedThreads);
+        }
+        k_op<T><<<grid, kRedThreads, 0, s>>>(dtab<T>(h), op, rc);
+        AMG_LAUNCH_CHECK();
+    }
 }
 
 }  // namespace
-
-// capture the preconditioner application B^_fine into a CUDA graph (once per precision)
-static void ensure_cycle_graph(amg_hierarchy *h, int prec) {
-    if (h->cycle_graph && h->cycle_graph_prec == prec) return;
-    if (h->cycle_graph) {
-        cudaGraphExecDestroy(h->cycle_graph);
-        h->cycle_graph = nullptr;
-    }
-    cudaStream_t s = h->stream;
-    AMG_CUDA(cudaStreamSynchronize(s));
-    cudaGraph_t g;
-    const int64_t launches_before = g_launches;
-    AMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    try {
-        if (prec == AMG_FP32) record_cycle<float>(h);
-        else record_cycle<double>(h);
-    } catch (...) {
-        cudaGraph_t dummy;
-        cudaStreamEndCapture(s, &dummy);
-        if (dummy) cudaGraphDestroy(dummy);
-        throw;
-    }
-    AMG_CUDA(cudaStreamEndCapture(s, &g));
-    h->graph_nodes = g_launches - launches_before;  // captured, not yet executed
-    g_launches = launches_before;
-    cudaError_t e = cudaGraphInstantiate(&h->cycle_graph, g, 0);
-    cudaGraphDestroy(g);
-    AMG_CUDA(e);
-    h->cycle_graph_prec = prec;
-}
 
 void allocate_solve_workspace(amg_hierarchy *h) {
     const int n = (int)h->N;
     h->red_partials = halloc<double>(h, (size_t)kRedBlocks * std::max(8, h->opt.max_iters + 8));
     h->red_counter = halloc<unsigned int>(h, 1);
     AMG_CUDA(cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned int), h->stream));
+    h->cyc_partials = halloc<double>(h, 2 * 4 * 1024);
+    h->bar = halloc<unsigned long long>(h, 32);
+    AMG_CUDA(cudaMemsetAsync(h->bar, 0, 32 * sizeof(unsigned long long), h->stream));
     alloc_vecs<double>(h);
-    // level-0 cycle input / output live in the outer solver's vectors
+    // level-0 cycle input / output are the outer solver's r and z
     h->xo = halloc<double>(h, n);
     h->ro = halloc<double>(h, n);
     h->zo = halloc<double>(h, n);
@@ -1041,8 +991,21 @@ void allocate_solve_workspace(amg_hierarchy *h) {
     h->dP = halloc<double *>(h, h->opt.max_iters);
     h->dQ = halloc<double *>(h, h->opt.max_iters);
     AMG_CUDA(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
+    for (int l = 0; l < h->nlev; l++) {
+        Level &lv = h->lev[l];
+        lv.dinv64 = halloc<double>(h, lv.n);
+        k_inv_diag<double><<<nblocks_for(lv.n, 256), 256, 0, h->stream>>>(lv.n, lv.A.sl_ptr, lv.A.val,
+                                                                          lv.dinv64);
+        AMG_LAUNCH_CHECK();
+    }
     fill_tables<double>(h);
-    build_tail<double>(h);
+    if (h->nlev > 1) build_engine<double>(h);
+}
+
+void free_engines(amg_hierarchy *h) {
+    delete h->eng64;
+    delete h->eng32;
+    h->eng64 = h->eng32 = nullptr;
 }
 
 static void ensure_directions(amg_hierarchy *h, int count) {
@@ -1061,8 +1024,8 @@ static void ensure_directions(amg_hierarchy *h, int count) {
                              h->stream));
 }
 
-static LevelDev<double> fine_view(amg_hierarchy *h) {
-    LevelDev<double> L;
+static GLev<double> fine_view(amg_hierarchy *h) {
+    GLev<double> L;
     std::memset(&L, 0, sizeof L);
     Level &lv = h->lev[0];
     L.n = lv.n;
@@ -1072,41 +1035,38 @@ static LevelDev<double> fine_view(amg_hierarchy *h) {
     return L;
 }
 
+static void check_device_error(amg_hierarchy *h) {
+    int err = 0;
+    AMG_CUDA(cudaMemcpyAsync(&err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    if (err & kErrTimeout) {
+        // the kernel left its op loop: clear the flag and the barrier state for the next launch
+        AMG_CUDA(cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
+        AMG_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream));
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        throw Error{AMG_ERR_TIMEOUT, "a grid barrier of the cycle kernel timed out"};
+    }
+}
+
 // one application of B^_0 to h->ro (FP64) into h->zo (FP64)
 static void apply_preconditioner(amg_hierarchy *h) {
     cudaStream_t s = h->stream;
     const int n = (int)h->N;
-    if (h->nlev == 1) {  // exact solve
-        LevelDev<double> L = fine_view(h);
-        (void)L;
-        Op op;
-        std::memset(&op, 0, sizeof op);
-        // rhs = ro, e = zo are the level-0 buffers of the table
-        k_coarse<double><<<1, 256, 0, s>>>((const LevelDev<double> *)h->lev_tab64, op);
+    if (h->nlev == 1) {  // exact solve on the only level
+        Op op = Builder::mk(OP_COARSE, 0);
+        RedCtx rc{h->red_partials, h->red_counter};
+        k_op<double><<<1, kRedThreads, 0, s>>>(dtab<double>(h), op, rc);
         AMG_LAUNCH_CHECK();
         return;
     }
-    int prec = h->opt.cycle_prec;
-    ensure_cycle_graph(h, prec);
-    if (prec == AMG_FP32) {
+    if (h->opt.cycle_prec == AMG_FP32) {
         k_convert<double, float><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->ro, h->r32);
         AMG_LAUNCH_CHECK();
-    }
-    AMG_CUDA(cudaGraphLaunch(h->cycle_graph, s));
-    g_launches += h->graph_nodes;
-    if (prec == AMG_FP32) {
+        launch_cycle<float>(h);
         k_convert<float, double><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->z32, h->zo);
         AMG_LAUNCH_CHECK();
-    }
-}
-
-static void prepare_precision(amg_hierarchy *h) {
-    if (h->opt.cycle_prec == AMG_FP32 && h->nlev > 1) {
-        ensure_fp32(h);
-        // FP32 level-0 in/out buffers are the conversion buffers
-        h->lev[0].v32.rhs = h->r32;
-        h->lev[0].v32.e = h->z32;
-        fill_tables<float>(h);
+    } else {
+        launch_cycle<double>(h);
     }
 }
 
@@ -1118,7 +1078,7 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
     Level &F = h->lev[0];
     RedCtx rc{h->red_partials, h->red_counter};
     const bool prof = profiling(h);
-    prepare_precision(h);
+    if (h->opt.cycle_prec == AMG_FP32 && h->nlev > 1) ensure_fp32(h);
     // x = 0, r = b (pi order)
     k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, b_nat, h->bo);
     AMG_LAUNCH_CHECK();
@@ -1134,46 +1094,48 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
     int status = AMG_ERR_NOT_CONVERGED;
     int it = 0;
     double rel = 1.0;
-    if (!std::isfinite(bn)) {
-        throw Error{AMG_ERR_INVALID_ARG, "non-finite right-hand side"};
-    }
+    if (!std::isfinite(bn)) throw Error{AMG_ERR_INVALID_ARG, "non-finite right-hand side"};
     if (bn == 0.0) {
         status = AMG_OK;
         rel = 0.0;
     } else {
         double *opq = h->osc + OS_ZQ + maxit;
-        LevelDev<double> Lf = fine_view(h);
+        GLev<double> Lf = fine_view(h);
+        const double nd = n, nnz = (double)F.A.stored;
         for (it = 0; it < maxit;) {
             ensure_directions(h, it + 1);
             apply_preconditioner(h);  // zo = B^[ro]
-            const double nd = n, nnz = (double)F.A.stored;
             Profiler::Rec rec{};
             if (prof) rec = h->prof->begin(K_OUTER_MULTIDOT, 0, 8.0 * nd * (1 + it), s);
             k_outer_multidot<<<red_grid(n), kRedThreads, 0, s>>>(n, h->zo, h->dQ, h->oit, h->osc, rc);
             AMG_LAUNCH_CHECK();
-            if (prof) h->prof->end(rec, s, false);
+            if (prof) h->prof->end(rec, s);
             if (prof) rec = h->prof->begin(K_OUTER_ORTH, 0, 8.0 * nd * (2 + it), s);
-            k_outer_orth<<<ew_grid(n), 256, 0, s>>>(n, h->zo, h->dP, h->oit, h->osc, opq);
+            k_outer_orth<<<nblocks_for(n, 256), 256, 0, s>>>(n, h->zo, h->dP, h->oit, h->osc, opq);
             AMG_LAUNCH_CHECK();
-            if (prof) h->prof->end(rec, s, false);
+            if (prof) h->prof->end(rec, s);
             if (prof) rec = h->prof->begin(K_OUTER_SPMV_DOT, 0, 12.0 * nnz + 24.0 * nd, s);
             k_outer_spmv_dot<<<red_grid(n), kRedThreads, 0, s>>>(Lf, h->dP, h->dQ, h->oit, h->ro,
                                                                  h->osc, opq, rc);
             AMG_LAUNCH_CHECK();
-            if (prof) h->prof->end(rec, s, false);
+            if (prof) h->prof->end(rec, s);
             if (prof) rec = h->prof->begin(K_OUTER_UPDATE, 0, 48.0 * nd, s);
             k_outer_update<<<red_grid(n), kRedThreads, 0, s>>>(n, h->dP, h->dQ, h->oit, h->xo,
                                                                h->ro, h->osc, opq, rc);
             AMG_LAUNCH_CHECK();
-            if (prof) h->prof->end(rec, s, false);
+            if (prof) h->prof->end(rec, s);
             k_bump<<<1, 32, 0, s>>>(h->oit);
             AMG_LAUNCH_CHECK();
             AMG_CUDA(cudaMemcpyAsync(h->h_pinned, h->osc, sizeof(double) * 8,
                                      cudaMemcpyDeviceToHost, s));
             AMG_CUDA(cudaStreamSynchronize(s));
+            if (h->nlev > 1) check_device_error(h);
             if (prof) {
-                h->prof->harvest_graph();
-                h->prof->harvest_pending();
+                h->prof->harvest();
+                if (h->nlev > 1) {
+                    if (h->opt.cycle_prec == AMG_FP32) harvest_cycle_timestamps<float>(h);
+                    else harvest_cycle_timestamps<double>(h);
+                }
             }
             it++;
             if (h->h_pinned[OS_STOP] != 0.0) {
@@ -1218,34 +1180,40 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
     return status;
 }
 
-// z = B^_level [f] in natural order (FP64), through the same ops as the solve
+// z = B^_level [f] in natural order (FP64). Level 0 runs the persistent kernel exactly as the
+// solve does; coarser levels run the standalone executor (one kernel per op).
 void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double *z_nat) {
     cudaStream_t s = h->stream;
     Level &lv = h->lev[level];
     const int n = lv.n;
-    double *zbuf = level == 0 ? h->zo : lv.v64.p[0];
-    double *fbuf = level == 0 ? h->ro : lv.v64.rhs;
+    RedCtx rc{h->red_partials, h->red_counter};
     if (lv.coarsest) {
-        // B^_1 = A_1^{-1}: on the coarsest level the cycle is the exact solve
-        k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, lv.v64.rhs ? lv.v64.rhs : h->ro);
+        double *fbuf = level == 0 ? h->ro : lv.v64.rhs;
+        double *ebuf = level == 0 ? h->zo : lv.v64.e;
+        k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, fbuf);
         AMG_LAUNCH_CHECK();
-        Op op;
-        std::memset(&op, 0, sizeof op);
-        op.level = level;
-        k_coarse<double><<<1, 256, 0, s>>>((const LevelDev<double> *)h->lev_tab64, op);
+        Op op = Builder::mk(OP_COARSE, level);
+        k_op<double><<<1, kRedThreads, 0, s>>>(dtab<double>(h), op, rc);
         AMG_LAUNCH_CHECK();
-        double *e = level == 0 ? h->zo : lv.v64.e;
-        k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, e, z_nat);
+        k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, ebuf, z_nat);
         AMG_LAUNCH_CHECK();
         AMG_CUDA(cudaStreamSynchronize(s));
         return;
     }
-    k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, fbuf);
+    if (level == 0) {
+        k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, h->ro);
+        AMG_LAUNCH_CHECK();
+        launch_cycle<double>(h);
+        k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, h->zo, z_nat);
+        AMG_LAUNCH_CHECK();
+        AMG_CUDA(cudaStreamSynchronize(s));
+        check_device_error(h);
+        return;
+    }
+    k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, lv.v64.rhs);
     AMG_LAUNCH_CHECK();
-    Emitter<double> em = make_emitter<double>(h);
-    if (level == 0) em.bhat(0, V_RHS, V_E);
-    else em.bhat(level, V_RHS, V_P0);
-    k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, zbuf, z_nat);
+    run_standalone<double>(h, level, V_RHS, V_P0);
+    k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, lv.v64.p[0], z_nat);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaStreamSynchronize(s));
 }
@@ -1260,19 +1228,20 @@ void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat
     k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, fbuf);
     k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, u_nat, ubuf);
     AMG_LAUNCH_CHECK();
-    Emitter<double> em = make_emitter<double>(h);
     const std::vector<int> &ranges = (level == 0) ? lv.color_blocks : lv.color_rows;
     const int nc = (int)ranges.size() - 1;
+    RedCtx rc{h->red_partials, h->red_counter};
     for (int k = 0; k < nc; k++) {
         int c = backward ? nc - 1 - k : k;
         if (ranges[c + 1] == ranges[c]) continue;
-        Op g = em.mk(OP_GS, level);
+        Op g = Builder::mk(OP_GS, level);
         g.i0 = ranges[c];
         g.i1 = ranges[c + 1];
         g.backward = backward;
         g.fsel = V_RHS;
         g.usel = V_E;
-        em.launch(g);
+        k_op<double><<<nblocks_for(g.i1 - g.i0, kRedThreads), kRedThreads, 0, s>>>(dtab<double>(h), g, rc);
+        AMG_LAUNCH_CHECK();
     }
     k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, ubuf, u_nat);
     AMG_LAUNCH_CHECK();
