@@ -162,6 +162,8 @@ int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_opti
     if (o.kcycle_n < 1 || o.kcycle_n > amg::kMaxKcycle)
         return fail(AMG_ERR_UNSUPPORTED, "kcycle_n must be 1..4");
     if (o.max_iters < 1 || o.max_iters > 100000) return fail(AMG_ERR_INVALID_ARG, "max_iters");
+    if (o.outer == AMG_OUTER_FGMRES && 2 * o.fgmres_restart + 1 > o.max_iters)
+        return fail(AMG_ERR_INVALID_ARG, "FGMRES needs max_iters >= 2 * fgmres_restart + 1");
     if (o.cycle_prec != AMG_FP64 && o.cycle_prec != AMG_FP32)
         return fail(AMG_ERR_INVALID_ARG, "cycle_prec");
     if (o.outer != AMG_OUTER_FCG && o.outer != AMG_OUTER_FGMRES)
@@ -212,8 +214,6 @@ int amg_solve(amg_hierarchy *h, const double *b, double tol, double *x, int *ite
               double *relres, void *stream) {
     if (!h || !b || !x) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
     if (!(tol >= 0.0)) return fail(AMG_ERR_INVALID_ARG, "tol must be >= 0");
-    if (h->opt.outer == AMG_OUTER_FGMRES)
-        return fail(AMG_ERR_UNSUPPORTED, "FGMRES outer iteration is not available");
     try {
         amg::bind_stream(h, stream);
         const size_t n = (size_t)h->N;

@@ -364,6 +364,82 @@ __global__ void k_bump(int *it_ptr) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *it_ptr += 1;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// FGMRES kernels (FP64, pi order); V and Z are arrays of vector pointers
+// w = A z
+__global__ void k_spmv(GLev<double> L, const double *__restrict__ z, double *__restrict__ w) {
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < L.n; row += gridDim.x * blockDim.x) {
+        const int s = row >> 5;
+        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+        w[row] = row_dot(L, base, 0, width, z);
+    }
+}
+
+// out[i] = (w, V[i]) for i < m: every block loops over i; the last block reduces every i
+__global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__restrict__ w,
+                                                      double *const *__restrict__ V, int m,
+                                                      double *out, RedCtx rc) {
+    __shared__ bool last;
+    for (int i = 0; i < m; i++) {
+        const double *v = V[i];
+        double a[1] = {0.0}, r[1];
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+            a[0] += w[k] * v[k];
+        block_sum<1, double>(a, r);
+        if (threadIdx.x == 0) rc.partials[(size_t)i * gridDim.x + blockIdx.x] = r[0];
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(rc.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        for (int i = 0; i < m; i++) {
+            double y = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+                y += __ldcg(&rc.partials[(size_t)i * gridDim.x + b]);
+            y = warp_sum(y);
+            if (threadIdx.x == 0) out[i] = y;
+        }
+    }
+    if (threadIdx.x == 0) *rc.counter = 0u;
+}
+
+// w -= sum_i c[i] V[i]; (w, w) -> *nrm2
+__global__ void __launch_bounds__(kRedThreads) k_orth_sub(int n, double *__restrict__ w,
+                                                          double *const *__restrict__ V, int m,
+                                                          const double *__restrict__ c,
+                                                          double *nrm2, RedCtx rc) {
+    double a[1] = {0.0};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double x = w[k];
+        for (int i = 0; i < m; i++) x -= c[i] * V[i][k];
+        w[k] = x;
+        a[0] += x * x;
+    }
+    double *o[1] = {nrm2};
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
+}
+
+// v = w * s
+__global__ void k_scale(int n, const double *__restrict__ w, double s, double *__restrict__ v) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) v[k] = w[k] * s;
+}
+
+// x += sum_j y[j] Z[j]
+__global__ void k_lincomb(int n, double *__restrict__ x, double *const *__restrict__ Z, int m,
+                          const double *__restrict__ y) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double acc = x[k];
+        for (int j = 0; j < m; j++) acc += y[j] * Z[j][k];
+        x[k] = acc;
+    }
+}
+
 // =======================================================================================
 // diagnostics: per-kernel timing and algorithmic bytes
 thread_local int64_t g_launches = 0;
@@ -990,7 +1066,7 @@ void allocate_solve_workspace(amg_hierarchy *h) {
     h->oit = halloc<int>(h, 1);
     h->dP = halloc<double *>(h, h->opt.max_iters);
     h->dQ = halloc<double *>(h, h->opt.max_iters);
-    AMG_CUDA(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
+    AMG_CUDA(cudaMallocHost(&h->h_pinned, (64 + 2 * (size_t)h->opt.max_iters) * sizeof(double)));
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
         lv.dinv64 = halloc<double>(h, lv.n);
@@ -1070,8 +1146,12 @@ static void apply_preconditioner(amg_hierarchy *h) {
     }
 }
 
+static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat,
+                        int *iters, double *relres);
+
 int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int *iters,
           double *relres) {
+    if (h->opt.outer == AMG_OUTER_FGMRES) return solve_fgmres(h, b_nat, tol, x_nat, iters, relres);
     cudaStream_t s = h->stream;
     const int n = (int)h->N;
     const int maxit = h->opt.max_iters;
@@ -1171,6 +1251,147 @@ int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int 
             AMG_CUDA(cudaStreamSynchronize(s));
             rel = std::sqrt(h->h_pinned[OS_TT]) / bn;
         }
+    }
+    k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, h->xo, x_nat);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return status;
+}
+
+
+// Restarted flexible GMRES(m) (right preconditioning, FP64 basis and Hessenberg matrix,
+// classical Gram-Schmidt applied twice): the outer iteration for a preconditioner that
+// varies between applications (the nonlinear AMLI-cycle, in FP32 or FP64). The host keeps the
+// (m+1) x m Hessenberg matrix and its Givens rotations; each iteration reads m+2 scalars.
+static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat,
+                        int *iters, double *relres) {
+    cudaStream_t s = h->stream;
+    const int n = (int)h->N;
+    const int maxit = h->opt.max_iters;
+    const int m = std::max(1, std::min(h->opt.fgmres_restart, maxit));
+    Level &F = h->lev[0];
+    RedCtx rc{h->red_partials, h->red_counter};
+    if (h->opt.cycle_prec == AMG_FP32 && h->nlev > 1) ensure_fp32(h);
+    // basis V[0..m], preconditioned directions Z[0..m-1] (the outer direction store)
+    ensure_directions(h, std::min(maxit, std::max(2 * m + 1, 1)));
+    if ((int)h->P.size() < 2 * m + 1) throw Error{AMG_ERR_UNSUPPORTED, "max_iters too small for the restart length"};
+    double **dV = h->dP;          // V[i] = P[i], i <= m
+    double **dZ = h->dP + m + 1;  // Z[j] = P[m + 1 + j]
+    double *w = h->to;
+    double *dh = h->osc + OS_ZQ;  // device scratch for m+2 scalars
+    GLev<double> Lf = fine_view(h);
+    k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, b_nat, h->bo);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaMemsetAsync(h->xo, 0, sizeof(double) * n, s));
+    k_norm2<<<red_grid(n), kRedThreads, 0, s>>>(n, h->bo, h->osc + OS_BB, rc);
+    AMG_LAUNCH_CHECK();
+    AMG_CUDA(cudaMemcpyAsync(h->h_pinned, h->osc, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    const double bn = std::sqrt(h->h_pinned[OS_BB]);
+    if (!std::isfinite(bn)) throw Error{AMG_ERR_INVALID_ARG, "non-finite right-hand side"};
+    int it = 0, status = AMG_ERR_NOT_CONVERGED;
+    double rel = 1.0;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    std::vector<double> hv(std::max(m + 2, 8));
+    double *dy = h->osc + OS_ZQ + maxit;  // coefficients for the update
+    auto read_scalars = [&](const double *d, int count, double *out) {
+        AMG_CUDA(cudaMemcpyAsync(h->h_pinned, d, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < count; k++) out[k] = h->h_pinned[k];
+    };
+    if (bn == 0.0) {
+        status = AMG_OK;
+        rel = 0.0;
+    }
+    // r = b - A x (x = 0 at the start)
+    AMG_CUDA(cudaMemcpyAsync(h->ro, h->bo, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double beta = bn;
+    while (status != AMG_OK && it < maxit) {
+        // V[0] = r / beta
+        k_scale<<<nblocks_for(n, 256), 256, 0, s>>>(n, h->ro, 1.0 / beta, h->P[0]);
+        AMG_LAUNCH_CHECK();
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        bool done = false;
+        for (; j < m && it < maxit; j++) {
+            // Z[j] = B^[V[j]]
+            AMG_CUDA(cudaMemcpyAsync(h->ro, h->P[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            apply_preconditioner(h);
+            AMG_CUDA(cudaMemcpyAsync(h->P[m + 1 + j], h->zo, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            // w = A Z[j], orthogonalised twice against V[0..j]
+            k_spmv<<<nblocks_for(n, 256), 256, 0, s>>>(Lf, h->P[m + 1 + j], w);
+            AMG_LAUNCH_CHECK();
+            for (int pass = 0; pass < 2; pass++) {
+                k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, rc);
+                AMG_LAUNCH_CHECK();
+                k_orth_sub<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, dh + j + 1, rc);
+                AMG_LAUNCH_CHECK();
+                read_scalars(dh, j + 2, hv.data());
+                for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = (pass ? H[(size_t)i * m + j] : 0.0) + hv[i];
+            }
+            if (h->nlev > 1) check_device_error(h);
+            it++;
+            const double hn = std::sqrt(hv[j + 1]);
+            H[(size_t)(j + 1) * m + j] = hn;
+            // apply the previous rotations to column j, then a new one
+            for (int i = 0; i < j; i++) {
+                double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b2;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+            }
+            double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
+            double r = std::hypot(a, b2);
+            if (!(r > 0.0) || !std::isfinite(r)) {
+                status = AMG_ERR_BREAKDOWN;
+                done = true;
+                break;
+            }
+            cs[j] = a / r;
+            sn[j] = b2 / r;
+            H[(size_t)j * m + j] = r;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            rel = std::fabs(g[j + 1]) / bn;
+            if (rel <= tol) {
+                j++;
+                done = true;
+                break;
+            }
+            if (hn > 0.0) {
+                k_scale<<<nblocks_for(n, 256), 256, 0, s>>>(n, w, 1.0 / hn, h->P[j + 1]);
+                AMG_LAUNCH_CHECK();
+            } else {  // exact solution in the Krylov space
+                j++;
+                done = true;
+                break;
+            }
+        }
+        const int k = std::min(j, m);
+        // y = H(0:k,0:k)^{-1} g(0:k); x += Z y
+        for (int i = k - 1; i >= 0; i--) {
+            double acc = g[i];
+            for (int l = i + 1; l < k; l++) acc -= H[(size_t)i * m + l] * y[l];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        if (k > 0) {
+            std::memcpy(h->h_pinned, y.data(), sizeof(double) * k);
+            AMG_CUDA(cudaMemcpyAsync(dy, h->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+            k_lincomb<<<nblocks_for(n, 256), 256, 0, s>>>(n, h->xo, dZ, k, dy);
+            AMG_LAUNCH_CHECK();
+        }
+        // true residual r = b - A x
+        k_true_residual<<<red_grid(n), kRedThreads, 0, s>>>(Lf, h->bo, h->xo, h->ro, h->osc + OS_TT, rc);
+        AMG_LAUNCH_CHECK();
+        read_scalars(h->osc, 8, hv.data());
+        beta = std::sqrt(hv[OS_TT]);
+        rel = beta / bn;
+        if (rel <= tol) status = AMG_OK;
+        else if (status == AMG_ERR_BREAKDOWN) break;
+        (void)done;
     }
     k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, h->xo, x_nat);
     AMG_LAUNCH_CHECK();

@@ -1,0 +1,73 @@
+"""GPU: FP32 AMLI-cycle with FP64 outer iteration (flexible CG or restarted flexible GMRES).
+
+The outer residual, the Krylov inner products, the solution update and the coarsest exact
+solve are FP64; the cycle (smoother, restriction, prolongation, coarse-level Alg. 1) is FP32.
+The result is judged against the FP64 oracle: the true relative residual, recomputed here
+in FP64, must meet the tolerance, and the solution's distance to the oracle's is reported
+and bounded.
+"""
+import numpy as np
+import pytest
+
+from paper_1209_5421_gb300.meshes import p1_poisson, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    from paper_1209_5421_gb300 import amg as A
+    from paper_1209_5421_gb300 import build
+
+    build.build()
+    return A
+
+
+def _check(amg, oracle_mod, prob, opts, outer, prec, tol=1e-8, it_slack=3):
+    G = amg.Hierarchy.from_problem(prob, outer=outer, cycle_prec=prec, **opts)
+    x, it, rr, st = G.solve(prob.b, tol)
+    assert st == amg.OK, st
+    A = prob.to_scipy()
+    true_rel = np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b)
+    assert true_rel <= tol, true_rel
+    O = oracle_mod.Hierarchy.from_problem(prob, **opts)
+    xo, ito, rro, sto = O.solve(prob.b, tol)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    print(f"outer={outer} prec={prec}: iters {it} (oracle FCG/FP64 {ito}), relres {true_rel:.2e}, "
+          f"|x - x_oracle|/|x_oracle| = {err:.2e}")
+    assert err <= 1e-6, err
+    assert it <= ito + it_slack, (it, ito)
+    return it, err
+
+
+CASES = [
+    (dict(n=65, jitter=0.2, seed=0, rhs="normal"), dict(aux_level=6)),
+    (dict(n=97, jitter=0.1, graded=True, kappa_blocks=16, seed=1, rhs="normal"), dict()),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("outer,prec", [(0, 1), (1, 1), (1, 0)])
+def test_fp32_cycle_and_fgmres(amg, oracle_mod, case, outer, prec):
+    spec, opts = CASES[case]
+    prob = p1_poisson(**spec)
+    slack = 3 if spec.get("graded") is None else 10
+    _check(amg, oracle_mod, prob, opts, outer, prec, it_slack=slack)
+
+
+def test_fgmres_short_restart(amg, oracle_mod):
+    prob = p1_poisson(65, jitter=0.2, seed=3, rhs="normal")
+    G = amg.Hierarchy.from_problem(prob, outer=amg.OUTER_FGMRES, fgmres_restart=3, max_iters=60)
+    x, it, rr, st = G.solve(prob.b, 1e-10)
+    assert st == amg.OK
+    A = prob.to_scipy()
+    assert np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b) <= 1e-10
+
+
+def test_full_size_quasi_uniform_fp32(amg, oracle_mod):
+    prob, aux = workload("quasi_uniform_1025")
+    _check(amg, oracle_mod, prob, dict(aux_level=aux), amg.OUTER_FGMRES, amg.FP32)

@@ -254,3 +254,18 @@ def test_ell_worked_example(amg):
     with pytest.raises(amg.AmgError):
         amg.csr_to_ell(np.array(g["rowptr"], np.int32), np.array(g["col"], np.int32),
                        np.array(g["val"]), 2)
+
+
+def test_full_size_quasi_uniform_parity(amg, oracle_mod):
+    """The 1025 x 1025 quasi-uniform workload at full size, in the launch configuration the
+    benchmark times (FP64 cycle, flexible CG outer): bit-exact aggregates, colours and spans on
+    every level, coarse operators within 1e-12 (row-scaled), iteration count within +-1."""
+    prob, aux = workload("quasi_uniform_1025")
+    G = amg.Hierarchy.from_problem(prob, aux_level=aux)
+    O = oracle_mod.Hierarchy.from_problem(prob, aux_level=aux)
+    compare_hierarchies(G, O)
+    x, it, rr, st = G.solve(prob.b, 1e-8)
+    xo, ito, rro, sto = O.solve(prob.b, 1e-8)
+    assert st == amg.OK and abs(it - ito) <= 1, (it, ito)
+    A = prob.to_scipy()
+    assert np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b) <= 1e-8
