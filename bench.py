@@ -6,6 +6,10 @@ relative residual + amg_free. Inputs (CSR, coordinates, rhs) are resident in HBM
 timed region starts; L2 is flushed (a 256 MiB write) before every timed step, outside the
 step's CUDA events.
 
+Default workload: 1025 x 1025 jittered P1 Poisson (1,046,529 unknowns), auxiliary grid
+1024 x 1024, FP32 AMLI-cycle inside FP64 restarted flexible GMRES, tol 1e-8. The plain FP64
+method (FP64 cycle, flexible-CG outer) is timed on the same workload and reported beside it.
+
   value : solves/s of the whole job (N ranks x steps / max-over-ranks time)
   e2e   : the same, through the C ABI with pinned HOST buffers (copies inside the step)
   roofline : the dominant kernel's algorithmic bytes / its CUDA-event duration, from a
@@ -44,7 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="quasi_uniform_1025")
     ap.add_argument("--tol", type=float, default=1e-8)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--outer", default="fgmres", choices=["fcg", "fgmres"])
+    ap.add_argument("--no-fp64-line", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -107,6 +113,33 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_source_hash():
+    import hashlib
+
+    hsh = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1209_5421_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def recorded_traffic(workload, prec):
+    """DRAM bytes per launch of the cycle kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "cycle_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    key = f"{workload}:{prec}"
+    ent = rec.get(key)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
 
 
 def measured_peak_hbm():
@@ -220,7 +253,8 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     prob, aux = workload(args.workload)
     prec = amg.FP32 if args.prec == "fp32" else amg.FP64
-    opts = dict(aux_level=aux, cycle_prec=prec)
+    outer = amg.OUTER_FGMRES if args.outer == "fgmres" else amg.OUTER_FCG
+    opts = dict(aux_level=aux, cycle_prec=prec, outer=outer)
     td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
     A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
     b = td(prob.b)
@@ -228,9 +262,13 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        h = amg.Hierarchy(*A, **opts)
+    launch_total = [0]
+
+    def step(o=opts):
+        h = amg.Hierarchy(*A, **o)
         _, it, rr, st = h.solve(b, args.tol, x=x)
+        su, so = h.launch_counts()
+        launch_total[0] += su + so
         h.close()
         if st != amg.OK:
             raise RuntimeError(f"solve failed: status {st}, relres {rr}")
@@ -240,6 +278,7 @@ def run_ours(args, world, rank, local):
         flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
+    launch_total[0] = 0
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     iters = []
@@ -257,6 +296,31 @@ def run_ours(args, world, rank, local):
     lat = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
     total_ms = max_over_ranks(world, sum(lat))
     value = world * args.steps / (total_ms / 1e3)
+    launches_timed = launch_total[0]
+
+    # ---- the plain FP64 method (FP64 cycle, flexible-CG outer) on the same workload
+    fp64_line = None
+    if not args.no_fp64_line and not (prec == amg.FP64 and outer == amg.OUTER_FCG):
+        o64 = dict(aux_level=aux, cycle_prec=amg.FP64, outer=amg.OUTER_FCG)
+        for _ in range(max(1, args.warmup)):
+            flush.fill_(1.0)
+            step(o64)
+        torch.cuda.synchronize()
+        lat64, its64 = [], []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            it64, _ = step(o64)
+            ev1.record(stream)
+            its64.append(it64)
+            torch.cuda.synchronize()
+            lat64.append(ev0.elapsed_time(ev1))
+        t64 = max_over_ranks(world, sum(lat64))
+        fp64_line = {"value": round(world * args.steps / (t64 / 1e3), 3), "unit": "solves/s",
+                     "ms_per_step": round(t64 / args.steps, 3), "iters": its64[-1],
+                     "method": "FP64 AMLI-cycle, flexible-CG outer"}
 
     # ---- e2e: the C ABI with pinned host buffers (H2D of inputs, D2H of x inside the step)
     e2e = None
@@ -294,7 +358,6 @@ def run_ours(args, world, rank, local):
     # ---- profiling pass: per-kernel CUDA-event durations and algorithmic bytes
     roofline = None
     kernels = None
-    launches = None
     if not args.no_profile:
         h = amg.Hierarchy(*A, **opts)
         h.profile(True)
@@ -303,15 +366,17 @@ def run_ours(args, world, rank, local):
         h.solve(b, args.tol, x=x)
         kernels = h.profile_read()
         h.close()
-        launches = sum(k["launches"] for k in kernels)
         peak, peak_kind = measured_peak_hbm()
-        dom = max(kernels, key=lambda k: k["ms"])
+        whole = [k for k in kernels if not k["name"].startswith(("in_cycle:", "in_tail:"))]
+        dom = max(whole, key=lambda k: k["ms"])
         ach = dom["bytes"] / dom["launches"] / (dom["ms"] / dom["launches"] / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(ach / peak, 4), "traffic": None,
-                    "kernel": dom["name"], "peak_source": peak_kind,
+                    "frac": round(ach / peak, 4),
+                    "traffic": recorded_traffic(args.workload, args.prec),
+                    "kernel": dom["name"], "peak_source": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                     "bytes_per_launch": dom["bytes"] / dom["launches"],
-                    "ms_per_launch": dom["ms"] / dom["launches"]}
+                    "ms_per_launch": dom["ms"] / dom["launches"],
+                    "launches_in_solve": dom["launches"]}
 
     out = None
     if rank == 0:
@@ -329,6 +394,9 @@ def run_ours(args, world, rank, local):
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == amg.FP64 else "f32-cycle/f64-outer",
+            "method": ("FP32" if prec == amg.FP32 else "FP64") + " AMLI-cycle, "
+                      + ("restarted flexible GMRES(30)" if outer == amg.OUTER_FGMRES else "flexible CG")
+                      + " outer in FP64",
             "data": "synthetic",
             "config": {"workload": args.workload, "unknowns": prob.n, "nnz": prob.nnz,
                        "aux_level": aux, "tol": args.tol, "iters": iters[-1],
@@ -338,7 +406,8 @@ def run_ours(args, world, rank, local):
                            "p99": round(float(np.percentile(lat_sorted, 99)), 3)},
             "clocks": clk.summary(),
             "e2e": e2e,
-            "gpu_launches": launches,
+            "gpu_launches": launches_timed,
+            "fp64_plain": fp64_line,
             "roofline": roofline,
             "cpu_baseline": cpu,
         }
@@ -346,7 +415,7 @@ def run_ours(args, world, rank, local):
             out["kernels"] = sorted(
                 [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 4),
                   "GBps": round(k["bytes"] / (k["ms"] / 1e3) / 1e9, 1) if k["ms"] > 0 else None}
-                 for k in kernels], key=lambda d: -d["ms"])[:12]
+                 for k in kernels], key=lambda d: -d["ms"])[:16]
         print(json.dumps(out), flush=True)
     return 0
 

@@ -445,7 +445,7 @@ __global__ void k_lincomb(int n, double *__restrict__ x, double *const *__restri
 thread_local int64_t g_launches = 0;
 
 enum : int { K_CYCLE = 11, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
-             K_TRUE_RESIDUAL, K_NUM };
+             K_TRUE_RESIDUAL, K_FGMRES_SPMV, K_FGMRES_MDOT, K_FGMRES_ORTH, K_NUM };
 constexpr int K_IN_CYCLE = 100;  // + op kind: an op timed inside the persistent kernel
 constexpr int K_IN_TAIL = 200;   // + op kind: an op timed inside the shared-memory tail
 
@@ -454,7 +454,8 @@ const char *kernel_name(int kind) {
                                        "coarse_solve", "alg1_multidot", "alg1_orth",
                                        "alg1_spmv_dot", "alg1_update", "tail_cta", "barrier_only",
                                        "cycle_persistent", "outer_multidot", "outer_orth",
-                                       "outer_spmv_dot", "outer_update", "true_residual"};
+                                       "outer_spmv_dot", "outer_update", "true_residual",
+                                       "fgmres_spmv", "fgmres_mdot", "fgmres_orth_sub"};
     static const char *incycle[K_NUM] = {"in_cycle:zero", "in_cycle:gs_colour",
                                          "in_cycle:resid_restrict", "in_cycle:prolong_correct",
                                          "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
@@ -1293,6 +1294,8 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
     if (!std::isfinite(bn)) throw Error{AMG_ERR_INVALID_ARG, "non-finite right-hand side"};
     int it = 0, status = AMG_ERR_NOT_CONVERGED;
     double rel = 1.0;
+    const bool prof = profiling(h);
+    const double nd = n, nnzf = (double)F.A.stored;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     std::vector<double> hv(std::max(m + 2, 8));
     double *dy = h->osc + OS_ZQ + maxit;  // coefficients for the update
@@ -1322,17 +1325,31 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
             apply_preconditioner(h);
             AMG_CUDA(cudaMemcpyAsync(h->P[m + 1 + j], h->zo, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             // w = A Z[j], orthogonalised twice against V[0..j]
+            Profiler::Rec rec{};
+            if (prof) rec = h->prof->begin(K_FGMRES_SPMV, 0, 12.0 * nnzf + 16.0 * nd, s);
             k_spmv<<<nblocks_for(n, 256), 256, 0, s>>>(Lf, h->P[m + 1 + j], w);
             AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s);
             for (int pass = 0; pass < 2; pass++) {
+                if (prof) rec = h->prof->begin(K_FGMRES_MDOT, 0, 8.0 * nd * (j + 2), s);
                 k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, rc);
                 AMG_LAUNCH_CHECK();
+                if (prof) h->prof->end(rec, s);
+                if (prof) rec = h->prof->begin(K_FGMRES_ORTH, 0, 8.0 * nd * (j + 3), s);
                 k_orth_sub<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, dh + j + 1, rc);
                 AMG_LAUNCH_CHECK();
+                if (prof) h->prof->end(rec, s);
                 read_scalars(dh, j + 2, hv.data());
                 for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = (pass ? H[(size_t)i * m + j] : 0.0) + hv[i];
             }
             if (h->nlev > 1) check_device_error(h);
+            if (prof) {
+                h->prof->harvest();
+                if (h->nlev > 1) {
+                    if (h->opt.cycle_prec == AMG_FP32) harvest_cycle_timestamps<float>(h);
+                    else harvest_cycle_timestamps<double>(h);
+                }
+            }
             it++;
             const double hn = std::sqrt(hv[j + 1]);
             H[(size_t)(j + 1) * m + j] = hn;
