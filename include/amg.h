@@ -196,6 +196,26 @@ int amg_smooth(amg_hierarchy *h, int level, int backward, const double *f, doubl
 int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, const double *val,
                    int32_t width, int diag_first, int32_t *Aj, double *Ax, void *stream);
 
+/*
+ * amg_csr_to_ell without any allocation, for callers that cannot allocate device memory
+ * when they call in -- for example because another allocator already owns all of the GPU's
+ * memory, or because a latency-critical loop forbids allocation calls. No counterpart in the
+ * paper: it is the ELL packing of Sec. 4.1 (same arguments and results as amg_csr_to_ell).
+ *   - All arrays must be device memory (host arrays would need staging buffers):
+ *     otherwise AMG_ERR_INVALID_ARG.
+ *   - Its scratch is a fixed array inside the library (about 64 KiB per GPU, held until the
+ *     process exits); rows is limited to 4,194,304: larger inputs return AMG_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up that array's device address (once per device);
+ *     make that first call before any stream capture.
+ *   - Every call on a device shares the array: calls that overlap on the GPU (other streams
+ *     or host threads) race and must be ordered by the caller.
+ *   - Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries; the call waits for
+ *     its kernels to finish.
+ */
+int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const int32_t *col,
+                           const double *val, int32_t width, int diag_first, int32_t *Aj,
+                           double *Ax, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * Diagnostics.
  * ------------------------------------------------------------------------------------- */

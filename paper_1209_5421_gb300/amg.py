@@ -77,6 +77,7 @@ def lib():
         L.amg_apply_cycle.argtypes = [P, C.c_int, P, P, P]
         L.amg_smooth.argtypes = [P, C.c_int, C.c_int, P, P, P]
         L.amg_csr_to_ell.argtypes = [C.c_int32, P, P, P, C.c_int32, C.c_int, P, P, P]
+        L.amg_csr_to_ell_noalloc.argtypes = [C.c_int32, P, P, P, C.c_int32, C.c_int, P, P, P]
         L.amg_launch_counts.argtypes = [P, P, P]
         L.amg_profile_enable.argtypes = [P, C.c_int]
         L.amg_profile_read.argtypes = [P, C.c_int, P, P, P, P, P, C.POINTER(C.c_int)]
@@ -84,7 +85,8 @@ def lib():
         L.amg_kernel_name.restype = C.c_char_p
         for f in ("amg_setup", "amg_solve", "amg_hierarchy_bytes", "amg_num_levels",
                   "amg_get_bbox", "amg_level_info", "amg_level_export", "amg_apply_cycle",
-                  "amg_smooth", "amg_csr_to_ell", "amg_launch_counts", "amg_profile_enable",
+                  "amg_smooth", "amg_csr_to_ell", "amg_csr_to_ell_noalloc", "amg_launch_counts",
+                  "amg_profile_enable",
                   "amg_profile_read"):
             getattr(L, f).restype = C.c_int
         _lib = L
