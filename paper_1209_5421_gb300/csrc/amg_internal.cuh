@@ -75,6 +75,7 @@ struct Level {
     int *inv = nullptr;     // [n] pi-row of natural index
     int *cell = nullptr;    // [n] cell index t1 + cellw * t2 of pi-row p
     int *agg_nat = nullptr; // [n] natural aggregate (next level) of natural row
+    unsigned short *col16 = nullptr;  // 16-bit columns (a tail level read in place)
     double *dinv64 = nullptr;  // 1 / a_ii (smoother), FP64 and FP32
     float *dinv32 = nullptr;
     double *Ainv = nullptr; // coarsest: dense inverse, pi order, row-major

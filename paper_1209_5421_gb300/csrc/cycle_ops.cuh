@@ -24,6 +24,7 @@ enum OpKind : int {
     OP_UPDATE,        // alpha_i; e (+)= alpha_i p_i; r = r_i - alpha_i q_i; sc[RR_i] = (r, r)
     OP_TAIL,          // persistent program: CTA 0 runs the tail program in shared memory
     OP_NOP,           // persistent program: only the prologue (finalise a reduction)
+    OP_GS_FIRST,      // point GS from zero, first colour: u_i = f_i / a_ii on [i0, i1), 0 elsewhere
 };
 
 struct Op {
@@ -54,6 +55,7 @@ struct LevelDev {
     const I *col;
     const T *val;
     const T *dinv;                  // 1 / a_ii (smoother)
+    const unsigned short *col16;    // 16-bit copy of col (levels read by the tail from HBM)
     const int *bptr;
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
@@ -234,7 +236,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err
 // The small levels are pure latency, so a row's slots are read in batches of 8: all column
 // indices and values of a batch are loaded before any gathered x[c], which turns a chain of
 // two dependent loads per slot into about three round trips per row.
-constexpr int kRowBatch = 8;
+constexpr int kRowBatch = 9;  // one batch for a 9-point row
 
 // sum over slots k0 <= k < width of a_ik x[c_ik] (padding contributes nothing)
 template <class LV>
@@ -305,25 +307,42 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
 }
 
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
-// coarser levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form)
+// coarser levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form),
+// one lane per child and a two-step shuffle (nth must be a multiple of 32)
 template <class LV>
 __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             const typename LV::val_t *u, typename LV::val_t *fc, int tid,
                             int nth) {
     using T = typename LV::val_t;
-    for (int R = tid; R < L.nnext; R += nth) {
-        T acc = 0;
-        if (L.fine) {
+    if (L.fine) {
+        for (int R = tid; R < L.nnext; R += nth) {
+            T acc = 0;
             for (int i = L.bptr[R]; i < L.bptr[R + 1]; i++) acc += row_residual(L, i, f, u);
-        } else {
-            const int4 ch = L.children[R];
-            if (ch.x >= 0) acc += row_residual(L, ch.x, f, u);
-            if (ch.y >= 0) acc += row_residual(L, ch.y, f, u);
-            if (ch.z >= 0) acc += row_residual(L, ch.z, f, u);
-            if (ch.w >= 0) acc += row_residual(L, ch.w, f, u);
+            fc[R] = acc;
         }
-        fc[R] = acc;
+        return;
     }
+    const int q = tid & 3, per_pass = nth >> 2;
+    for (int base = 0; base < L.nnext; base += per_pass) {
+        const int R = base + (tid >> 2);
+        T v = 0;
+        if (R < L.nnext) {
+            const int4 ch = L.children[R];
+            const int c = q == 0 ? ch.x : q == 1 ? ch.y : q == 2 ? ch.z : ch.w;
+            if (c >= 0) v = row_residual(L, c, f, u);
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (R < L.nnext && q == 0) fc[R] = v;
+    }
+}
+
+// first colour of a forward sweep from u = 0 on a point-smoothed level: rows of one colour
+// are never coupled, so u_i = f_i / a_ii there, and every other row is still 0
+template <class LV>
+__device__ void op_gs_first(const LV &L, const Op &op, const typename LV::val_t *f,
+                            typename LV::val_t *u, int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) u[i] = (i >= op.i0 && i < op.i1) ? f[i] * L.dinv[i] : 0;
 }
 
 // u_i += e_{agg(i)} (Sec. 4.3 prolongation)
@@ -468,6 +487,7 @@ __device__ __forceinline__ void run_op(const LV *tab, const Op &op, const RedCtx
     switch (op.kind) {
         case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
         case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
+        case OP_GS_FIRST: op_gs_first(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_RESTRICT:
             op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), tab[op.level + 1].rhs, tid, nth);
             break;

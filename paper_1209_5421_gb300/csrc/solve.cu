@@ -31,6 +31,7 @@ constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
 // shared-memory image of the tail levels (byte offsets into the dynamic shared memory)
 struct TailLevelLayout {
     int n, nslices, padded;
+    int gmem;    // 1: the level stays in HBM/L2 (top tail level only); its scalars are staged
     int sl, col, val, dinv, parent, children, Ainv, rhs, e, r;
     int p[kMaxKcycle], q[kMaxKcycle];
 };
@@ -76,6 +77,33 @@ __device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *st
     for (int l = Y.tl; l < Y.nlev; l++) {
         const TailLevelLayout &y = Y.lv[l];
         const GLev<T> &G = a.tab[l];
+        if (y.gmem) {  // read in place from HBM / L2
+            if (tid == 0) {
+                SLev<T> &S = stab[l];
+                S.n = G.n;
+                S.fine = 0;
+                S.sl = G.sl;
+                S.col = G.col16;
+                S.val = G.val;
+                S.dinv = G.dinv;
+                S.col16 = nullptr;
+                S.bptr = nullptr;
+                S.parent = G.parent;
+                S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
+                                 ? (const int4 *)(sm + Y.lv[l + 1].children) : nullptr;
+                S.Ainv = G.Ainv;
+                S.rhs = G.rhs;
+                S.e = G.e;
+                S.r = G.r;
+                for (int k = 0; k < kMaxKcycle; k++) {
+                    S.p[k] = G.p[k];
+                    S.q[k] = G.q[k];
+                }
+                S.sc = (double *)(sm + Y.sc) + (size_t)(l - Y.tl) * SC_N;
+                S.nnext = G.nnext;
+            }
+            continue;
+        }
         int *sl = (int *)(sm + y.sl);
         unsigned short *col = (unsigned short *)(sm + y.col);
         T *val = (T *)(sm + y.val);
@@ -102,6 +130,7 @@ __device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *st
             S.col = col;
             S.val = val;
             S.dinv = y.dinv >= 0 ? (const T *)(sm + y.dinv) : nullptr;
+            S.col16 = nullptr;
             S.bptr = nullptr;
             S.parent = y.parent >= 0 ? (const int *)(sm + y.parent) : nullptr;
             S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
@@ -127,9 +156,11 @@ template <class T>
 __device__ void run_tail(const CycleArgs<T> &a, const SLev<T> *stab, unsigned char *sm) {
     const int tl = a.lay.tl, n = a.lay.lv[tl].n;
     const int tid = threadIdx.x, nth = blockDim.x;
+    const bool inplace = a.lay.lv[tl].gmem != 0;
     const T *grhs = a.tab[tl].rhs;
     T *srhs = stab[tl].rhs;
-    for (int i = tid; i < n; i += nth) srhs[i] = grhs[i];
+    if (!inplace)
+        for (int i = tid; i < n; i += nth) srhs[i] = grhs[i];
     __syncthreads();
     RedCtx rc{nullptr, nullptr};
     const Op *prog = (const Op *)(sm + a.lay.prog);
@@ -145,6 +176,7 @@ __device__ void run_tail(const CycleArgs<T> &a, const SLev<T> *stab, unsigned ch
             t0 = t1;
         }
     }
+    if (inplace) return;
     T *ge = a.tab[tl].e;
     const T *se = stab[tl].e;
     for (int i = tid; i < n; i += nth) ge[i] = se[i];
@@ -217,6 +249,12 @@ __global__ void k_scatter(int n, const int *__restrict__ idx, const double *__re
                           double *__restrict__ dst) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) dst[idx[p]] = src[p];
+}
+
+// 16-bit copy of column indices (padding -1 -> 0xFFFF)
+__global__ void k_col16(int n, const int *__restrict__ col, unsigned short *__restrict__ c16) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c16[i] = col[i] >= 0 ? (unsigned short)col[i] : (unsigned short)0xFFFF;
 }
 
 // 1 / a_ii of every row (slot 0 of the sliced ELL holds the diagonal)
@@ -444,7 +482,7 @@ __global__ void k_lincomb(int n, double *__restrict__ x, double *const *__restri
 // diagnostics: per-kernel timing and algorithmic bytes
 thread_local int64_t g_launches = 0;
 
-enum : int { K_CYCLE = 11, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
+enum : int { K_CYCLE = 12, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
              K_TRUE_RESIDUAL, K_FGMRES_SPMV, K_FGMRES_MDOT, K_FGMRES_ORTH, K_NUM };
 constexpr int K_IN_CYCLE = 100;  // + op kind: an op timed inside the persistent kernel
 constexpr int K_IN_TAIL = 200;   // + op kind: an op timed inside the shared-memory tail
@@ -453,22 +491,23 @@ const char *kernel_name(int kind) {
     static const char *names[K_NUM] = {"zero", "gs_colour", "resid_restrict", "prolong_correct",
                                        "coarse_solve", "alg1_multidot", "alg1_orth",
                                        "alg1_spmv_dot", "alg1_update", "tail_cta", "barrier_only",
+                                       "gs_first_colour",
                                        "cycle_persistent", "outer_multidot", "outer_orth",
                                        "outer_spmv_dot", "outer_update", "true_residual",
                                        "fgmres_spmv", "fgmres_mdot", "fgmres_orth_sub"};
-    static const char *incycle[K_NUM] = {"in_cycle:zero", "in_cycle:gs_colour",
-                                         "in_cycle:resid_restrict", "in_cycle:prolong_correct",
-                                         "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
-                                         "in_cycle:alg1_orth", "in_cycle:alg1_spmv_dot",
-                                         "in_cycle:alg1_update", "in_cycle:tail_cta",
-                                         "in_cycle:barrier_only"};
-    static const char *intail[11] = {"in_tail:zero", "in_tail:gs_colour", "in_tail:resid_restrict",
+    static const char *incycle[12] = {"in_cycle:zero", "in_cycle:gs_colour",
+                                      "in_cycle:resid_restrict", "in_cycle:prolong_correct",
+                                      "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
+                                      "in_cycle:alg1_orth", "in_cycle:alg1_spmv_dot",
+                                      "in_cycle:alg1_update", "in_cycle:tail_cta",
+                                      "in_cycle:barrier_only", "in_cycle:gs_first_colour"};
+    static const char *intail[12] = {"in_tail:zero", "in_tail:gs_colour", "in_tail:resid_restrict",
                                      "in_tail:prolong_correct", "in_tail:coarse_solve",
                                      "in_tail:alg1_multidot", "in_tail:alg1_orth",
                                      "in_tail:alg1_spmv_dot", "in_tail:alg1_update", "in_tail:?",
-                                     "in_tail:?"};
-    if (kind >= K_IN_CYCLE && kind < K_IN_CYCLE + 11) return incycle[kind - K_IN_CYCLE];
-    if (kind >= K_IN_TAIL && kind < K_IN_TAIL + 11) return intail[kind - K_IN_TAIL];
+                                     "in_tail:?", "in_tail:gs_first_colour"};
+    if (kind >= K_IN_CYCLE && kind < K_IN_CYCLE + 12) return incycle[kind - K_IN_CYCLE];
+    if (kind >= K_IN_TAIL && kind < K_IN_TAIL + 12) return intail[kind - K_IN_TAIL];
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "unknown";
 }
 
@@ -564,6 +603,7 @@ static double op_bytes(const amg_hierarchy *h, const Op &op, int w) {
     const double nn = op.level + 1 < h->nlev ? h->lev[op.level + 1].n : 0;
     switch (op.kind) {
         case OP_ZERO: return w * n;
+        case OP_GS_FIRST: return w * n + 2.0 * w * (op.i1 - op.i0);
         case OP_GS: {
             const std::vector<int> &ranges = op.level == 0 ? lv.color_blocks : lv.color_rows;
             int c = 0;
@@ -643,12 +683,24 @@ struct Builder {
     // z = B^_l [f] (Alg. 2)
     void bhat(int l, int fsel, int zsel) {
         Level &lv = h->lev[l];
-        Op z = mk(OP_ZERO, l);
-        z.usel = zsel;
-        emit(z);
         const std::vector<int> &ranges = (l == 0) ? lv.color_blocks : lv.color_rows;
         const int nc = (int)ranges.size() - 1;
-        for (int c = 0; c < nc; c++) {  // pre-smoothing u1 = R_k f, colours ascending
+        int c0 = 0;  // pre-smoothing u1 = R_k f from zero, colours ascending
+        if (l == 0) {
+            Op z = mk(OP_ZERO, l);
+            z.usel = zsel;
+            emit(z);
+        } else {  // first non-empty colour fused with the zero fill (point smoother)
+            while (c0 < nc && ranges[c0 + 1] == ranges[c0]) c0++;
+            Op g = mk(OP_GS_FIRST, l);
+            g.i0 = c0 < nc ? ranges[c0] : 0;
+            g.i1 = c0 < nc ? ranges[c0 + 1] : 0;
+            g.fsel = fsel;
+            g.usel = zsel;
+            emit(g);
+            c0++;
+        }
+        for (int c = c0; c < nc; c++) {
             if (ranges[c + 1] == ranges[c]) continue;
             Op g = mk(OP_GS, l);
             g.i0 = ranges[c];
@@ -768,6 +820,7 @@ void fill_tables(amg_hierarchy *h) {
         else d.val = (const T *)lv.A.val32;
         if constexpr (sizeof(T) == 8) d.dinv = (const T *)lv.dinv64;
         else d.dinv = (const T *)lv.dinv32;
+        d.col16 = lv.col16;
         d.bptr = lv.bptr;
         d.parent = lv.parent;
         d.children = (l + 1 < h->nlev) ? h->lev[l + 1].children : nullptr;
@@ -795,7 +848,7 @@ const GLev<T> *dtab(amg_hierarchy *h) {
 }
 
 // shared-memory image of levels l0..nlev-1; returns false if a level is too large
-bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, TailLayout &Y) {
+bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, bool top_in_gmem, TailLayout &Y) {
     std::memset(&Y, 0, sizeof Y);
     Y.tl = l0;
     Y.nlev = h->nlev;
@@ -808,11 +861,19 @@ bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, TailLayout &Y) {
     const int kc = h->opt.kcycle_n;
     for (int l = l0; l < h->nlev; l++) {
         const Level &lv = h->lev[l];
-        if (lv.n > kTailRowsMax) return false;
         TailLevelLayout &y = Y.lv[l];
         y.n = lv.n;
         y.nslices = lv.A.nslices;
         y.padded = (int)lv.A.padded;
+        if (l == l0 && top_in_gmem) {
+            if (lv.n > 65535 || lv.coarsest) return false;
+            y.gmem = 1;
+            y.sl = y.col = y.val = y.dinv = y.parent = y.children = y.Ainv = -1;
+            y.rhs = y.e = y.r = -1;
+            for (int k = 0; k < kMaxKcycle; k++) y.p[k] = y.q[k] = -1;
+            continue;
+        }
+        if (lv.n > kTailRowsMax) return false;
         y.sl = take(sizeof(int) * (size_t)(lv.A.nslices + 1));
         y.col = take(2 * (size_t)lv.A.padded);
         y.val = take((size_t)w * lv.A.padded);
@@ -861,17 +922,28 @@ void build_engine(amg_hierarchy *h) {
     const long budget = std::min<long>((long)optin - (long)fa.sharedSizeBytes - 1024,
                                        (long)max_tail_bytes());
     // the tail: the finest coarse level from which every level fits in shared memory
+    // the tail: the finest coarse level from which everything fits in shared memory, or
+    // fits once that top level is left in HBM/L2 (read in place by CTA 0)
     int tl = h->nlev;
-    for (int l = 1; l < h->nlev; l++) {
-        TailLayout Y;
+    for (int l = 1; l < h->nlev && tl == h->nlev; l++) {
         std::vector<Op> tp;
         Builder bt{h, &tp, h->nlev + 1};
         bt.btilde(l);
-        if (tail_layout(h, l, sizeof(T), (int)tp.size(), Y) && Y.bytes <= budget) {
-            tl = l;
-            E->lay = Y;
-            break;
+        for (int top_gmem = 0; top_gmem <= 1; top_gmem++) {
+            TailLayout Y;
+            if (tail_layout(h, l, sizeof(T), (int)tp.size(), top_gmem != 0, Y) && Y.bytes <= budget) {
+                tl = l;
+                E->lay = Y;
+                break;
+            }
         }
+    }
+    if (tl < h->nlev && E->lay.lv[tl].gmem && !h->lev[tl].col16) {
+        Level &lv = h->lev[tl];
+        lv.col16 = halloc<unsigned short>(h, lv.A.padded);
+        k_col16<<<nblocks_for(lv.A.padded, 256), 256, 0, h->stream>>>((int)lv.A.padded, lv.A.col, lv.col16);
+        AMG_LAUNCH_CHECK();
+        fill_tables<T>(h);
     }
     if (tl == h->nlev) {
         std::memset(&E->lay, 0, sizeof E->lay);
