@@ -172,7 +172,9 @@ int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *c
 
 /*
  * One application of the AMLI-cycle preconditioner z = B^_level[f] (Alg. 2) on level
- * `level` (0 = finest), in FP64, vectors in that level's natural row order.
+ * `level` (0 = finest), vectors in that level's natural row order. Level 0 runs the solve's
+ * preconditioner in the hierarchy's cycle precision (options.cycle_prec; with AMG_FP32 the
+ * cycle computes in FP32 between FP64 f and z); coarser levels run in FP64.
  * f, z: device or host arrays of n doubles (z caller-allocated).
  */
 int amg_apply_cycle(amg_hierarchy *h, int level, const double *f, double *z, void *stream);

@@ -79,7 +79,7 @@ struct Level {
     double *dinv64 = nullptr;  // 1 / a_ii (smoother), FP64 and FP32
     float *dinv32 = nullptr;
     double *Ainv = nullptr; // coarsest: dense inverse, pi order, row-major
-    float *Ainv32 = nullptr;
+    float *Ainv32 = nullptr; // the same inverse as float high parts then low parts (2 n^2)
     Vecs<double> v64;
     Vecs<float> v32;
     double *sc = nullptr;   // [SC_N] device scalars of Alg. 1 on this level

@@ -59,30 +59,95 @@ struct LevelDev {
     const int *bptr;
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
-    const double *Ainv;             // coarsest: dense inverse (FP64 in both cycles)
+    const double *Ainv;             // coarsest: dense inverse, FP64 (FP64 cycle)
+    const float *Ainv2;             // coarsest, FP32 cycle: the same inverse as n*n high parts
+                                    // followed by n*n low parts (Ainv ~ high + low)
     T *rhs, *e, *r;
     T *p[kMaxKcycle], *q[kMaxKcycle];
     double *sc;
     int nnext;
 };
 
+// view of a level staged in shared memory with one slice width for the whole level: entry k
+// of row i at (i / 32) 32 w + 32 k + i % 32, w = W (compile-time) or the member w (W = 0).
+// No slice pointers to load, and with W fixed every row loop is unrolled without bounds.
+template <class T, int W>
+struct StagedLevel {
+    using val_t = T;
+    using idx_t = unsigned short;
+    static constexpr int fine = 0;  // point smoother (staged levels are coarse)
+    int n, w;
+    const unsigned short *col;
+    const T *val;
+    const T *dinv;
+    const int *bptr;                // unused (fine = 0)
+    const int *parent;
+    const int4 *children;           // children of the NEXT coarser level's rows
+    const double *Ainv;
+    const float *Ainv2;
+    T *rhs, *e, *r;
+    T *p[kMaxKcycle], *q[kMaxKcycle];
+    double *sc;
+    int nnext;
+};
+
+// first slot and slot count of row i
+template <class T, class I>
+__device__ __forceinline__ void row_span(const LevelDev<T, I> &L, int i, int &base, int &width) {
+    const int s = i >> 5;
+    const int a = L.sl[s];
+    base = a + (i & 31);
+    width = (L.sl[s + 1] - a) >> 5;
+}
+template <class T, int W>
+__device__ __forceinline__ void row_span(const StagedLevel<T, W> &L, int i, int &base,
+                                         int &width) {
+    width = W > 0 ? W : L.w;
+    base = (i >> 5) * 32 * width + (i & 31);
+}
+
 __device__ __forceinline__ bool col_ok(int c) { return c >= 0; }
 __device__ __forceinline__ bool col_ok(unsigned short c) { return c != (unsigned short)0xFFFF; }
 
+// a[i] for a run-time i, as a chain of selects: a view built in registers keeps its pointer
+// arrays in registers (an indexed access would move them to the stack)
+template <class P>
+__device__ __forceinline__ P pick(const P (&a)[kMaxKcycle], int i) {
+    P r = a[0];
+#pragma unroll
+    for (int k = 1; k < kMaxKcycle; k++)
+        if (i == k) r = a[k];
+    return r;
+}
+
 template <class LV>
 __device__ __forceinline__ typename LV::val_t *vec_of(const LV &L, int sel) {
-    return sel == V_RHS ? L.rhs : sel == V_E ? L.e : sel == V_R ? L.r : L.p[sel - V_P0];
+    return sel == V_RHS ? L.rhs : sel == V_E ? L.e : sel == V_R ? L.r : pick(L.p, sel - V_P0);
 }
+
+// ---------------------------------------------------------------------------------------
+// the threads of one CTA that run an op together, and the barrier they meet at
+struct BlockGroup {  // every thread of the CTA; barrier 0
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int nwarps() const { return (blockDim.x + 31) >> 5; }
+};
+struct WarpGroup {  // warps [0, nthreads / 32) of the CTA; hardware barrier 1
+    int nthreads;   // multiple of 32
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+    }
+    __device__ __forceinline__ int nwarps() const { return nthreads >> 5; }
+};
 
 // ---------------------------------------------------------------------------------------
 // reductions: fixed-order trees, no floating-point atomics (bitwise reproducible)
 enum : int { RM_LASTBLOCK = 0, RM_BLOCK = 1, RM_PARTIAL = 2 };
 
 // GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, so reductions keep
-// FP64 work low: FP32 partials (FP32 cycle) are summed by a warp tree in FP32 and only the
-// per-warp sums are combined in FP64; FP64 partials go through shared memory and one warp
-// sums them (32 values per lane in fixed order, then a 5-level shuffle tree), about one
-// FP64 add per partial instead of five for a shuffle tree over every warp.
+// FP64 work low: in the FP32 cycle a block sums in FP32 (a warp tree, then one warp over the
+// per-warp sums) and only the sum over CTAs is FP64; FP64 partials go through shared memory
+// and one warp sums them (32 values per lane in fixed order, then a 5-level shuffle tree),
+// about one FP64 add per partial instead of five for a shuffle tree over every warp.
 __device__ __forceinline__ double *red_scratch() {
     __shared__ double s[1024];  // >= blockDim.x (1024 at most)
     return s;
@@ -94,35 +159,43 @@ __device__ __forceinline__ double warp_sum(double y) {
     return y;
 }
 
-// r[k] (valid in thread 0) = block sum of v[k]; every thread must call it
-template <int NV, class A>
-__device__ __forceinline__ void block_sum(const A (&v)[NV], double (&r)[NV]) {
+// r[k] (valid in thread 0) = sum of v[k] over group g; every thread of g must call it. The
+// caller synchronises g before the scratch is used again (every executor puts a barrier
+// between two ops, and no op reduces twice).
+template <int NV, class A, class G>
+__device__ __forceinline__ void block_sum(const A (&v)[NV], double (&r)[NV], const G &g) {
     double *s = red_scratch();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = g.nwarps();
     if constexpr (sizeof(A) == 4) {
+        // FP32 cycle: a warp tree, then one warp combines the per-warp sums, all in FP32
+        float *sf = reinterpret_cast<float *>(s);
 #pragma unroll
         for (int k = 0; k < NV; k++) {
             float x = v[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) s[k * 32 + w] = (double)x;
+            if (lane == 0) sf[k * 32 + w] = x;
         }
-        __syncthreads();
+        g.sync();
         if (w == 0)
 #pragma unroll
-            for (int k = 0; k < NV; k++) r[k] = warp_sum(lane < nw ? s[k * 32 + lane] : 0.0);
-        __syncthreads();
+            for (int k = 0; k < NV; k++) {
+                float x = lane < nw ? sf[k * 32 + lane] : 0.f;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                r[k] = (double)x;
+            }
     } else {
 #pragma unroll
         for (int k = 0; k < NV; k++) {
+            if (k > 0) g.sync();
             s[threadIdx.x] = (double)v[k];
-            __syncthreads();
+            g.sync();
             if (w == 0) {
                 double y = 0.0;
-                for (int j = lane; j < (int)blockDim.x; j += 32) y += s[j];
+                for (int j = lane; j < 32 * nw; j += 32) y += s[j];
                 r[k] = warp_sum(y);
             }
-            __syncthreads();
         }
     }
 }
@@ -135,17 +208,16 @@ struct RedCtx {
 // RM_LASTBLOCK: per-block partial; the last block to finish sums them in block order.
 // RM_BLOCK (one CTA): the block sum. RM_PARTIAL (persistent kernel): per-block partials
 // into buffer pb; the next op sums them. Final values are stored by thread 0 into out[k].
-template <int NV, int RM, class A>
+template <int NV, int RM, class A, class G>
 __device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&out)[NV],
-                                             const RedCtx &rc, int pb) {
+                                             const RedCtx &rc, int pb, const G &g) {
     double r[NV];
-    block_sum<NV, A>(v, r);
-    if (RM == RM_BLOCK) {
+    block_sum<NV, A>(v, r, g);
+    if (RM == RM_BLOCK) {  // visible to the block after the executor's next barrier
         if (threadIdx.x == 0)
 #pragma unroll
             for (int k = 0; k < NV; k++)
                 if (out[k]) *out[k] = r[k];
-        __syncthreads();
         return;
     }
     if (RM == RM_PARTIAL) {
@@ -163,7 +235,7 @@ __device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&o
         unsigned t = atomicAdd(rc.counter, 1u);
         last = (t == gridDim.x - 1);
     }
-    __syncthreads();
+    g.sync();
     if (last && threadIdx.x < 32) {
         __threadfence();
 #pragma unroll
@@ -267,8 +339,8 @@ template <class LV>
 __device__ __forceinline__ typename LV::val_t row_residual(const LV &L, int i,
                                                            const typename LV::val_t *f,
                                                            const typename LV::val_t *u) {
-    const int s = i >> 5;
-    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+    int base, width;
+    row_span(L, i, base, width);
     return f[i] - row_dot(L, base, 0, width, u);
 }
 
@@ -277,8 +349,8 @@ __device__ __forceinline__ typename LV::val_t row_residual(const LV &L, int i,
 template <class LV>
 __device__ __forceinline__ void gs_row(const LV &L, int i, const typename LV::val_t *f,
                                        typename LV::val_t *u) {
-    const int s = i >> 5;
-    const int base = L.sl[s] + (i & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+    int base, width;
+    row_span(L, i, base, width);
     u[i] = (f[i] - row_dot(L, base, 1, width, u)) * L.dinv[i];
 }
 
@@ -352,8 +424,29 @@ __device__ void op_prolong(const LV &L, const typename LV::val_t *e, typename LV
     for (int i = tid; i < L.n; i += nth) u[i] += e[L.parent[i]];
 }
 
-// e = A^{-1} rhs with the dense inverse of the coarsest level, accumulated in FP64 by g
-// lanes per row (g = largest power of two <= 32 with g * n <= nth) and a shuffle tree
+// e = A^{-1} rhs with the dense inverse of the coarsest level, g lanes per row (g = largest
+// power of two <= 32 with g * n <= nth) and a shuffle tree. The FP64 cycle accumulates in
+// FP64. The FP32 cycle keeps the same accuracy with FP32 instructions (FP64 throughput is
+// scarce on this GPU): the inverse is stored as a pair of floats (high + low) and products
+// and sums are carried as unevaluated float pairs, with Dekker's exact product (one fma)
+// and Knuth's two-sum giving each rounding error exactly; the pair is rounded to FP32 at the
+// end, as the FP64 sum is.
+// (the _rn intrinsics keep the compiler from fusing these steps into FMAs, which would
+// break their exactness)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (sh, sl) += (ph, pl) for float pairs with |pl| <= ulp(ph) and |sl| <= ulp(sh)
+__device__ __forceinline__ void pair_add(float &sh, float &sl, float ph, float pl) {
+    float s, e;
+    two_sum(sh, ph, s, e);
+    e = __fadd_rn(e, __fadd_rn(sl, pl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+
 template <class LV>
 __device__ void op_coarse(const LV &L, int tid, int nth) {
     using T = typename LV::val_t;
@@ -363,22 +456,42 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
     const int sub = tid & (g - 1), rows_per_pass = nth / g;
     for (int base = 0; base < n; base += rows_per_pass) {
         const int i = base + tid / g;
-        double s = 0.0;
-        if (i < n) {
-            const double *a = L.Ainv + (size_t)i * n;
-            for (int j = sub; j < n; j += g) s += a[j] * (double)L.rhs[j];
+        if constexpr (sizeof(T) == 4) {
+            float sh = 0.f, sl = 0.f;
+            if (i < n) {
+                const float *ah = L.Ainv2 + (size_t)i * n, *al = ah + (size_t)n * n;
+                for (int j = sub; j < n; j += g) {
+                    const float x = L.rhs[j];
+                    const float ph = __fmul_rn(ah[j], x);
+                    const float pl = fmaf(al[j], x, fmaf(ah[j], x, -ph));  // error of ph + low part
+                    pair_add(sh, sl, ph, pl);
+                }
+            }
+            for (int o = g >> 1; o > 0; o >>= 1) {
+                const float oh = __shfl_down_sync(0xffffffffu, sh, o, g);
+                const float ol = __shfl_down_sync(0xffffffffu, sl, o, g);
+                pair_add(sh, sl, oh, ol);
+            }
+            if (i < n && sub == 0) L.e[i] = sh + sl;
+        } else {
+            double s = 0.0;
+            if (i < n) {
+                const double *a = L.Ainv + (size_t)i * n;
+                for (int j = sub; j < n; j += g) s += a[j] * (double)L.rhs[j];
+            }
+            for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+            if (i < n && sub == 0) L.e[i] = (T)s;
         }
-        for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
-        if (i < n && sub == 0) L.e[i] = (T)s;
     }
 }
 
-template <class LV, int RM>
-__device__ void op_multidot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+template <class LV, int RM, class G>
+__device__ void op_multidot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth,
+                            const G &g) {
     using T = typename LV::val_t;
     const int i = op.step;
     T v[kMaxKcycle] = {};
-    const T *z = L.p[i];
+    const T *z = pick(L.p, i);
     for (int r = tid; r < L.n; r += nth) {
         T zr = z[r];
 #pragma unroll
@@ -388,14 +501,14 @@ __device__ void op_multidot(const LV &L, const Op &op, const RedCtx &rc, int tid
     double *out[kMaxKcycle];
 #pragma unroll
     for (int j = 0; j < kMaxKcycle; j++) out[j] = j < i ? &L.sc[SC_ZQ0 + j] : nullptr;
-    reduce_store<kMaxKcycle, RM, T>(v, out, rc, op.red_pb);
+    reduce_store<kMaxKcycle, RM, T>(v, out, rc, op.red_pb, g);
 }
 
 // p_i = z + sum_j beta_ij p_j, beta_ij = -(z, p_j)_A / (p_j, p_j)_A  (Alg. 1, step 2).
 // The coefficients are computed once per CTA (FP64 division is scarce on this GPU) and
 // broadcast through shared memory.
-template <class LV>
-__device__ void op_orth(const LV &L, const Op &op, int tid, int nth) {
+template <class LV, class G>
+__device__ void op_orth(const LV &L, const Op &op, int tid, int nth, const G &g) {
     using T = typename LV::val_t;
     __shared__ double beta_s[kMaxKcycle];
     const int i = op.step;
@@ -404,11 +517,11 @@ __device__ void op_orth(const LV &L, const Op &op, int tid, int nth) {
         double pq = L.sc[SC_PQ0 + j];
         beta_s[j] = (j < i && pq > 0.0) ? -L.sc[SC_ZQ0 + j] / pq : 0.0;
     }
-    __syncthreads();
+    g.sync();
     T beta[kMaxKcycle];
 #pragma unroll
     for (int j = 0; j < kMaxKcycle; j++) beta[j] = (T)beta_s[j];
-    T *p = L.p[i];
+    T *p = pick(L.p, i);
     for (int r = tid; r < L.n; r += nth) {
         T acc = p[r];
 #pragma unroll
@@ -419,17 +532,18 @@ __device__ void op_orth(const LV &L, const Op &op, int tid, int nth) {
 }
 
 // q_i = A p_i; (p_i, q_i); (r_i, p_i) with r_0 = rhs
-template <class LV, int RM>
-__device__ void op_spmv_dot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+template <class LV, int RM, class G>
+__device__ void op_spmv_dot(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth,
+                            const G &g) {
     using T = typename LV::val_t;
     const int i = op.step;
-    const T *p = L.p[i];
-    T *q = L.q[i];
+    const T *p = pick(L.p, i);
+    T *q = pick(L.q, i);
     const T *r = i == 0 ? L.rhs : L.r;
     T v[2] = {0, 0};
     for (int row = tid; row < L.n; row += nth) {
-        const int s = row >> 5;
-        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+        int base, width;
+        row_span(L, row, base, width);
         const T acc = row_dot(L, base, 0, width, p);
         q[row] = acc;
         T pr = p[row];
@@ -437,13 +551,14 @@ __device__ void op_spmv_dot(const LV &L, const Op &op, const RedCtx &rc, int tid
         v[1] += r[row] * pr;
     }
     double *out[2] = {&L.sc[SC_PQ0 + i], &L.sc[SC_RP0 + i]};
-    reduce_store<2, RM, T>(v, out, rc, op.red_pb);
+    reduce_store<2, RM, T>(v, out, rc, op.red_pb, g);
 }
 
 // alpha_i = (r_i, p_i) / (p_i, p_i)_A; u_{i+1} = u_i + alpha_i p_i; r_{i+1} = r_i - alpha_i q_i.
 // Alg. 1 stops (alpha = 0 from then on) once (p_i, p_i)_A <= 0 or a residual is exactly zero.
-template <class LV, int RM>
-__device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth) {
+template <class LV, int RM, class G>
+__device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, int nth,
+                          const G &g) {
     using T = typename LV::val_t;
     __shared__ double coef[2];  // alpha, stopped: computed once per CTA
     const int i = op.step, last = op.last;
@@ -455,11 +570,11 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
         coef[0] = stopped ? 0.0 : L.sc[SC_RP0 + i] / pq;
         coef[1] = stopped ? 1.0 : 0.0;
     }
-    __syncthreads();
+    g.sync();
     const T a = (T)coef[0];
     const bool stopped = coef[1] != 0.0;
-    const T *p = L.p[i];
-    const T *q = L.q[i];
+    const T *p = pick(L.p, i);
+    const T *q = pick(L.q, i);
     const T *r_in = i == 0 ? L.rhs : L.r;
     T *e = L.e;
     T v[1] = {0};
@@ -473,32 +588,40 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
     }
     if (!last) {
         double *out[1] = {&L.sc[SC_RR0 + i]};
-        reduce_store<1, RM, T>(v, out, rc, op.red_pb);
+        reduce_store<1, RM, T>(v, out, rc, op.red_pb, g);
     }
     if ((RM == RM_BLOCK || blockIdx.x == 0) && threadIdx.x == 0)
         L.sc[SC_STOP0 + i] = stopped ? 1.0 : 0.0;
 }
 
-// run one op (everything except OP_TAIL / OP_NOP)
-template <class LV, int RM>
-__device__ __forceinline__ void run_op(const LV *tab, const Op &op, const RedCtx &rc, int tid,
-                                       int nth) {
-    const LV &L = tab[op.level];
+// run one op (everything except OP_TAIL / OP_NOP) on level view L by threads tid < nth of
+// group g; next() gives the view of the next coarser level (only its rhs and e are used)
+template <class LV, int RM, class G, class Next>
+__device__ __forceinline__ void run_op_on(const LV &L, const Next &next, const Op &op,
+                                          const RedCtx &rc, int tid, int nth, const G &g) {
     switch (op.kind) {
         case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
         case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_GS_FIRST: op_gs_first(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_RESTRICT:
-            op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), tab[op.level + 1].rhs, tid, nth);
+            op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), next().rhs, tid, nth);
             break;
-        case OP_PROLONG: op_prolong(L, tab[op.level + 1].e, vec_of(L, op.usel), tid, nth); break;
+        case OP_PROLONG: op_prolong(L, next().e, vec_of(L, op.usel), tid, nth); break;
         case OP_COARSE: op_coarse(L, tid, nth); break;
-        case OP_MULTIDOT: op_multidot<LV, RM>(L, op, rc, tid, nth); break;
-        case OP_ORTH: op_orth(L, op, tid, nth); break;
-        case OP_SPMV_DOT: op_spmv_dot<LV, RM>(L, op, rc, tid, nth); break;
-        case OP_UPDATE: op_update<LV, RM>(L, op, rc, tid, nth); break;
+        case OP_MULTIDOT: op_multidot<LV, RM>(L, op, rc, tid, nth, g); break;
+        case OP_ORTH: op_orth(L, op, tid, nth, g); break;
+        case OP_SPMV_DOT: op_spmv_dot<LV, RM>(L, op, rc, tid, nth, g); break;
+        case OP_UPDATE: op_update<LV, RM>(L, op, rc, tid, nth, g); break;
         default: break;
     }
+}
+
+// run one op on level op.level of a table of views, every thread of the CTA taking part
+template <class LV, int RM>
+__device__ __forceinline__ void run_op(const LV *tab, const Op &op, const RedCtx &rc, int tid,
+                                       int nth) {
+    run_op_on<LV, RM>(tab[op.level], [&]() -> const LV & { return tab[op.level + 1]; }, op, rc,
+                      tid, nth, BlockGroup{});
 }
 
 }  // namespace amg

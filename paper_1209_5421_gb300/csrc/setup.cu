@@ -460,7 +460,9 @@ __global__ void k_chol_inverse(int n, double *a, double *w, double *ainv, float 
         double s = 0.0;
         for (int k = max(i, j); k < n; k++) s += w[(size_t)k * n + i] * w[(size_t)k * n + j];
         ainv[e] = s;
-        if (ainv32) ainv32[e] = (float)s;
+        const float hi = (float)s;  // FP32 cycle: high and low parts, s ~ hi + lo
+        ainv32[e] = hi;
+        ainv32[(size_t)n * n + e] = (float)(s - (double)hi);
     }
 }
 
@@ -607,7 +609,7 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
     k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val, a);
     AMG_LAUNCH_CHECK();
     lv.Ainv = halloc<double>(h, (size_t)n * n);
-    lv.Ainv32 = halloc<float>(h, (size_t)n * n);
+    lv.Ainv32 = halloc<float>(h, 2 * (size_t)n * n);
     k_chol_inverse<<<1, 256, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
     AMG_LAUNCH_CHECK();
 }

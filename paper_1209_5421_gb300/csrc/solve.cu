@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "cycle_ops.cuh"
 
@@ -28,35 +29,43 @@ using SLev = LevelDev<T, unsigned short>;      // level staged in shared memory
 constexpr int kPThreads = 1024;     // persistent kernel CTA size (one CTA per SM)
 constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
 
+
 // shared-memory image of the tail levels (byte offsets into the dynamic shared memory)
 struct TailLevelLayout {
     int n, nslices, padded;
     int gmem;    // 1: the level stays in HBM/L2 (top tail level only); its scalars are staged
-    int sl, col, val, dinv, parent, children, Ainv, rhs, e, r;
+    int w;       // staged: slice width of the image (every slice padded to it)
+    int colors, ncolors;  // staged int[ncolors + 1]: pi-row range of each colour
+    int col, val, dinv, parent, children, Ainv, rhs, e, r;
     int p[kMaxKcycle], q[kMaxKcycle];
 };
 struct TailLayout {
-    int tl;      // first staged level (nlev = none)
+    int tl;      // first tail level (nlev = none)
     int nlev;
+    int narrow;  // threads (whole warps) that run the ops of the staged levels
+    int kc;      // Alg. 1 steps (kcycle_n)
+    int W;       // slice width of every staged level when fixed (9), else 0
     int bytes;
-    int prog;    // the tail program (ops)
     int sc;      // the tail levels' Alg. 1 scalars, SC_N doubles per level
     TailLevelLayout lv[kMaxLevels];
 };
+
+constexpr int kTprofCount = 16 * kMaxLevels;  // tail profile slots: 16 op kinds per level
 
 template <class T>
 struct CycleArgs {
     const GLev<T> *tab;
     const Op *prog;
     int nops;
-    const Op *tail_prog;
-    int tail_nops;
+    const int *tail_colors;      // colour ranges of the tail levels, copied to shared memory
+    int tail_color_words;
     TailLayout lay;
     double *partials;            // [2][4][gridDim]
     unsigned long long *bar;     // barrier counter (zeroed before every launch)
     int *err;
     unsigned long long *ts;      // per-op end timestamps (profiling) or null
-    unsigned long long *tprof;   // tail: [kind] cycles, [16 + kind] count (profiling) or null
+    unsigned long long *tprof;   // tail: [16 level + kind] cycles, [kTprofCount + 16 level +
+                                 // kind] count (profiling) or null
 };
 
 // ---------------------------------------------------------------------------------------
@@ -69,17 +78,240 @@ __global__ void __launch_bounds__(kRedThreads) k_op(const GLev<T> *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------
-// persistent cycle kernel
+// persistent cycle kernel: the shared-memory tail
+//
+// CTA 0 runs B~ of the tail levels (Alg. 1 with Alg. 2 inside, down to the exact coarsest
+// solve) as structured code: one device function per level depth, every op a direct call,
+// no op decoding. Staged levels are addressed from the dynamic shared-memory base through
+// the byte offsets of the layout (kept in shared memory), so every access is a shared-memory
+// load, and their slices have one width W (compile-time 9 for the 3x3-cell stencils of
+// span-1 levels). Their ops run on the first `narrow` threads (whole warps) with hardware
+// barrier 1: the other warps would only add issue slots and barrier arrivals to ops of a
+// few hundred rows. The ops of an HBM-resident top level (thousands of rows, each a chain
+// of L2 round trips) run on the whole CTA with CTA-wide barriers.
+extern __shared__ __align__(16) unsigned char amg_smem[];
+
+struct TailCtl {
+    int tl, nlev, narrow, kc, sc_off;
+    int *err;
+    unsigned long long *tprof;
+    long long t0;
+};
+__shared__ TailCtl tail_ctl;
+__shared__ TailLevelLayout tail_lay[kMaxLevels];
+__shared__ __align__(16) unsigned char tail_gview[sizeof(SLev<double>)];  // SLev<T> of the top
+
+template <class T, int W>
+__device__ __forceinline__ StagedLevel<T, W> staged_level(int l) {
+    const TailLevelLayout &y = tail_lay[l];
+    const int nlev = tail_ctl.nlev;
+    auto at = [](int off) { return amg_smem + (off > 0 ? off : 0); };  // -1: absent, never read
+    StagedLevel<T, W> V;
+    V.n = y.n;
+    V.w = y.w;
+    V.col = (const unsigned short *)at(y.col);
+    V.val = (const T *)at(y.val);
+    V.dinv = (const T *)at(y.dinv);
+    V.bptr = nullptr;
+    V.parent = (const int *)at(y.parent);
+    V.children = (const int4 *)at(l + 1 < nlev ? tail_lay[l + 1].children : -1);
+    V.Ainv = (const double *)at(y.Ainv);  // FP64 cycle: n*n doubles
+    V.Ainv2 = (const float *)at(y.Ainv);  // FP32 cycle: 2*n*n floats, the same bytes
+    V.rhs = (T *)at(y.rhs);
+    V.e = (T *)at(y.e);
+    V.r = (T *)at(y.r);
+#pragma unroll
+    for (int k = 0; k < kMaxKcycle; k++) {
+        V.p[k] = (T *)at(y.p[k]);
+        V.q[k] = (T *)at(y.q[k]);
+    }
+    V.sc = (double *)(amg_smem + tail_ctl.sc_off) + (size_t)(l - tail_ctl.tl) * SC_N;
+    V.nnext = l + 1 < nlev ? tail_lay[l + 1].n : 0;
+    return V;
+}
+
+// tail profiling: SM cycles of the op just finished, by level and kind (thread 0)
+__device__ __forceinline__ void tail_mark(int l, int kind) {
+    if (tail_ctl.tprof && threadIdx.x == 0) {
+        const long long t1 = clock64();
+        const int slot = 16 * l + kind;
+        atomicAdd(&tail_ctl.tprof[slot], (unsigned long long)(t1 - tail_ctl.t0));
+        atomicAdd(&tail_ctl.tprof[kTprofCount + slot], 1ull);
+        tail_ctl.t0 = t1;
+    }
+}
+
+__device__ __forceinline__ Op tail_op() {
+    Op o;
+    memset(&o, 0, sizeof o);
+    o.red_pb = -1;
+    o.fin_pb = -1;
+    return o;
+}
+
+// The recursion of B~ (Alg. 1) and B^ (Alg. 2) over the tail levels is walked as a state
+// machine with three phases per level: ENTER (B~_l starts: the exact solve on the coarsest
+// level, else step 0), PRE (B^_l for step i up to the restriction, then B~_{l+1}) and POST
+// (the prolongation, post-smoothing and the Alg. 1 updates of step i). Every thread of the
+// CTA walks it with the same state, so all know which phases are the top level's.
+enum : int { PH_ENTER = 0, PH_PRE, PH_POST };
+
+// pre-smoothing from zero (colours ascending; the first non-empty colour is u = D^-1 f) and
+// next.rhs = P^t (f - A u1), for z = p_i = B^_l [f], f = rhs (i = 0) or r
+template <class T, int W, class LV, class G>
+__device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int l, int i) {
+    const int tid = threadIdx.x;
+    const T *f = i == 0 ? L.rhs : L.r;
+    T *z = pick(L.p, i);
+    const int *cr = (const int *)(amg_smem + tail_lay[l].colors);
+    const int nc = tail_lay[l].ncolors;
+    int c = 0;
+    while (c < nc && cr[c + 1] == cr[c]) c++;
+    Op op = tail_op();
+    op.i0 = c < nc ? cr[c] : 0;
+    op.i1 = c < nc ? cr[c + 1] : 0;
+    op_gs_first(L, op, f, z, tid, nth);
+    g.sync();
+    tail_mark(l, OP_GS_FIRST);
+    for (c++; c < nc; c++) {
+        if (cr[c + 1] == cr[c]) continue;
+        op.i0 = cr[c];
+        op.i1 = cr[c + 1];
+        op_gs(L, op, f, z, tid, nth);
+        g.sync();
+        tail_mark(l, OP_GS);
+    }
+    op_restrict(L, f, z, staged_level<T, W>(l + 1).rhs, tid, nth);
+    g.sync();
+    tail_mark(l, OP_RESTRICT);
+}
+
+// u2 = u1 + P next.e, post-smoothing (colours descending), then Alg. 1 step i on level l
+template <class T, int W, class LV, class G>
+__device__ __forceinline__ void phase_post(const LV &L, const G &g, int nth, int l, int i) {
+    const int tid = threadIdx.x;
+    const T *f = i == 0 ? L.rhs : L.r;
+    T *z = pick(L.p, i);
+    op_prolong(L, staged_level<T, W>(l + 1).e, z, tid, nth);
+    g.sync();
+    tail_mark(l, OP_PROLONG);
+    const int *cr = (const int *)(amg_smem + tail_lay[l].colors);
+    Op op = tail_op();
+    op.backward = 1;
+    for (int c = tail_lay[l].ncolors - 1; c >= 0; c--) {
+        if (cr[c + 1] == cr[c]) continue;
+        op.i0 = cr[c];
+        op.i1 = cr[c + 1];
+        op_gs(L, op, f, z, tid, nth);
+        g.sync();
+        tail_mark(l, OP_GS);
+    }
+    const RedCtx rc{nullptr, nullptr};
+    const int kc = tail_ctl.kc;
+    op = tail_op();
+    op.step = i;
+    op.last = (i == kc - 1);
+    if (i > 0) {
+        op_multidot<LV, RM_BLOCK>(L, op, rc, tid, nth, g);
+        g.sync();
+        tail_mark(l, OP_MULTIDOT);
+        op_orth(L, op, tid, nth, g);
+        g.sync();
+        tail_mark(l, OP_ORTH);
+    }
+    op_spmv_dot<LV, RM_BLOCK>(L, op, rc, tid, nth, g);
+    g.sync();
+    tail_mark(l, OP_SPMV_DOT);
+    op_update<LV, RM_BLOCK>(L, op, rc, tid, nth, g);
+    g.sync();
+    tail_mark(l, OP_UPDATE);
+}
+
+// ENTER on the coarsest level: e = A^{-1} rhs
+template <class LV, class G>
+__device__ __forceinline__ void phase_coarse(const LV &L, const G &g, int nth, int l) {
+    op_coarse(L, threadIdx.x, nth);
+    g.sync();
+    tail_mark(l, OP_COARSE);
+}
+
+// e_tl = B~_tl [rhs_tl] over the whole tail (every thread of CTA 0 calls it)
+template <class T, int W>
+__device__ void tail_btilde(bool inplace) {
+    const int tl = tail_ctl.tl, nlev = tail_ctl.nlev, kc = tail_ctl.kc, narrow = tail_ctl.narrow;
+    const int tid = threadIdx.x;
+    const WarpGroup ng{narrow};
+    const SLev<T> &top = *reinterpret_cast<const SLev<T> *>(tail_gview);
+    int step[kMaxLevels] = {};
+    int l = tl, ph = PH_ENTER;
+    bool prev_top = true;  // the caller's barrier
+    for (;;) {
+        const bool coarsest = tail_lay[l].Ainv >= 0;
+        const int i = step[l];
+        if (inplace && l == tl) {  // the HBM-resident top level: the whole CTA
+            if (!prev_top) __syncthreads();  // the narrow warps' phases are complete
+            prev_top = true;
+            const int nth = blockDim.x;
+            if (ph == PH_PRE) phase_pre<T, W>(top, BlockGroup{}, nth, l, i);
+            else if (ph == PH_POST) phase_post<T, W>(top, BlockGroup{}, nth, l, i);
+        } else {
+            prev_top = false;
+            if (tid < narrow) {
+                const StagedLevel<T, W> L = staged_level<T, W>(l);
+                if (ph == PH_ENTER && coarsest) phase_coarse(L, ng, narrow, l);
+                else if (ph == PH_PRE) phase_pre<T, W>(L, ng, narrow, l, i);
+                else if (ph == PH_POST) phase_post<T, W>(L, ng, narrow, l, i);
+            }
+        }
+        // next state (the same in every thread)
+        if (ph == PH_ENTER && !coarsest) {
+            step[l] = 0;
+            ph = PH_PRE;
+            continue;
+        }
+        if (ph == PH_PRE) {  // descend: B~_{l+1}
+            if (l + 1 >= nlev || l + 1 - tl >= kMaxLevels) break;  // never: the coarsest ends it
+            l++;
+            ph = PH_ENTER;
+            continue;
+        }
+        if (ph == PH_POST && i + 1 < kc) {
+            step[l] = i + 1;
+            ph = PH_PRE;
+            continue;
+        }
+        // B~_l done (coarsest solved, or its last step): back to level l-1's POST
+        if (l == tl) break;
+        l--;
+        ph = PH_POST;
+    }
+    if (inplace && !prev_top) __syncthreads();
+}
+
+// CTA 0, kernel start: copy the staged levels into shared memory (slices padded to width w)
 template <class T>
-__device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *stab) {
+__device__ void stage_tail(const CycleArgs<T> &a) {
     const TailLayout &Y = a.lay;
     const int tid = threadIdx.x, nth = blockDim.x;
+    {
+        const int words = Y.nlev * (int)(sizeof(TailLevelLayout) / sizeof(int));
+        for (int i = tid; i < words; i += nth) ((int *)tail_lay)[i] = ((const int *)Y.lv)[i];
+    }
+    if (tid == 0) {
+        tail_ctl.tl = Y.tl;
+        tail_ctl.nlev = Y.nlev;
+        tail_ctl.narrow = Y.narrow;
+        tail_ctl.kc = Y.kc;
+        tail_ctl.sc_off = Y.sc;
+        tail_ctl.err = a.err;
+        tail_ctl.tprof = a.tprof;
+    }
     for (int l = Y.tl; l < Y.nlev; l++) {
         const TailLevelLayout &y = Y.lv[l];
         const GLev<T> &G = a.tab[l];
         if (y.gmem) {  // read in place from HBM / L2
             if (tid == 0) {
-                SLev<T> &S = stab[l];
+                SLev<T> &S = *reinterpret_cast<SLev<T> *>(tail_gview);
                 S.n = G.n;
                 S.fine = 0;
                 S.sl = G.sl;
@@ -90,8 +322,9 @@ __device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *st
                 S.bptr = nullptr;
                 S.parent = G.parent;
                 S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
-                                 ? (const int4 *)(sm + Y.lv[l + 1].children) : nullptr;
+                                 ? (const int4 *)(amg_smem + Y.lv[l + 1].children) : nullptr;
                 S.Ainv = G.Ainv;
+                S.Ainv2 = G.Ainv2;
                 S.rhs = G.rhs;
                 S.e = G.e;
                 S.r = G.r;
@@ -99,86 +332,68 @@ __device__ void stage_tail(const CycleArgs<T> &a, unsigned char *sm, SLev<T> *st
                     S.p[k] = G.p[k];
                     S.q[k] = G.q[k];
                 }
-                S.sc = (double *)(sm + Y.sc) + (size_t)(l - Y.tl) * SC_N;
+                S.sc = (double *)(amg_smem + Y.sc) + (size_t)(l - Y.tl) * SC_N;
                 S.nnext = G.nnext;
             }
             continue;
         }
-        int *sl = (int *)(sm + y.sl);
-        unsigned short *col = (unsigned short *)(sm + y.col);
-        T *val = (T *)(sm + y.val);
-        for (int i = tid; i <= y.nslices; i += nth) sl[i] = G.sl[i];
-        for (int i = tid; i < y.padded; i += nth) {
-            int c = G.col[i];
+        // slot (s, k, lane) of the image <- slot k of slice s in HBM, or padding
+        unsigned short *col = (unsigned short *)(amg_smem + y.col);
+        T *val = (T *)(amg_smem + y.val);
+        const int img = y.nslices * 32 * y.w;
+        for (int i = tid; i < img; i += nth) {
+            const int sidx = i / (32 * y.w), rem = i - sidx * 32 * y.w;
+            const int k = rem >> 5, lane = rem & 31;
+            const int s0 = G.sl[sidx], width = (G.sl[sidx + 1] - s0) >> 5;
+            int c = -1;
+            T v = 0;
+            if (k < width) {
+                c = G.col[s0 + 32 * k + lane];
+                v = G.val[s0 + 32 * k + lane];
+            }
             col[i] = c >= 0 ? (unsigned short)c : (unsigned short)0xFFFF;
-            val[i] = G.val[i];
+            val[i] = c >= 0 ? v : T(0);
         }
         if (y.dinv >= 0)
-            for (int i = tid; i < y.n; i += nth) ((T *)(sm + y.dinv))[i] = G.dinv[i];
+            for (int i = tid; i < y.n; i += nth) ((T *)(amg_smem + y.dinv))[i] = G.dinv[i];
         if (y.parent >= 0)
-            for (int i = tid; i < y.n; i += nth) ((int *)(sm + y.parent))[i] = G.parent[i];
+            for (int i = tid; i < y.n; i += nth) ((int *)(amg_smem + y.parent))[i] = G.parent[i];
         if (y.children >= 0)  // children of this level's rows (in level l-1)
             for (int i = tid; i < y.n; i += nth)
-                ((int4 *)(sm + y.children))[i] = a.tab[l - 1].children[i];
-        if (y.Ainv >= 0)
-            for (int i = tid; i < y.n * y.n; i += nth) ((double *)(sm + y.Ainv))[i] = G.Ainv[i];
-        if (tid == 0) {
-            SLev<T> &S = stab[l];
-            S.n = y.n;
-            S.fine = 0;
-            S.sl = sl;
-            S.col = col;
-            S.val = val;
-            S.dinv = y.dinv >= 0 ? (const T *)(sm + y.dinv) : nullptr;
-            S.col16 = nullptr;
-            S.bptr = nullptr;
-            S.parent = y.parent >= 0 ? (const int *)(sm + y.parent) : nullptr;
-            S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
-                             ? (const int4 *)(sm + Y.lv[l + 1].children) : nullptr;
-            S.Ainv = y.Ainv >= 0 ? (const double *)(sm + y.Ainv) : nullptr;
-            S.rhs = (T *)(sm + y.rhs);
-            S.e = (T *)(sm + y.e);
-            S.r = y.r >= 0 ? (T *)(sm + y.r) : nullptr;
-            for (int k = 0; k < kMaxKcycle; k++) {
-                S.p[k] = y.p[k] >= 0 ? (T *)(sm + y.p[k]) : nullptr;
-                S.q[k] = y.q[k] >= 0 ? (T *)(sm + y.q[k]) : nullptr;
-            }
-            S.sc = (double *)(sm + Y.sc) + (size_t)(l - Y.tl) * SC_N;
-            S.nnext = l + 1 < Y.nlev ? Y.lv[l + 1].n : 0;
+                ((int4 *)(amg_smem + y.children))[i] = a.tab[l - 1].children[i];
+        if (y.Ainv >= 0) {  // n*n doubles or 2*n*n floats
+            if (sizeof(T) == 8)
+                for (int i = tid; i < y.n * y.n; i += nth)
+                    ((double *)(amg_smem + y.Ainv))[i] = G.Ainv[i];
+            else
+                for (int i = tid; i < 2 * y.n * y.n; i += nth)
+                    ((float *)(amg_smem + y.Ainv))[i] = G.Ainv2[i];
         }
     }
-    const int words = a.tail_nops * (int)(sizeof(Op) / sizeof(int));
-    for (int i = tid; i < words; i += nth)
-        ((int *)(sm + Y.prog))[i] = ((const int *)a.tail_prog)[i];
+    // colour ranges: every level's int[ncolors + 1] at its offset, in one block of words
+    if (a.tail_color_words > 0) {
+        int *dst = (int *)(amg_smem + Y.lv[Y.tl].colors);
+        for (int i = tid; i < a.tail_color_words; i += nth) dst[i] = a.tail_colors[i];
+    }
 }
 
-template <class T>
-__device__ void run_tail(const CycleArgs<T> &a, const SLev<T> *stab, unsigned char *sm) {
-    const int tl = a.lay.tl, n = a.lay.lv[tl].n;
+template <class T, int W>
+__device__ void run_tail(const CycleArgs<T> &a) {
+    const int tl = a.lay.tl, n = tail_lay[tl].n;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const bool inplace = a.lay.lv[tl].gmem != 0;
-    const T *grhs = a.tab[tl].rhs;
-    T *srhs = stab[tl].rhs;
-    if (!inplace)
+    const bool inplace = tail_lay[tl].gmem != 0;
+    if (!inplace) {
+        const T *grhs = a.tab[tl].rhs;
+        T *srhs = (T *)(amg_smem + tail_lay[tl].rhs);
         for (int i = tid; i < n; i += nth) srhs[i] = grhs[i];
-    __syncthreads();
-    RedCtx rc{nullptr, nullptr};
-    const Op *prog = (const Op *)(sm + a.lay.prog);
-    long long t0 = clock64();
-    for (int k = 0; k < a.tail_nops; k++) {
-        const Op &op = prog[k];  // read in place: a local copy would go through the stack
-        run_op<SLev<T>, RM_BLOCK>(stab, op, rc, tid, nth);
-        __syncthreads();
-        if (a.tprof && tid == 0) {
-            long long t1 = clock64();
-            atomicAdd(&a.tprof[op.kind & 15], (unsigned long long)(t1 - t0));
-            atomicAdd(&a.tprof[16 + (op.kind & 15)], 1ull);
-            t0 = t1;
-        }
     }
+    if (tid == 0) tail_ctl.t0 = clock64();
+    __syncthreads();
+    tail_btilde<T, W>(inplace);
     if (inplace) return;
+    __syncthreads();
     T *ge = a.tab[tl].e;
-    const T *se = stab[tl].e;
+    const T *se = (const T *)(amg_smem + tail_lay[tl].e);
     for (int i = tid; i < n; i += nth) ge[i] = se[i];
 }
 
@@ -200,10 +415,8 @@ __device__ __forceinline__ void finalize(const CycleArgs<T> &a, const GLev<T> *t
     __syncthreads();
 }
 
-template <class T>
+template <class T, int W>
 __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ SLev<T> stab[kMaxLevels];
     __shared__ GLev<T> gtab[kMaxLevels];
     __shared__ unsigned long long target;
     __shared__ int abort_flag;
@@ -216,7 +429,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
         for (int i = threadIdx.x; i < words; i += blockDim.x)
             ((int *)gtab)[i] = ((const int *)a.tab)[i];
     }
-    if (blockIdx.x == 0 && a.lay.tl < a.lay.nlev) stage_tail(a, sm, stab);
+    if (blockIdx.x == 0 && a.lay.tl < a.lay.nlev) stage_tail(a);
     __syncthreads();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnth = gridDim.x * blockDim.x;
     const RedCtx rc{a.partials, nullptr};
@@ -224,7 +437,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
     for (int k = 0; k < a.nops; k++) {
         if (op.fin_pb >= 0) finalize(a, gtab, op);
         if (op.kind == OP_TAIL) {
-            if (blockIdx.x == 0) run_tail(a, stab, sm);
+            if (blockIdx.x == 0) run_tail<T, W>(a);
         } else if (op.kind != OP_NOP) {
             run_op<GLev<T>, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
         }
@@ -278,7 +491,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(int n, const double *__re
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         a[0] += v[i] * v[i];
     double *o[1] = {out};
-    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0, BlockGroup{});
 }
 
 // t = b - A x, (t, t) -> out
@@ -294,7 +507,7 @@ __global__ void __launch_bounds__(kRedThreads) k_true_residual(GLev<double> L,
         a[0] += ri * ri;
     }
     double *o[1] = {out};
-    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0, BlockGroup{});
 }
 
 // outer scalars: osc[OS_BB] = (b,b), osc[OS_RR] = (r,r), osc[OS_STOP] = breakdown flag,
@@ -313,8 +526,9 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const dou
         double a[1] = {0.0}, r[1];
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
             a[0] += z[i] * q[i];
-        block_sum<1, double>(a, r);
+        block_sum<1, double>(a, r, BlockGroup{});
         if (threadIdx.x == 0) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = r[0];
+        __syncthreads();  // the reduction scratch is reused by the next j
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -370,7 +584,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_spmv_dot(GLev<double> L,
         v[1] += r[row] * p[row];
     }
     double *out[2] = {&opq[it], &osc[OS_RP]};
-    reduce_store<2, RM_LASTBLOCK, double>(v, out, rc, 0);
+    reduce_store<2, RM_LASTBLOCK, double>(v, out, rc, 0, BlockGroup{});
 }
 
 // alpha = (r, p) / (p, Ap); x += alpha p; r -= alpha q; (r, r)
@@ -394,7 +608,7 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_update(int n, double *con
         v[0] += rn * rn;
     }
     double *out[1] = {&osc[OS_RR]};
-    reduce_store<1, RM_LASTBLOCK, double>(v, out, rc, 0);
+    reduce_store<1, RM_LASTBLOCK, double>(v, out, rc, 0, BlockGroup{});
     if (blockIdx.x == 0 && threadIdx.x == 0 && bad) osc[OS_STOP] = 1.0;
 }
 
@@ -424,8 +638,9 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__res
         double a[1] = {0.0}, r[1];
         for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
             a[0] += w[k] * v[k];
-        block_sum<1, double>(a, r);
+        block_sum<1, double>(a, r, BlockGroup{});
         if (threadIdx.x == 0) rc.partials[(size_t)i * gridDim.x + blockIdx.x] = r[0];
+        __syncthreads();  // the reduction scratch is reused by the next i
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -460,7 +675,7 @@ __global__ void __launch_bounds__(kRedThreads) k_orth_sub(int n, double *__restr
         a[0] += x * x;
     }
     double *o[1] = {nrm2};
-    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0);
+    reduce_store<1, RM_LASTBLOCK, double>(a, o, rc, 0, BlockGroup{});
 }
 
 // v = w * s
@@ -630,8 +845,8 @@ static double op_bytes(const amg_hierarchy *h, const Op &op, int w) {
 struct EngineBase {
     Op *prog = nullptr;
     int nops = 0;
-    Op *tail_prog = nullptr;
-    int tail_nops = 0;
+    int *tail_colors = nullptr;  // colour ranges of the tail levels
+    int tail_color_words = 0;
     TailLayout lay{};
     size_t smem = 0;
     int grid = 0;
@@ -825,6 +1040,7 @@ void fill_tables(amg_hierarchy *h) {
         d.parent = lv.parent;
         d.children = (l + 1 < h->nlev) ? h->lev[l + 1].children : nullptr;
         d.Ainv = lv.Ainv;
+        d.Ainv2 = lv.Ainv32;
         Vecs<T> &v = vecs<T>(lv);
         d.rhs = v.rhs;
         d.e = v.e;
@@ -848,16 +1064,43 @@ const GLev<T> *dtab(amg_hierarchy *h) {
 }
 
 // shared-memory image of levels l0..nlev-1; returns false if a level is too large
-bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, bool top_in_gmem, TailLayout &Y) {
+// widest slice (slots per row) of each level, from its slice pointers
+std::vector<int> slice_widths(amg_hierarchy *h) {
+    std::vector<int> w(h->nlev, 0);
+    for (int l = 0; l < h->nlev; l++) {
+        const Sell &A = h->lev[l].A;
+        std::vector<int> sl(A.nslices + 1);
+        AMG_CUDA(cudaMemcpyAsync(sl.data(), A.sl_ptr, sizeof(int) * sl.size(),
+                                 cudaMemcpyDeviceToHost, h->stream));
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        for (int k = 0; k < A.nslices; k++) w[l] = std::max(w[l], (sl[k + 1] - sl[k]) / kSliceH);
+    }
+    return w;
+}
+
+// shared-memory image of the tail from level l0 down (value size `vb` bytes); the top level
+// may stay in HBM (top_in_gmem). False if a level is too large or the tail too deep.
+bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
+                 const std::vector<int> &widths, TailLayout &Y) {
     std::memset(&Y, 0, sizeof Y);
     Y.tl = l0;
     Y.nlev = h->nlev;
+    Y.kc = h->opt.kcycle_n;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         int o = (int)off;
         off += align16(bytes);
         return o;
     };
+    // colour ranges of every tail level, one block
+    int words = 0;
+    for (int l = l0; l < h->nlev; l++) words += (int)h->lev[l].color_rows.size();
+    const int cbase = take(sizeof(int) * (size_t)words);
+    int cw = 0;
+    // one slice width for the staged levels: 9 (3x3-cell stencils) if every one fits
+    bool w9 = true;
+    for (int l = l0 + (top_in_gmem ? 1 : 0); l < h->nlev; l++) w9 = w9 && widths[l] <= 9;
+    Y.W = w9 ? 9 : 0;
     const int kc = h->opt.kcycle_n;
     for (int l = l0; l < h->nlev; l++) {
         const Level &lv = h->lev[l];
@@ -865,33 +1108,43 @@ bool tail_layout(amg_hierarchy *h, int l0, int w, int tail_ops, bool top_in_gmem
         y.n = lv.n;
         y.nslices = lv.A.nslices;
         y.padded = (int)lv.A.padded;
+        y.colors = cbase + (int)sizeof(int) * cw;
+        y.ncolors = (int)lv.color_rows.size() - 1;
+        cw += (int)lv.color_rows.size();
         if (l == l0 && top_in_gmem) {
             if (lv.n > 65535 || lv.coarsest) return false;
             y.gmem = 1;
-            y.sl = y.col = y.val = y.dinv = y.parent = y.children = y.Ainv = -1;
+            y.w = 0;
+            y.col = y.val = y.dinv = y.parent = y.children = y.Ainv = -1;
             y.rhs = y.e = y.r = -1;
             for (int k = 0; k < kMaxKcycle; k++) y.p[k] = y.q[k] = -1;
             continue;
         }
         if (lv.n > kTailRowsMax) return false;
-        y.sl = take(sizeof(int) * (size_t)(lv.A.nslices + 1));
-        y.col = take(2 * (size_t)lv.A.padded);
-        y.val = take((size_t)w * lv.A.padded);
-        y.dinv = lv.coarsest ? -1 : take((size_t)w * lv.n);
+        y.w = w9 ? 9 : std::max(1, widths[l]);
+        const size_t img = (size_t)lv.A.nslices * kSliceH * y.w;
+        y.col = take(2 * img);
+        y.val = take((size_t)vb * img);
+        y.dinv = lv.coarsest ? -1 : take((size_t)vb * lv.n);
         y.parent = lv.coarsest ? -1 : take(sizeof(int) * (size_t)lv.n);
         y.children = (l > l0) ? take(sizeof(int4) * (size_t)lv.n) : -1;
         y.Ainv = lv.coarsest ? take(sizeof(double) * lv.n * lv.n) : -1;
-        y.rhs = take((size_t)w * lv.n);
-        y.e = take((size_t)w * lv.n);
-        y.r = lv.coarsest ? -1 : take((size_t)w * lv.n);
+        y.rhs = take((size_t)vb * lv.n);
+        y.e = take((size_t)vb * lv.n);
+        y.r = lv.coarsest ? -1 : take((size_t)vb * lv.n);
         for (int k = 0; k < kMaxKcycle; k++) {
-            y.p[k] = (!lv.coarsest && k < kc) ? take((size_t)w * lv.n) : -1;
-            y.q[k] = (!lv.coarsest && k < kc) ? take((size_t)w * lv.n) : -1;
+            y.p[k] = (!lv.coarsest && k < kc) ? take((size_t)vb * lv.n) : -1;
+            y.q[k] = (!lv.coarsest && k < kc) ? take((size_t)vb * lv.n) : -1;
         }
         if (off > (size_t)INT32_MAX) return false;
     }
+    // narrow group: about one thread per row of a colour of the largest staged level (a
+    // quarter of its rows for the 2x2 colouring), whole warps, 128..1024 threads
+    int nmax = 0;
+    for (int l = l0; l < h->nlev; l++)
+        if (!Y.lv[l].gmem) nmax = std::max(nmax, Y.lv[l].n);
+    Y.narrow = std::min(1024, std::max(128, (nmax / 4 + 31) / 32 * 32));
     Y.sc = take(sizeof(double) * SC_N * (size_t)(h->nlev - l0));
-    Y.prog = take(sizeof(Op) * (size_t)tail_ops);
     Y.bytes = (int)off;
     return true;
 }
@@ -910,6 +1163,11 @@ int max_tail_bytes() {
 }
 
 template <class T>
+void *cycle_kernel(int W) {
+    return W == 9 ? (void *)k_cycle<T, 9> : (void *)k_cycle<T, 0>;
+}
+
+template <class T>
 void build_engine(amg_hierarchy *h) {
     EngineBase *&E = engine_slot<T>(h);
     if (!E) E = new EngineBase();
@@ -917,21 +1175,22 @@ void build_engine(amg_hierarchy *h) {
     int dev = h->device, optin = 0, nsm = 0;
     AMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     AMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    cudaFuncAttributes fa;
-    AMG_CUDA(cudaFuncGetAttributes(&fa, k_cycle<T>));
-    const long budget = std::min<long>((long)optin - (long)fa.sharedSizeBytes - 1024,
+    size_t static_smem = 0;
+    for (int W : {0, 9}) {
+        cudaFuncAttributes fa;
+        AMG_CUDA(cudaFuncGetAttributes(&fa, cycle_kernel<T>(W)));
+        static_smem = std::max(static_smem, fa.sharedSizeBytes);
+    }
+    const long budget = std::min<long>((long)optin - (long)static_smem - 1024,
                                        (long)max_tail_bytes());
-    // the tail: the finest coarse level from which every level fits in shared memory
     // the tail: the finest coarse level from which everything fits in shared memory, or
     // fits once that top level is left in HBM/L2 (read in place by CTA 0)
+    const std::vector<int> widths = slice_widths(h);
     int tl = h->nlev;
     for (int l = 1; l < h->nlev && tl == h->nlev; l++) {
-        std::vector<Op> tp;
-        Builder bt{h, &tp, h->nlev + 1};
-        bt.btilde(l);
         for (int top_gmem = 0; top_gmem <= 1; top_gmem++) {
             TailLayout Y;
-            if (tail_layout(h, l, sizeof(T), (int)tp.size(), top_gmem != 0, Y) && Y.bytes <= budget) {
+            if (tail_layout(h, l, sizeof(T), top_gmem != 0, widths, Y) && Y.bytes <= budget) {
                 tl = l;
                 E->lay = Y;
                 break;
@@ -956,36 +1215,40 @@ void build_engine(amg_hierarchy *h) {
     Builder b{h, &E->hprog, tl};
     b.bhat(0, V_RHS, V_E);
     annotate_reductions(E->hprog);
+    E->tail_color_words = 0;
     if (tl < h->nlev) {
-        Builder bt{h, &E->htail, h->nlev + 1};
+        Builder bt{h, &E->htail, h->nlev + 1};  // the tail's ops (traffic accounting only)
         bt.btilde(tl);
+        std::vector<int> words;
+        for (int l = tl; l < h->nlev; l++)
+            words.insert(words.end(), h->lev[l].color_rows.begin(), h->lev[l].color_rows.end());
+        E->tail_color_words = (int)words.size();
+        E->tail_colors = halloc<int>(h, words.size());
+        AMG_CUDA(cudaMemcpyAsync(E->tail_colors, words.data(), sizeof(int) * words.size(),
+                                 cudaMemcpyHostToDevice, s));
+        AMG_CUDA(cudaStreamSynchronize(s));  // words is a local
     }
     E->tail_bytes = 0;
     for (const Op &op : E->htail) E->tail_bytes += op_bytes(h, op, sizeof(T));
-    E->cycle_bytes = E->tail_bytes * 0;
+    E->cycle_bytes = 0;
     for (const Op &op : E->hprog)
         E->cycle_bytes += (op.kind == OP_TAIL) ? E->tail_bytes
                           : (op.kind == OP_NOP) ? 0.0 : op_bytes(h, op, sizeof(T));
     E->nops = (int)E->hprog.size();
-    E->tail_nops = (int)E->htail.size();
     E->prog = halloc<Op>(h, E->hprog.size());
     AMG_CUDA(cudaMemcpyAsync(E->prog, E->hprog.data(), sizeof(Op) * E->hprog.size(),
                              cudaMemcpyHostToDevice, s));
-    if (E->tail_nops) {
-        E->tail_prog = halloc<Op>(h, E->htail.size());
-        AMG_CUDA(cudaMemcpyAsync(E->tail_prog, E->htail.data(), sizeof(Op) * E->htail.size(),
-                                 cudaMemcpyHostToDevice, s));
-    }
     E->smem = tl < h->nlev ? (size_t)E->lay.bytes : 0;
-    AMG_CUDA(cudaFuncSetAttribute(k_cycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    void *kern = cycle_kernel<T>(E->lay.W);
+    AMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)E->smem));
     int per_sm = 0;
-    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle<T>, kPThreads, E->smem));
+    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, E->smem));
     if (per_sm < 1) throw Error{AMG_ERR_CUDA, "persistent cycle kernel cannot be resident"};
     E->grid = nsm;  // one CTA per SM (co-resident: cooperative launch)
     E->ts = halloc<unsigned long long>(h, E->hprog.size() + 1);
-    E->tprof = halloc<unsigned long long>(h, 32);
-    AMG_CUDA(cudaMemsetAsync(E->tprof, 0, 32 * sizeof(unsigned long long), s));
+    E->tprof = halloc<unsigned long long>(h, 2 * kTprofCount);
+    AMG_CUDA(cudaMemsetAsync(E->tprof, 0, 2 * kTprofCount * sizeof(unsigned long long), s));
 }
 
 template <class T>
@@ -1044,8 +1307,8 @@ void launch_cycle(amg_hierarchy *h) {
     a.tab = dtab<T>(h);
     a.prog = E->prog;
     a.nops = E->nops;
-    a.tail_prog = E->tail_prog;
-    a.tail_nops = E->tail_nops;
+    a.tail_colors = E->tail_colors;
+    a.tail_color_words = E->tail_color_words;
     a.lay = E->lay;
     a.partials = h->cyc_partials;
     a.bar = h->bar;
@@ -1060,8 +1323,8 @@ void launch_cycle(amg_hierarchy *h) {
         rec = h->prof->begin(K_CYCLE, 0, E->cycle_bytes, s);
     }
     void *args[] = {&a};
-    AMG_CUDA(cudaLaunchCooperativeKernel((void *)k_cycle<T>, dim3(E->grid), dim3(kPThreads), args,
-                                         E->smem, s));
+    AMG_CUDA(cudaLaunchCooperativeKernel(cycle_kernel<T>(E->lay.W), dim3(E->grid),
+                                         dim3(kPThreads), args, E->smem, s));
     AMG_LAUNCH_CHECK();
     if (prof) h->prof->end(rec, s);
 }
@@ -1081,14 +1344,17 @@ void harvest_cycle_timestamps(amg_hierarchy *h) {
                        : (op.kind == OP_NOP) ? 0.0 : op_bytes(h, op, sizeof(T));
         h->prof->add(K_IN_CYCLE + op.kind, op.level, ms, bytes);
     }
-    // inside the tail: SM cycles per op kind, reported at the nominal clock of this device
-    unsigned long long tp[32];
-    AMG_CUDA(cudaMemcpy(tp, E->tprof, sizeof tp, cudaMemcpyDeviceToHost));
-    AMG_CUDA(cudaMemset(E->tprof, 0, sizeof tp));
+    // inside the tail: SM cycles per op kind and level, reported at the nominal clock
+    std::vector<unsigned long long> tp(2 * kTprofCount);
+    AMG_CUDA(cudaMemcpy(tp.data(), E->tprof, sizeof(unsigned long long) * tp.size(),
+                        cudaMemcpyDeviceToHost));
+    AMG_CUDA(cudaMemset(E->tprof, 0, sizeof(unsigned long long) * tp.size()));
     int khz = 0;
     AMG_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, h->device));
-    for (int k = 0; k < 16; k++)
-        if (tp[16 + k]) h->prof->add(K_IN_TAIL + k, E->lay.tl, (double)tp[k] / khz, 0.0, (int64_t)tp[16 + k]);
+    for (int slot = 0; slot < kTprofCount; slot++)
+        if (tp[kTprofCount + slot])
+            h->prof->add(K_IN_TAIL + (slot & 15), slot / 16, (double)tp[slot] / khz, 0.0,
+                         (int64_t)tp[kTprofCount + slot]);
 }
 
 // standalone execution of B^_l (diagnostic path): one kernel per op, every level in HBM
@@ -1510,10 +1776,11 @@ void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double 
         AMG_CUDA(cudaStreamSynchronize(s));
         return;
     }
-    if (level == 0) {
+    if (level == 0) {  // the solve's preconditioner, in the configured cycle precision
+        if (h->opt.cycle_prec == AMG_FP32) ensure_fp32(h);
         k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, f_nat, h->ro);
         AMG_LAUNCH_CHECK();
-        launch_cycle<double>(h);
+        apply_preconditioner(h);
         k_scatter<<<nblocks_for(n, 256), 256, 0, s>>>(n, lv.nat, h->zo, z_nat);
         AMG_LAUNCH_CHECK();
         AMG_CUDA(cudaStreamSynchronize(s));

@@ -71,3 +71,24 @@ def test_fgmres_short_restart(amg, oracle_mod):
 def test_full_size_quasi_uniform_fp32(amg, oracle_mod):
     prob, aux = workload("quasi_uniform_1025")
     _check(amg, oracle_mod, prob, dict(aux_level=aux), amg.OUTER_FGMRES, amg.FP32)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_fp32_cycle_matches_oracle(amg, oracle_mod, case):
+    """One application of the FP32 cycle (Alg. 2 with Alg. 1 on the coarse levels) against the
+    oracle's FP64 B^_0. The FP32 cycle is the same sequence of operations as the FP64 one with
+    every vector entry, matrix entry and product rounded to FP32 (unit roundoff 6e-8); a few
+    hundred dependent roundings through a contraction keep the relative distance near 1e-6,
+    and a wrong step of the cycle would show as an O(1) difference."""
+    spec, opts = CASES[case]
+    prob = p1_poisson(**spec)
+    G = amg.Hierarchy.from_problem(prob, cycle_prec=amg.FP32, **opts)
+    O = oracle_mod.Hierarchy.from_problem(prob, **opts)
+    f = np.random.default_rng(7 + case).standard_normal(prob.n)
+    z = G.apply_cycle(0, f)
+    zo = O.bhat(0, f)
+    rel = np.linalg.norm(z - zo) / np.linalg.norm(zo)
+    print(f"FP32 cycle vs oracle: {rel:.2e}")
+    assert rel <= 1e-5, rel
+    # and the same call twice gives the same bits (fixed-order reductions)
+    assert np.array_equal(G.apply_cycle(0, f), z)
