@@ -222,17 +222,19 @@ int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const int32_t *c
  * Diagnostics.
  * ------------------------------------------------------------------------------------- */
 
-/* Kernel launches made by the last amg_setup and the last amg_solve on h (graph replays
- * count every kernel node of the graph). */
+/* Kernel launches made by the last amg_setup and the last amg_solve on h. */
 int amg_launch_counts(const amg_hierarchy *h, int64_t *setup_launches, int64_t *solve_launches);
 
 /*
- * Per-kernel timing: with enable = 1, every kernel of the following solves is bracketed by
- * CUDA events on the hierarchy's stream (also inside the captured cycle graph), and its
- * duration is accumulated per (kernel kind, level) together with its algorithmic bytes: the
- * bytes of every array it must read or write once at its width (4-byte indices, value width
- * of the cycle precision; no padding). Enabling or disabling resets the totals. Timing adds
- * event nodes between kernels; measure throughput with profiling off.
+ * Per-kernel timing. enable = 0: off. enable = 1 or 2: every kernel of the following solves
+ * is bracketed by CUDA events on the hierarchy's stream and its duration is accumulated per
+ * (kernel kind, level) together with its algorithmic bytes: the bytes of every array it must
+ * read or write once at its width (4-byte indices, value width of the cycle precision; no
+ * padding). Inside the persistent cycle kernel every op is timed from in-kernel timestamps
+ * (each op's time includes the grid barrier that ends it); with enable = 1 the ops of the
+ * shared-memory tail are also timed one by one (SM clock cycles, which adds work to the tail),
+ * with enable = 2 the tail is timed as a whole. Enabling or disabling resets the totals.
+ * Measure throughput with profiling off. Errors: AMG_ERR_INVALID_ARG for another value.
  */
 int amg_profile_enable(amg_hierarchy *h, int enable);
 

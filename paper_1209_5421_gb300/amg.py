@@ -246,7 +246,9 @@ class Hierarchy:
         _check(lib().amg_launch_counts(self.h, _ptr(s), _ptr(v)), "amg_launch_counts")
         return int(s[0]), int(v[0])
 
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool | int = True):
+        """0/False: off; 1/True: per-kernel and per-op timing, tail ops one by one; 2: the
+        same with the shared-memory tail timed as a whole (no per-op work added to it)."""
         _check(lib().amg_profile_enable(self.h, int(enable)), "amg_profile_enable")
 
     def profile_read(self) -> list[dict]:

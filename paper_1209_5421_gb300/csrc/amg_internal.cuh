@@ -50,6 +50,7 @@ struct Sell {
     float *val32 = nullptr;  // FP32 copy of val (FP32 cycle only)
     int64_t padded = 0;
     int64_t stored = 0;
+    int uw = 0;              // > 0: every slice has this width (sl_ptr[s] = 32 uw s)
 };
 
 template <class T>
@@ -216,7 +217,7 @@ inline void bind_stream(amg_hierarchy *h, void *user_stream) {
 
 void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y);
 void free_engines(amg_hierarchy *h);
-void profiler_enable(amg_hierarchy *h, bool on);
+void profiler_enable(amg_hierarchy *h, int mode);
 void profiler_free(amg_hierarchy *h);
 int profiler_read(const amg_hierarchy *h, int cap, int32_t *kind, int32_t *level,
                   int64_t *launches, double *ms, double *bytes);

@@ -428,7 +428,8 @@ int amg_profile_enable(amg_hierarchy *h, int enable) {
     if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
     try {
         AMG_CUDA(cudaStreamSynchronize(h->stream));
-        amg::profiler_enable(h, enable != 0);
+        if (enable < 0 || enable > 2) return fail(AMG_ERR_INVALID_ARG, "profiling mode is 0, 1 or 2");
+        amg::profiler_enable(h, enable);
         return AMG_OK;
     }
     AMG_CATCH

@@ -51,6 +51,7 @@ struct LevelDev {
     using idx_t = I;
     int n;
     int fine;                       // 1 on the finest level (block smoother, bptr)
+    int w;                          // > 0: every slice has width w (sl not read)
     const int *sl;
     const I *col;
     const T *val;
@@ -95,9 +96,14 @@ struct StagedLevel {
 template <class T, class I>
 __device__ __forceinline__ void row_span(const LevelDev<T, I> &L, int i, int &base, int &width) {
     const int s = i >> 5;
-    const int a = L.sl[s];
-    base = a + (i & 31);
-    width = (L.sl[s + 1] - a) >> 5;
+    if (L.w > 0) {
+        width = L.w;
+        base = s * 32 * width + (i & 31);
+    } else {
+        const int a = L.sl[s];
+        base = a + (i & 31);
+        width = (L.sl[s + 1] - a) >> 5;
+    }
 }
 template <class T, int W>
 __device__ __forceinline__ void row_span(const StagedLevel<T, W> &L, int i, int &base,
@@ -426,25 +432,19 @@ __device__ void op_prolong(const LV &L, const typename LV::val_t *e, typename LV
 
 // e = A^{-1} rhs with the dense inverse of the coarsest level, g lanes per row (g = largest
 // power of two <= 32 with g * n <= nth) and a shuffle tree. The FP64 cycle accumulates in
-// FP64. The FP32 cycle keeps the same accuracy with FP32 instructions (FP64 throughput is
-// scarce on this GPU): the inverse is stored as a pair of floats (high + low) and products
-// and sums are carried as unevaluated float pairs, with Dekker's exact product (one fma)
-// and Knuth's two-sum giving each rounding error exactly; the pair is rounded to FP32 at the
-// end, as the FP64 sum is.
-// (the _rn intrinsics keep the compiler from fusing these steps into FMAs, which would
-// break their exactness)
+// FP64. The FP32 cycle keeps that accuracy with FP32 instructions (FP64 throughput is
+// scarce on this GPU): the inverse is stored as float pairs (high + low) and the row sum is
+// the compensated dot product "Dot2" of Ogita, Rump and Oishi (Accurate sum and dot
+// product, SIAM J. Sci. Comput. 26, 2005): each product is split exactly into a float and
+// its rounding error (one fma), each running sum into a float and its rounding error
+// (Knuth's two-sum), and the errors are summed on the side; the result is as accurate as a
+// sum in twice the working precision, rounded once to FP32 at the end as the FP64 sum is.
+// Only the running sum's addition is on the loop-carried path.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    // (the _rn intrinsics keep these steps from being fused into FMAs)
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// (sh, sl) += (ph, pl) for float pairs with |pl| <= ulp(ph) and |sl| <= ulp(sh)
-__device__ __forceinline__ void pair_add(float &sh, float &sl, float ph, float pl) {
-    float s, e;
-    two_sum(sh, ph, s, e);
-    e = __fadd_rn(e, __fadd_rn(sl, pl));
-    sh = __fadd_rn(s, e);
-    sl = __fsub_rn(e, __fsub_rn(sh, s));
 }
 
 template <class LV>
@@ -457,22 +457,28 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
     for (int base = 0; base < n; base += rows_per_pass) {
         const int i = base + tid / g;
         if constexpr (sizeof(T) == 4) {
-            float sh = 0.f, sl = 0.f;
+            float s = 0.f, c = 0.f;  // running sum, sum of all rounding errors
             if (i < n) {
                 const float *ah = L.Ainv2 + (size_t)i * n, *al = ah + (size_t)n * n;
                 for (int j = sub; j < n; j += g) {
                     const float x = L.rhs[j];
                     const float ph = __fmul_rn(ah[j], x);
-                    const float pl = fmaf(al[j], x, fmaf(ah[j], x, -ph));  // error of ph + low part
-                    pair_add(sh, sl, ph, pl);
+                    const float pe = fmaf(al[j], x, fmaf(ah[j], x, -ph));  // error + low part
+                    float t, e;
+                    two_sum(s, ph, t, e);
+                    s = t;
+                    c = __fadd_rn(c, __fadd_rn(e, pe));
                 }
             }
-            for (int o = g >> 1; o > 0; o >>= 1) {
-                const float oh = __shfl_down_sync(0xffffffffu, sh, o, g);
-                const float ol = __shfl_down_sync(0xffffffffu, sl, o, g);
-                pair_add(sh, sl, oh, ol);
+            for (int o = g >> 1; o > 0; o >>= 1) {  // combine lanes: (s, c) + (s', c')
+                const float so = __shfl_down_sync(0xffffffffu, s, o, g);
+                const float co = __shfl_down_sync(0xffffffffu, c, o, g);
+                float t, e;
+                two_sum(s, so, t, e);
+                s = t;
+                c = __fadd_rn(c, __fadd_rn(co, e));
             }
-            if (i < n && sub == 0) L.e[i] = sh + sl;
+            if (i < n && sub == 0) L.e[i] = __fadd_rn(s, c);
         } else {
             double s = 0.0;
             if (i < n) {
@@ -504,6 +510,17 @@ __device__ void op_multidot(const LV &L, const Op &op, const RedCtx &rc, int tid
     reduce_store<kMaxKcycle, RM, T>(v, out, rc, op.red_pb, g);
 }
 
+// a / b for an Alg. 1 coefficient: in FP64 for the FP64 cycle, in FP32 for the FP32 cycle
+// (whose vectors are FP32; an FP64 division is a long dependent chain of FP64 operations,
+// which run at a small fraction of the FP32 rate on this GPU)
+template <class T>
+__device__ __forceinline__ double ratio(double a, double b) {
+    if constexpr (sizeof(T) == 4)
+        return (double)__fdiv_rn((float)a, (float)b);
+    else
+        return a / b;
+}
+
 // p_i = z + sum_j beta_ij p_j, beta_ij = -(z, p_j)_A / (p_j, p_j)_A  (Alg. 1, step 2).
 // The coefficients are computed once per CTA (FP64 division is scarce on this GPU) and
 // broadcast through shared memory.
@@ -515,7 +532,7 @@ __device__ void op_orth(const LV &L, const Op &op, int tid, int nth, const G &g)
     if (threadIdx.x < kMaxKcycle) {
         const int j = threadIdx.x;
         double pq = L.sc[SC_PQ0 + j];
-        beta_s[j] = (j < i && pq > 0.0) ? -L.sc[SC_ZQ0 + j] / pq : 0.0;
+        beta_s[j] = (j < i && pq > 0.0) ? -ratio<T>(L.sc[SC_ZQ0 + j], pq) : 0.0;
     }
     g.sync();
     T beta[kMaxKcycle];
@@ -567,7 +584,7 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
         const bool prev_stop =
             i > 0 && (L.sc[SC_STOP0 + i - 1] != 0.0 || L.sc[SC_RR0 + i - 1] == 0.0);
         const bool stopped = prev_stop || !(pq > 0.0) || !isfinite(pq);
-        coef[0] = stopped ? 0.0 : L.sc[SC_RP0 + i] / pq;
+        coef[0] = stopped ? 0.0 : ratio<T>(L.sc[SC_RP0 + i], pq);
         coef[1] = stopped ? 1.0 : 0.0;
     }
     g.sync();

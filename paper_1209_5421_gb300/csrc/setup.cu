@@ -254,6 +254,26 @@ __global__ void k_slice_width(int n, int nslices, const int *__restrict__ len, i
     if (lane == 0) sw[s] = 32 * v;
 }
 
+// out[0] = max of v[0..n) (one block)
+__global__ void k_max_int(int n, const int *__restrict__ v, int *__restrict__ out) {
+    __shared__ int part[kT];
+    int m = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = max(m, v[i]);
+    part[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] = max(part[threadIdx.x], part[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = part[0];
+}
+
+// sl[s] = s * slots for s <= nslices (every slice `slots` = 32 w entries)
+__global__ void k_uniform_slices(int nslices, int slots, int *__restrict__ sl) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= nslices) sl[s] = s * slots;
+}
+
 // fine operator in pi order: row p <- input row nat[p], diagonal in slot 0, then the other
 // entries in CSR order, columns renumbered to pi order
 __global__ void k_fill_csr(int n, const int *__restrict__ nat, const int *__restrict__ inv,
@@ -506,8 +526,11 @@ int bits_for(int64_t maxval) {  // bits to hold values in [0, maxval]
     return b;
 }
 
-// sliced-ELL slice pointers from row lengths; returns padded size
-int64_t slice_pointers(amg_hierarchy *h, Sell &A, int n, const int *len) {
+// sliced-ELL slice pointers from row lengths; returns padded size. With `uniform`, every
+// slice gets the widest slice's width when that costs little (width <= 9, the 3x3-cell
+// stencil of a span-1 coarse level, or <= 25% more slots): a row's first slot is then
+// computed, not loaded, which takes one dependent memory round trip off every row kernel.
+int64_t slice_pointers(amg_hierarchy *h, Sell &A, int n, const int *len, bool uniform) {
     cudaStream_t s = h->stream;
     A.n = n;
     A.nslices = (n + 31) / 32;
@@ -518,6 +541,21 @@ int64_t slice_pointers(amg_hierarchy *h, Sell &A, int n, const int *len) {
     AMG_LAUNCH_CHECK();
     exclusive_scan(sw, A.sl_ptr, A.nslices, A.sl_ptr + A.nslices, s);
     A.padded = read_int(A.sl_ptr + A.nslices, s);
+    A.uw = 0;
+    if (uniform) {
+        int *d_max = tmp.get<int>(1);
+        k_max_int<<<1, kT, 0, s>>>(A.nslices, sw, d_max);
+        AMG_LAUNCH_CHECK();
+        const int wmax = read_int(d_max, s) / 32;
+        const int64_t up = (int64_t)A.nslices * 32 * wmax;
+        if (wmax > 0 && up <= INT32_MAX && (wmax <= 9 || up * 4 <= A.padded * 5)) {
+            k_uniform_slices<<<nblocks_for(A.nslices + 1, kT), kT, 0, s>>>(A.nslices, 32 * wmax,
+                                                                         A.sl_ptr);
+            AMG_LAUNCH_CHECK();
+            A.padded = up;
+            A.uw = wmax;
+        }
+    }
     A.col = halloc<int>(h, A.padded);
     A.val = halloc<double>(h, A.padded);
     return A.padded;
@@ -593,7 +631,7 @@ void galerkin(amg_hierarchy *h, Level &f, Level &c, bool fine) {
     int *scanned = tmp.get<int>(c.n);
     exclusive_scan(len, scanned, c.n, d_tot, s);
     c.A.stored = read_int(d_tot, s);
-    slice_pointers(h, c.A, c.n, len);
+    slice_pointers(h, c.A, c.n, len, true);
     color_nnz(h, c, len);
     if (fine) launch_rap<true>(h, f, c, true, nullptr);
     else launch_rap<false>(h, f, c, true, nullptr);
@@ -739,7 +777,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         int *len = tmp.get<int>(n);
         k_rowlen_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, nullptr, Ain.rowptr, len);
         AMG_LAUNCH_CHECK();
-        slice_pointers(h, F.A, n, len);
+        slice_pointers(h, F.A, n, len, false);
         k_fill_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, nullptr, nullptr, Ain.rowptr, Ain.col,
                                                      Ain.val, F.A.sl_ptr, F.A.col, F.A.val);
         AMG_LAUNCH_CHECK();
@@ -791,7 +829,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         int *len = tmp.get<int>(n);
         k_rowlen_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, Ain.rowptr, len);
         AMG_LAUNCH_CHECK();
-        slice_pointers(h, F.A, n, len);
+        slice_pointers(h, F.A, n, len, false);
         k_fill_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, F.inv, Ain.rowptr, Ain.col, Ain.val,
                                                      F.A.sl_ptr, F.A.col, F.A.val);
         AMG_LAUNCH_CHECK();

@@ -314,6 +314,7 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
                 SLev<T> &S = *reinterpret_cast<SLev<T> *>(tail_gview);
                 S.n = G.n;
                 S.fine = 0;
+                S.w = G.w;
                 S.sl = G.sl;
                 S.col = G.col16;
                 S.val = G.val;
@@ -398,17 +399,27 @@ __device__ void run_tail(const CycleArgs<T> &a) {
 }
 
 // sum the per-CTA partials of the previous op (every CTA, identical order) into sc; one
-// warp does it in FP64
+// warp does it, in FP64 for the FP64 cycle and in FP32 for the FP32 cycle (whose per-CTA
+// partials are FP32 sums)
 template <class T>
 __device__ __forceinline__ void finalize(const CycleArgs<T> &a, const GLev<T> *tab, const Op &op) {
     if (threadIdx.x < 32) {
         const int G = gridDim.x;
         double *sc = tab[op.fin_level].sc;
         for (int k = 0; k < op.fin_n; k++) {
-            double y = 0.0;
-            for (int b = threadIdx.x; b < G; b += 32)
-                y += __ldcg(&a.partials[((size_t)op.fin_pb * 4 + k) * G + b]);
-            y = warp_sum(y);
+            const double *part = a.partials + ((size_t)op.fin_pb * 4 + k) * G;
+            double y;
+            if constexpr (sizeof(T) == 4) {
+                float x = 0.f;
+                for (int b = threadIdx.x; b < G; b += 32) x += (float)__ldcg(&part[b]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                y = (double)x;
+            } else {
+                y = 0.0;
+                for (int b = threadIdx.x; b < G; b += 32) y += __ldcg(&part[b]);
+                y = warp_sum(y);
+            }
             if (threadIdx.x == 0 && op.fin_dst[k] >= 0) sc[op.fin_dst[k]] = y;
         }
     }
@@ -431,20 +442,27 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
     }
     if (blockIdx.x == 0 && a.lay.tl < a.lay.nlev) stage_tail(a);
     __syncthreads();
+    // the op descriptors pass through shared memory: a few threads fetch the next one while
+    // the CTA waits at the barrier, and every thread reads its fields from there (a per-thread
+    // copy would cost every thread a 72-byte global load and a local-memory round trip)
+    __shared__ Op sop[2];
+    constexpr int kOpWords = (int)(sizeof(Op) / sizeof(int));
+    if (threadIdx.x < kOpWords) ((int *)&sop[0])[threadIdx.x] = ((const int *)a.prog)[threadIdx.x];
+    __syncthreads();
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnth = gridDim.x * blockDim.x;
     const RedCtx rc{a.partials, nullptr};
-    Op op = a.prog[0];
     for (int k = 0; k < a.nops; k++) {
+        const Op &op = sop[k & 1];
         if (op.fin_pb >= 0) finalize(a, gtab, op);
         if (op.kind == OP_TAIL) {
             if (blockIdx.x == 0) run_tail<T, W>(a);
         } else if (op.kind != OP_NOP) {
             run_op<GLev<T>, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
         }
-        const Op next = a.prog[k + 1 < a.nops ? k + 1 : k];  // fetched while waiting
+        if (threadIdx.x < kOpWords && k + 1 < a.nops)  // the other buffer: last read by op k-1
+            ((int *)&sop[(k + 1) & 1])[threadIdx.x] = ((const int *)(a.prog + k + 1))[threadIdx.x];
         if (!grid_barrier(a.bar, a.err, target, abort_flag)) break;
         if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
-        op = next;
     }
 }
 
@@ -733,6 +751,7 @@ struct Profiler {
         cudaEvent_t a, b;
     };
     bool on = false;
+    bool tail_ops = false;  // also time every op inside the shared-memory tail
     std::vector<Rec> pending;
     struct Acc {
         int64_t launches = 0;
@@ -781,9 +800,10 @@ struct Profiler {
     }
 };
 
-void profiler_enable(amg_hierarchy *h, bool on) {
+void profiler_enable(amg_hierarchy *h, int mode) {
     if (!h->prof) h->prof = new Profiler();
-    h->prof->on = on;
+    h->prof->on = mode != 0;
+    h->prof->tail_ops = mode == 1;
     h->prof->acc.clear();
 }
 
@@ -1029,6 +1049,7 @@ void fill_tables(amg_hierarchy *h) {
         std::memset(&d, 0, sizeof d);
         d.n = lv.n;
         d.fine = (l == 0) ? 1 : 0;
+        d.w = lv.A.uw;
         d.sl = lv.A.sl_ptr;
         d.col = lv.A.col;
         if constexpr (sizeof(T) == 8) d.val = (const T *)lv.A.val;
@@ -1315,7 +1336,7 @@ void launch_cycle(amg_hierarchy *h) {
     a.err = h->err_flag;
     AMG_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), s));
     a.ts = prof ? E->ts + 1 : nullptr;
-    a.tprof = prof ? E->tprof : nullptr;
+    a.tprof = (prof && h->prof->tail_ops) ? E->tprof : nullptr;
     Profiler::Rec rec{};
     if (prof) {
         k_timestamp<<<1, 1, 0, s>>>(E->ts);
@@ -1444,6 +1465,7 @@ static GLev<double> fine_view(amg_hierarchy *h) {
     std::memset(&L, 0, sizeof L);
     Level &lv = h->lev[0];
     L.n = lv.n;
+    L.w = lv.A.uw;
     L.sl = lv.A.sl_ptr;
     L.col = lv.A.col;
     L.val = lv.A.val;
