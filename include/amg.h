@@ -129,6 +129,60 @@ int amg_hierarchy_bytes(const amg_hierarchy *h, size_t *bytes);
 /* Release a hierarchy and its device memory (NULL is ignored). */
 void amg_free(amg_hierarchy *h);
 
+/*
+ * Batched systems. The paper solves one system at a time and has no counterpart of these
+ * calls: they apply the setup and solve above to many independent systems at once. Each
+ * system gets its own hierarchy, exactly as amg_setup would build it from its block; the
+ * solve runs every system's outer iteration and AMLI-cycle in one persistent kernel, one
+ * CTA per system at a time (largest systems first), with flexible CG as the outer method.
+ */
+typedef struct amg_batch amg_batch;
+
+/*
+ *   nprob   : number of systems (>= 1).
+ *   row_off : host array of nprob + 1 row offsets, row_off[0] = 0, strictly increasing,
+ *             row_off[nprob] = A->n: system p owns rows [row_off[p], row_off[p+1]).
+ *   A       : the block-diagonal matrix of all systems as one CSR (global row pointers and
+ *             global column indices; every column of a row of system p lies in system p),
+ *             device or host, borrowed.
+ *   x, y    : node coordinates of every row, A->n doubles each (device or host).
+ *   opt     : options of every system (aux_level 0 = chosen per system); outer must be
+ *             AMG_OUTER_FCG. NULL = defaults.
+ *   out     : receives the batch (owned by the library until amg_batch_free).
+ * Errors: as amg_setup (a system's failure fails the call), AMG_ERR_UNSUPPORTED for the
+ * FGMRES outer method. On error *out is NULL.
+ */
+int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                    const double *y, const amg_options *opt, void *stream, amg_batch **out);
+
+/*
+ * Solves every system: b and x hold all right-hand sides / solutions concatenated in row_off
+ * order (A->n doubles each, device or host; x caller-allocated). iters, relres, status: host
+ * arrays of nprob entries receiving each system's outer iterations, true relative residual
+ * and status (as amg_solve would return it); each may be NULL. The first call also times the
+ * candidate launch shapes on this batch (every timed solve is a complete solve) and keeps
+ * the fastest; the launch sequence is captured in a CUDA graph and replayed while b, x and
+ * tol stay the same. Returns AMG_OK if every system converged, else the first non-OK system
+ * status in system order.
+ */
+int amg_batch_solve(amg_batch *bt, const double *b, double tol, double *x, int32_t *iters,
+                    double *relres, int32_t *status, void *stream);
+
+/*
+ * nprob: systems; threads, ctas: the launch shape chosen by the first solve (0 before it);
+ * tuned_ms: one batch solve's time for each of the 4 candidate shapes (1024 threads x 1 CTA
+ * per SM, 512 x 2, 512 x 1, 256 x 4; -1 if not timed); bytes: device memory of the batch
+ * with its hierarchies. Each output may be NULL.
+ */
+int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_t *ctas,
+                   double tuned_ms[4], size_t *bytes);
+
+/* System p's hierarchy (owned by the batch; valid until amg_batch_free), NULL if none. */
+amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p);
+
+/* Release a batch, its hierarchies and its device memory (NULL is ignored). */
+void amg_batch_free(amg_batch *bt);
+
 /* Static, human-readable text of a status code. */
 const char *amg_status_string(int status);
 

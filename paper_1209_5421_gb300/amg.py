@@ -83,6 +83,16 @@ def lib():
         L.amg_profile_read.argtypes = [P, C.c_int, P, P, P, P, P, C.POINTER(C.c_int)]
         L.amg_kernel_name.argtypes = [C.c_int]
         L.amg_kernel_name.restype = C.c_char_p
+        L.amg_batch_setup.argtypes = [C.c_int32, P, C.POINTER(Csr), P, P, C.POINTER(Options), P,
+                                      C.POINTER(P)]
+        L.amg_batch_solve.argtypes = [P, P, C.c_double, P, P, P, P, P]
+        L.amg_batch_info.argtypes = [P, P, P, P, P, P]
+        L.amg_batch_system.argtypes = [P, C.c_int32]
+        L.amg_batch_system.restype = P
+        L.amg_batch_free.argtypes = [P]
+        L.amg_batch_free.restype = None
+        for f in ("amg_batch_setup", "amg_batch_solve", "amg_batch_info"):
+            getattr(L, f).restype = C.c_int
         for f in ("amg_setup", "amg_solve", "amg_hierarchy_bytes", "amg_num_levels",
                   "amg_get_bbox", "amg_level_info", "amg_level_export", "amg_apply_cycle",
                   "amg_smooth", "amg_csr_to_ell", "amg_csr_to_ell_noalloc", "amg_launch_counts",
@@ -293,3 +303,88 @@ def csr_to_ell(rowptr, col, val, width, diag_first=True, stream=None):
                                 int(diag_first), _ptr(Aj), _ptr(Ax), _stream(stream)),
            "amg_csr_to_ell")
     return Aj, Ax
+
+
+class Batch:
+    """amg_batch_setup / amg_batch_solve: many independent systems, one persistent kernel.
+
+    problems: list of (rowptr, col, val, x, y) of each system (local indexing, host arrays);
+    they are concatenated into one block-diagonal CSR here (the layout the C ABI takes).
+    """
+
+    def __init__(self, problems, aux_level=0, coarsest_max=64, kcycle_n=2, max_iters=200,
+                 cycle_prec=FP64, stream=None, device=None):
+        L = lib()
+        sizes = [len(p[0]) - 1 for p in problems]
+        nnzs = [len(p[1]) for p in problems]
+        row_off = np.zeros(len(problems) + 1, np.int64)
+        row_off[1:] = np.cumsum(sizes)
+        nz_off = np.zeros(len(problems) + 1, np.int64)
+        nz_off[1:] = np.cumsum(nnzs)
+        rp = np.concatenate([np.asarray(p[0], np.int64)[:-1] + nz_off[k]
+                             for k, p in enumerate(problems)] + [nz_off[-1:]]).astype(np.int32)
+        cl = np.concatenate([np.asarray(p[1], np.int64) + row_off[k]
+                             for k, p in enumerate(problems)]).astype(np.int32)
+        vl = np.concatenate([np.asarray(p[2], np.float64) for p in problems])
+        xx = np.concatenate([np.asarray(p[3], np.float64) for p in problems])
+        yy = np.concatenate([np.asarray(p[4], np.float64) for p in problems])
+        arrays = [rp, cl, vl, xx, yy]
+        if device is not None:
+            import torch
+
+            arrays = [torch.as_tensor(a).to(device) for a in arrays]
+        rp, cl, vl, xx, yy = arrays
+        self.row_off = row_off
+        self.n = int(row_off[-1])
+        self.nprob = len(problems)
+        A = Csr(self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(vl))
+        o = Options()
+        L.amg_options_default(C.byref(o))
+        o.aux_level, o.coarsest_max, o.kcycle_n, o.max_iters = aux_level, coarsest_max, kcycle_n, max_iters
+        o.cycle_prec, o.outer = cycle_prec, OUTER_FCG
+        b = C.c_void_p()
+        st = L.amg_batch_setup(self.nprob, row_off.ctypes.data, C.byref(A), _ptr(xx), _ptr(yy),
+                               C.byref(o), _stream(stream), C.byref(b))
+        _check(st, "amg_batch_setup")
+        self.b = b
+
+    @classmethod
+    def from_problems(cls, probs, **kw):
+        return cls([(p.rowptr, p.col, p.val, p.x, p.y) for p in probs], **kw)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().amg_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, rhs, tol=1e-8, x=None, stream=None):
+        """All systems: rhs concatenated (numpy or device tensor). Returns (x, iters, relres,
+        status) with per-system numpy arrays; the call's own status is max-severity first."""
+        rhs = _as(rhs, np.float64)
+        if x is None:
+            x = np.empty(self.n) if isinstance(rhs, np.ndarray) else rhs.new_empty(self.n)
+        it = np.zeros(self.nprob, np.int32)
+        rr = np.zeros(self.nprob, np.float64)
+        st = np.zeros(self.nprob, np.int32)
+        r = lib().amg_batch_solve(self.b, _ptr(rhs), tol, _ptr(x), it.ctypes.data,
+                                  rr.ctypes.data, st.ctypes.data, _stream(stream))
+        if r not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(r, "amg_batch_solve")
+        return x, it, rr, st
+
+    def info(self) -> dict:
+        n = C.c_int32()
+        t = C.c_int32()
+        c = C.c_int32()
+        ms = (C.c_double * 4)()
+        nb = C.c_size_t()
+        _check(lib().amg_batch_info(self.b, C.byref(n), C.byref(t), C.byref(c), ms, C.byref(nb)),
+               "amg_batch_info")
+        return {"nprob": n.value, "threads": t.value, "ctas": c.value,
+                "tuned_ms": list(ms), "bytes": nb.value}

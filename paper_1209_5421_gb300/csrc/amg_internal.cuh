@@ -226,6 +226,24 @@ void allocate_solve_workspace(amg_hierarchy *h);
 int solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
           double *relres);
 void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double *z_nat);
+void prepare_cycle(amg_hierarchy *h);
+const void *level_table(const amg_hierarchy *h, bool fp32);
+
+// ---- batched solves (batch.cu) ------------------------------------------------------------
+struct BatchEngine;
+// hierarchies of the systems (built, not owned); row_off[p] = first row of system p in the
+// concatenated vectors (nprob + 1 entries); every hierarchy has the same options
+BatchEngine *batch_create(const std::vector<amg_hierarchy *> &hs, const std::vector<int64_t> &row_off,
+                          cudaStream_t stream);
+void batch_destroy(BatchEngine *E);
+size_t batch_bytes(const BatchEngine *E);
+// b, x: device, concatenated; per-system results into host arrays (may be null); returns
+// AMG_OK or the first failing system's status
+int batch_solve(BatchEngine *E, const double *b, double tol, double *x, int *iters,
+                double *relres, int *status);
+// chosen launch shape (-1 before the first solve): threads per CTA, CTAs, and the time of
+// one solve of the batch for every candidate shape (ms, -1 if not runnable)
+int batch_shape(const BatchEngine *E, int *threads, int *ctas, double *tuned_ms);
 void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
                   double *u_nat);
 

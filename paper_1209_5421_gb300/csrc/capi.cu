@@ -143,19 +143,10 @@ const char *amg_status_string(int s) {
     }
 }
 
-int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_options *opt,
-              void *stream, amg_hierarchy **out) {
-    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (!A || !x || !y || !A->rowptr || !A->col || !A->val)
-        return fail(AMG_ERR_INVALID_ARG, "NULL argument");
-    if (A->n <= 0) return fail(AMG_ERR_INVALID_ARG, "n must be positive");
-    if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
-        return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
-    if (A->nnz < A->n) return fail(AMG_ERR_BAD_MATRIX, "every row needs its diagonal");
-    amg_options o;
-    if (opt) o = *opt;
-    else amg_options_default(&o);
+namespace {
+
+// option checks shared by amg_setup and amg_batch_setup
+int check_options(const amg_options &o) {
     if (o.aux_level < 0 || o.aux_level > 14) return fail(AMG_ERR_UNSUPPORTED, "aux_level must be 0..14");
     if (o.coarsest_max < 1 || o.coarsest_max > amg::kMaxCoarsest)
         return fail(AMG_ERR_UNSUPPORTED, "coarsest_max must be 1..256");
@@ -172,42 +163,66 @@ int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_opti
         return fail(AMG_ERR_INVALID_ARG, "fgmres_restart");
     if (o.has_bbox && !(o.bbox[1] > o.bbox[0] && o.bbox[3] > o.bbox[2]))
         return fail(AMG_ERR_INVALID_ARG, "bbox must have b1 > a1 and b2 > a2");
+    return AMG_OK;
+}
+
+// a hierarchy from device arrays (A's arrays, x, y on the device); throws amg::Error
+amg_hierarchy *setup_device(const amg_csr &Ad, const double *xd, const double *yd,
+                            const amg_options &o, void *stream) {
     amg_hierarchy *h = nullptr;
     try {
         h = new amg_hierarchy();
         h->opt = o;
-        h->N = A->n;
+        h->N = Ad.n;
         AMG_CUDA(cudaGetDevice(&h->device));
         init_pool_once(h->device);
         AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
         AMG_CUDA(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
         amg::bind_stream(h, stream);
-        const int n = (int)A->n;
-        Scratch tmp(h->stream);
-        amg_csr Ad = *A;
-        Ad.rowptr = to_device(A->rowptr, (size_t)n + 1, tmp);
-        Ad.col = to_device(A->col, (size_t)A->nnz, tmp);
-        Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
-        const double *xd = to_device(x, (size_t)n, tmp);
-        const double *yd = to_device(y, (size_t)n, tmp);
         const int64_t l0 = amg::g_launches;
         h->err_flag = amg::halloc<int>(h, 1);
         amg::build_hierarchy(h, Ad, xd, yd);
         amg::allocate_solve_workspace(h);
         AMG_CUDA(cudaStreamSynchronize(h->stream));
         h->setup_launches = amg::g_launches - l0;
-        *out = h;
-        return AMG_OK;
-    } catch (const Error &e) {
-        destroy(h);
-        return fail(e.status, e.what);
-    } catch (const std::bad_alloc &) {
-        destroy(h);
-        return fail(AMG_ERR_OOM, "host allocation failed");
+        return h;
     } catch (...) {
         destroy(h);
-        return fail(AMG_ERR_CUDA, "unexpected internal exception");
+        throw;
     }
+}
+
+}  // namespace
+
+int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_options *opt,
+              void *stream, amg_hierarchy **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A || !x || !y || !A->rowptr || !A->col || !A->val)
+        return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (A->n <= 0) return fail(AMG_ERR_INVALID_ARG, "n must be positive");
+    if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
+        return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
+    if (A->nnz < A->n) return fail(AMG_ERR_BAD_MATRIX, "every row needs its diagonal");
+    amg_options o;
+    if (opt) o = *opt;
+    else amg_options_default(&o);
+    if (int st = check_options(o)) return st;
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Scratch tmp(us);
+        const int n = (int)A->n;
+        amg_csr Ad = *A;
+        Ad.rowptr = to_device(A->rowptr, (size_t)n + 1, tmp);
+        Ad.col = to_device(A->col, (size_t)A->nnz, tmp);
+        Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
+        const double *xd = to_device(x, (size_t)n, tmp);
+        const double *yd = to_device(y, (size_t)n, tmp);
+        *out = setup_device(Ad, xd, yd, o, stream);
+        AMG_CUDA(cudaStreamSynchronize(us));  // the staging copies are read by the setup
+        return AMG_OK;
+    }
+    AMG_CATCH
 }
 
 int amg_solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
@@ -241,6 +256,170 @@ int amg_hierarchy_bytes(const amg_hierarchy *h, size_t *bytes) {
 }
 
 void amg_free(amg_hierarchy *h) { destroy(h); }
+
+// ---------------------------------------------------------------------------------------
+// batched systems
+
+struct amg_batch {
+    std::vector<amg_hierarchy *> hs;
+    std::vector<int64_t> row_off;
+    amg::BatchEngine *eng = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t order_ev = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+void destroy_batch(amg_batch *bt) {
+    if (!bt) return;
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    amg::batch_destroy(bt->eng);
+    for (amg_hierarchy *h : bt->hs) destroy(h);
+    if (bt->order_ev) cudaEventDestroy(bt->order_ev);
+    if (bt->stream) cudaStreamDestroy(bt->stream);
+    delete bt;
+}
+
+// rowptr[r0 + i] - nz0 and col[nz0 + k] - r0: the rows of one system, indexed locally
+__global__ void k_localize_rows(int n, const int *__restrict__ rowptr, int nz0,
+                                int *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) out[i] = rowptr[i] - nz0;
+}
+__global__ void k_localize_cols(int nnz, const int *__restrict__ col, int r0, int *__restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) out[k] = col[k] - r0;
+}
+
+}  // namespace
+
+int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                    const double *y, const amg_options *opt, void *stream, amg_batch **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || !row_off || !A || !x || !y || !A->rowptr || !A->col || !A->val)
+        return fail(AMG_ERR_INVALID_ARG, "NULL argument or no system");
+    if (is_device_ptr(row_off)) return fail(AMG_ERR_INVALID_ARG, "row_off must be host memory");
+    if (row_off[0] != 0 || row_off[nprob] != A->n)
+        return fail(AMG_ERR_INVALID_ARG, "row_off must run from 0 to A->n");
+    for (int p = 0; p < nprob; p++)
+        if (row_off[p + 1] <= row_off[p]) return fail(AMG_ERR_INVALID_ARG, "every system needs a row");
+    if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
+        return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
+    amg_options o;
+    if (opt) o = *opt;
+    else amg_options_default(&o);
+    if (int st = check_options(o)) return st;
+    if (o.outer != AMG_OUTER_FCG)
+        return fail(AMG_ERR_UNSUPPORTED, "batched systems use the flexible-CG outer iteration");
+    amg_batch *bt = nullptr;
+    try {
+        bt = new amg_batch();
+        AMG_CUDA(cudaGetDevice(&bt->device));
+        init_pool_once(bt->device);
+        AMG_CUDA(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
+        AMG_CUDA(cudaEventCreateWithFlags(&bt->order_ev, cudaEventDisableTiming));
+        cudaStream_t us = (cudaStream_t)stream;
+        Scratch tmp(us);
+        const size_t N = (size_t)A->n;
+        const int *rp = to_device(A->rowptr, N + 1, tmp);
+        const int *cl = to_device(A->col, (size_t)A->nnz, tmp);
+        const double *vl = to_device(A->val, (size_t)A->nnz, tmp);
+        const double *xd = to_device(x, N, tmp);
+        const double *yd = to_device(y, N, tmp);
+        // nonzero offset of every system: rowptr[row_off[p]]
+        std::vector<int> nz(nprob + 1);
+        for (int p = 0; p <= nprob; p++)
+            AMG_CUDA(cudaMemcpyAsync(&nz[p], rp + row_off[p], sizeof(int), cudaMemcpyDeviceToHost, us));
+        AMG_CUDA(cudaStreamSynchronize(us));
+        if (nz[0] != 0 || nz[nprob] != A->nnz)
+            throw Error{AMG_ERR_BAD_MATRIX, "rowptr does not run from 0 to nnz"};
+        bt->row_off.assign(row_off, row_off + nprob + 1);
+        for (int p = 0; p < nprob; p++) {
+            const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
+            const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
+            if (nnz < n) throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
+            Scratch loc(us);
+            int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
+            k_localize_rows<<<(n + 256) / 256, 256, 0, us>>>(n, rp + r0, z0, lrp);
+            k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
+            AMG_CUDA(cudaGetLastError());
+            amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
+            bt->hs.push_back(setup_device(Ap, xd + r0, yd + r0, o, stream));
+        }
+        bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream);
+        AMG_CUDA(cudaStreamSynchronize(us));
+        *out = bt;
+        return AMG_OK;
+    } catch (const Error &e) {
+        destroy_batch(bt);
+        return fail(e.status, e.what);
+    } catch (const std::bad_alloc &) {
+        destroy_batch(bt);
+        return fail(AMG_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        destroy_batch(bt);
+        return fail(AMG_ERR_CUDA, "unexpected internal exception");
+    }
+}
+
+int amg_batch_solve(amg_batch *bt, const double *b, double tol, double *x, int32_t *iters,
+                    double *relres, int32_t *status, void *stream) {
+    if (!bt || !b || !x) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol >= 0.0)) return fail(AMG_ERR_INVALID_ARG, "tol must be >= 0");
+    try {
+        AMG_CUDA(cudaEventRecord(bt->order_ev, (cudaStream_t)stream));
+        AMG_CUDA(cudaStreamWaitEvent(bt->stream, bt->order_ev, 0));
+        const size_t N = (size_t)bt->row_off.back();
+        Scratch tmp(bt->stream);
+        const double *bd = to_device(b, N, tmp);
+        const bool xhost = !is_device_ptr(x);
+        double *xd = xhost ? tmp.get<double>(N) : x;
+        std::vector<int> it(bt->hs.size()), st(bt->hs.size());
+        int r = amg::batch_solve(bt->eng, bd, tol, xd, it.data(), relres, st.data());
+        if (xhost) {
+            AMG_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * N, cudaMemcpyDeviceToHost, bt->stream));
+            AMG_CUDA(cudaStreamSynchronize(bt->stream));
+        }
+        for (size_t p = 0; p < bt->hs.size(); p++) {
+            if (iters) iters[p] = it[p];
+            if (status) status[p] = st[p];
+        }
+        if (r != AMG_OK) g_last_error = amg_status_string(r);
+        return r;
+    }
+    AMG_CATCH
+}
+
+int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_t *ctas,
+                   double tuned_ms[4], size_t *bytes) {
+    if (!bt) return fail(AMG_ERR_INVALID_ARG, "NULL batch");
+    if (nprob) *nprob = (int32_t)bt->hs.size();
+    int t = 0, c = 0;
+    double ms[4] = {-1, -1, -1, -1};
+    const int shape = amg::batch_shape(bt->eng, &t, &c, ms);
+    if (threads) *threads = shape < 0 ? 0 : t;
+    if (ctas) *ctas = shape < 0 ? 0 : c;
+    if (tuned_ms)
+        for (int k = 0; k < 4; k++) tuned_ms[k] = ms[k];
+    if (bytes) {
+        size_t s = amg::batch_bytes(bt->eng);
+        for (amg_hierarchy *h : bt->hs) s += h->bytes;
+        *bytes = s;
+    }
+    return AMG_OK;
+}
+
+amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p) {
+    if (!bt || p < 0 || p >= (int32_t)bt->hs.size()) {
+        fail(AMG_ERR_INVALID_ARG, "no such system");
+        return nullptr;
+    }
+    return bt->hs[p];
+}
+
+void amg_batch_free(amg_batch *bt) { destroy_batch(bt); }
 
 int amg_num_levels(const amg_hierarchy *h, int *num_levels, int *aux_level) {
     if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");

@@ -1405,6 +1405,27 @@ void run_standalone(amg_hierarchy *h, int l, int fsel, int zsel) {
 
 }  // namespace
 
+// the cycle's level copies in its precision (FP32 copies are made once, on first use)
+void prepare_cycle(amg_hierarchy *h) {
+    if (h->opt.cycle_prec != AMG_FP32 || h->fp32_ready) return;
+    if (h->nlev > 1) {
+        ensure_fp32(h);
+        return;
+    }
+    // one level: the cycle is the exact solve (high/low float inverse) on FP32 vectors
+    h->r32 = halloc<float>(h, h->N);
+    h->z32 = halloc<float>(h, h->N);
+    h->lev[0].v32.rhs = h->r32;
+    h->lev[0].v32.e = h->z32;
+    fill_tables<float>(h);
+    h->fp32_ready = true;
+}
+
+// device level table of the cycle precision (LevelDev<T, int>[nlev])
+const void *level_table(const amg_hierarchy *h, bool fp32) {
+    return fp32 ? h->lev_tab32 : h->lev_tab64;
+}
+
 void allocate_solve_workspace(amg_hierarchy *h) {
     const int n = (int)h->N;
     h->red_partials = halloc<double>(h, (size_t)kRedBlocks * std::max(8, h->opt.max_iters + 8));

@@ -50,3 +50,32 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(libpath):
     assert L.amg_setup(ctypes.byref(A), None, None, None, None, ctypes.byref(h)) == amg.ERR_INVALID_ARG
     assert h.value is None
     assert L.amg_setup(None, None, None, None, None, None) == amg.ERR_INVALID_ARG
+
+
+def test_batch_setup_rejects_bad_arguments_before_touching_the_gpu(libpath):
+    L = amg.lib()
+    b = ctypes.c_void_p()
+    rp = (ctypes.c_int32 * 3)(0, 1, 2)
+    cl = (ctypes.c_int32 * 2)(0, 1)
+    vl = (ctypes.c_double * 2)(1.0, 1.0)
+    xy = (ctypes.c_double * 2)(0.0, 1.0)
+    A = amg.Csr(2, 2, ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(cl, ctypes.c_void_p),
+                ctypes.cast(vl, ctypes.c_void_p))
+    xp = ctypes.cast(xy, ctypes.c_void_p)
+    bad_offsets = [(0, 2, 2), (0, 1, 3), (1, 1, 2), (0, 2, 1)]  # empty, past n, not from 0, ...
+    for offs in bad_offsets:
+        ro = (ctypes.c_int64 * 3)(*offs)
+        st = L.amg_batch_setup(2, ctypes.cast(ro, ctypes.c_void_p), ctypes.byref(A), xp, xp, None,
+                               None, ctypes.byref(b))
+        assert st == amg.ERR_INVALID_ARG, offs
+        assert b.value is None
+    ro = (ctypes.c_int64 * 3)(0, 1, 2)
+    assert L.amg_batch_setup(0, ctypes.cast(ro, ctypes.c_void_p), ctypes.byref(A), xp, xp, None,
+                             None, ctypes.byref(b)) == amg.ERR_INVALID_ARG
+    o = amg.Options()
+    L.amg_options_default(ctypes.byref(o))
+    o.outer = amg.OUTER_FGMRES
+    assert L.amg_batch_setup(2, ctypes.cast(ro, ctypes.c_void_p), ctypes.byref(A), xp, xp,
+                             ctypes.byref(o), None, ctypes.byref(b)) == amg.ERR_UNSUPPORTED
+    assert L.amg_batch_solve(None, None, 1e-8, None, None, None, None, None) == amg.ERR_INVALID_ARG
+    L.amg_batch_free(None)

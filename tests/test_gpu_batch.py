@@ -1,0 +1,115 @@
+"""GPU: batched systems (amg_batch_setup / amg_batch_solve) against the oracle.
+
+Every system of a batch is solved by one CTA of one persistent kernel with the same
+hierarchy amg_setup builds. Each system's solution must meet the tolerance in FP64 (true
+residual recomputed here), agree with the oracle's solution as closely as two converged
+solves of the same system can (1e-6 relative, the bound the FP32-cycle tests use), take about
+the oracle's number of outer iterations, and be the same when the system is solved alone.
+"""
+import numpy as np
+import pytest
+
+from paper_1209_5421_gb300.meshes import p1_poisson
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    from paper_1209_5421_gb300 import amg as A
+    from paper_1209_5421_gb300 import build
+
+    build.build()
+    return A
+
+
+# uneven sizes, a graded mesh with coefficient jumps, and a system small enough to have one
+# level (its "cycle" is the exact dense solve)
+SPECS = [
+    dict(n=65, jitter=0.2, seed=0, rhs="normal"),
+    dict(n=17, jitter=0.2, seed=1, rhs="normal"),
+    dict(n=97, jitter=0.1, graded=True, kappa_blocks=16, seed=2, rhs="normal"),
+    dict(n=45, jitter=0.2, seed=3, rhs="normal"),
+    dict(n=6, jitter=0.1, seed=4, rhs="normal"),
+    dict(n=129, jitter=0.2, seed=5, rhs="normal"),
+]
+
+
+def _check_system(amg, oracle_mod, prob, x, it, rr, st, tol, slack):
+    assert st == amg.OK, st
+    A = prob.to_scipy()
+    true_rel = np.linalg.norm(prob.b - A @ x) / np.linalg.norm(prob.b)
+    assert true_rel <= tol, true_rel
+    assert abs(rr - true_rel) <= 1e-3 * tol + 1e-14, (rr, true_rel)
+    O = oracle_mod.Hierarchy.from_problem(prob)
+    xo, ito, _, _ = O.solve(prob.b, tol)
+    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+    assert err <= 1e-6, err
+    assert it <= ito + slack, (it, ito)
+    return err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_matches_oracle(amg, oracle_mod, prec):
+    probs = [p1_poisson(**s) for s in SPECS]
+    cp = amg.FP32 if prec == "fp32" else amg.FP64
+    B = amg.Batch.from_problems(probs, cycle_prec=cp)
+    rhs = np.concatenate([p.b for p in probs])
+    tol = 1e-8
+    x, it, rr, st = B.solve(rhs, tol)
+    info = B.info()
+    assert info["nprob"] == len(probs) and info["threads"] in (256, 512, 1024)
+    assert info["ctas"] >= 1 and info["bytes"] > 0
+    off = B.row_off
+    for k, p in enumerate(probs):
+        slack = 10 if SPECS[k].get("graded") else 3
+        _check_system(amg, oracle_mod, p, x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, slack)
+    # a second solve replays the captured launch: same bits
+    x2, it2, _, _ = B.solve(rhs, tol)
+    assert np.array_equal(x2, x) and np.array_equal(it2, it)
+    B.close()
+
+
+def test_system_alone_and_in_the_batch(amg):
+    probs = [p1_poisson(**s) for s in SPECS]
+    tol = 1e-8
+    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP32)
+    xb, itb, _, _ = B.solve(np.concatenate([p.b for p in probs]), tol)
+    off = B.row_off
+    for k in (0, 2):
+        alone = amg.Batch.from_problems([probs[k]], cycle_prec=amg.FP32)
+        xa, ita, _, sta = alone.solve(probs[k].b, tol)
+        assert sta[0] == amg.OK
+        xk = xb[off[k]:off[k + 1]]
+        assert np.linalg.norm(xa - xk) / np.linalg.norm(xk) <= 1e-6
+        assert abs(int(ita[0]) - int(itb[k])) <= 1
+        # and against the single-system solver on the same system
+        H = amg.Hierarchy.from_problem(probs[k], cycle_prec=amg.FP32)
+        xs, its, _, sts = H.solve(probs[k].b, tol)
+        assert sts == amg.OK
+        assert np.linalg.norm(xs - xk) / np.linalg.norm(xk) <= 1e-6
+        assert abs(its - int(itb[k])) <= 1
+        alone.close()
+        H.close()
+    B.close()
+
+
+def test_batch_device_buffers_and_zero_rhs(amg):
+    import torch
+
+    probs = [p1_poisson(**s) for s in SPECS[:4]]
+    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP32, device="cuda")
+    rhs = np.concatenate([p.b for p in probs])
+    off = B.row_off
+    rhs[off[1]:off[2]] = 0.0  # system 1 has b = 0: x = 0 after no iteration
+    xd, it, rr, st = B.solve(torch.as_tensor(rhs).cuda(), 1e-8)
+    x = xd.cpu().numpy()
+    assert (st == amg.OK).all()
+    assert it[1] == 0 and rr[1] == 0.0 and not x[off[1]:off[2]].any()
+    xh, ith, _, _ = B.solve(rhs, 1e-8)  # host buffers: the same numbers
+    assert np.array_equal(xh, x) and np.array_equal(ith, it)
+    B.close()
