@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-systems", type=int, default=256)
     return ap.parse_args()
 
 
@@ -243,6 +245,91 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batched(args, world, flush, dev, stream):
+    """The batched form: `batch_systems` independent jittered P1 Poisson systems of uneven
+    sizes (n x n nodes, n log-uniform in [45, 450]) solved together by one persistent kernel
+    (FP32 cycle, FP64 flexible-CG outer, tol as the headline), hierarchies resident. Beside
+    it: the plain FP64 method (single-system solver, FP64 cycle) on a sample of the same
+    systems solved one after another, and the batch's own FP64-cycle form."""
+    import torch
+
+    from paper_1209_5421_gb300 import amg
+    from paper_1209_5421_gb300.meshes import batch_workload
+
+    probs = batch_workload(count=args.batch_systems)
+    rhs = torch.as_tensor(np.concatenate([p.b for p in probs])).to(dev)
+    x = torch.empty_like(rhs)
+    res = {}
+    for name, prec in (("fp32", amg.FP32), ("fp64", amg.FP64)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = amg.Batch.from_problems(probs, cycle_prec=prec, device=dev)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        for _ in range(max(3, args.warmup)):  # the first solve also picks the launch shape
+            flush.fill_(1.0)
+            B.solve(rhs, args.tol, x=x)
+        lat, its, rrs, sts, sys_lat = [], None, None, None, []
+        barrier(world)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, its, rrs, sts = B.solve(rhs, args.tol, x=x)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(ev0.elapsed_time(ev1))
+            sys_lat.extend((B.timeline()[1] / 1e6).tolist())
+        barrier(world)
+        t = max_over_ranks(world, sum(lat))
+        info = B.info()
+        B.close()
+        if not (sts == amg.OK).all():
+            raise RuntimeError(f"batched {name}: statuses {sorted(set(sts.tolist()))}")
+        res[name] = {
+            "value": round(world * len(probs) * args.steps / (t / 1e3), 2), "unit": "solves/s",
+            "ms_per_batch": round(t / args.steps, 3),
+            "setup_ms": round(1e3 * setup_s, 1),
+            "with_setup": round(len(probs) / (setup_s + t / args.steps / 1e3), 2),
+            "system_latency_ms": {"p50": round(float(np.percentile(sys_lat, 50)), 3),
+                                  "p99": round(float(np.percentile(sys_lat, 99)), 3)},
+            "iters": [int(its.min()), int(its.max())], "relres_max": float(rrs.max()),
+            "launch_shape": {"threads": info["threads"], "ctas": info["ctas"],
+                             "tuned_ms": [round(v, 2) for v in info["tuned_ms"]]},
+            "device_bytes": info["bytes"],
+        }
+    # the plain FP64 method, one system at a time (every 16th system, hierarchies resident)
+    sample = probs[::16]
+    hs = [amg.Hierarchy.from_problem(p, cycle_prec=amg.FP64) for p in sample]
+    bs = [torch.as_tensor(p.b).to(dev) for p in sample]
+    xs = [torch.empty_like(b) for b in bs]
+    for h, b, xx in zip(hs, bs, xs):
+        h.solve(b, args.tol, x=xx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, b, xx in zip(hs, bs, xs):
+        _, _, _, st = h.solve(b, args.tol, x=xx)
+        if st != amg.OK:
+            raise RuntimeError(f"single-system FP64 solve failed: {st}")
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    return {
+        "workload": f"{len(probs)} jittered P1 Poisson systems, n x n nodes, n log-uniform in "
+                    f"[45, 450] ({sum(p.n for p in probs)} unknowns)",
+        "method": "FP32 AMLI-cycle, FP64 flexible-CG outer, one CTA per system",
+        **res.pop("fp32"),
+        "fp64_cycle_batched": res["fp64"],
+        "fp64_plain_sequential": {
+            "value": round(len(sample) / seq, 2), "unit": "solves/s",
+            "sample": f"every 16th system ({len(sample)} systems, "
+                      f"{sum(p.n for p in sample)} unknowns), single-system FP64 solver, "
+                      "one after another"},
+    }
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -378,6 +465,8 @@ def run_ours(args, world, rank, local):
                     "ms_per_launch": dom["ms"] / dom["launches"],
                     "launches_in_solve": dom["launches"]}
 
+    batched = None if args.no_batch else run_batched(args, world, flush, dev, stream)
+
     out = None
     if rank == 0:
         cpu = None
@@ -410,6 +499,7 @@ def run_ours(args, world, rank, local):
             "fp64_plain": fp64_line,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         if kernels:
             out["kernels"] = sorted(

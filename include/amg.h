@@ -177,6 +177,13 @@ int amg_batch_solve(amg_batch *bt, const double *b, double tol, double *x, int32
 int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_t *ctas,
                    double tuned_ms[4], size_t *bytes);
 
+/*
+ * When each system of the last amg_batch_solve started and finished on the device: host
+ * arrays of nprob entries, ns after the earliest start (device clock); each may be NULL.
+ * end_ns is each system's latency from the launch of the batch.
+ */
+int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns);
+
 /* System p's hierarchy (owned by the batch; valid until amg_batch_free), NULL if none. */
 amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p);
 

@@ -87,6 +87,8 @@ def lib():
                                       C.POINTER(P)]
         L.amg_batch_solve.argtypes = [P, P, C.c_double, P, P, P, P, P]
         L.amg_batch_info.argtypes = [P, P, P, P, P, P]
+        L.amg_batch_timeline.argtypes = [P, P, P]
+        L.amg_batch_timeline.restype = C.c_int
         L.amg_batch_system.argtypes = [P, C.c_int32]
         L.amg_batch_system.restype = P
         L.amg_batch_free.argtypes = [P]
@@ -388,3 +390,10 @@ class Batch:
                "amg_batch_info")
         return {"nprob": n.value, "threads": t.value, "ctas": c.value,
                 "tuned_ms": list(ms), "bytes": nb.value}
+
+    def timeline(self):
+        """(start_ns, end_ns) of every system in the last solve, after the earliest start."""
+        a = np.zeros(self.nprob, np.int64)
+        e = np.zeros(self.nprob, np.int64)
+        _check(lib().amg_batch_timeline(self.b, a.ctypes.data, e.ctypes.data), "amg_batch_timeline")
+        return a, e

@@ -244,6 +244,8 @@ int batch_solve(BatchEngine *E, const double *b, double tol, double *x, int *ite
 // chosen launch shape (-1 before the first solve): threads per CTA, CTAs, and the time of
 // one solve of the batch for every candidate shape (ms, -1 if not runnable)
 int batch_shape(const BatchEngine *E, int *threads, int *ctas, double *tuned_ms);
+// per-system start / end of the last solve (ns after the earliest start; host arrays)
+void batch_timeline(const BatchEngine *E, int64_t *start_ns, int64_t *end_ns);
 void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
                   double *u_nat);
 

@@ -343,7 +343,8 @@ template <class T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_batch(const BatchProb<T> *__restrict__ probs, const int *__restrict__ order, int nprob,
         int *next, int kc, const double *__restrict__ b, double *__restrict__ x, double tol,
-        int maxit, int *iters, double *relres, int *status) {
+        int maxit, int *iters, double *relres, int *status, unsigned long long *t_start,
+        unsigned long long *t_end) {
     __shared__ BatchProb<T> sp;
     __shared__ BLev<T> stab[kMaxLevels];
     __shared__ int q;
@@ -366,7 +367,9 @@ k_batch(const BatchProb<T> *__restrict__ probs, const int *__restrict__ order, i
         }
         __syncthreads();
         BatchCycle<T> cyc{stab, sp.colors, sp.cofs, sp.ncol, sp.nlev, kc};
+        if (threadIdx.x == 0) t_start[p] = global_ns();
         solve_one(sp, cyc, b, x, tol, maxit, iters, relres, status, p);
+        if (threadIdx.x == 0) t_end[p] = global_ns();
         // (solve_one ends with a barrier: q may be overwritten)
     }
 }
@@ -402,6 +405,7 @@ struct BatchEngine {
     void *probs = nullptr;  // BatchProb<T>[nprob]
     int *order = nullptr, *next = nullptr, *iters = nullptr, *status = nullptr;
     double *relres = nullptr;
+    unsigned long long *t_start = nullptr, *t_end = nullptr;  // per system, device clock (ns)
     int shape = -1;            // chosen launch shape (-1: not tuned yet)
     int grid[kNumShapes] = {};
     double tuned_ms[kNumShapes] = {};
@@ -509,6 +513,8 @@ BatchEngine *batch_create(const std::vector<amg_hierarchy *> &hs, const std::vec
         E->iters = balloc<int>(E, E->nprob);
         E->status = balloc<int>(E, E->nprob);
         E->relres = balloc<double>(E, E->nprob);
+        E->t_start = balloc<unsigned long long>(E, E->nprob);
+        E->t_end = balloc<unsigned long long>(E, E->nprob);
         AMG_CUDA(cudaStreamSynchronize(E->stream));
     } catch (...) {
         batch_destroy(E);
@@ -532,8 +538,9 @@ static void launch_batch(BatchEngine *E, int shape, const double *b, double *x, 
     AMG_CUDA(cudaMemsetAsync(E->next, 0, sizeof(int), E->stream));
     void *kern = E->fp32 ? batch_kernel<float>(shape) : batch_kernel<double>(shape);
     int nprob = E->nprob, kc = E->kc, maxit = E->maxit;
-    void *args[] = {&E->probs, &E->order, &nprob, &E->next, &kc, &b, &x, &tol, &maxit,
-                    &E->iters, &E->relres, &E->status};
+    void *args[] = {&E->probs, &E->order, &nprob, &E->next, &kc,       &b,
+                    &x,        &tol,      &maxit, &E->iters, &E->relres, &E->status,
+                    &E->t_start, &E->t_end};
     AMG_CUDA(cudaLaunchKernel(kern, dim3(E->grid[shape]), dim3(kShapes[shape].threads), args, 0,
                               E->stream));
     AMG_LAUNCH_CHECK();
@@ -603,6 +610,19 @@ int batch_solve(BatchEngine *E, const double *b, double tol, double *x, int *ite
         if (first_bad == AMG_OK && st[p] != AMG_OK) first_bad = st[p];
     }
     return first_bad;
+}
+
+// per-system start and end of the last solve, ns after the earliest start
+void batch_timeline(const BatchEngine *E, int64_t *start_ns, int64_t *end_ns) {
+    std::vector<unsigned long long> a(E->nprob), b(E->nprob);
+    AMG_CUDA(cudaMemcpyAsync(a.data(), E->t_start, 8 * a.size(), cudaMemcpyDeviceToHost, E->stream));
+    AMG_CUDA(cudaMemcpyAsync(b.data(), E->t_end, 8 * b.size(), cudaMemcpyDeviceToHost, E->stream));
+    AMG_CUDA(cudaStreamSynchronize(E->stream));
+    const unsigned long long t0 = *std::min_element(a.begin(), a.end());
+    for (int p = 0; p < E->nprob; p++) {
+        if (start_ns) start_ns[p] = (int64_t)(a[p] - t0);
+        if (end_ns) end_ns[p] = (int64_t)(b[p] - t0);
+    }
 }
 
 int batch_shape(const BatchEngine *E, int *threads, int *ctas, double *tuned_ms) {

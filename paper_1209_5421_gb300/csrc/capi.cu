@@ -411,6 +411,15 @@ int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_
     return AMG_OK;
 }
 
+int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns) {
+    if (!bt) return fail(AMG_ERR_INVALID_ARG, "NULL batch");
+    try {
+        amg::batch_timeline(bt->eng, start_ns, end_ns);
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
 amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p) {
     if (!bt || p < 0 || p >= (int32_t)bt->hs.size()) {
         fail(AMG_ERR_INVALID_ARG, "no such system");

@@ -1261,8 +1261,11 @@ void build_engine(amg_hierarchy *h) {
                              cudaMemcpyHostToDevice, s));
     E->smem = tl < h->nlev ? (size_t)E->lay.bytes : 0;
     void *kern = cycle_kernel<T>(E->lay.W);
+    // the kernel's dynamic shared-memory limit is a property of the function, shared by every
+    // hierarchy of the process: set it to the device maximum (never lower it below what
+    // another hierarchy's launches use); each launch passes its own size
     AMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)E->smem));
+                                  (int)std::max<long>(0, (long)optin - (long)static_smem)));
     int per_sm = 0;
     AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, E->smem));
     if (per_sm < 1) throw Error{AMG_ERR_CUDA, "persistent cycle kernel cannot be resident"};

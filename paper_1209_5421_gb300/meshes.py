@@ -241,3 +241,16 @@ def workload(name: str, **overrides) -> tuple[Problem, int]:
     spec.update(overrides)
     aux = spec.pop("aux_level")
     return p1_poisson(name=name, **spec), aux
+
+
+def batch_workload(count: int = 256, nmin: int = 45, nmax: int = 450, seed: int = 4,
+                   jitter: float = 0.2) -> list[Problem]:
+    """Independent jittered P1 Poisson systems of uneven sizes: system k has n_k x n_k nodes,
+    n_k drawn log-uniform in [nmin, nmax] (so E[(n_k - 2)^2] is about 43k unknowns for the
+    defaults), N(0,1) right-hand side; mesh seed `seed` + k + 1. The auxiliary level is chosen
+    per system (aux_level 0)."""
+    rng = np.random.default_rng(seed)
+    sides = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=count))
+    sides = np.clip(np.rint(sides).astype(int), nmin, nmax)
+    return [p1_poisson(int(m), jitter=jitter, seed=seed + k + 1, rhs="normal",
+                       name=f"batch_{k}_n{int(m)}") for k, m in enumerate(sides)]
