@@ -156,6 +156,22 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
                     const double *y, const amg_options *opt, void *stream, amg_batch **out);
 
 /*
+ * A batch over hierarchies that already exist (built by amg_setup or amg_batch_setup; all
+ * with the same cycle_prec and kcycle_n; borrowed: they must outlive the batch, and a
+ * hierarchy must not be solved by two calls at the same time). System p is hs[p]; its rows in
+ * the concatenated vectors follow those of hs[0..p-1]. threads: 0 = choose the launch shape
+ * by timing on the first solve; 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs
+ * per SM). With a fixed shape a system's result does not depend on the other systems of the
+ * batch (each system is computed by one CTA in a fixed order). The first batched solve of a
+ * hierarchy allocates its outer-iteration workspace (64 FP64 directions, about 1 KB per
+ * unknown), owned by the hierarchy and counted by amg_hierarchy_bytes.
+ * Errors: AMG_ERR_INVALID_ARG (NULL, mixed precisions, a repeated hierarchy, other threads),
+ * AMG_ERR_OOM, AMG_ERR_CUDA.
+ */
+int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, void *stream,
+                     amg_batch **out);
+
+/*
  * Solves every system: b and x hold all right-hand sides / solutions concatenated in row_off
  * order (A->n doubles each, device or host; x caller-allocated). iters, relres, status: host
  * arrays of nprob entries receiving each system's outer iterations, true relative residual
@@ -187,7 +203,8 @@ int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns);
 /* System p's hierarchy (owned by the batch; valid until amg_batch_free), NULL if none. */
 amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p);
 
-/* Release a batch, its hierarchies and its device memory (NULL is ignored). */
+/* Release a batch and its device memory, and the hierarchies amg_batch_setup built (not
+ * those given to amg_batch_create). NULL is ignored. */
 void amg_batch_free(amg_batch *bt);
 
 /* Static, human-readable text of a status code. */

@@ -86,6 +86,8 @@ def lib():
         L.amg_batch_setup.argtypes = [C.c_int32, P, C.POINTER(Csr), P, P, C.POINTER(Options), P,
                                       C.POINTER(P)]
         L.amg_batch_solve.argtypes = [P, P, C.c_double, P, P, P, P, P]
+        L.amg_batch_create.argtypes = [C.c_int32, P, C.c_int32, P, C.POINTER(P)]
+        L.amg_batch_create.restype = C.c_int
         L.amg_batch_info.argtypes = [P, P, P, P, P, P]
         L.amg_batch_timeline.argtypes = [P, P, P]
         L.amg_batch_timeline.restype = C.c_int
@@ -353,6 +355,23 @@ class Batch:
     @classmethod
     def from_problems(cls, probs, **kw):
         return cls([(p.rowptr, p.col, p.val, p.x, p.y) for p in probs], **kw)
+
+    @classmethod
+    def over(cls, hierarchies, threads=0, stream=None):
+        """A batch over existing Hierarchy objects (borrowed: keep them alive)."""
+        self = cls.__new__(cls)
+        hs = (C.c_void_p * len(hierarchies))(*[h.h for h in hierarchies])
+        b = C.c_void_p()
+        _check(lib().amg_batch_create(len(hierarchies), C.cast(hs, C.c_void_p), threads,
+                                      _stream(stream), C.byref(b)), "amg_batch_create")
+        self.b = b
+        self.nprob = len(hierarchies)
+        sizes = [h.n for h in hierarchies]
+        self.row_off = np.zeros(self.nprob + 1, np.int64)
+        self.row_off[1:] = np.cumsum(sizes)
+        self.n = int(self.row_off[-1])
+        self._borrowed = list(hierarchies)
+        return self
 
     def close(self):
         if getattr(self, "b", None):

@@ -89,6 +89,16 @@ struct Level {
 struct Profiler;
 struct EngineBase;
 
+// outer-iteration workspace of a hierarchy solved inside a batch (batch.cu); allocated on the
+// hierarchy's first batched solve and owned by it
+struct BatchWs {
+    int cap = 0;                    // directions kept before a restart
+    double *bo = nullptr, *xo = nullptr, *to = nullptr;
+    double *P = nullptr, *Q = nullptr, *osc = nullptr;
+    int *colors = nullptr;          // colour ranges of every level, concatenated
+    int cofs[kMaxLevels] = {}, ncol[kMaxLevels] = {};
+};
+
 }  // namespace amg
 
 struct amg_hierarchy {
@@ -134,6 +144,7 @@ struct amg_hierarchy {
     void *lev_tab64 = nullptr, *lev_tab32 = nullptr;
     int tail_level = -1;
     bool fp32_ready = false;
+    amg::BatchWs bws;                  // batched solves (allocated on first use)
     // diagnostics: per-op CUDA-event profiling and launch counts (solve.cu)
     amg::Profiler *prof = nullptr;
     int64_t setup_launches = 0, solve_launches = 0;
@@ -233,8 +244,10 @@ const void *level_table(const amg_hierarchy *h, bool fp32);
 struct BatchEngine;
 // hierarchies of the systems (built, not owned); row_off[p] = first row of system p in the
 // concatenated vectors (nprob + 1 entries); every hierarchy has the same options
+// shape_threads: 0 = time the candidate launch shapes on the first solve and keep the
+// fastest; 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs per SM)
 BatchEngine *batch_create(const std::vector<amg_hierarchy *> &hs, const std::vector<int64_t> &row_off,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int shape_threads);
 void batch_destroy(BatchEngine *E);
 size_t batch_bytes(const BatchEngine *E);
 // b, x: device, concatenated; per-system results into host arrays (may be null); returns

@@ -427,24 +427,49 @@ U *balloc(BatchEngine *E, size_t count) {
     return (U *)p;
 }
 
+// the hierarchy's batched-solve workspace, allocated (owned by the hierarchy) on first use
+const BatchWs &batch_ws(amg_hierarchy *h) {
+    BatchWs &w = h->bws;
+    if (w.bo) return w;
+    const size_t n = (size_t)h->N;
+    w.cap = kBatchCap;
+    w.bo = halloc<double>(h, n);
+    w.xo = halloc<double>(h, n);
+    w.to = halloc<double>(h, n);
+    w.P = halloc<double>(h, (size_t)kBatchCap * n);
+    w.Q = halloc<double>(h, (size_t)kBatchCap * n);
+    w.osc = halloc<double>(h, kBatchOsc);
+    std::vector<int> colors;
+    for (int l = 0; l < h->nlev; l++) {
+        const std::vector<int> &r = (l == 0) ? h->lev[0].color_blocks : h->lev[l].color_rows;
+        w.cofs[l] = (int)colors.size();
+        w.ncol[l] = std::max(0, (int)r.size() - 1);
+        colors.insert(colors.end(), r.begin(), r.end());
+    }
+    w.colors = halloc<int>(h, colors.size());
+    AMG_CUDA(cudaMemcpyAsync(w.colors, colors.data(), sizeof(int) * colors.size(),
+                             cudaMemcpyHostToDevice, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));  // colors is a local
+    return w;
+}
+
 template <class T>
 void build_probs(BatchEngine *E) {
     const int np = E->nprob;
     std::vector<BatchProb<T>> hp(np);
-    std::vector<int> colors;
     for (int p = 0; p < np; p++) {
         amg_hierarchy *h = E->hs[p];
+        const BatchWs &w = batch_ws(h);
         BatchProb<T> &B = hp[p];
         std::memset(&B, 0, sizeof B);
         B.n = (int)h->N;
         B.nlev = h->nlev;
         B.off = E->row_off[p];
         B.tab = (const BLev<T> *)level_table(h, sizeof(T) == 4);
-        for (int l = 0; l < h->nlev; l++) {
-            const std::vector<int> &r = (l == 0) ? h->lev[0].color_blocks : h->lev[l].color_rows;
-            B.cofs[l] = (int)colors.size();
-            B.ncol[l] = std::max(0, (int)r.size() - 1);
-            colors.insert(colors.end(), r.begin(), r.end());
+        B.colors = w.colors;
+        for (int l = 0; l < kMaxLevels; l++) {
+            B.cofs[l] = w.cofs[l];
+            B.ncol[l] = w.ncol[l];
         }
         const Level &F = h->lev[0];
         B.A0.n = F.n;
@@ -453,38 +478,37 @@ void build_probs(BatchEngine *E) {
         B.A0.col = F.A.col;
         B.A0.val = F.A.val;
         B.nat = F.nat;
-        const size_t n = (size_t)B.n;
-        B.bo = balloc<double>(E, n);
-        B.xo = balloc<double>(E, n);
+        B.bo = w.bo;
+        B.xo = w.xo;
         B.ro = h->ro;  // the FP64 cycle's level-0 input and output are the outer r and z
         B.zo = h->zo;
-        B.to = balloc<double>(E, n);
-        B.P = balloc<double>(E, kBatchCap * n);
-        B.Q = balloc<double>(E, kBatchCap * n);
-        B.osc = balloc<double>(E, kBatchOsc);
+        B.to = w.to;
+        B.P = w.P;
+        B.Q = w.Q;
+        B.osc = w.osc;
     }
-    int *dcolors = balloc<int>(E, colors.size());
-    AMG_CUDA(cudaMemcpyAsync(dcolors, colors.data(), sizeof(int) * colors.size(),
-                             cudaMemcpyHostToDevice, E->stream));
-    for (int p = 0; p < np; p++) hp[p].colors = dcolors;
     BatchProb<T> *dp = balloc<BatchProb<T>>(E, np);
     AMG_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(BatchProb<T>) * np, cudaMemcpyHostToDevice,
                              E->stream));
     E->probs = dp;
+    int nsm = 0;
+    AMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, E->hs[0]->device));
     for (int s = 0; s < kNumShapes; s++) {
-        int nsm = 0, per = 0;
-        AMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, E->hs[0]->device));
+        int per = 0;
         AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<T>(s),
                                                                kShapes[s].threads, 0));
         E->grid[s] = std::min(np, nsm * std::min(per, kShapes[s].per_sm));
     }
-    AMG_CUDA(cudaStreamSynchronize(E->stream));  // host tables are locals
+    AMG_CUDA(cudaStreamSynchronize(E->stream));  // hp is a local
 }
 
 BatchEngine *batch_create(const std::vector<amg_hierarchy *> &hs, const std::vector<int64_t> &row_off,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int shape_threads) {
     BatchEngine *E = new BatchEngine();
     try {
+        if (shape_threads == 1024) E->shape = 0;
+        else if (shape_threads == 512) E->shape = 1;
+        else if (shape_threads == 256) E->shape = 3;
         E->hs = hs;
         E->row_off = row_off;
         E->nprob = (int)hs.size();

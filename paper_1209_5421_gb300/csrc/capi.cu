@@ -262,6 +262,7 @@ void amg_free(amg_hierarchy *h) { destroy(h); }
 
 struct amg_batch {
     std::vector<amg_hierarchy *> hs;
+    bool owns = true;  // hierarchies built by amg_batch_setup (else borrowed)
     std::vector<int64_t> row_off;
     amg::BatchEngine *eng = nullptr;
     cudaStream_t stream = nullptr;
@@ -275,7 +276,8 @@ void destroy_batch(amg_batch *bt) {
     if (!bt) return;
     if (bt->stream) cudaStreamSynchronize(bt->stream);
     amg::batch_destroy(bt->eng);
-    for (amg_hierarchy *h : bt->hs) destroy(h);
+    if (bt->owns)
+        for (amg_hierarchy *h : bt->hs) destroy(h);
     if (bt->order_ev) cudaEventDestroy(bt->order_ev);
     if (bt->stream) cudaStreamDestroy(bt->stream);
     delete bt;
@@ -348,8 +350,49 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
             amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
             bt->hs.push_back(setup_device(Ap, xd + r0, yd + r0, o, stream));
         }
-        bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream);
+        bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, 0);
         AMG_CUDA(cudaStreamSynchronize(us));
+        *out = bt;
+        return AMG_OK;
+    } catch (const Error &e) {
+        destroy_batch(bt);
+        return fail(e.status, e.what);
+    } catch (const std::bad_alloc &) {
+        destroy_batch(bt);
+        return fail(AMG_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        destroy_batch(bt);
+        return fail(AMG_ERR_CUDA, "unexpected internal exception");
+    }
+}
+
+int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, void *stream,
+                     amg_batch **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || !hs) return fail(AMG_ERR_INVALID_ARG, "no system");
+    if (threads != 0 && threads != 1024 && threads != 512 && threads != 256)
+        return fail(AMG_ERR_INVALID_ARG, "threads must be 0, 1024, 512 or 256");
+    for (int p = 0; p < nprob; p++) {
+        if (!hs[p]) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+        if (hs[p]->opt.cycle_prec != hs[0]->opt.cycle_prec || hs[p]->opt.kcycle_n != hs[0]->opt.kcycle_n)
+            return fail(AMG_ERR_INVALID_ARG, "every hierarchy needs the same cycle_prec and kcycle_n");
+        for (int q = 0; q < p; q++)
+            if (hs[q] == hs[p]) return fail(AMG_ERR_INVALID_ARG, "a hierarchy appears twice");
+    }
+    amg_batch *bt = nullptr;
+    try {
+        bt = new amg_batch();
+        bt->owns = false;
+        AMG_CUDA(cudaGetDevice(&bt->device));
+        AMG_CUDA(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
+        AMG_CUDA(cudaEventCreateWithFlags(&bt->order_ev, cudaEventDisableTiming));
+        AMG_CUDA(cudaEventRecord(bt->order_ev, (cudaStream_t)stream));
+        AMG_CUDA(cudaStreamWaitEvent(bt->stream, bt->order_ev, 0));
+        bt->hs.assign(hs, hs + nprob);
+        bt->row_off.assign(1, 0);
+        for (int p = 0; p < nprob; p++) bt->row_off.push_back(bt->row_off.back() + hs[p]->N);
+        bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, threads);
         *out = bt;
         return AMG_OK;
     } catch (const Error &e) {

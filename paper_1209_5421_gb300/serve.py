@@ -1,0 +1,342 @@
+"""Continuous-batching solve server on one GPU (resident hierarchies, HBM-budget admission).
+
+Requests are (matrix key, right-hand side). A matrix is set up once (amg_setup) and its
+hierarchy stays resident for later right-hand sides until memory is needed: admission
+charges each hierarchy's device bytes (amg_hierarchy_bytes, plus the batched-solve workspace
+it will allocate) against a budget and evicts the least recently used idle hierarchies.
+
+Two lanes share the GPU:
+  * the batch lane: whenever systems are ready, a worker takes all of them (up to
+    `max_batch`) and solves them in one persistent-kernel launch, one CTA per system, on its
+    own CUDA stream (amg_batch_create over the resident hierarchies, fixed launch shape).
+    Several workers run at once, so a system that becomes ready while others are on the GPU
+    starts on free SMs without waiting for them: the device holds CTAs of several batches;
+  * the large lane: a system above `large_unknowns` is solved by the single-system solver
+    (the grid-wide cycle kernel over all SMs). It runs alone: batch workers drain first and
+    wait while it runs.
+Setups run on a separate thread (each on the hierarchy's own stream).
+
+Every system is computed by code whose result does not depend on the other work in flight:
+in the batch lane by one CTA of fixed size, in the large lane by the single-system kernel.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import amg
+
+# device bytes per unknown of the batched-solve workspace a hierarchy allocates on its first
+# batched solve (64 FP64 directions and their images, 3 vectors, colour ranges)
+_BATCH_WS_BYTES_PER_UNKNOWN = 8 * (2 * 64 + 3)
+
+
+@dataclass
+class Request:
+    key: object
+    b: np.ndarray
+    tol: float
+    t_arrival: float
+    lane: str = ""
+    x: np.ndarray | None = None
+    iters: int = -1
+    relres: float = float("nan")
+    status: int = -1
+    t_done: float = 0.0
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class _Resident:
+    def __init__(self, h: amg.Hierarchy, nbytes: int):
+        self.h = h
+        self.nbytes = nbytes
+        self.busy = False
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 150 << 30, cycle_prec: int = amg.FP32,
+                 workers: int = 4, max_batch: int = 152, large_unknowns: int = 250_000,
+                 device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.budget = int(budget_bytes)
+        self.prec = cycle_prec
+        self.max_batch = max_batch
+        self.large = large_unknowns
+        self.matrices: dict = {}                  # key -> (rowptr, col, val, x, y)
+        self.res: OrderedDict = OrderedDict()      # key -> _Resident (LRU order)
+        self.used = 0
+        self.max_used = 0
+        self.cv = threading.Condition()
+        self.need_setup: deque = deque()           # requests whose matrix is not resident
+        self.ready: deque = deque()                # requests whose hierarchy is resident
+        self.setting_up: set = set()
+        self.active_batches = 0
+        self.large_waiting = 0
+        self.large_running = False
+        self.stop = False
+        self.completed: list[Request] = []
+        self.evictions = 0
+        self.setups = 0
+        self.batches = 0
+        self.errors: list[str] = []
+        # setups and large-lane solves never overlap: the grid-wide kernel wants every SM
+        self.grid_lock = threading.Lock()
+        self.threads = [threading.Thread(target=self._setup_loop, daemon=True)]
+        self.threads += [threading.Thread(target=self._batch_loop, daemon=True)
+                         for _ in range(workers)]
+        self.threads.append(threading.Thread(target=self._large_loop, daemon=True))
+        for t in self.threads:
+            t.start()
+
+    # ---- client side ------------------------------------------------------------------
+    def register(self, key, rowptr, col, val, x, y):
+        """Make a matrix known to the server (host arrays); it is set up on first use."""
+        with self.cv:
+            self.matrices[key] = (np.asarray(rowptr, np.int32), np.asarray(col, np.int32),
+                                  np.asarray(val, np.float64), np.asarray(x, np.float64),
+                                  np.asarray(y, np.float64))
+
+    def submit(self, key, b, tol: float = 1e-8) -> Request:
+        r = Request(key, np.ascontiguousarray(b, np.float64), tol, time.perf_counter())
+        with self.cv:
+            if key in self.res:
+                self.res.move_to_end(key)
+                self.ready.append(r)
+            else:
+                self.need_setup.append(r)
+            self.cv.notify_all()
+        return r
+
+    def drain(self, timeout: float = 600.0):
+        """Wait until every submitted request has completed."""
+        t_end = time.perf_counter() + timeout
+        with self.cv:
+            while self.need_setup or self.ready or self.setting_up or self.active_batches \
+                    or self.large_running or self.large_waiting:
+                if self.errors:
+                    raise RuntimeError(self.errors[0])
+                left = t_end - time.perf_counter()
+                if left <= 0:
+                    raise TimeoutError("server did not drain")
+                self.cv.wait(min(left, 0.05))
+            if self.errors:
+                raise RuntimeError(self.errors[0])
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join(timeout=60)
+        for r in self.res.values():
+            r.h.close()
+        self.res.clear()
+
+    def stats(self) -> dict:
+        lat = sorted(r.latency for r in self.completed)
+        if not lat:
+            return {"completed": 0}
+        t0 = min(r.t_arrival for r in self.completed)
+        t1 = max(r.t_done for r in self.completed)
+        return {"completed": len(lat), "solves_per_s": len(lat) / (t1 - t0),
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "setups": self.setups, "evictions": self.evictions, "batches": self.batches,
+                "max_resident_bytes": self.max_used, "budget_bytes": self.budget,
+                "large_lane": sum(r.lane == "large" for r in self.completed)}
+
+    # ---- internals --------------------------------------------------------------------
+    def _fail(self, msg: str):
+        with self.cv:
+            self.errors.append(msg)
+            self.cv.notify_all()
+
+    def _finish(self, r: Request, x, it, rr, st, lane):
+        r.x, r.iters, r.relres, r.status, r.lane = x, int(it), float(rr), int(st), lane
+        r.t_done = time.perf_counter()
+        r.done.set()
+        self.completed.append(r)
+
+    def _admit(self, need: int) -> bool:
+        """Evict idle LRU hierarchies until `need` more bytes fit (caller holds cv)."""
+        if need > self.budget:
+            return False
+        for key in list(self.res.keys()):
+            if self.used + need <= self.budget:
+                break
+            ent = self.res[key]
+            if ent.busy or any(q.key == key for q in self.ready):
+                continue
+            del self.res[key]
+            self.used -= ent.nbytes
+            self.evictions += 1
+            ent.h.close()
+        return self.used + need <= self.budget
+
+    def _setup_loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        while True:
+            with self.cv:
+                while not self.stop and not self.need_setup:
+                    self.cv.wait()
+                if self.stop:
+                    return
+                r = self.need_setup[0]
+                if r.key in self.res:  # set up meanwhile for an earlier request
+                    self.need_setup.popleft()
+                    self.ready.append(r)
+                    self.cv.notify_all()
+                    continue
+                m = self.matrices.get(r.key)
+                if m is None:
+                    self.need_setup.popleft()
+                    self.errors.append(f"unknown matrix {r.key!r}")
+                    self.cv.notify_all()
+                    continue
+                n = len(m[0]) - 1
+                est = int(n * (400 + _BATCH_WS_BYTES_PER_UNKNOWN))  # refined after setup
+                while not self.stop and not self._admit(est):
+                    if est > self.budget:
+                        self.need_setup.popleft()
+                        self.errors.append(f"matrix {r.key!r} does not fit the budget")
+                        self.cv.notify_all()
+                        break
+                    self.cv.wait(0.01)  # wait for hierarchies to become idle
+                else:
+                    self.need_setup.popleft()
+                    self.setting_up.add(r.key)
+                    self.used += est
+                    self.max_used = max(self.max_used, self.used)
+                if self.stop:
+                    return
+                if r.key not in self.setting_up:
+                    continue
+            try:
+                with self.grid_lock:
+                    h = amg.Hierarchy(*m, cycle_prec=self.prec,
+                                      outer=amg.OUTER_FGMRES if n > self.large else amg.OUTER_FCG)
+                    if n <= self.large:  # the cycle copies and batched workspace, allocated now
+                        amg.Batch.over([h], threads=1024).close()
+                nbytes = h.nbytes
+            except Exception as e:  # noqa: BLE001
+                self._fail(f"setup of {r.key!r}: {e}")
+                return
+            with self.cv:
+                self.setting_up.discard(r.key)
+                self.used += nbytes - est
+                self.max_used = max(self.max_used, self.used)
+                self.res[r.key] = _Resident(h, nbytes)
+                self.setups += 1
+                self.ready.append(r)
+                # later requests for the same matrix that queued meanwhile
+                for q in [q for q in self.need_setup if q.key == r.key]:
+                    self.need_setup.remove(q)
+                    self.ready.append(q)
+                self.cv.notify_all()
+
+    def _take_ready(self, large: bool):
+        """Ready requests of one lane whose hierarchy is idle (caller holds cv)."""
+        out, seen = [], set()
+        for q in list(self.ready):
+            ent = self.res.get(q.key)
+            if ent is None or ent.busy or q.key in seen:
+                continue
+            if (ent.h.n > self.large) != large:
+                continue
+            out.append(q)
+            seen.add(q.key)
+            if large or len(out) >= self.max_batch:
+                break
+        for q in out:
+            self.ready.remove(q)
+            self.res[q.key].busy = True
+        return out
+
+    def _batch_loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        stream = torch.cuda.Stream(self.dev)
+        while True:
+            with self.cv:
+                while not self.stop:
+                    if not self.large_running and not self.large_waiting:
+                        batch = self._take_ready(large=False)
+                        if batch:
+                            break
+                    self.cv.wait()
+                if self.stop:
+                    return
+                self.active_batches += 1
+                self.batches += 1
+                hs = [self.res[q.key].h for q in batch]
+            try:
+                with torch.cuda.stream(stream):
+                    B = amg.Batch.over(hs, threads=1024, stream=stream)
+                    rhs = torch.from_numpy(np.concatenate([q.b for q in batch])).to(self.dev)
+                    x, it, rr, st = B.solve(rhs, batch[0].tol if len({q.tol for q in batch}) == 1
+                                            else min(q.tol for q in batch), stream=stream)
+                    xh = x.cpu().numpy()
+                    B.close()
+                off = B.row_off
+                for k, q in enumerate(batch):
+                    self._finish(q, xh[off[k]:off[k + 1]].copy(), it[k], rr[k], st[k], "batch")
+            except Exception as e:  # noqa: BLE001
+                self._fail(f"batch solve: {e}")
+                return
+            finally:
+                with self.cv:
+                    for q in batch:
+                        ent = self.res.get(q.key)
+                        if ent is not None:
+                            ent.busy = False
+                    self.active_batches -= 1
+                    self.cv.notify_all()
+
+    def _large_loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        stream = torch.cuda.Stream(self.dev)
+        while True:
+            with self.cv:
+                while not self.stop:
+                    job = self._take_ready(large=True)
+                    if job:
+                        break
+                    self.cv.wait()
+                if self.stop:
+                    return
+                q = job[0]
+                self.large_waiting += 1
+                while self.active_batches and not self.stop:  # the GPU to itself
+                    self.cv.wait()
+                self.large_waiting -= 1
+                self.large_running = True
+                h = self.res[q.key].h
+            try:
+                with self.grid_lock, torch.cuda.stream(stream):
+                    b = torch.from_numpy(q.b).to(self.dev)
+                    x, it, rr, st = h.solve(b, q.tol, stream=stream)
+                    xh = x.cpu().numpy()
+                self._finish(q, xh, it, rr, st, "large")
+            except Exception as e:  # noqa: BLE001
+                self._fail(f"large solve: {e}")
+                return
+            finally:
+                with self.cv:
+                    self.large_running = False
+                    ent = self.res.get(q.key)
+                    if ent is not None:
+                        ent.busy = False
+                    self.cv.notify_all()
