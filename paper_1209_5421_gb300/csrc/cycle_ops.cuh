@@ -272,12 +272,14 @@ __device__ __forceinline__ int ld_volatile_int(const int *p) {
     return *reinterpret_cast<const volatile int *>(p);
 }
 
-// Monotonic counter barrier: every CTA adds 1 with a release reduction and waits (relaxed
-// polling, then an acquire fence) until the counter reaches (k+1) * gridDim.x for its k-th
-// barrier. The counter is zeroed before every launch. Returns false if the kernel must stop.
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+// Monotonic counter barrier: every CTA adds 1 with a release reduction and polls with acquire
+// loads until the counter reaches (k+1) * gridDim.x for its k-th barrier (the load that sees
+// the last arrival orders every later access after the other CTAs' writes; the CTA's other
+// threads follow through the closing __syncthreads). The counter is zeroed before every
+// launch. Returns false if the kernel must stop.
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
     unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
@@ -292,7 +294,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err
         red_release_add_u64(count, 1ull);
         unsigned long long t0 = 0;
         int spins = 0;
-        while (ld_relaxed_u64(count) < target) {
+        while (ld_acquire_u64(count) < target) {
             if ((++spins & 1023) == 0) {
                 if (t0 == 0) {
                     t0 = global_ns();
@@ -303,7 +305,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return abort_flag == 0;

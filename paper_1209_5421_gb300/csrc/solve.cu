@@ -453,14 +453,16 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
     const RedCtx rc{a.partials, nullptr};
     for (int k = 0; k < a.nops; k++) {
         const Op &op = sop[k & 1];
+        // the next descriptor into the other buffer (last read by op k-1), issued before op k
+        // runs: a load still in flight at the barrier would delay its release fence
+        if (threadIdx.x < kOpWords && k + 1 < a.nops)
+            ((int *)&sop[(k + 1) & 1])[threadIdx.x] = ((const int *)(a.prog + k + 1))[threadIdx.x];
         if (op.fin_pb >= 0) finalize(a, gtab, op);
         if (op.kind == OP_TAIL) {
             if (blockIdx.x == 0) run_tail<T, W>(a);
         } else if (op.kind != OP_NOP) {
             run_op<GLev<T>, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
         }
-        if (threadIdx.x < kOpWords && k + 1 < a.nops)  // the other buffer: last read by op k-1
-            ((int *)&sop[(k + 1) & 1])[threadIdx.x] = ((const int *)(a.prog + k + 1))[threadIdx.x];
         if (!grid_barrier(a.bar, a.err, target, abort_flag)) break;
         if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
     }
