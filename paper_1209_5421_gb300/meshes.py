@@ -232,6 +232,9 @@ WORKLOADS = {
     # 1449x1449 nodes graded x->x^2, y->y^2, jitter 0.1h, kappa on 16x16 blocks, L auto (=10)
     "graded_1449": dict(n=1449, jitter=0.1, graded=True, kappa_blocks=16, seed=0,
                         rhs="normal", aux_level=0),
+    # disk of radius 0.5 cut from 1921x1921 nodes (jitter 0.2h): about 2.89M unknowns, the
+    # size of the paper's smaller disk example; empty auxiliary cells in the corners; L auto
+    "disk_1921": dict(disk=True, n=1921, jitter=0.2, seed=0, rhs="normal", aux_level=0),
 }
 
 
@@ -240,6 +243,8 @@ def workload(name: str, **overrides) -> tuple[Problem, int]:
     spec = dict(WORKLOADS[name])
     spec.update(overrides)
     aux = spec.pop("aux_level")
+    if spec.pop("disk", False):
+        return disk_poisson(name=name, **spec), aux
     return p1_poisson(name=name, **spec), aux
 
 
@@ -254,3 +259,36 @@ def batch_workload(count: int = 256, nmin: int = 45, nmax: int = 450, seed: int 
     sides = np.clip(np.rint(sides).astype(int), nmin, nmax)
     return [p1_poisson(int(m), jitter=jitter, seed=seed + k + 1, rhs="normal",
                        name=f"batch_{k}_n{int(m)}") for k, m in enumerate(sides)]
+
+
+def disk_poisson(n: int, jitter: float = 0.2, seed: int = 0, rhs: str = "normal",
+                 radius: float = 0.5, name: str = "") -> Problem:
+    """P1 Poisson on a disk cut from the jittered n x n triangulation of the unit square: the
+    unknowns are the interior nodes at distance < radius from (0.5, 0.5), every other node is
+    held at zero (Dirichlet), so the matrix is the principal submatrix of the square's on
+    those nodes (SPD) and the domain is the union of elements with a node inside, a staircase
+    approximation of the disk. The auxiliary grid over the nodes' bounding box then has empty
+    cells in its four corners, as the paper's disk examples do. rhs: "normal" = N(0,1) from
+    default_rng(seed + 1) over the kept unknowns, "load" = the square's load vector there."""
+    sq = p1_poisson(n, jitter=jitter, seed=seed, rhs="load" if rhs == "load" else "zero")
+    keep = np.flatnonzero((sq.x - 0.5) ** 2 + (sq.y - 0.5) ** 2 < radius * radius)
+    if keep.size == 0:
+        raise ValueError("no node inside the disk")
+    newid = np.full(sq.n, -1, np.int64)
+    newid[keep] = np.arange(keep.size)
+    counts = np.diff(sq.rowptr.astype(np.int64))
+    rows = np.repeat(np.arange(sq.n), counts)
+    cnew = newid[sq.col]
+    ok = (newid[rows] >= 0) & (cnew >= 0)
+    r2, c2, v2 = newid[rows[ok]], cnew[ok], sq.val[ok]  # rows ascending, columns ascending
+    rowptr = np.zeros(keep.size + 1, np.int64)
+    np.add.at(rowptr, r2 + 1, 1)
+    np.cumsum(rowptr, out=rowptr)
+    if rhs == "normal":
+        b = np.random.default_rng(seed + 1).standard_normal(keep.size)
+    elif rhs == "load":
+        b = sq.b[keep].copy()
+    else:
+        raise ValueError(f"unknown rhs {rhs!r}")
+    return Problem(int(keep.size), rowptr.astype(np.int32), c2.astype(np.int32),
+                   v2.astype(np.float64), sq.x[keep].copy(), sq.y[keep].copy(), b, name=name)

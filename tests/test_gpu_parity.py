@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from paper_1209_5421_gb300.meshes import five_point_grid, p1_poisson, workload
+from paper_1209_5421_gb300.meshes import disk_poisson, five_point_grid, p1_poisson, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -154,6 +154,26 @@ def test_empty_cells(amg, oracle_mod):
     O = oracle_mod.Hierarchy.from_problem(prob, **opts)
     assert G.level(1)["n"] < 4**6
     compare_hierarchies(G, O)
+
+
+@pytest.mark.parametrize("n,opts", [(65, dict()), (129, dict(aux_level=7)),
+                                    (257, dict(aux_level=8, cycle_prec=1))])
+def test_disk_domain_parity(amg, oracle_mod, n, opts):
+    # the disk cut from the square (Sec. 5 disk examples): empty auxiliary cells in the corners
+    prob = disk_poisson(n, seed=n)
+    gopts = dict(opts)
+    oopts = {k: v for k, v in opts.items() if k != "cycle_prec"}
+    G = amg.Hierarchy.from_problem(prob, **gopts)
+    O = oracle_mod.Hierarchy.from_problem(prob, **oopts)
+    compare_hierarchies(G, O)
+    assert G.level(1)["n"] < 0.85 * 4 ** G.L
+    tol = 1e-8
+    xg, itg, rrg, stg = G.solve(prob.b, tol)
+    xo, ito, _, _ = O.solve(prob.b, tol)
+    assert stg == amg.OK and abs(itg - ito) <= (1 if "cycle_prec" not in opts else 3)
+    A = prob.to_scipy()
+    assert np.linalg.norm(prob.b - A @ xg) / np.linalg.norm(prob.b) <= tol
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
 @pytest.mark.parametrize("n,cmax", [(6, 64), (9, 49), (12, 256)])
