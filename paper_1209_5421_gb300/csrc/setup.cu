@@ -79,19 +79,27 @@ __global__ void k_minmax_partial(int n, const double *__restrict__ x,
     if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
 }
 
+// one warp: min / max of the per-block partials (exact in any order)
 __global__ void k_minmax_final(int nb, const double *part, double *bbox) {
-    if (threadIdx.x != 0) return;
     double a1 = INFINITY, b1 = -INFINITY, a2 = INFINITY, b2 = -INFINITY;
-    for (int b = 0; b < nb; b++) {
+    for (int b = threadIdx.x; b < nb; b += 32) {
         a1 = fmin(a1, part[4 * b]);
         b1 = fmax(b1, part[4 * b + 1]);
         a2 = fmin(a2, part[4 * b + 2]);
         b2 = fmax(b2, part[4 * b + 3]);
     }
-    bbox[0] = a1;
-    bbox[1] = b1;
-    bbox[2] = a2;
-    bbox[3] = b2;
+    for (int o = 16; o > 0; o >>= 1) {
+        a1 = fmin(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+        b1 = fmax(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+        a2 = fmin(a2, __shfl_xor_sync(0xffffffffu, a2, o));
+        b2 = fmax(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+    }
+    if (threadIdx.x == 0) {
+        bbox[0] = a1;
+        bbox[1] = b1;
+        bbox[2] = a2;
+        bbox[3] = b2;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -215,9 +223,17 @@ __global__ void k_colors(int n, const int *__restrict__ cell, int w, int m,
     color[i] = (c % w) % m + m * ((c / w) % m);
 }
 
-__global__ void k_count(int n, const int *__restrict__ key, int *__restrict__ cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[key[i]], 1);
+// cnt[k] += number of i with key[i] == k, keys in [0, nbins): a shared-memory histogram per
+// block, then one global add per bin and block (integer counts: exact in any order)
+__global__ void k_count(int n, const int *__restrict__ key, int nbins, int *__restrict__ cnt) {
+    extern __shared__ int hist[];
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&hist[key[i]], 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        if (hist[k]) atomicAdd(&cnt[k], hist[k]);
 }
 
 // block pointers from sorted block keys (every block non-empty)
@@ -394,17 +410,24 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
 }
 
 // stored entries per colour (rows of colour c are the range [cr[c], cr[c+1]))
-__global__ void k_color_nnz(int n, const int *__restrict__ len, const int *__restrict__ cr,
-                            int ncol, unsigned long long *__restrict__ out) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int lo = 0, hi = ncol;  // largest c with cr[c] <= p
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (cr[mid] <= p) lo = mid;
-        else hi = mid;
+// out[c] = sum of len over colour c's rows [cr[c], cr[c+1]) (rows are in colour order):
+// block (c, j) sums chunk j of the range in shared memory and adds it once (integer sums:
+// exact in any order)
+__global__ void k_color_nnz(const int *__restrict__ len, const int *__restrict__ cr,
+                            unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long part[kT];
+    const int c = blockIdx.x;
+    const int r0 = cr[c], r1 = cr[c + 1];
+    unsigned long long acc = 0;
+    for (int p = r0 + blockIdx.y * blockDim.x + threadIdx.x; p < r1; p += gridDim.y * blockDim.x)
+        acc += (unsigned long long)len[p];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
     }
-    atomicAdd(&out[lo], (unsigned long long)len[p]);
+    if (threadIdx.x == 0 && part[0]) atomicAdd(&out[c], part[0]);
 }
 
 // parent pi-row of every pi-row: inv_next[agg_nat[nat[p]]]
@@ -438,11 +461,19 @@ __global__ void k_dense_from_sell(int n, const int *__restrict__ sl, const int *
     }
 }
 
-__global__ void k_chol_inverse(int n, double *a, double *w, double *ainv, float *ainv32,
+__global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, float *ainv32,
                                int *err) {
+    // the factor and the inverse factor live in shared memory when they fit (every access
+    // of the n^3 loops is then a shared-memory access), else in the global scratch
+    extern __shared__ double smat[];
+    const bool in_smem = (ga == nullptr);
+    double *a = in_smem ? smat : ga;
+    double *w = in_smem ? smat + (size_t)n * n : gw;
     __shared__ int bad;
     const int t = threadIdx.x, T = blockDim.x;
     if (t == 0) bad = 0;
+    if (in_smem)
+        for (int e = t; e < n * n; e += T) a[e] = ainv[e];  // the dense matrix arrives in ainv
     __syncthreads();
     for (int j = 0; j < n; j++) {
         if (t == 0) {
@@ -512,7 +543,8 @@ void color_nnz(amg_hierarchy *h, Level &lv, const int *len) {
     AMG_CUDA(cudaMemcpyAsync(cr, lv.color_rows.data(), sizeof(int) * (nc + 1),
                              cudaMemcpyHostToDevice, s));
     AMG_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nc, s));
-    k_color_nnz<<<nblocks_for(lv.n, kT), kT, 0, s>>>(lv.n, len, cr, nc, out);
+    const int per = std::max(1, std::min(64, nblocks_for(lv.n, kT) / std::max(1, nc)));
+    k_color_nnz<<<dim3(nc, per), kT, 0, s>>>(len, cr, out);
     AMG_LAUNCH_CHECK();
     std::vector<unsigned long long> v(nc);
     AMG_CUDA(cudaMemcpyAsync(v.data(), out, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost, s));
@@ -582,7 +614,8 @@ void order_level(amg_hierarchy *h, Level &lv, const int *cell_nat, int *color_na
     k_scatter_inv<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.nat, lv.inv);
     AMG_LAUNCH_CHECK();
     AMG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * lv.ncolors, s));
-    k_count<<<nblocks_for(n, kT), kT, 0, s>>>(n, color_nat, cnt);
+    k_count<<<std::min(nblocks_for(n, kT), 1216), kT, sizeof(int) * lv.ncolors, s>>>(
+        n, color_nat, lv.ncolors, cnt);
     AMG_LAUNCH_CHECK();
     std::vector<int> c = read_ints(cnt, lv.ncolors, s);
     lv.color_rows.assign(lv.ncolors + 1, 0);
@@ -641,14 +674,29 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
     cudaStream_t s = h->stream;
     int n = lv.n;
     Scratch tmp(s);
-    double *a = tmp.get<double>((size_t)n * n);
-    double *w = tmp.get<double>((size_t)n * n);
-    AMG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * n * n, s));
-    k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val, a);
-    AMG_LAUNCH_CHECK();
     lv.Ainv = halloc<double>(h, (size_t)n * n);
     lv.Ainv32 = halloc<float>(h, 2 * (size_t)n * n);
-    k_chol_inverse<<<1, 256, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
+    const size_t smem = 2 * sizeof(double) * (size_t)n * n;  // factor + inverse factor
+    if (smem <= 160 * 1024) {  // n <= 102: everything in shared memory; the matrix via Ainv
+        AMG_CUDA(cudaMemsetAsync(lv.Ainv, 0, sizeof(double) * n * n, s));
+        k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val,
+                                                          lv.Ainv);
+        AMG_LAUNCH_CHECK();
+        static bool attr = false;  // opt in to more than 48 KB once per process
+        if (!attr) {
+            AMG_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          160 * 1024));
+            attr = true;
+        }
+        k_chol_inverse<<<1, 256, smem, s>>>(n, nullptr, nullptr, lv.Ainv, lv.Ainv32, h->err_flag);
+    } else {
+        double *a = tmp.get<double>((size_t)n * n);
+        double *w = tmp.get<double>((size_t)n * n);
+        AMG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * n * n, s));
+        k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val, a);
+        AMG_LAUNCH_CHECK();
+        k_chol_inverse<<<1, 256, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
+    }
     AMG_LAUNCH_CHECK();
 }
 
