@@ -82,6 +82,17 @@ struct BatchCycle {
     int nlev, kc;
 };
 
+// first non-empty colour [r0, r1) of level l >= 1
+template <class T>
+__device__ __forceinline__ void first_colour(const BatchCycle<T> &c, int l, int &r0, int &r1) {
+    const int *cr = c.colors + c.cofs[l];
+    const int nc = c.ncol[l];
+    int k = 0;
+    while (k < nc && cr[k + 1] == cr[k]) k++;
+    r0 = k < nc ? cr[k] : 0;
+    r1 = k < nc ? cr[k + 1] : 0;
+}
+
 // pre-smoothing and restriction of B^_l: level 0 from u = 0 (block smoother, all colours);
 // coarse levels for z = p_i, f = rhs (i = 0) or r, the first non-empty colour as u = D^-1 f
 template <class T>
@@ -97,12 +108,8 @@ __device__ __forceinline__ void bc_pre(const BatchCycle<T> &c, int l, int i) {
     if (l == 0) {
         op_zero(L, z, tid, nth);
         __syncthreads();
-    } else {
+    } else {  // the first colour was done by the restriction into this level or the last UPDATE
         while (col < nc && cr[col + 1] == cr[col]) col++;
-        op.i0 = col < nc ? cr[col] : 0;
-        op.i1 = col < nc ? cr[col + 1] : 0;
-        op_gs_first(L, op, f, z, tid, nth);
-        __syncthreads();
         col++;
     }
     for (; col < nc; col++) {
@@ -112,7 +119,14 @@ __device__ __forceinline__ void bc_pre(const BatchCycle<T> &c, int l, int i) {
         op_gs(L, op, f, z, tid, nth);
         __syncthreads();
     }
-    op_restrict(L, f, z, c.tab[l + 1].rhs, tid, nth);
+    const BLev<T> &N = c.tab[l + 1];
+    if (l + 1 < c.nlev - 1) {  // the next level smooths: its first colour from zero too
+        int f0, f1;
+        first_colour(c, l + 1, f0, f1);
+        op_restrict(L, f, z, N.rhs, tid, nth, N.p[0], N.dinv, f0, f1);
+    } else {
+        op_restrict(L, f, z, N.rhs, tid, nth);
+    }
     __syncthreads();
 }
 
@@ -140,6 +154,10 @@ __device__ __forceinline__ void bc_post(const BatchCycle<T> &c, int l, int i) {
     op = batch_op();
     op.step = i;
     op.last = (i == c.kc - 1);
+    if (!op.last) {  // the UPDATE also starts step i+1's pre-smoothing
+        op.fuse = 1;
+        first_colour(c, l, op.f0, op.f1);
+    }
     if (i > 0) {
         op_multidot<BLev<T>, RM_BLOCK>(L, op, rc, tid, nth, BlockGroup{});
         __syncthreads();

@@ -40,6 +40,11 @@ struct Op {
     int red_pb;
     int fin_pb, fin_level, fin_n;
     int fin_dst[4];
+    // RESTRICT / UPDATE: also do the first op of the next pre-smoothing, the point-GS first
+    // colour [f0, f1) from zero (OP_GS_FIRST), on the value just computed in the same thread:
+    // RESTRICT for B^ of the next level (u = next.p_0, f = next.rhs), UPDATE (not last) for
+    // the next Alg. 1 step (u = p_{i+1}, f = r)
+    int fuse, f0, f1;
 };
 
 enum : int { V_RHS = 0, V_E, V_R, V_P0 };  // V_P0 + i = p_i
@@ -388,16 +393,20 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
 // coarser levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form),
 // one lane per child and a two-step shuffle (nth must be a multiple of 32)
+// With un non-null, the next level's smoothing starts here as well (Op::fuse):
+// un[R] = fc[R] / a_RR on the next level's first colour [f0, f1), 0 elsewhere.
 template <class LV>
 __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             const typename LV::val_t *u, typename LV::val_t *fc, int tid,
-                            int nth) {
+                            int nth, typename LV::val_t *un = nullptr,
+                            const typename LV::val_t *dinv_n = nullptr, int f0 = 0, int f1 = 0) {
     using T = typename LV::val_t;
     if (L.fine) {
         for (int R = tid; R < L.nnext; R += nth) {
             T acc = 0;
             for (int i = L.bptr[R]; i < L.bptr[R + 1]; i++) acc += row_residual(L, i, f, u);
             fc[R] = acc;
+            if (un) un[R] = (R >= f0 && R < f1) ? acc * dinv_n[R] : T(0);
         }
         return;
     }
@@ -412,7 +421,10 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
         }
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
-        if (R < L.nnext && q == 0) fc[R] = v;
+        if (R < L.nnext && q == 0) {
+            fc[R] = v;
+            if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
+        }
     }
 }
 
@@ -596,12 +608,14 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
     const T *r_in = i == 0 ? L.rhs : L.r;
     T *e = L.e;
     T v[1] = {0};
+    T *pn = (op.fuse && !last) ? pick(L.p, i + 1) : nullptr;  // next step's first colour
     for (int row = tid; row < L.n; row += nth) {
         e[row] = (i == 0) ? a * p[row] : e[row] + a * p[row];
         if (!last) {
             T rn = r_in[row] - a * q[row];
             L.r[row] = rn;
             v[0] += rn * rn;
+            if (pn) pn[row] = (row >= op.f0 && row < op.f1) ? rn * L.dinv[row] : T(0);
         }
     }
     if (!last) {
@@ -621,9 +635,12 @@ __device__ __forceinline__ void run_op_on(const LV &L, const Next &next, const O
         case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
         case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_GS_FIRST: op_gs_first(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
-        case OP_RESTRICT:
-            op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), next().rhs, tid, nth);
+        case OP_RESTRICT: {
+            const auto &N = next();
+            op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), N.rhs, tid, nth,
+                        op.fuse ? N.p[0] : nullptr, N.dinv, op.f0, op.f1);
             break;
+        }
         case OP_PROLONG: op_prolong(L, next().e, vec_of(L, op.usel), tid, nth); break;
         case OP_COARSE: op_coarse(L, tid, nth); break;
         case OP_MULTIDOT: op_multidot<LV, RM>(L, op, rc, tid, nth, g); break;

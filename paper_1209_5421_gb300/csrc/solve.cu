@@ -158,6 +158,19 @@ enum : int { PH_ENTER = 0, PH_PRE, PH_POST };
 
 // pre-smoothing from zero (colours ascending; the first non-empty colour is u = D^-1 f) and
 // next.rhs = P^t (f - A u1), for z = p_i = B^_l [f], f = rhs (i = 0) or r
+// first non-empty colour [r0, r1) of tail level l (its point-GS first colour)
+__device__ __forceinline__ void tail_first_colour(int l, int &r0, int &r1) {
+    const int *cr = (const int *)(amg_smem + tail_lay[l].colors);
+    const int nc = tail_lay[l].ncolors;
+    int c = 0;
+    while (c < nc && cr[c + 1] == cr[c]) c++;
+    r0 = c < nc ? cr[c] : 0;
+    r1 = c < nc ? cr[c + 1] : 0;
+}
+
+// The first colour of a pre-smoothing was already done by the op before it, except for step
+// 0 of the top tail level: by the last UPDATE (i > 0) or by the restriction into this level
+// (i = 0), which also starts the next level's first colour unless that level is the coarsest.
 template <class T, int W, class LV, class G>
 __device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int l, int i) {
     const int tid = threadIdx.x;
@@ -168,11 +181,13 @@ __device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int 
     int c = 0;
     while (c < nc && cr[c + 1] == cr[c]) c++;
     Op op = tail_op();
-    op.i0 = c < nc ? cr[c] : 0;
-    op.i1 = c < nc ? cr[c + 1] : 0;
-    op_gs_first(L, op, f, z, tid, nth);
-    g.sync();
-    tail_mark(l, OP_GS_FIRST);
+    if (i == 0 && l == tail_ctl.tl) {
+        op.i0 = c < nc ? cr[c] : 0;
+        op.i1 = c < nc ? cr[c + 1] : 0;
+        op_gs_first(L, op, f, z, tid, nth);
+        g.sync();
+        tail_mark(l, OP_GS_FIRST);
+    }
     for (c++; c < nc; c++) {
         if (cr[c + 1] == cr[c]) continue;
         op.i0 = cr[c];
@@ -181,7 +196,14 @@ __device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int 
         g.sync();
         tail_mark(l, OP_GS);
     }
-    op_restrict(L, f, z, staged_level<T, W>(l + 1).rhs, tid, nth);
+    const StagedLevel<T, W> N = staged_level<T, W>(l + 1);
+    if (tail_lay[l + 1].Ainv < 0) {  // the next level smooths: its first colour too
+        int f0, f1;
+        tail_first_colour(l + 1, f0, f1);
+        op_restrict(L, f, z, N.rhs, tid, nth, N.p[0], N.dinv, f0, f1);
+    } else {
+        op_restrict(L, f, z, N.rhs, tid, nth);
+    }
     g.sync();
     tail_mark(l, OP_RESTRICT);
 }
@@ -211,6 +233,10 @@ __device__ __forceinline__ void phase_post(const LV &L, const G &g, int nth, int
     op = tail_op();
     op.step = i;
     op.last = (i == kc - 1);
+    if (!op.last) {  // the UPDATE also starts step i+1's pre-smoothing
+        op.fuse = 1;
+        tail_first_colour(l, op.f0, op.f1);
+    }
     if (i > 0) {
         op_multidot<LV, RM_BLOCK>(L, op, rc, tid, nth, g);
         g.sync();
@@ -917,8 +943,23 @@ struct Builder {
     }
     void emit(const Op &o) { out->push_back(o); }
 
-    // z = B^_l [f] (Alg. 2)
-    void bhat(int l, int fsel, int zsel) {
+    // first non-empty colour of level l (its point-GS first colour), [r0, r1)
+    void first_colour(int l, int &r0, int &r1) const {
+        const std::vector<int> &ranges = h->lev[l].color_rows;
+        const int nc = (int)ranges.size() - 1;
+        int c0 = 0;
+        while (c0 < nc && ranges[c0 + 1] == ranges[c0]) c0++;
+        r0 = c0 < nc ? ranges[c0] : 0;
+        r1 = c0 < nc ? ranges[c0 + 1] : 0;
+    }
+    // does B~_l start with the point-GS first colour of B^_l (step 0) in this program?
+    bool starts_with_first_colour(int l) const {
+        return l >= 1 && l < h->nlev && l != stop_level && !h->lev[l].coarsest;
+    }
+
+    // z = B^_l [f] (Alg. 2). first_done: the first colour of the pre-smoothing was already
+    // done by the op before (a fused RESTRICT or UPDATE)
+    void bhat(int l, int fsel, int zsel, bool first_done = false) {
         Level &lv = h->lev[l];
         const std::vector<int> &ranges = (l == 0) ? lv.color_blocks : lv.color_rows;
         const int nc = (int)ranges.size() - 1;
@@ -929,12 +970,14 @@ struct Builder {
             emit(z);
         } else {  // first non-empty colour fused with the zero fill (point smoother)
             while (c0 < nc && ranges[c0 + 1] == ranges[c0]) c0++;
-            Op g = mk(OP_GS_FIRST, l);
-            g.i0 = c0 < nc ? ranges[c0] : 0;
-            g.i1 = c0 < nc ? ranges[c0 + 1] : 0;
-            g.fsel = fsel;
-            g.usel = zsel;
-            emit(g);
+            if (!first_done) {
+                Op g = mk(OP_GS_FIRST, l);
+                g.i0 = c0 < nc ? ranges[c0] : 0;
+                g.i1 = c0 < nc ? ranges[c0 + 1] : 0;
+                g.fsel = fsel;
+                g.usel = zsel;
+                emit(g);
+            }
             c0++;
         }
         for (int c = c0; c < nc; c++) {
@@ -949,8 +992,13 @@ struct Builder {
         Op rs = mk(OP_RESTRICT, l);  // next.rhs = P^t (f - A u1)
         rs.fsel = fsel;
         rs.usel = zsel;
+        const bool fuse = starts_with_first_colour(l + 1);
+        if (fuse) {  // and the next level's first colour from zero
+            rs.fuse = 1;
+            first_colour(l + 1, rs.f0, rs.f1);
+        }
         emit(rs);
-        btilde(l + 1);               // next.e = B~_{k-1}[next.rhs]
+        btilde(l + 1, fuse);         // next.e = B~_{k-1}[next.rhs]
         Op pr = mk(OP_PROLONG, l);   // u2 = u1 + P e
         pr.usel = zsel;
         emit(pr);
@@ -966,8 +1014,9 @@ struct Builder {
         }
     }
 
-    // e = B~_l [rhs] (Alg. 1 with kcycle_n steps; exact on the coarsest level)
-    void btilde(int l) {
+    // e = B~_l [rhs] (Alg. 1 with kcycle_n steps; exact on the coarsest level). first_done:
+    // step 0's first colour was done by the restriction into this level
+    void btilde(int l, bool first_done = false) {
         if (l == stop_level) {
             emit(mk(OP_TAIL, l));
             return;
@@ -979,7 +1028,7 @@ struct Builder {
         }
         const int n = h->opt.kcycle_n;
         for (int i = 0; i < n; i++) {
-            bhat(l, i == 0 ? V_RHS : V_R, V_P0 + i);
+            bhat(l, i == 0 ? V_RHS : V_R, V_P0 + i, i == 0 ? first_done : true);
             if (i > 0) {
                 Op md = mk(OP_MULTIDOT, l);
                 md.step = i;
@@ -994,6 +1043,10 @@ struct Builder {
             Op up = mk(OP_UPDATE, l);
             up.step = i;
             up.last = (i == n - 1);
+            if (!up.last) {  // and the next step's first colour from zero, on r_{i+1}
+                up.fuse = 1;
+                first_colour(l, up.f0, up.f1);
+            }
             emit(up);
         }
     }
