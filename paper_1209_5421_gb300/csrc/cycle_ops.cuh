@@ -467,13 +467,19 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
     int g = 1;
     while (g < 32 && 2 * g * n <= nth) g *= 2;
     const int sub = tid & (g - 1), rows_per_pass = nth / g;
+    // the lanes of a warp read 32 / g rows at once: lane `sub` of a row reads columns
+    // sub + g t, t < T, starting at t = its row group in the warp, so that rows whose stride
+    // is a multiple of the 32 shared-memory banks do not read the same banks in the same step
+    const int T_ = (n + g - 1) / g, rot = (tid & 31) / g;
     for (int base = 0; base < n; base += rows_per_pass) {
         const int i = base + tid / g;
         if constexpr (sizeof(T) == 4) {
             float s = 0.f, c = 0.f;  // running sum, sum of all rounding errors
             if (i < n) {
                 const float *ah = L.Ainv2 + (size_t)i * n, *al = ah + (size_t)n * n;
-                for (int j = sub; j < n; j += g) {
+                for (int tt = 0; tt < T_; tt++) {
+                    const int j = sub + g * ((tt + rot) % T_);
+                    if (j >= n) continue;
                     const float x = L.rhs[j];
                     const float ph = __fmul_rn(ah[j], x);
                     const float pe = fmaf(al[j], x, fmaf(ah[j], x, -ph));  // error + low part
@@ -496,7 +502,10 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
             double s = 0.0;
             if (i < n) {
                 const double *a = L.Ainv + (size_t)i * n;
-                for (int j = sub; j < n; j += g) s += a[j] * (double)L.rhs[j];
+                for (int tt = 0; tt < T_; tt++) {
+                    const int j = sub + g * ((tt + rot) % T_);
+                    if (j < n) s += a[j] * (double)L.rhs[j];
+                }
             }
             for (int o = g >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
             if (i < n && sub == 0) L.e[i] = (T)s;

@@ -1220,6 +1220,10 @@ bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
     for (int l = l0; l < h->nlev; l++)
         if (!Y.lv[l].gmem) nmax = std::max(nmax, Y.lv[l].n);
     Y.narrow = std::min(1024, std::max(128, (nmax / 4 + 31) / 32 * 32));
+    if (const char *e = getenv("AMG_TAIL_NARROW")) {  // tuning knob: threads of the narrow group
+        const int v = atoi(e);
+        if (v >= 32 && v <= 1024 && v % 32 == 0) Y.narrow = v;
+    }
     Y.sc = take(sizeof(double) * SC_N * (size_t)(h->nlev - l0));
     Y.bytes = (int)off;
     return true;
