@@ -41,6 +41,8 @@ typedef struct {
     int has_bbox;      /* 1: use bbox below instead of eq. ab12 */
     double bbox[4];    /* a1, b1, a2, b2 */
     int no_factor;     /* 1: skip the coarsest Cholesky (inspect operators of singular A) */
+    int dim;           /* 2 (quadtree, default when 0) or 3 (octree, Sec. 3.1 / Sec. 6) */
+    double zbox[2];    /* a3, b3 (dim 3 with has_bbox) */
 } oamg_opts;
 
 typedef struct {
@@ -49,6 +51,7 @@ typedef struct {
     double *val;
     int cellw;          /* cells per side of the grid this level's rows live on */
     int *t1, *t2;       /* cell coordinates of each row (fine level: its level-L cell) */
+    int *t3;            /* third cell coordinate (octree only; NULL for the quadtree) */
     int span;           /* s: max cell offset over the nonzeros */
     int m;              /* colour modulus max(2, s+1) */
     int *color;         /* colour of each row */
@@ -61,7 +64,8 @@ typedef struct {
     int nlev;
     olevel lev[40];
     int L;              /* depth of the auxiliary grid */
-    double bbox[4];
+    int dim;            /* 2: quadtree, 3: octree */
+    double bbox[6];     /* a1, b1, a2, b2, a3, b3 */
     oamg_opts opt;
     double *work;       /* scratch vectors */
 } oamg_h;
@@ -98,6 +102,13 @@ static int check_csr(int n, const int *rp, const int *ci, const double *v) {
 int oamg_auto_level(long long N) {
     int L = 0;
     while (N >= (1LL << (2 * (L + 1)))) L++;
+    return L;
+}
+
+/* The octree's depth (Sec. 3.1 with 8 children per cell): the largest L with 8^L <= N. */
+int oamg_auto_level3(long long N) {
+    int L = 0;
+    while (N >= (1LL << (3 * (L + 1)))) L++;
     return L;
 }
 
@@ -148,6 +159,10 @@ static int level_span(const olevel *lv) {
             int d2 = abs(lv->t2[i] - lv->t2[j]);
             if (d1 > s) s = d1;
             if (d2 > s) s = d2;
+            if (lv->t3) {
+                int d3 = abs(lv->t3[i] - lv->t3[j]);
+                if (d3 > s) s = d3;
+            }
         }
     return s;
 }
@@ -157,8 +172,11 @@ static int level_span(const olevel *lv) {
  * not coupled. */
 static void level_colors(olevel *lv) {
     lv->m = lv->span + 1 > 2 ? lv->span + 1 : 2;
-    for (int i = 0; i < lv->n; i++)
+    for (int i = 0; i < lv->n; i++) {
         lv->color[i] = (lv->t1[i] % lv->m) + lv->m * (lv->t2[i] % lv->m);
+        /* octree: + m^2 (t3 mod m), m^3 colours (8 when s <= 1, Sec. 6) */
+        if (lv->t3) lv->color[i] += lv->m * lv->m * (lv->t3[i] % lv->m);
+    }
 }
 
 /* Galerkin operator A_c = P^t A P (Sec. 2, eq. def:Ac), entrywise eq. acsum:
@@ -274,7 +292,7 @@ void oamg_free(oamg_h *h) {
     if (!h) return;
     for (int k = 0; k < h->nlev; k++) {
         olevel *lv = &h->lev[k];
-        free(lv->rowptr); free(lv->col); free(lv->val); free(lv->t1); free(lv->t2);
+        free(lv->rowptr); free(lv->col); free(lv->val); free(lv->t1); free(lv->t2); free(lv->t3);
         free(lv->color); free(lv->perm); free(lv->agg); free(lv->chol);
     }
     free(h->work);
@@ -285,33 +303,53 @@ void oamg_free(oamg_h *h) {
  * Setup (Sec. 3 and 4): aggregates on every level, Galerkin operators, colours, sweep order,
  * coarsest Cholesky factor.
  * ------------------------------------------------------------------------------------- */
-int oamg_setup(int n, const int *rowptr, const int *col, const double *val, const double *x,
-               const double *y, const oamg_opts *opt, oamg_h **out) {
+/* One setup for both trees: dim 2 (quadtree, z unused) or dim 3 (octree). The octree is the
+ * quadtree's construction with a third coordinate throughout: the box gains [a3, b3], a cell
+ * has coordinates (t1, t2, t3) and index t1 + w t2 + w^2 t3, a parent halves all three, and
+ * the colouring has m^3 colours. */
+static int setup_impl(int n, const int *rowptr, const int *col, const double *val,
+                      const double *x, const double *y, const double *z, const oamg_opts *opt,
+                      oamg_h **out) {
     *out = NULL;
-    if (n <= 0 || !rowptr || !col || !val || !x || !y || !opt) return OAMG_ERR_INVALID_ARG;
-    if (opt->coarsest_max < 1 || opt->kcycle_n < 1 || opt->aux_level < 0 || opt->aux_level > 15)
+    const int dim = (opt && opt->dim == 3) ? 3 : 2;
+    if (n <= 0 || !rowptr || !col || !val || !x || !y || !opt || (dim == 3 && !z))
+        return OAMG_ERR_INVALID_ARG;
+    if (opt->dim != 0 && opt->dim != 2 && opt->dim != 3) return OAMG_ERR_INVALID_ARG;
+    if (opt->coarsest_max < 1 || opt->kcycle_n < 1 || opt->aux_level < 0 ||
+        opt->aux_level > (dim == 3 ? 10 : 15))
         return OAMG_ERR_INVALID_ARG;
     int st = check_csr(n, rowptr, col, val);
     if (st) return st;
     for (int j = 0; j < n; j++)
-        if (!isfinite(x[j]) || !isfinite(y[j])) return OAMG_ERR_INVALID_ARG;
+        if (!isfinite(x[j]) || !isfinite(y[j]) || (dim == 3 && !isfinite(z[j])))
+            return OAMG_ERR_INVALID_ARG;
 
     oamg_h *h = (oamg_h *)xcalloc(1, sizeof(oamg_h));
     h->opt = *opt;
-    /* eq. ab12: a1 = min x, b1 = max x, a2 = min y, b2 = max y */
+    h->dim = dim;
+    /* eq. ab12: a1 = min x, b1 = max x, a2 = min y, b2 = max y (and a3, b3 for z) */
     if (opt->has_bbox) {
-        memcpy(h->bbox, opt->bbox, sizeof h->bbox);
+        memcpy(h->bbox, opt->bbox, 4 * sizeof(double));
+        h->bbox[4] = opt->zbox[0];
+        h->bbox[5] = opt->zbox[1];
     } else {
         double a1 = x[0], b1 = x[0], a2 = y[0], b2 = y[0];
+        double a3 = dim == 3 ? z[0] : 0.0, b3 = a3;
         for (int j = 1; j < n; j++) {
             if (x[j] < a1) a1 = x[j];
             if (x[j] > b1) b1 = x[j];
             if (y[j] < a2) a2 = y[j];
             if (y[j] > b2) b2 = y[j];
+            if (dim == 3) {
+                if (z[j] < a3) a3 = z[j];
+                if (z[j] > b3) b3 = z[j];
+            }
         }
         h->bbox[0] = a1; h->bbox[1] = b1; h->bbox[2] = a2; h->bbox[3] = b2;
+        h->bbox[4] = a3; h->bbox[5] = b3;
     }
-    int L = opt->aux_level ? opt->aux_level : oamg_auto_level(n);
+    int L = opt->aux_level ? opt->aux_level
+                           : (dim == 3 ? oamg_auto_level3(n) : oamg_auto_level(n));
     h->L = L;
 
     /* level 0: the given fine matrix */
@@ -330,9 +368,11 @@ int oamg_setup(int n, const int *rowptr, const int *col, const double *val, cons
     f->cellw = 1 << L;
     f->t1 = (int *)malloc(sizeof(int) * (size_t)n);
     f->t2 = (int *)malloc(sizeof(int) * (size_t)n);
+    f->t3 = dim == 3 ? (int *)malloc(sizeof(int) * (size_t)n) : NULL;
     for (int j = 0; j < n; j++) {
         f->t1[j] = cell_index_1d(x[j], h->bbox[0], h->bbox[1], L);
         f->t2[j] = cell_index_1d(y[j], h->bbox[2], h->bbox[3], L);
+        if (dim == 3) f->t3[j] = cell_index_1d(z[j], h->bbox[4], h->bbox[5], L);
     }
 
     /* Build coarser levels while the current level is larger than coarsest_max. */
@@ -344,12 +384,13 @@ int oamg_setup(int n, const int *rowptr, const int *col, const double *val, cons
         /* cell of each row of fl at quadtree level k: on the fine level its level-L cell,
          * otherwise the parent (t1 >> 1, t2 >> 1) of its own cell (reading R2: Sec. 4.2
          * listing form / Sec. 4.3 restriction form, parent = floor(t2/2) 2^(k) + floor(t1/2)) */
-        long long ncell = (long long)w * w;
+        long long ncell = (long long)w * w * (dim == 3 ? w : 1);
         int *cid = (int *)malloc(sizeof(int) * (size_t)fl->n);
         for (int i = 0; i < fl->n; i++) {
             int c1 = (h->nlev == 1) ? fl->t1[i] : (fl->t1[i] >> 1);
             int c2 = (h->nlev == 1) ? fl->t2[i] : (fl->t2[i] >> 1);
-            cid[i] = c2 * w + c1;
+            int c3 = dim == 3 ? ((h->nlev == 1) ? fl->t3[i] : (fl->t3[i] >> 1)) : 0;
+            cid[i] = (c3 * w + c2) * w + c1;
         }
         /* aggregates = non-empty cells, numbered in ascending (lexicographic) cell index
          * (eq. agg_L / agg_k; aggregates must be non-empty, Sec. 2; reading R6) */
@@ -363,10 +404,12 @@ int oamg_setup(int n, const int *rowptr, const int *col, const double *val, cons
         cl->cellw = w;
         cl->t1 = (int *)malloc(sizeof(int) * (size_t)nc);
         cl->t2 = (int *)malloc(sizeof(int) * (size_t)nc);
+        cl->t3 = dim == 3 ? (int *)malloc(sizeof(int) * (size_t)nc) : NULL;
         for (long long c = 0; c < ncell; c++)
             if (num[c] >= 0) {
                 cl->t1[num[c]] = (int)(c % w);
-                cl->t2[num[c]] = (int)(c / w);
+                cl->t2[num[c]] = (int)((c / w) % w);
+                if (dim == 3) cl->t3[num[c]] = (int)(c / ((long long)w * w));
             }
         free(num);
         free(cid);
@@ -403,7 +446,8 @@ int oamg_setup(int n, const int *rowptr, const int *col, const double *val, cons
             blockkey = ident;
             nblock = lv->n;
         }
-        sweep_order(lv->n, lv->color, lv->m * lv->m, blockkey, nblock, lv->perm);
+        sweep_order(lv->n, lv->color, lv->m * lv->m * (dim == 3 ? lv->m : 1), blockkey, nblock,
+                    lv->perm);
         free(ident);
     }
     if (!opt->no_factor) {
@@ -413,6 +457,21 @@ int oamg_setup(int n, const int *rowptr, const int *col, const double *val, cons
     h->work = (double *)xcalloc((size_t)n * 2, sizeof(double));
     *out = h;
     return OAMG_OK;
+}
+
+int oamg_setup(int n, const int *rowptr, const int *col, const double *val, const double *x,
+               const double *y, const oamg_opts *opt, oamg_h **out) {
+    if (opt && opt->dim == 3) return OAMG_ERR_INVALID_ARG;  /* the octree needs z */
+    return setup_impl(n, rowptr, col, val, x, y, NULL, opt, out);
+}
+
+/* Octree setup (dim 3): coordinates (x, y, z) of every unknown. */
+int oamg_setup3(int n, const int *rowptr, const int *col, const double *val, const double *x,
+                const double *y, const double *z, const oamg_opts *opt, oamg_h **out) {
+    if (!opt) return OAMG_ERR_INVALID_ARG;
+    oamg_opts o = *opt;
+    o.dim = 3;
+    return setup_impl(n, rowptr, col, val, x, y, z, &o, out);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -588,7 +647,16 @@ int oamg_solve(const oamg_h *h, const double *b, double tol, double *x, int *ite
  * ------------------------------------------------------------------------------------- */
 int oamg_num_levels(const oamg_h *h) { return h->nlev; }
 int oamg_aux_level(const oamg_h *h) { return h->L; }
-void oamg_get_bbox(const oamg_h *h, double *bb) { memcpy(bb, h->bbox, sizeof h->bbox); }
+void oamg_get_bbox(const oamg_h *h, double *bb) { memcpy(bb, h->bbox, 4 * sizeof(double)); }
+void oamg_get_zbox(const oamg_h *h, double *bb) { memcpy(bb, h->bbox + 4, 2 * sizeof(double)); }
+int oamg_dim(const oamg_h *h) { return h->dim; }
+
+/* third cell coordinate of every row of level l (octree) */
+int oamg_level_t3(const oamg_h *h, int l, int *t3) {
+    if (l < 0 || l >= h->nlev || !h->lev[l].t3) return OAMG_ERR_INVALID_ARG;
+    memcpy(t3, h->lev[l].t3, sizeof(int) * (size_t)h->lev[l].n);
+    return OAMG_OK;
+}
 
 int oamg_level_info(const oamg_h *h, int l, int *info /* n, nnz, cellw, span, m */) {
     if (l < 0 || l >= h->nlev) return OAMG_ERR_INVALID_ARG;
@@ -639,5 +707,14 @@ int oamg_btilde(const oamg_h *h, int l, const double *f, double *u) {
 void oamg_bin(int n, const double *x, const double *y, const double *bbox, int L, int *cell) {
     for (int j = 0; j < n; j++)
         cell[j] = cell_index_1d(y[j], bbox[2], bbox[3], L) * (1 << L) +
+                  cell_index_1d(x[j], bbox[0], bbox[1], L);
+}
+
+/* Level-L octree cell indices t1 + 2^L t2 + 4^L t3 of arbitrary points (box a1,b1,a2,b2,a3,b3). */
+void oamg_bin3(int n, const double *x, const double *y, const double *z, const double *bbox,
+               int L, int *cell) {
+    for (int j = 0; j < n; j++)
+        cell[j] = (cell_index_1d(z[j], bbox[4], bbox[5], L) * (1 << L) +
+                   cell_index_1d(y[j], bbox[2], bbox[3], L)) * (1 << L) +
                   cell_index_1d(x[j], bbox[0], bbox[1], L);
 }

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class Opts(C.Structure):
     _fields_ = [("aux_level", C.c_int), ("coarsest_max", C.c_int), ("kcycle_n", C.c_int),
                 ("max_iters", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4),
-                ("no_factor", C.c_int)]
+                ("no_factor", C.c_int), ("dim", C.c_int), ("zbox", C.c_double * 2)]
 
 
 def lib():
@@ -50,6 +50,19 @@ def lib():
             dp = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
             L.oamg_setup.argtypes = [C.c_int, ip, ip, dp, dp, dp, C.POINTER(Opts), C.POINTER(P)]
             L.oamg_setup.restype = C.c_int
+            L.oamg_setup3.argtypes = [C.c_int, ip, ip, dp, dp, dp, dp, C.POINTER(Opts),
+                                      C.POINTER(P)]
+            L.oamg_setup3.restype = C.c_int
+            L.oamg_get_zbox.argtypes = [P, dp]
+            L.oamg_get_zbox.restype = None
+            L.oamg_dim.argtypes = [P]
+            L.oamg_dim.restype = C.c_int
+            L.oamg_level_t3.argtypes = [P, C.c_int, ip]
+            L.oamg_level_t3.restype = C.c_int
+            L.oamg_bin3.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int, ip]
+            L.oamg_bin3.restype = None
+            L.oamg_auto_level3.argtypes = [C.c_longlong]
+            L.oamg_auto_level3.restype = C.c_int
             L.oamg_solve.argtypes = [P, dp, C.c_double, dp, C.POINTER(C.c_int),
                                      C.POINTER(C.c_double)]
             L.oamg_solve.restype = C.c_int
@@ -92,8 +105,15 @@ class OracleError(RuntimeError):
         self.status = status
 
 
-def auto_level(N: int) -> int:
-    return lib().oamg_auto_level(N)
+def auto_level(N: int, dim: int = 2) -> int:
+    return lib().oamg_auto_level3(N) if dim == 3 else lib().oamg_auto_level(N)
+
+
+def bin_points3(x, y, z, bbox6, L) -> np.ndarray:
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    cell = np.empty(len(x), np.int32)
+    lib().oamg_bin3(len(x), x, y, z, _f64(bbox6), L, cell)
+    return cell
 
 
 def bin_points(x, y, bbox, L) -> np.ndarray:
@@ -106,10 +126,10 @@ def bin_points(x, y, bbox, L) -> np.ndarray:
 class Level:
     """One level of the oracle hierarchy, copied out to numpy."""
 
-    def __init__(self, n, rowptr, col, val, t1, t2, color, perm, agg, cellw, span, m):
+    def __init__(self, n, rowptr, col, val, t1, t2, color, perm, agg, cellw, span, m, t3=None):
         self.n, self.rowptr, self.col, self.val = n, rowptr, col, val
         self.t1, self.t2, self.color, self.perm, self.agg = t1, t2, color, perm, agg
-        self.cellw, self.span, self.m = cellw, span, m
+        self.cellw, self.span, self.m, self.t3 = cellw, span, m, t3
 
     def to_scipy(self):
         import scipy.sparse as sp
@@ -121,15 +141,21 @@ class Hierarchy:
     """Oracle setup (Sec. 3-4 of the paper) for one matrix + node coordinates."""
 
     def __init__(self, rowptr, col, val, x, y, aux_level=0, coarsest_max=64, kcycle_n=2,
-                 max_iters=200, bbox=None, no_factor=False):
+                 max_iters=200, bbox=None, no_factor=False, z=None):
+        """z given: the octree (3D) variant; bbox then has 6 entries a1,b1,a2,b2,a3,b3."""
         L = lib()
         self._keep = (_i32(rowptr), _i32(col), _f64(val), _f64(x), _f64(y))
+        bb = tuple(bbox) if bbox is not None else (0.0,) * 6
         o = Opts(aux_level, coarsest_max, kcycle_n, max_iters, 0 if bbox is None else 1,
-                 (C.c_double * 4)(*(bbox if bbox is not None else (0, 0, 0, 0))),
-                 int(no_factor))
+                 (C.c_double * 4)(*bb[:4]), int(no_factor), 3 if z is not None else 2,
+                 (C.c_double * 2)(*(bb[4:6] if len(bb) >= 6 else (0.0, 0.0))))
         h = C.c_void_p()
         n = len(self._keep[0]) - 1
-        st = L.oamg_setup(n, *self._keep, C.byref(o), C.byref(h))
+        if z is not None:
+            self._keep = self._keep + (_f64(z),)
+            st = L.oamg_setup3(n, *self._keep, C.byref(o), C.byref(h))
+        else:
+            st = L.oamg_setup(n, *self._keep, C.byref(o), C.byref(h))
         if st != OK:
             raise OracleError(st, "oamg_setup")
         self.h = h
@@ -137,7 +163,20 @@ class Hierarchy:
 
     @classmethod
     def from_problem(cls, prob, **kw):
+        z = getattr(prob, "z", None)
+        if z is not None:
+            kw.setdefault("z", z)
         return cls(prob.rowptr, prob.col, prob.val, prob.x, prob.y, **kw)
+
+    @property
+    def dim(self) -> int:
+        return lib().oamg_dim(self.h)
+
+    @property
+    def zbox(self) -> np.ndarray:
+        b = np.empty(2)
+        lib().oamg_get_zbox(self.h, b)
+        return b
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -177,7 +216,11 @@ class Hierarchy:
         ptr = lambda a: a.ctypes.data if a is not None else None  # noqa: E731
         lib().oamg_level_get(self.h, l, ptr(rowptr), ptr(col), ptr(val), ptr(t1), ptr(t2),
                              ptr(color), ptr(perm), ptr(agg))
-        return Level(n, rowptr, col, val, t1, t2, color, perm, agg, cellw, span, m)
+        t3 = None
+        if self.dim == 3:
+            t3 = np.empty(n, np.int32)
+            lib().oamg_level_t3(self.h, l, t3)
+        return Level(n, rowptr, col, val, t1, t2, color, perm, agg, cellw, span, m, t3)
 
     def levels(self):
         return [self.level(l) for l in range(self.nlev)]

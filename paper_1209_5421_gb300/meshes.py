@@ -43,6 +43,7 @@ class Problem:
     y: np.ndarray
     b: np.ndarray
     name: str = ""
+    z: np.ndarray | None = None  # third coordinate (3D problems only)
 
     @property
     def nnz(self) -> int:
@@ -292,3 +293,93 @@ def disk_poisson(n: int, jitter: float = 0.2, seed: int = 0, rhs: str = "normal"
         raise ValueError(f"unknown rhs {rhs!r}")
     return Problem(int(keep.size), rowptr.astype(np.int32), c2.astype(np.int32),
                    v2.astype(np.float64), sq.x[keep].copy(), sq.y[keep].copy(), b, name=name)
+
+
+# Kuhn triangulation of the unit cube: one tetrahedron per ordering of the axes, the path
+# (0,0,0) -> (0,0,0) + e_a -> ... + e_b -> (1,1,1); conforming across neighbouring cubes
+_KUHN = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def p1_poisson_3d(n: int, jitter: float = 0.15, seed: int = 0, rhs: str = "normal",
+                  name: str = "") -> Problem:
+    """P1 stiffness matrix of -Laplace(u) on the unit cube, an ``n x n x n``-node grid with
+    every cube split into the 6 tetrahedra of the Kuhn triangulation, interior nodes jittered
+    by U(-jitter*h, jitter*h) per coordinate (default_rng(seed), lexicographic node order,
+    x, y, z per node), zero Dirichlet data (the unknowns are the (n-2)^3 interior nodes,
+    lexicographic with x fastest). rhs: "normal" = N(0,1) from default_rng(seed + 1), "load"
+    = the load vector of f = 1 (|T|/4 per vertex). Assembled element by element; entries of
+    one (row, column) pair are summed in element order, the
+    same bits on every machine; the matrix is exactly symmetric. Tetrahedra are asserted
+    non-degenerate."""
+    if n < 3:
+        raise ValueError("need at least 3 nodes per side")
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n - 1)
+    g = np.arange(n) * h
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")  # [k, j, i]
+    if jitter:
+        d = rng.uniform(-jitter * h, jitter * h, size=(n, n, n, 3))
+        inner = np.zeros((n, n, n), bool)
+        inner[1:-1, 1:-1, 1:-1] = True
+        X = X + np.where(inner, d[..., 0], 0.0)
+        Y = Y + np.where(inner, d[..., 1], 0.0)
+        Z = Z + np.where(inner, d[..., 2], 0.0)
+    P = np.stack([X, Y, Z], axis=-1).reshape(-1, 3)  # node id = i + n j + n^2 k
+    kk, jj, ii = np.meshgrid(np.arange(n - 1), np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    base = (ii + n * jj + n * n * kk).ravel()
+    step = np.array([1, n, n * n])
+    tets = []
+    for perm in _KUHN:
+        v0 = base
+        v1 = v0 + step[perm[0]]
+        v2 = v1 + step[perm[1]]
+        v3 = v2 + step[perm[2]]
+        tets.append(np.stack([v0, v1, v2, v3], axis=1))
+    T = np.concatenate(tets, axis=0)
+    V = P[T]  # [ne, 4, 3]
+    E = V[:, 1:, :] - V[:, :1, :]  # edges from vertex 0
+    det = np.linalg.det(E)
+    vol = np.abs(det) / 6.0
+    if not np.all(np.abs(det) > 0):
+        raise ValueError("degenerate tetrahedron")
+    # gradients of the barycentric functions: rows of inv(E)^T for vertices 1..3, minus sum
+    Ginv = np.linalg.inv(E)  # [ne, 3, 3]; grad(lambda_a) = Ginv[:, :, a-1] for a = 1..3
+    G = np.empty((T.shape[0], 4, 3))
+    G[:, 1:, :] = np.transpose(Ginv, (0, 2, 1))
+    G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
+    K = vol[:, None, None] * np.einsum("eai,ebi->eab", G, G)  # [ne, 4, 4]
+    K = 0.5 * (K + np.transpose(K, (0, 2, 1)))  # exactly symmetric (IEEE + commutes)
+    # unknowns: interior nodes
+    N = (n - 2) ** 3
+    uid = np.full(n ** 3, -1, np.int64)
+    node_i = np.arange(n ** 3)
+    ni, nj, nk = node_i % n, (node_i // n) % n, node_i // (n * n)
+    inner = (ni > 0) & (ni < n - 1) & (nj > 0) & (nj < n - 1) & (nk > 0) & (nk < n - 1)
+    uid[inner] = np.arange(N)
+    r = uid[T][:, :, None].repeat(4, axis=2)
+    c = uid[T][:, None, :].repeat(4, axis=1)
+    keep = (r >= 0) & (c >= 0)
+    import scipy.sparse as sp
+
+    # sum the contributions of each (row, column) in element order (a stable sort of the
+    # keys), so that (i, j) and (j, i) add the same values in the same order
+    rr, cc, vv = r[keep], c[keep], K[keep]
+    key = rr * N + cc
+    order = np.argsort(key, kind="stable")
+    key, vv = key[order], vv[order]
+    first = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    vals = np.add.reduceat(vv, first)
+    ukey = key[first]
+    A = sp.csr_matrix((vals, (ukey // N, ukey % N)), shape=(N, N))
+    A.sort_indices()
+    xs, ys, zs = P[inner, 0].copy(), P[inner, 1].copy(), P[inner, 2].copy()
+    if rhs == "normal":
+        b = np.random.default_rng(seed + 1).standard_normal(N)
+    elif rhs == "load":
+        load = np.zeros(n ** 3)
+        np.add.at(load, T.ravel(), np.repeat(vol / 4.0, 4))
+        b = load[inner].copy()
+    else:
+        raise ValueError(f"unknown rhs {rhs!r}")
+    return Problem(N, A.indptr.astype(np.int32), A.indices.astype(np.int32),
+                   A.data.astype(np.float64), xs, ys, b, name=name, z=zs)
