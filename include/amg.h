@@ -83,6 +83,7 @@ typedef struct {
     int has_bbox;       /* 1: use bbox as the auxiliary box Omega_0^0 instead of the
                            coordinates' min/max (eq. ab12) [0] */
     double bbox[4];     /* a1, b1, a2, b2 */
+    double zbox[2];     /* a3, b3: the box's third side (amg_setup3 with has_bbox) */
 } amg_options;
 
 typedef struct amg_hierarchy amg_hierarchy;
@@ -106,6 +107,19 @@ void amg_options_default(amg_options *opt);
  */
 int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_options *opt,
               void *stream, amg_hierarchy **out);
+
+/*
+ * The octree variant (paper Sec. 3.1 and Sec. 6: the same construction in three dimensions,
+ * 8 children per cell, 27-point coarse stencils, 8 colours): the setup above with node
+ * coordinates (x, y, z). The auxiliary box gains [a3, b3] (min / max of z, or zbox with
+ * has_bbox); cells have coordinates (t1, t2, t3) and index t1 + 2^k (t2 + 2^k t3) on level
+ * k; the parent of a cell halves all three; colours are (t1 mod m) + m (t2 mod m) +
+ * m^2 (t3 mod m); the automatic depth is the largest L with 8^L <= n. Coupling spans above 2
+ * cells return AMG_ERR_UNSUPPORTED. Solve, inspection and batching work on the result as on
+ * a quadtree hierarchy. Arguments and errors as amg_setup; z: n doubles (device or host).
+ */
+int amg_setup3(const amg_csr *A, const double *x, const double *y, const double *z,
+               const amg_options *opt, void *stream, amg_hierarchy **out);
 
 /*
  * Solve phase: x = A^{-1} b by the outer Krylov iteration preconditioned with the nonlinear
@@ -227,6 +241,10 @@ int amg_num_levels(const amg_hierarchy *h, int *num_levels, int *aux_level);
 /* The auxiliary box a1, b1, a2, b2 actually used (eq. ab12). */
 int amg_get_bbox(const amg_hierarchy *h, double bbox[4]);
 
+/* Tree dimension (2 or 3) and the whole auxiliary box a1, b1, a2, b2, a3, b3 (a3 = b3 = 0
+ * for a quadtree). Either output may be NULL. */
+int amg_get_box3(const amg_hierarchy *h, int *dim, double box[6]);
+
 /*
  * info[0] = n (unknowns), info[1] = stored entries of A_l (without padding),
  * info[2] = cells per side of the grid the rows live on (level 0: the level-L grid),
@@ -242,11 +260,14 @@ int amg_level_info(const amg_hierarchy *h, int level, int64_t info[8]);
  * coarse: aggregate number). Any pointer may be NULL to skip it. Sizes: n for agg, color,
  * t1, t2; n+1 for rowptr; info[1] for col and val (CSR, columns ascending).
  *   agg    : row of the next coarser level containing each row (-1 on the coarsest).
- *   color  : colour (t1 mod m) + m (t2 mod m) of each row's cell.
- *   t1, t2 : cell coordinates of each row.
+ *   color  : colour (t1 mod m) + m (t2 mod m) [+ m^2 (t3 mod m)] of each row's cell.
+ *   t1, t2 : cell coordinates of each row (amg_level_t3 gives the octree's third).
  */
 int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *color,
                      int32_t *t1, int32_t *t2, int32_t *rowptr, int32_t *col, double *val);
+
+/* Octree: the third cell coordinate t3 of every row of `level`, natural order (host, n). */
+int amg_level_t3(const amg_hierarchy *h, int level, int32_t *t3);
 
 /*
  * One application of the AMLI-cycle preconditioner z = B^_level[f] (Alg. 2) on level

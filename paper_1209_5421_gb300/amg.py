@@ -37,7 +37,8 @@ class Csr(C.Structure):
 class Options(C.Structure):
     _fields_ = [("aux_level", C.c_int), ("coarsest_max", C.c_int), ("kcycle_n", C.c_int),
                 ("max_iters", C.c_int), ("outer", C.c_int), ("cycle_prec", C.c_int),
-                ("fgmres_restart", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4)]
+                ("fgmres_restart", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4),
+                ("zbox", C.c_double * 2)]
 
 
 _lib = None
@@ -72,6 +73,12 @@ def lib():
         L.amg_last_error.restype = C.c_char_p
         L.amg_num_levels.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.amg_get_bbox.argtypes = [P, P]
+        L.amg_setup3.argtypes = [C.POINTER(Csr), P, P, P, C.POINTER(Options), P, C.POINTER(P)]
+        L.amg_setup3.restype = C.c_int
+        L.amg_get_box3.argtypes = [P, P, P]
+        L.amg_get_box3.restype = C.c_int
+        L.amg_level_t3.argtypes = [P, C.c_int, P]
+        L.amg_level_t3.restype = C.c_int
         L.amg_level_info.argtypes = [P, C.c_int, P]
         L.amg_level_export.argtypes = [P, C.c_int] + [P] * 7
         L.amg_apply_cycle.argtypes = [P, C.c_int, P, P, P]
@@ -157,10 +164,12 @@ class Hierarchy:
 
     def __init__(self, rowptr, col, val, x, y, aux_level=0, coarsest_max=64, kcycle_n=2,
                  max_iters=200, cycle_prec=FP64, outer=OUTER_FCG, fgmres_restart=30,
-                 bbox=None, stream=None):
+                 bbox=None, stream=None, z=None):
+        """z given: the octree (3D) variant (amg_setup3); bbox then has 6 entries."""
         L = lib()
         self._keep = (_as(rowptr, np.int32), _as(col, np.int32), _as(val, np.float64),
                       _as(x, np.float64), _as(y, np.float64))
+        zz = _as(z, np.float64) if z is not None else None
         rp, cl, vl, xx, yy = self._keep
         n = len(rp) - 1
         nnz = len(cl)
@@ -173,8 +182,15 @@ class Hierarchy:
             o.has_bbox = 1
             for k in range(4):
                 o.bbox[k] = bbox[k]
+            if len(bbox) >= 6:
+                o.zbox[0], o.zbox[1] = bbox[4], bbox[5]
         h = C.c_void_p()
-        st = L.amg_setup(C.byref(A), _ptr(xx), _ptr(yy), C.byref(o), _stream(stream), C.byref(h))
+        if zz is not None:
+            st = L.amg_setup3(C.byref(A), _ptr(xx), _ptr(yy), _ptr(zz), C.byref(o),
+                              _stream(stream), C.byref(h))
+        else:
+            st = L.amg_setup(C.byref(A), _ptr(xx), _ptr(yy), C.byref(o), _stream(stream),
+                             C.byref(h))
         self._keep = None
         _check(st, "amg_setup")
         self.h = h
@@ -182,12 +198,26 @@ class Hierarchy:
 
     @classmethod
     def from_problem(cls, prob, **kw):
+        if getattr(prob, "z", None) is not None:
+            kw.setdefault("z", prob.z)
         return cls(prob.rowptr, prob.col, prob.val, prob.x, prob.y, **kw)
 
     def close(self):
         if getattr(self, "h", None):
             lib().amg_free(self.h)
             self.h = None
+
+    @property
+    def dim(self) -> int:
+        d = C.c_int()
+        _check(lib().amg_get_box3(self.h, C.byref(d), None), "amg_get_box3")
+        return d.value
+
+    @property
+    def box3(self) -> np.ndarray:
+        b = np.empty(6)
+        _check(lib().amg_get_box3(self.h, None, _ptr(b)), "amg_get_box3")
+        return b
 
     def __del__(self):
         try:
@@ -251,6 +281,9 @@ class Hierarchy:
         _check(lib().amg_level_export(self.h, l, _ptr(out["agg"]), _ptr(out["color"]),
                                       _ptr(out["t1"]), _ptr(out["t2"]), _ptr(out["rowptr"]),
                                       _ptr(out["col"]), _ptr(out["val"])), "amg_level_export")
+        if self.dim == 3:
+            out["t3"] = np.empty(n, np.int32)
+            _check(lib().amg_level_t3(self.h, l, _ptr(out["t3"])), "amg_level_t3")
         out.update(inf)
         return out
 

@@ -72,6 +72,7 @@ struct Level {
     int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block
     int *parent = nullptr;  // [n] pi-row of the next coarser level
     int4 *children = nullptr;  // level >= 2: [n] children pi-rows in level-1 by quadrant
+    int4 *children2 = nullptr; // octree: children 4..7 (octant (t1&1) + 2 (t2&1) + 4 (t3&1))
     int *nat = nullptr;     // [n] natural index of pi-row p
     int *inv = nullptr;     // [n] pi-row of natural index
     int *cell = nullptr;    // [n] cell index t1 + cellw * t2 of pi-row p
@@ -104,7 +105,8 @@ struct BatchWs {
 struct amg_hierarchy {
     amg_options opt{};
     int L = 0;
-    double bbox[4] = {0, 0, 0, 0};
+    int dim = 2;                        // 2: quadtree (x, y), 3: octree (x, y, z)
+    double bbox[6] = {0, 0, 0, 0, 0, 0};  // a1, b1, a2, b2, a3, b3
     int nlev = 0;
     int64_t N = 0;
     std::vector<amg::Level> lev;
@@ -226,7 +228,9 @@ inline void bind_stream(amg_hierarchy *h, void *user_stream) {
     AMG_CUDA(cudaStreamWaitEvent(h->stream, h->order_ev, 0));
 }
 
-void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y);
+// z: NULL for the quadtree (h->dim 2), the third coordinates for the octree (h->dim 3)
+void build_hierarchy(amg_hierarchy *h, const amg_csr &A, const double *x, const double *y,
+                     const double *z);
 void free_engines(amg_hierarchy *h);
 void profiler_enable(amg_hierarchy *h, int mode);
 void profiler_free(amg_hierarchy *h);

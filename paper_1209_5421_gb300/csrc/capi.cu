@@ -126,6 +126,7 @@ void amg_options_default(amg_options *o) {
     o->fgmres_restart = 30;
     o->has_bbox = 0;
     o->bbox[0] = o->bbox[1] = o->bbox[2] = o->bbox[3] = 0.0;
+    o->zbox[0] = o->zbox[1] = 0.0;
 }
 
 const char *amg_status_string(int s) {
@@ -168,12 +169,13 @@ int check_options(const amg_options &o) {
 
 // a hierarchy from device arrays (A's arrays, x, y on the device); throws amg::Error
 amg_hierarchy *setup_device(const amg_csr &Ad, const double *xd, const double *yd,
-                            const amg_options &o, void *stream) {
+                            const double *zd, const amg_options &o, void *stream) {
     amg_hierarchy *h = nullptr;
     try {
         h = new amg_hierarchy();
         h->opt = o;
         h->N = Ad.n;
+        h->dim = zd ? 3 : 2;
         AMG_CUDA(cudaGetDevice(&h->device));
         init_pool_once(h->device);
         AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
@@ -181,7 +183,7 @@ amg_hierarchy *setup_device(const amg_csr &Ad, const double *xd, const double *y
         amg::bind_stream(h, stream);
         const int64_t l0 = amg::g_launches;
         h->err_flag = amg::halloc<int>(h, 1);
-        amg::build_hierarchy(h, Ad, xd, yd);
+        amg::build_hierarchy(h, Ad, xd, yd, zd);
         amg::allocate_solve_workspace(h);
         AMG_CUDA(cudaStreamSynchronize(h->stream));
         h->setup_launches = amg::g_launches - l0;
@@ -218,8 +220,43 @@ int amg_setup(const amg_csr *A, const double *x, const double *y, const amg_opti
         Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
         const double *xd = to_device(x, (size_t)n, tmp);
         const double *yd = to_device(y, (size_t)n, tmp);
-        *out = setup_device(Ad, xd, yd, o, stream);
+        *out = setup_device(Ad, xd, yd, nullptr, o, stream);
         AMG_CUDA(cudaStreamSynchronize(us));  // the staging copies are read by the setup
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_setup3(const amg_csr *A, const double *x, const double *y, const double *z,
+               const amg_options *opt, void *stream, amg_hierarchy **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A || !x || !y || !z || !A->rowptr || !A->col || !A->val)
+        return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (A->n <= 0) return fail(AMG_ERR_INVALID_ARG, "n must be positive");
+    if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
+        return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
+    if (A->nnz < A->n) return fail(AMG_ERR_BAD_MATRIX, "every row needs its diagonal");
+    amg_options o;
+    if (opt) o = *opt;
+    else amg_options_default(&o);
+    if (int st = check_options(o)) return st;
+    if (o.aux_level > 10) return fail(AMG_ERR_UNSUPPORTED, "octree aux_level must be 0..10");
+    if (o.has_bbox && !(o.zbox[1] > o.zbox[0]))
+        return fail(AMG_ERR_INVALID_ARG, "zbox must have b3 > a3");
+    try {
+        cudaStream_t us = (cudaStream_t)stream;
+        Scratch tmp(us);
+        const int n = (int)A->n;
+        amg_csr Ad = *A;
+        Ad.rowptr = to_device(A->rowptr, (size_t)n + 1, tmp);
+        Ad.col = to_device(A->col, (size_t)A->nnz, tmp);
+        Ad.val = to_device(A->val, (size_t)A->nnz, tmp);
+        const double *xd = to_device(x, (size_t)n, tmp);
+        const double *yd = to_device(y, (size_t)n, tmp);
+        const double *zd = to_device(z, (size_t)n, tmp);
+        *out = setup_device(Ad, xd, yd, zd, o, stream);
+        AMG_CUDA(cudaStreamSynchronize(us));
         return AMG_OK;
     }
     AMG_CATCH
@@ -348,7 +385,7 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
             k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
             AMG_CUDA(cudaGetLastError());
             amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
-            bt->hs.push_back(setup_device(Ap, xd + r0, yd + r0, o, stream));
+            bt->hs.push_back(setup_device(Ap, xd + r0, yd + r0, nullptr, o, stream));
         }
         bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, 0);
         AMG_CUDA(cudaStreamSynchronize(us));
@@ -501,6 +538,29 @@ int amg_level_info(const amg_hierarchy *h, int level, int64_t info[8]) {
     return AMG_OK;
 }
 
+int amg_level_t3(const amg_hierarchy *h, int level, int32_t *t3) {
+    if (!h || !t3) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    if (level < 0 || level >= h->nlev) return fail(AMG_ERR_INVALID_ARG, "level out of range");
+    try {
+        const amg::Level &lv = h->lev[level];
+        const int n = lv.n;
+        AMG_CUDA(cudaStreamSynchronize(h->stream));
+        std::vector<int> c(n);
+        AMG_CUDA(cudaMemcpy(c.data(), h->cell_nat[level], sizeof(int) * n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; i++) t3[i] = c[i] / lv.cellw / lv.cellw;
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_get_box3(const amg_hierarchy *h, int *dim, double box[6]) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    if (dim) *dim = h->dim;
+    if (box)
+        for (int k = 0; k < 6; k++) box[k] = h->bbox[k];
+    return AMG_OK;
+}
+
 int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *color,
                      int32_t *t1, int32_t *t2, int32_t *rowptr, int32_t *col, double *val) {
     if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
@@ -518,9 +578,9 @@ int amg_level_export(const amg_hierarchy *h, int level, int32_t *agg, int32_t *c
         if (t1 || t2) {
             std::vector<int> c(n);
             AMG_CUDA(cudaMemcpy(c.data(), h->cell_nat[level], sizeof(int) * n, cudaMemcpyDeviceToHost));
-            for (int i = 0; i < n; i++) {
+            for (int i = 0; i < n; i++) {  // cell = t1 + w (t2 + w t3)
                 if (t1) t1[i] = c[i] % lv.cellw;
-                if (t2) t2[i] = c[i] / lv.cellw;
+                if (t2) t2[i] = (c[i] / lv.cellw) % lv.cellw;
             }
         }
         if (rowptr || col || val) {

@@ -65,6 +65,7 @@ struct LevelDev {
     const int *bptr;
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
+    const int4 *children2;          // octree: their children 4..7 (NULL on a quadtree)
     const double *Ainv;             // coarsest: dense inverse, FP64 (FP64 cycle)
     const float *Ainv2;             // coarsest, FP32 cycle: the same inverse as n*n high parts
                                     // followed by n*n low parts (Ainv ~ high + low)
@@ -89,6 +90,7 @@ struct StagedLevel {
     const int *bptr;                // unused (fine = 0)
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
+    const int4 *children2;          // octree: their children 4..7 (NULL on a quadtree)
     const double *Ainv;
     const float *Ainv2;
     T *rhs, *e, *r;
@@ -391,8 +393,8 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
 }
 
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
-// coarser levels the (up to four) children of each coarse cell (Sec. 4.3 explicit form),
-// one lane per child and a two-step shuffle (nth must be a multiple of 32)
+// coarser levels the (up to four, octree eight) children of each coarse cell (Sec. 4.3
+// explicit form), one lane per child and a shuffle tree (nth must be a multiple of 32)
 // With un non-null, the next level's smoothing starts here as well (Op::fuse):
 // un[R] = fc[R] / a_RR on the next level's first colour [f0, f1), 0 elsewhere.
 template <class LV>
@@ -410,17 +412,21 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
         }
         return;
     }
-    const int q = tid & 3, per_pass = nth >> 2;
+    const bool oct = L.children2 != nullptr;
+    const int lg = oct ? 3 : 2;  // log2 of the lanes per coarse row
+    const int q = tid & ((1 << lg) - 1), per_pass = nth >> lg;
     for (int base = 0; base < L.nnext; base += per_pass) {
-        const int R = base + (tid >> 2);
+        const int R = base + (tid >> lg);
         T v = 0;
         if (R < L.nnext) {
-            const int4 ch = L.children[R];
-            const int c = q == 0 ? ch.x : q == 1 ? ch.y : q == 2 ? ch.z : ch.w;
+            const int4 ch = (q < 4 ? L.children : L.children2)[R];
+            const int qq = q & 3;
+            const int c = qq == 0 ? ch.x : qq == 1 ? ch.y : qq == 2 ? ch.z : ch.w;
             if (c >= 0) v = row_residual(L, c, f, u);
         }
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (oct) v += __shfl_xor_sync(0xffffffffu, v, 4);
         if (R < L.nnext && q == 0) {
             fc[R] = v;
             if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);

@@ -20,7 +20,7 @@ constexpr int kT = 256;
 __global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rowptr,
                            const int *__restrict__ col, const double *__restrict__ val,
                            const double *__restrict__ x, const double *__restrict__ y,
-                           int *err) {
+                           const double *__restrict__ z, int *err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int flags = 0;
@@ -45,7 +45,7 @@ __global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rowptr,
         }
         if (!diag) flags |= 1;
     }
-    if (!isfinite(x[i]) || !isfinite(y[i])) flags |= 2;
+    if (!isfinite(x[i]) || !isfinite(y[i]) || (z && !isfinite(z[i]))) flags |= 2;
     if (flags) atomicOr(err, flags);
 }
 
@@ -117,13 +117,25 @@ __device__ __forceinline__ int cell_1d(double v, double lo, double hi, int L) {
 }
 
 // level-L aggregate label of every unknown (eq. agg_L): i = ty * 2^L + tx
+// Cells are indexed t1 + w (t2 + w t3), w = 2^level: t3 = 0 on the quadtree, so the same
+// decoding serves both trees (cell_t1 / cell_t2 / cell_t3 below).
 __global__ void k_bin(int n, const double *__restrict__ x, const double *__restrict__ y,
-                      const double *__restrict__ bbox, int L, int *__restrict__ cell) {
+                      const double *__restrict__ z, const double *__restrict__ bbox, int L,
+                      int *__restrict__ cell) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int tx = cell_1d(x[j], bbox[0], bbox[1], L);
     int ty = cell_1d(y[j], bbox[2], bbox[3], L);
-    cell[j] = ty * (1 << L) + tx;
+    int tz = z ? cell_1d(z[j], bbox[4], bbox[5], L) : 0;
+    cell[j] = (tz * (1 << L) + ty) * (1 << L) + tx;
+}
+__device__ __forceinline__ int cell_t1(int c, int w) { return c % w; }
+__device__ __forceinline__ int cell_t2(int c, int w) { return (c / w) % w; }
+__device__ __forceinline__ int cell_t3(int c, int w) { return c / w / w; }
+// parent cell on the grid of width w/2: every coordinate halved (eq. agg_k, both trees)
+__device__ __forceinline__ int parent_cell(int c, int w) {
+    const int h = w >> 1;
+    return ((cell_t3(c, w) >> 1) * h + (cell_t2(c, w) >> 1)) * h + (cell_t1(c, w) >> 1);
 }
 
 // parent cell of a cell of a grid of width w (Sec. 4.2 coarse-level form):
@@ -131,8 +143,7 @@ __global__ void k_bin(int n, const double *__restrict__ x, const double *__restr
 __global__ void k_parent_cell(int n, const int *__restrict__ cell, int w, int *__restrict__ pc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int c = cell[i];
-    pc[i] = ((c / w) >> 1) * (w >> 1) + ((c % w) >> 1);
+    pc[i] = parent_cell(cell[i], w);
 }
 
 __global__ void k_mark(int n, const int *__restrict__ cid, int *__restrict__ occ) {
@@ -165,8 +176,9 @@ __global__ void k_scatter_inv(int n, const int *__restrict__ nat, int *__restric
 // ---------------------------------------------------------------------------------------
 // span s: the largest |dt1|, |dt2| between the cells of the row and column of an entry
 __device__ __forceinline__ int cell_dist(int a, int b, int w) {
-    int d1 = abs(a % w - b % w), d2 = abs(a / w - b / w);
-    return d1 > d2 ? d1 : d2;
+    int d1 = abs(cell_t1(a, w) - cell_t1(b, w)), d2 = abs(cell_t2(a, w) - cell_t2(b, w));
+    int d3 = abs(cell_t3(a, w) - cell_t3(b, w));
+    return max(max(d1, d2), d3);
 }
 
 __device__ __forceinline__ void block_max_atomic(int v, int *out) {
@@ -201,14 +213,11 @@ __global__ void k_span_parent(int n, const int *__restrict__ sl, const int *__re
     int s = 0;
     if (i < n) {
         const int base = sl[i >> 5] + (i & 31), width = (sl[(i >> 5) + 1] - sl[i >> 5]) >> 5;
-        int ci = cell[i];
-        int pi = ((ci / w) >> 1) * (w >> 1) + ((ci % w) >> 1);
+        int pi = parent_cell(cell[i], w);
         for (int k = 0; k < width; k++) {
             int c = col[base + 32 * k];
             if (c < 0) continue;
-            int cc = cell[c];
-            int pc = ((cc / w) >> 1) * (w >> 1) + ((cc % w) >> 1);
-            s = max(s, cell_dist(pi, pc, w >> 1));
+            s = max(s, cell_dist(pi, parent_cell(cell[c], w), w >> 1));
         }
     }
     block_max_atomic(s, span);
@@ -220,7 +229,7 @@ __global__ void k_colors(int n, const int *__restrict__ cell, int w, int m,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cell[i];
-    color[i] = (c % w) % m + m * ((c / w) % m);
+    color[i] = cell_t1(c, w) % m + m * (cell_t2(c, w) % m) + m * m * (cell_t3(c, w) % m);
 }
 
 // cnt[k] += number of i with key[i] == k, keys in [0, nbins): a shared-memory histogram per
@@ -326,15 +335,17 @@ __global__ void k_fill_csr(int n, const int *__restrict__ nat, const int *__rest
 // summation order (members ascending, slots ascending): deterministic, no atomics.
 // COUNT pass writes the row lengths; FILL pass writes diagonal slot first, then the touched
 // slots in ascending offset order (= ascending coarse aggregate number).
-template <int SMAX, bool FINE, bool FILL>
+template <int SMAX, bool FINE, bool FILL, int DIM>
 __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restrict__ children,
+                      const int4 *__restrict__ children2,
                       const int *__restrict__ fsl, const int *__restrict__ fcol,
                       const double *__restrict__ fval, const int *__restrict__ fparent,
                       const int *__restrict__ ccell, int cw, int s, const int *__restrict__ csl,
                       int *__restrict__ clen, int *__restrict__ ccol,
                       double *__restrict__ cval, int *err) {
     constexpr int WMAX = 2 * SMAX + 1;
-    constexpr int NS = WMAX * WMAX;
+    constexpr int NS = DIM == 3 ? WMAX * WMAX * WMAX : WMAX * WMAX;
+    constexpr int NKIDS = DIM == 3 ? 8 : 4;
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
     const int W = 2 * s + 1;
@@ -347,9 +358,9 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
         for (int t = 0; t < NS; t++) acc[t] = 0.0;
     }
     const int cP = ccell[P];
-    const int p1 = cP % cw, p2 = cP / cw;
+    const int p1 = cell_t1(cP, cw), p2 = cell_t2(cP, cw), p3 = cell_t3(cP, cw);
     int rbeg, rend;
-    int kids[4];
+    int kids[NKIDS];
     if (FINE) {
         rbeg = bptr[P];
         rend = bptr[P + 1];
@@ -359,8 +370,15 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
         kids[1] = ch.y;
         kids[2] = ch.z;
         kids[3] = ch.w;
+        if constexpr (DIM == 3) {
+            int4 c2 = children2[P];
+            kids[4] = c2.x;
+            kids[5] = c2.y;
+            kids[6] = c2.z;
+            kids[7] = c2.w;
+        }
         rbeg = 0;
-        rend = 4;
+        rend = NKIDS;
     }
     for (int it = rbeg; it < rend; it++) {
         int i = FINE ? it : kids[it];
@@ -371,12 +389,13 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
             if (c < 0) continue;
             int C = fparent[c];
             int cC = ccell[C];
-            int d1 = cC % cw - p1, d2 = cC / cw - p2;
-            if (d1 < -s || d1 > s || d2 < -s || d2 > s) {
+            int d1 = cell_t1(cC, cw) - p1, d2 = cell_t2(cC, cw) - p2, d3 = cell_t3(cC, cw) - p3;
+            if (d1 < -s || d1 > s || d2 < -s || d2 > s || d3 < -s || d3 > s) {
                 atomicOr(err, 4);
                 continue;
             }
-            int t = (d2 + s) * W + (d1 + s);
+            // slots in ascending offset order (d3, d2, d1) = ascending coarse cell index
+            int t = ((DIM == 3 ? (d3 + s) * W : 0) + (d2 + s)) * W + (d1 + s);
             bits[t >> 6] |= 1ull << (t & 63);
             if (FILL) {
                 acc[t] += fval[base + 32 * k];
@@ -384,7 +403,8 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
             }
         }
     }
-    const int center = s * W + s;
+    const int center = DIM == 3 ? (s * W + s) * W + s : s * W + s;
+    const int nslot = DIM == 3 ? W * W * W : W * W;
     if (!FILL) {
         int cnt = 0;
 #pragma unroll
@@ -397,7 +417,7 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
     ccol[base] = P;
     cval[base] = acc[center];
     int k = 1;
-    for (int t = 0; t < W * W; t++) {
+    for (int t = 0; t < nslot; t++) {
         if (t == center || !((bits[t >> 6] >> (t & 63)) & 1ull)) continue;
         ccol[base + 32 * k] = cof[t];
         cval[base + 32 * k] = acc[t];
@@ -438,13 +458,16 @@ __global__ void k_parent_pi(int n, const int *__restrict__ nat, const int *__res
 }
 
 // children of every coarse pi-row by quadrant q = (t1 & 1) + 2 (t2 & 1) of the child cell
+// child of its parent by quadrant / octant q = (t1&1) + 2 (t2&1) + 4 (t3&1): q < 4 in
+// children, q >= 4 (octree) in children2
 __global__ void k_children(int n, const int *__restrict__ parent, const int *__restrict__ cell,
-                           int cw, int4 *__restrict__ children) {
+                           int cw, int4 *__restrict__ children, int4 *__restrict__ children2) {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int c = cell[p];
-    int q = ((c % cw) & 1) + 2 * ((c / cw) & 1);
-    reinterpret_cast<int *>(children + parent[p])[q] = p;
+    int q = (cell_t1(c, cw) & 1) + 2 * (cell_t2(c, cw) & 1) + 4 * (cell_t3(c, cw) & 1);
+    int4 *dst = q < 4 ? children : children2;
+    reinterpret_cast<int *>(dst + parent[p])[q & 3] = p;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -599,7 +622,7 @@ void order_level(amg_hierarchy *h, Level &lv, const int *cell_nat, int *color_na
     cudaStream_t s = h->stream;
     int n = lv.n;
     lv.m = std::max(2, lv.span + 1);
-    lv.ncolors = lv.m * lv.m;
+    lv.ncolors = lv.m * lv.m * (h->dim == 3 ? lv.m : 1);
     k_colors<<<nblocks_for(n, kT), kT, 0, s>>>(n, cell_nat, lv.cellw, lv.m, color_nat);
     AMG_LAUNCH_CHECK();
     Scratch tmp(s);
@@ -630,25 +653,31 @@ void launch_rap(amg_hierarchy *h, Level &f, Level &c, bool fill, int *len) {
     cudaStream_t s = h->stream;
     int span = c.span;
     int nb = nblocks_for(c.n, 128);
-#define AMG_RAP_CASE(SM)                                                                    \
+#define AMG_RAP_CASE(SM, D)                                                                 \
     if (fill)                                                                               \
-        k_rap<SM, FINE, true><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, f.A.sl_ptr,       \
-                                                 f.A.col, f.A.val, f.parent, c.cell,       \
-                                                 c.cellw, span, c.A.sl_ptr, nullptr,       \
-                                                 c.A.col, c.A.val, h->err_flag);           \
+        k_rap<SM, FINE, true, D><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, c.children2,   \
+                                                    f.A.sl_ptr, f.A.col, f.A.val, f.parent, \
+                                                    c.cell, c.cellw, span, c.A.sl_ptr,      \
+                                                    nullptr, c.A.col, c.A.val, h->err_flag); \
     else                                                                                    \
-        k_rap<SM, FINE, false><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, f.A.sl_ptr,      \
-                                                  f.A.col, f.A.val, f.parent, c.cell,      \
-                                                  c.cellw, span, nullptr, len, nullptr,    \
-                                                  nullptr, h->err_flag);
-    if (span <= 1) {
-        AMG_RAP_CASE(1)
+        k_rap<SM, FINE, false, D><<<nb, 128, 0, s>>>(c.n, f.bptr, c.children, c.children2,  \
+                                                     f.A.sl_ptr, f.A.col, f.A.val, f.parent,\
+                                                     c.cell, c.cellw, span, nullptr, len,   \
+                                                     nullptr, nullptr, h->err_flag);
+    if (h->dim == 3) {  // octree: spans up to 2 (build_hierarchy rejects wider ones)
+        if (span <= 1) {
+            AMG_RAP_CASE(1, 3)
+        } else {
+            AMG_RAP_CASE(2, 3)
+        }
+    } else if (span <= 1) {
+        AMG_RAP_CASE(1, 2)
     } else if (span <= 2) {
-        AMG_RAP_CASE(2)
+        AMG_RAP_CASE(2, 2)
     } else if (span <= 4) {
-        AMG_RAP_CASE(4)
+        AMG_RAP_CASE(4, 2)
     } else {
-        AMG_RAP_CASE(8)
+        AMG_RAP_CASE(8, 2)
     }
 #undef AMG_RAP_CASE
     AMG_LAUNCH_CHECK();
@@ -703,7 +732,8 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
 }  // namespace
 
 // =======================================================================================
-void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, const double *y) {
+void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, const double *y,
+                     const double *z) {
     cudaStream_t s = h->stream;
     const int n = (int)Ain.n;
     const amg_options &o = h->opt;
@@ -711,18 +741,21 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
     // ---- validation
     AMG_CUDA(cudaMemsetAsync(h->err_flag, 0, sizeof(int), s));
     k_validate<<<nblocks_for(n, kT), kT, 0, s>>>(n, Ain.nnz, Ain.rowptr, Ain.col, Ain.val, x, y,
-                                                h->err_flag);
+                                                z, h->err_flag);
     AMG_LAUNCH_CHECK();
     int err = read_int(h->err_flag, s);
     if (err & 1) throw Error{AMG_ERR_BAD_MATRIX, "matrix is not valid SPD CSR input"};
     if (err & 2) throw Error{AMG_ERR_INVALID_ARG, "non-finite coordinate"};
 
     Scratch tmp(s);
-    // ---- auxiliary box (eq. ab12)
-    double *d_bbox = tmp.get<double>(4);
+    // ---- auxiliary box (eq. ab12; the octree adds [a3, b3] from z)
+    const int dim = h->dim;
+    double *d_bbox = tmp.get<double>(6);
     if (o.has_bbox) {
         for (int k = 0; k < 4; k++) h->bbox[k] = o.bbox[k];
-        AMG_CUDA(cudaMemcpyAsync(d_bbox, h->bbox, sizeof(double) * 4, cudaMemcpyHostToDevice, s));
+        h->bbox[4] = o.zbox[0];
+        h->bbox[5] = o.zbox[1];
+        AMG_CUDA(cudaMemcpyAsync(d_bbox, h->bbox, sizeof(double) * 6, cudaMemcpyHostToDevice, s));
     } else {
         int nb = std::min(nblocks_for(n, kT), 1024);
         double *part = tmp.get<double>(4 * nb);
@@ -730,17 +763,25 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         AMG_LAUNCH_CHECK();
         k_minmax_final<<<1, 32, 0, s>>>(nb, part, d_bbox);
         AMG_LAUNCH_CHECK();
-        AMG_CUDA(cudaMemcpyAsync(h->bbox, d_bbox, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        if (dim == 3) {  // (z, z): a3, b3 twice, into d_bbox[4..7]
+            double *zb = tmp.get<double>(4);
+            k_minmax_partial<<<nb, kT, 0, s>>>(n, z, z, part);
+            AMG_LAUNCH_CHECK();
+            k_minmax_final<<<1, 32, 0, s>>>(nb, part, zb);
+            AMG_LAUNCH_CHECK();
+            AMG_CUDA(cudaMemcpyAsync(d_bbox + 4, zb, sizeof(double) * 2, cudaMemcpyDeviceToDevice, s));
+        }
+        AMG_CUDA(cudaMemcpyAsync(h->bbox, d_bbox, sizeof(double) * 6, cudaMemcpyDeviceToHost, s));
     }
-    // ---- depth L (Sec. 3.1): largest L with 4^L <= n
+    // ---- depth L (Sec. 3.1): the largest L with 4^L <= n (octree: 8^L <= n)
     int L = o.aux_level;
     if (L == 0)
-        while ((int64_t)1 << (2 * (L + 1)) <= (int64_t)n) L++;
+        while ((int64_t)1 << (dim * (L + 1)) <= (int64_t)n) L++;
     h->L = L;
 
     // ---- level-L cells of the unknowns
     int *cellL = tmp.get<int>(n);
-    k_bin<<<nblocks_for(n, kT), kT, 0, s>>>(n, x, y, d_bbox, L, cellL);
+    k_bin<<<nblocks_for(n, kT), kT, 0, s>>>(n, x, y, dim == 3 ? z : nullptr, d_bbox, L, cellL);
     AMG_LAUNCH_CHECK();
 
     // ---- aggregates of every level, natural numbering (ascending cell index)
@@ -756,7 +797,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
     while (nat.back().n > o.coarsest_max) {
         Nat &cur = nat.back();
         const int w = 1 << k;
-        const int64_t ncell = (int64_t)w * w;
+        const int64_t ncell = (int64_t)w * w * (dim == 3 ? w : 1);
         int *cid;
         if (nat.size() == 1) {
             cid = cur.cell;
@@ -807,13 +848,15 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
     AMG_LAUNCH_CHECK();
     int span0 = read_int(d_span, s);
     if (span0 > 8) throw Error{AMG_ERR_UNSUPPORTED, "fine couplings span more than 8 auxiliary cells"};
+    if (dim == 3 && span0 > 2)
+        throw Error{AMG_ERR_UNSUPPORTED, "octree: fine couplings span more than 2 auxiliary cells"};
 
     Level &F = h->lev[0];
     F.span = span0;
     if (nlev == 1) {
         // the fine level is the coarsest: natural order, exact inverse only
         F.m = std::max(2, span0 + 1);
-        F.ncolors = F.m * F.m;
+        F.ncolors = F.m * F.m * (dim == 3 ? F.m : 1);
         k_colors<<<nblocks_for(n, kT), kT, 0, s>>>(n, cellL, 1 << L, F.m, color_nat[0]);
         AMG_LAUNCH_CHECK();
         F.nat = halloc<int>(h, n);
@@ -896,14 +939,20 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
                                                               f.cellw, d_span);
             AMG_LAUNCH_CHECK();
             c.span = read_int(d_span, s);
+            if (dim == 3 && c.span > 2)
+                throw Error{AMG_ERR_UNSUPPORTED, "octree: a coarse operator spans more than 2 cells"};
             order_level(h, c, cell_nat[l], color_nat[l]);
             f.parent = halloc<int>(h, f.n);
             k_parent_pi<<<nblocks_for(f.n, kT), kT, 0, s>>>(f.n, f.nat, f.agg_nat, c.inv, f.parent);
             AMG_LAUNCH_CHECK();
             c.children = halloc<int4>(h, c.n);
             AMG_CUDA(cudaMemsetAsync(c.children, 0xff, sizeof(int4) * c.n, s));
+            if (dim == 3) {
+                c.children2 = halloc<int4>(h, c.n);
+                AMG_CUDA(cudaMemsetAsync(c.children2, 0xff, sizeof(int4) * c.n, s));
+            }
             k_children<<<nblocks_for(f.n, kT), kT, 0, s>>>(f.n, f.parent, f.cell, f.cellw,
-                                                           c.children);
+                                                           c.children, c.children2);
             AMG_LAUNCH_CHECK();
             galerkin(h, f, c, false);
         }

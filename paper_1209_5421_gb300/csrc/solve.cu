@@ -36,7 +36,7 @@ struct TailLevelLayout {
     int gmem;    // 1: the level stays in HBM/L2 (top tail level only); its scalars are staged
     int w;       // staged: slice width of the image (every slice padded to it)
     int colors, ncolors;  // staged int[ncolors + 1]: pi-row range of each colour
-    int col, val, dinv, parent, children, Ainv, rhs, e, r;
+    int col, val, dinv, parent, children, children2, Ainv, rhs, e, r;
     int p[kMaxKcycle], q[kMaxKcycle];
 };
 struct TailLayout {
@@ -115,6 +115,8 @@ __device__ __forceinline__ StagedLevel<T, W> staged_level(int l) {
     V.bptr = nullptr;
     V.parent = (const int *)at(y.parent);
     V.children = (const int4 *)at(l + 1 < nlev ? tail_lay[l + 1].children : -1);
+    V.children2 = (l + 1 < nlev && tail_lay[l + 1].children2 >= 0)
+                      ? (const int4 *)(amg_smem + tail_lay[l + 1].children2) : nullptr;
     V.Ainv = (const double *)at(y.Ainv);  // FP64 cycle: n*n doubles
     V.Ainv2 = (const float *)at(y.Ainv);  // FP32 cycle: 2*n*n floats, the same bytes
     V.rhs = (T *)at(y.rhs);
@@ -350,6 +352,8 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
                 S.parent = G.parent;
                 S.children = (l + 1 < Y.nlev && Y.lv[l + 1].children >= 0)
                                  ? (const int4 *)(amg_smem + Y.lv[l + 1].children) : nullptr;
+                S.children2 = (l + 1 < Y.nlev && Y.lv[l + 1].children2 >= 0)
+                                  ? (const int4 *)(amg_smem + Y.lv[l + 1].children2) : nullptr;
                 S.Ainv = G.Ainv;
                 S.Ainv2 = G.Ainv2;
                 S.rhs = G.rhs;
@@ -388,6 +392,9 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
         if (y.children >= 0)  // children of this level's rows (in level l-1)
             for (int i = tid; i < y.n; i += nth)
                 ((int4 *)(amg_smem + y.children))[i] = a.tab[l - 1].children[i];
+        if (y.children2 >= 0)  // octree: children 4..7
+            for (int i = tid; i < y.n; i += nth)
+                ((int4 *)(amg_smem + y.children2))[i] = a.tab[l - 1].children2[i];
         if (y.Ainv >= 0) {  // n*n doubles or 2*n*n floats
             if (sizeof(T) == 8)
                 for (int i = tid; i < y.n * y.n; i += nth)
@@ -1115,6 +1122,7 @@ void fill_tables(amg_hierarchy *h) {
         d.bptr = lv.bptr;
         d.parent = lv.parent;
         d.children = (l + 1 < h->nlev) ? h->lev[l + 1].children : nullptr;
+        d.children2 = (l + 1 < h->nlev) ? h->lev[l + 1].children2 : nullptr;
         d.Ainv = lv.Ainv;
         d.Ainv2 = lv.Ainv32;
         Vecs<T> &v = vecs<T>(lv);
@@ -1191,7 +1199,7 @@ bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
             if (lv.n > 65535 || lv.coarsest) return false;
             y.gmem = 1;
             y.w = 0;
-            y.col = y.val = y.dinv = y.parent = y.children = y.Ainv = -1;
+            y.col = y.val = y.dinv = y.parent = y.children = y.children2 = y.Ainv = -1;
             y.rhs = y.e = y.r = -1;
             for (int k = 0; k < kMaxKcycle; k++) y.p[k] = y.q[k] = -1;
             continue;
@@ -1204,6 +1212,7 @@ bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
         y.dinv = lv.coarsest ? -1 : take((size_t)vb * lv.n);
         y.parent = lv.coarsest ? -1 : take(sizeof(int) * (size_t)lv.n);
         y.children = (l > l0) ? take(sizeof(int4) * (size_t)lv.n) : -1;
+        y.children2 = (l > l0 && lv.children2) ? take(sizeof(int4) * (size_t)lv.n) : -1;
         y.Ainv = lv.coarsest ? take(sizeof(double) * lv.n * lv.n) : -1;
         y.rhs = take((size_t)vb * lv.n);
         y.e = take((size_t)vb * lv.n);
