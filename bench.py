@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-octree", action="store_true")
+    ap.add_argument("--octree-n", type=int, default=129)
     ap.add_argument("--serve-rate", type=float, default=100.0)
     ap.add_argument("--serve-requests", type=int, default=96)
     return ap.parse_args()
@@ -333,6 +335,57 @@ def run_batched(args, world, flush, dev, stream):
     }
 
 
+def run_octree(args, world, flush, dev, stream):
+    """The octree (3D) variant: P1 Poisson on the unit cube, an octree_n^3-node Kuhn
+    tetrahedral grid with jittered interior nodes ((octree_n - 2)^3 unknowns), setup + solve
+    per step like the headline (FP32 AMLI-cycle with FGMRES(30), and the plain FP64 method)."""
+    import torch
+
+    from paper_1209_5421_gb300 import amg
+    from paper_1209_5421_gb300.meshes import p1_poisson_3d
+
+    prob = p1_poisson_3d(args.octree_n, seed=0)
+    td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
+    A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
+    z = td(prob.z)
+    b = td(prob.b)
+    x = torch.empty_like(b)
+    out = {"workload": f"3D jittered P1 Poisson, {args.octree_n}^3-node Kuhn tetrahedral grid",
+           "unknowns": prob.n, "nnz": prob.nnz}
+    steps = max(1, min(args.steps, 5))
+    for name, o in (("fp32_fgmres", dict(cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES)),
+                    ("fp64_fcg", dict(cycle_prec=amg.FP64, outer=amg.OUTER_FCG))):
+        def step():
+            h = amg.Hierarchy(*A, z=z, **o)
+            _, it, rr, st = h.solve(b, args.tol, x=x)
+            nlev = h.nlev
+            h.close()
+            if st != amg.OK:
+                raise RuntimeError(f"octree {name}: status {st}, relres {rr}")
+            return it, nlev
+
+        for _ in range(max(1, args.warmup)):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize()
+        barrier(world)
+        lat = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            it, nlev = step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(ev0.elapsed_time(ev1))
+        barrier(world)
+        t = max_over_ranks(world, sum(lat))
+        out[name] = {"value": round(world * steps / (t / 1e3), 3), "unit": "solves/s",
+                     "ms_per_step": round(t / steps, 3), "iters": it, "levels": nlev}
+    return out
+
+
 def run_served(args, local):
     """The served form: a Poisson stream of solve requests at `serve_rate` req/s into the
     continuous-batching server (HBM budget 150 GB). Matrices: 32 jittered P1 Poisson systems,
@@ -520,6 +573,7 @@ def run_ours(args, world, rank, local):
 
     batched = None if args.no_batch else run_batched(args, world, flush, dev, stream)
     served = None if (args.no_serve or rank != 0) else run_served(args, local)
+    octree = None if args.no_octree else run_octree(args, world, flush, dev, stream)
 
     out = None
     if rank == 0:
@@ -555,6 +609,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "batched": batched,
             "served": served,
+            "octree": octree,
         }
         if kernels:
             out["kernels"] = sorted(

@@ -307,9 +307,9 @@ def p1_poisson_3d(n: int, jitter: float = 0.15, seed: int = 0, rhs: str = "norma
     by U(-jitter*h, jitter*h) per coordinate (default_rng(seed), lexicographic node order,
     x, y, z per node), zero Dirichlet data (the unknowns are the (n-2)^3 interior nodes,
     lexicographic with x fastest). rhs: "normal" = N(0,1) from default_rng(seed + 1), "load"
-    = the load vector of f = 1 (|T|/4 per vertex). Assembled element by element; entries of
-    one (row, column) pair are summed in element order, the
-    same bits on every machine; the matrix is exactly symmetric. Tetrahedra are asserted
+    = the load vector of f = 1 (|T|/4 per vertex). Assembled in stencil form (one array per
+    node offset); the entries of one (row, column) pair are summed by tetrahedron type, then
+    by local vertex pair, the same bits on every machine; the matrix is exactly symmetric. Tetrahedra are asserted
     non-degenerate."""
     if n < 3:
         raise ValueError("need at least 3 nodes per side")
@@ -326,60 +326,65 @@ def p1_poisson_3d(n: int, jitter: float = 0.15, seed: int = 0, rhs: str = "norma
         Z = Z + np.where(inner, d[..., 2], 0.0)
     P = np.stack([X, Y, Z], axis=-1).reshape(-1, 3)  # node id = i + n j + n^2 k
     kk, jj, ii = np.meshgrid(np.arange(n - 1), np.arange(n - 1), np.arange(n - 1), indexing="ij")
-    base = (ii + n * jj + n * n * kk).ravel()
+    base = (ii + n * jj + n * n * kk).ravel()  # lowest node of each cube
     step = np.array([1, n, n * n])
-    tets = []
-    for perm in _KUHN:
-        v0 = base
-        v1 = v0 + step[perm[0]]
-        v2 = v1 + step[perm[1]]
-        v3 = v2 + step[perm[2]]
-        tets.append(np.stack([v0, v1, v2, v3], axis=1))
-    T = np.concatenate(tets, axis=0)
-    V = P[T]  # [ne, 4, 3]
-    E = V[:, 1:, :] - V[:, :1, :]  # edges from vertex 0
-    det = np.linalg.det(E)
-    vol = np.abs(det) / 6.0
-    if not np.all(np.abs(det) > 0):
-        raise ValueError("degenerate tetrahedron")
-    # gradients of the barycentric functions: rows of inv(E)^T for vertices 1..3, minus sum
-    Ginv = np.linalg.inv(E)  # [ne, 3, 3]; grad(lambda_a) = Ginv[:, :, a-1] for a = 1..3
-    G = np.empty((T.shape[0], 4, 3))
-    G[:, 1:, :] = np.transpose(Ginv, (0, 2, 1))
-    G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
-    K = vol[:, None, None] * np.einsum("eai,ebi->eab", G, G)  # [ne, 4, 4]
-    K = 0.5 * (K + np.transpose(K, (0, 2, 1)))  # exactly symmetric (IEEE + commutes)
-    # unknowns: interior nodes
-    N = (n - 2) ** 3
-    uid = np.full(n ** 3, -1, np.int64)
     node_i = np.arange(n ** 3)
     ni, nj, nk = node_i % n, (node_i // n) % n, node_i // (n * n)
     inner = (ni > 0) & (ni < n - 1) & (nj > 0) & (nj < n - 1) & (nk > 0) & (nk < n - 1)
+    # A in stencil form: entry (i, i + d) of every node i, one array per node offset d. Every
+    # tetrahedron type puts its vertices at fixed offsets from the cube's base node, so a
+    # (type, local pair) adds to one offset at distinct nodes. Contributions are added type by
+    # type, and within a type by unordered local pair, so (i, j) and (j, i) add the same values
+    # in the same order and A is exactly symmetric.
+    stencil: dict = {}
+    vols, tets = [], []
+    for perm in _KUHN:
+        off = np.cumsum([0] + [int(step[q]) for q in perm])  # vertex offsets from the base
+        T = base[:, None] + off[None, :]
+        V = P[T]  # [ne, 4, 3]
+        E = V[:, 1:, :] - V[:, :1, :]  # edges from vertex 0
+        det = np.linalg.det(E)
+        if not np.all(np.abs(det) > 0):
+            raise ValueError("degenerate tetrahedron")
+        vol = np.abs(det) / 6.0
+        # gradients of the barycentric functions: grad(lambda_a) = column a-1 of inv(E), a >= 1
+        Ginv = np.linalg.inv(E)
+        G = np.empty((T.shape[0], 4, 3))
+        G[:, 1:, :] = np.transpose(Ginv, (0, 2, 1))
+        G[:, 0, :] = -G[:, 1:, :].sum(axis=1)
+        for a in range(4):
+            for b in range(a, 4):
+                kab = vol * np.einsum("ei,ei->e", G[:, a], G[:, b])
+                for (s, t) in ((a, b),) if a == b else ((a, b), (b, a)):
+                    d = int(off[t] - off[s])
+                    acc = stencil.setdefault(d, np.zeros(n ** 3))
+                    acc[T[:, s]] += kab  # distinct nodes within one (type, pair)
+        vols.append(vol)
+        tets.append(T)
+    # unknowns: interior nodes; keep the entries whose column is interior too
+    N = (n - 2) ** 3
+    uid = np.full(n ** 3, -1, np.int64)
     uid[inner] = np.arange(N)
-    r = uid[T][:, :, None].repeat(4, axis=2)
-    c = uid[T][:, None, :].repeat(4, axis=1)
-    keep = (r >= 0) & (c >= 0)
-    import scipy.sparse as sp
-
-    # sum the contributions of each (row, column) in element order (a stable sort of the
-    # keys), so that (i, j) and (j, i) add the same values in the same order
-    rr, cc, vv = r[keep], c[keep], K[keep]
-    key = rr * N + cc
-    order = np.argsort(key, kind="stable")
-    key, vv = key[order], vv[order]
-    first = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
-    vals = np.add.reduceat(vv, first)
-    ukey = key[first]
-    A = sp.csr_matrix((vals, (ukey // N, ukey % N)), shape=(N, N))
-    A.sort_indices()
+    rows_node = node_i[inner]
+    ds = sorted(stencil)
+    cols = np.stack([uid[np.clip(rows_node + d, 0, n ** 3 - 1)] for d in ds], axis=1)
+    vals = np.stack([stencil[d][rows_node] for d in ds], axis=1)
+    valid = np.stack([(rows_node + d >= 0) & (rows_node + d < n ** 3) for d in ds], axis=1)
+    valid &= cols >= 0
+    cnt = valid.sum(axis=1)
+    indptr = np.zeros(N + 1, np.int64)
+    indptr[1:] = np.cumsum(cnt)
+    # offsets ascend, and so do the interior ids of i + d: each row comes out sorted
+    indices, data = cols[valid], vals[valid]
     xs, ys, zs = P[inner, 0].copy(), P[inner, 1].copy(), P[inner, 2].copy()
     if rhs == "normal":
         b = np.random.default_rng(seed + 1).standard_normal(N)
     elif rhs == "load":
         load = np.zeros(n ** 3)
-        np.add.at(load, T.ravel(), np.repeat(vol / 4.0, 4))
+        for T, vol in zip(tets, vols):
+            np.add.at(load, T.ravel(), np.repeat(vol / 4.0, 4))
         b = load[inner].copy()
     else:
         raise ValueError(f"unknown rhs {rhs!r}")
-    return Problem(N, A.indptr.astype(np.int32), A.indices.astype(np.int32),
-                   A.data.astype(np.float64), xs, ys, b, name=name, z=zs)
+    return Problem(N, indptr.astype(np.int32), indices.astype(np.int32),
+                   data.astype(np.float64), xs, ys, b, name=name, z=zs)

@@ -73,7 +73,7 @@ class Server:
         self.prec = cycle_prec
         self.max_batch = max_batch
         self.large = large_unknowns
-        self.matrices: dict = {}                  # key -> (rowptr, col, val, x, y)
+        self.matrices: dict = {}                  # key -> (rowptr, col, val, x, y, z)
         self.res: OrderedDict = OrderedDict()      # key -> _Resident (LRU order)
         self.used = 0
         self.max_used = 0
@@ -100,12 +100,15 @@ class Server:
             t.start()
 
     # ---- client side ------------------------------------------------------------------
-    def register(self, key, rowptr, col, val, x, y):
-        """Make a matrix known to the server (host arrays); it is set up on first use."""
+    def register(self, key, rowptr, col, val, x, y, z=None):
+        """Make a matrix known to the server (host arrays); it is set up on first use.
+
+        With `z` the nodes are points in 3D and the octree auxiliary grid aggregates them."""
         with self.cv:
             self.matrices[key] = (np.asarray(rowptr, np.int32), np.asarray(col, np.int32),
                                   np.asarray(val, np.float64), np.asarray(x, np.float64),
-                                  np.asarray(y, np.float64))
+                                  np.asarray(y, np.float64),
+                                  None if z is None else np.asarray(z, np.float64))
 
     def submit(self, key, b, tol: float = 1e-8) -> Request:
         r = Request(key, np.ascontiguousarray(b, np.float64), tol, time.perf_counter())
@@ -225,7 +228,7 @@ class Server:
                     continue
             try:
                 with self.grid_lock:
-                    h = amg.Hierarchy(*m, cycle_prec=self.prec,
+                    h = amg.Hierarchy(*m[:5], z=m[5], cycle_prec=self.prec,
                                       outer=amg.OUTER_FGMRES if n > self.large else amg.OUTER_FCG)
                     if n <= self.large:  # the cycle copies and batched workspace, allocated now
                         amg.Batch.over([h], threads=1024).close()

@@ -98,3 +98,48 @@ def test_octree_fp32_cycle_full(amg, oracle_mod):
         assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
         assert it <= ito + 3, (it, ito)
         G.close()
+
+
+def test_octree_systems_in_a_batch(amg, oracle_mod):
+    # 3D hierarchies (amg_setup3) batched with a 2D one: one CTA per system, FP32 and FP64
+    from paper_1209_5421_gb300.meshes import p1_poisson
+
+    probs = [p1_poisson_3d(17, seed=1), p1_poisson(65, jitter=0.2, seed=2, rhs="normal"),
+             p1_poisson_3d(33, seed=3), p1_poisson_3d(9, seed=4)]
+    tol = 1e-8
+    for prec in (amg.FP32, amg.FP64):
+        hs = [amg.Hierarchy.from_problem(p, cycle_prec=prec) for p in probs]
+        B = amg.Batch.over(hs)
+        x, it, rr, st = B.solve(np.concatenate([p.b for p in probs]), tol)
+        off = B.row_off
+        for k, p in enumerate(probs):
+            assert st[k] == amg.OK
+            xk = x[off[k]:off[k + 1]]
+            A = p.to_scipy()
+            assert np.linalg.norm(p.b - A @ xk) / np.linalg.norm(p.b) <= tol
+            xo, ito, _, _ = oracle_mod.Hierarchy.from_problem(p).solve(p.b, tol)
+            assert np.linalg.norm(xk - xo) <= 1e-6 * np.linalg.norm(xo)
+            assert it[k] <= ito + 3, (k, it[k], ito)
+        B.close()
+        for h in hs:
+            h.close()
+
+
+def test_octree_served(amg):
+    from paper_1209_5421_gb300.serve import Server
+
+    p = p1_poisson_3d(33, seed=5)
+    S = Server(budget_bytes=1 << 30, workers=2)
+    try:
+        S.register("cube", p.rowptr, p.col, p.val, p.x, p.y, z=p.z)
+        rng = np.random.default_rng(0)
+        bs = [rng.standard_normal(p.n) for _ in range(3)]
+        rs = [S.submit("cube", b) for b in bs]
+        S.drain()
+        A = p.to_scipy()
+        for b, r in zip(bs, rs):
+            assert r.status == amg.OK
+            assert np.linalg.norm(b - A @ r.x) / np.linalg.norm(b) <= 1e-8
+        assert S.stats()["setups"] == 1
+    finally:
+        S.close()
