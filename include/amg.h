@@ -148,7 +148,8 @@ void amg_free(amg_hierarchy *h);
  * calls: they apply the setup and solve above to many independent systems at once. Each
  * system gets its own hierarchy, exactly as amg_setup would build it from its block; the
  * solve runs every system's outer iteration and AMLI-cycle in one persistent kernel, one
- * CTA per system at a time (largest systems first), with flexible CG as the outer method.
+ * CTA (or a team of CTAs for the largest systems) per system at a time, largest systems
+ * first, with flexible CG as the outer method.
  */
 typedef struct amg_batch amg_batch;
 
@@ -174,9 +175,10 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
  * with the same cycle_prec and kcycle_n; borrowed: they must outlive the batch, and a
  * hierarchy must not be solved by two calls at the same time). System p is hs[p]; its rows in
  * the concatenated vectors follow those of hs[0..p-1]. threads: 0 = choose the launch shape
- * by timing on the first solve; 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs
- * per SM). With a fixed shape a system's result does not depend on the other systems of the
- * batch (each system is computed by one CTA in a fixed order). The first batched solve of a
+ * by timing on the first solve, with teams of CTAs for the largest systems (see
+ * amg_batch_set_teams); 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs per
+ * SM), one CTA per system. With a fixed shape a system's result does not depend on the
+ * other systems of the batch (each system is computed by one CTA in a fixed order). The first batched solve of a
  * hierarchy allocates its outer-iteration workspace (64 FP64 directions, about 1 KB per
  * unknown), owned by the hierarchy and counted by amg_hierarchy_bytes.
  * Errors: AMG_ERR_INVALID_ARG (NULL, mixed precisions, a repeated hierarchy, other threads),
@@ -213,6 +215,27 @@ int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_
  * end_ns is each system's latency from the launch of the batch.
  */
 int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns);
+
+/*
+ * Teams of CTAs for the largest systems of a batch. A system far larger than the batch's
+ * average work per CTA would alone set the batch's time on one CTA, so it can be solved by a
+ * team of up to 8 CTAs that split every step's rows and meet at a barrier of their own
+ * (bounded: a wait that runs out ends that system with AMG_ERR_TIMEOUT). A system gets about
+ * ceil(its unknowns / (the batch's unknowns / CTAs of the launch)) CTAs, largest systems
+ * first, while the teams hold at most half of the launch's CTAs. Team sums add the members'
+ * partial sums in a fixed order, so results are reproducible, but they differ in rounding
+ * from a one-CTA solve of the same system.
+ *   max_team: 0 = teams sized as above (the default of a batch created with threads = 0),
+ *             1 = one CTA per system (the default with a fixed shape: a system's result then
+ *             does not depend on the other systems), 2..8 = sized as above, at most max_team.
+ * A batch whose shape is chosen by timing times its shapes again on the next solve.
+ * Errors: AMG_ERR_INVALID_ARG (NULL, max_team outside 0..8).
+ */
+int amg_batch_set_teams(amg_batch *bt, int32_t max_team);
+
+/* CTAs of each system's team in the launch shape in use: team is a host array of nprob
+ * entries (-1 each before the first solve). Errors: AMG_ERR_INVALID_ARG (NULL). */
+int amg_batch_teams(const amg_batch *bt, int32_t *team);
 
 /* System p's hierarchy (owned by the batch; valid until amg_batch_free), NULL if none. */
 amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p);

@@ -98,6 +98,10 @@ def lib():
         L.amg_batch_info.argtypes = [P, P, P, P, P, P]
         L.amg_batch_timeline.argtypes = [P, P, P]
         L.amg_batch_timeline.restype = C.c_int
+        L.amg_batch_set_teams.argtypes = [P, C.c_int32]
+        L.amg_batch_set_teams.restype = C.c_int
+        L.amg_batch_teams.argtypes = [P, P]
+        L.amg_batch_teams.restype = C.c_int
         L.amg_batch_system.argtypes = [P, C.c_int32]
         L.amg_batch_system.restype = P
         L.amg_batch_free.argtypes = [P]
@@ -405,6 +409,17 @@ class Batch:
         self.n = int(self.row_off[-1])
         self._borrowed = list(hierarchies)
         return self
+
+    def set_teams(self, max_team: int):
+        """amg_batch_set_teams: 0 = teams sized per system, 1 = one CTA per system, k = at
+        most k CTAs per system."""
+        _check(lib().amg_batch_set_teams(self.b, int(max_team)), "amg_batch_set_teams")
+
+    def teams(self) -> np.ndarray:
+        """amg_batch_teams: CTAs of each system's team in the launch shape in use."""
+        t = np.zeros(self.nprob, np.int32)
+        _check(lib().amg_batch_teams(self.b, t.ctypes.data), "amg_batch_teams")
+        return t
 
     def close(self):
         if getattr(self, "b", None):

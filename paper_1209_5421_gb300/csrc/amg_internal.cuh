@@ -95,7 +95,7 @@ struct EngineBase;
 struct BatchWs {
     int cap = 0;                    // directions kept before a restart
     double *bo = nullptr, *xo = nullptr, *to = nullptr;
-    double *P = nullptr, *Q = nullptr, *osc = nullptr;
+    double *P = nullptr, *Q = nullptr;
     int *colors = nullptr;          // colour ranges of every level, concatenated
     int cofs[kMaxLevels] = {}, ncol[kMaxLevels] = {};
 };
@@ -263,6 +263,11 @@ int batch_solve(BatchEngine *E, const double *b, double tol, double *x, int *ite
 int batch_shape(const BatchEngine *E, int *threads, int *ctas, double *tuned_ms);
 // per-system start / end of the last solve (ns after the earliest start; host arrays)
 void batch_timeline(const BatchEngine *E, int64_t *start_ns, int64_t *end_ns);
+// teams: max_team 0 = sized per system, 1 = one CTA per system, 2..8 = sized, at most that
+// many CTAs; an autotuned batch times its shapes again on the next solve
+void batch_set_teams(BatchEngine *E, int max_team);
+// CTAs of each system's team in the chosen launch shape (host array; -1 before a solve)
+void batch_teams(const BatchEngine *E, int *team);
 void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
                   double *u_nat);
 

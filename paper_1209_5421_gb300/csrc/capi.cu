@@ -500,6 +500,24 @@ int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns) 
     AMG_CATCH
 }
 
+int amg_batch_set_teams(amg_batch *bt, int32_t max_team) {
+    if (!bt) return fail(AMG_ERR_INVALID_ARG, "NULL batch");
+    if (max_team < 0 || max_team > 8) return fail(AMG_ERR_INVALID_ARG, "max_team must be 0..8");
+    try {
+        amg::batch_set_teams(bt->eng, max_team);
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
+int amg_batch_teams(const amg_batch *bt, int32_t *team) {
+    if (!bt || !team) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    std::vector<int> t(bt->hs.size());
+    amg::batch_teams(bt->eng, t.data());
+    for (size_t p = 0; p < t.size(); p++) team[p] = t[p];
+    return AMG_OK;
+}
+
 amg_hierarchy *amg_batch_system(amg_batch *bt, int32_t p) {
     if (!bt || p < 0 || p >= (int32_t)bt->hs.size()) {
         fail(AMG_ERR_INVALID_ARG, "no such system");

@@ -154,7 +154,7 @@ struct WarpGroup {  // warps [0, nthreads / 32) of the CTA; hardware barrier 1
 
 // ---------------------------------------------------------------------------------------
 // reductions: fixed-order trees, no floating-point atomics (bitwise reproducible)
-enum : int { RM_LASTBLOCK = 0, RM_BLOCK = 1, RM_PARTIAL = 2 };
+enum : int { RM_LASTBLOCK = 0, RM_BLOCK = 1, RM_PARTIAL = 2, RM_TEAM = 3 };
 
 // GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, so reductions keep
 // FP64 work low: in the FP32 cycle a block sums in FP32 (a warp tree, then one warp over the
@@ -214,19 +214,48 @@ __device__ __forceinline__ void block_sum(const A (&v)[NV], double (&r)[NV], con
 }
 
 struct RedCtx {
-    double *partials;        // LASTBLOCK: [NV][gridDim]; PARTIAL: [2][4][gridDim]
-    unsigned int *counter;   // LASTBLOCK only
+    double *partials;        // LASTBLOCK: [NV][gridDim]; PARTIAL: [2][4][gridDim]; TEAM: [4][size]
+    unsigned int *counter;   // LASTBLOCK and TEAM
+    int rank = 0, size = 1;  // TEAM: this CTA's rank in the team of CTAs that runs the op
 };
+
+// RM_TEAM over more than one CTA (out of line: the one-CTA path of the same ops stays
+// small). Every thread of the CTA calls it; r is valid in thread 0. The team's partials are
+// summed in rank order by its last CTA to arrive, which also re-arms the counter.
+static __device__ __noinline__ void team_reduce_store(const double *r, int nv,
+                                                      double *const *out, RedCtx rc) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < nv; k++) rc.partials[k * rc.size + rc.rank] = r[k];
+        __threadfence();
+        const unsigned t = atomicAdd(rc.counter, 1u);
+        last = (t == (unsigned)rc.size - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x < 32) {
+        __threadfence();
+        for (int k = 0; k < nv; k++) {
+            double y = 0.0;
+            for (int b = threadIdx.x; b < rc.size; b += 32) y += __ldcg(&rc.partials[k * rc.size + b]);
+            y = warp_sum(y);
+            if (threadIdx.x == 0 && out[k]) *out[k] = y;
+        }
+        if (threadIdx.x == 0) *rc.counter = 0u;
+    }
+}
 
 // RM_LASTBLOCK: per-block partial; the last block to finish sums them in block order.
 // RM_BLOCK (one CTA): the block sum. RM_PARTIAL (persistent kernel): per-block partials
-// into buffer pb; the next op sums them. Final values are stored by thread 0 into out[k].
+// into buffer pb; the next op sums them. RM_TEAM: LASTBLOCK over the rc.size CTAs of a team
+// (team_reduce_store; a team of one is RM_BLOCK; the group must be the whole CTA). Final
+// values are stored by thread 0 into out[k]; they are visible to the team after its next
+// barrier.
 template <int NV, int RM, class A, class G>
 __device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&out)[NV],
                                              const RedCtx &rc, int pb, const G &g) {
     double r[NV];
     block_sum<NV, A>(v, r, g);
-    if (RM == RM_BLOCK) {  // visible to the block after the executor's next barrier
+    if (RM == RM_BLOCK || (RM == RM_TEAM && rc.size == 1)) {  // visible after the next barrier
         if (threadIdx.x == 0)
 #pragma unroll
             for (int k = 0; k < NV; k++)
@@ -240,13 +269,18 @@ __device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&o
                 rc.partials[((size_t)pb * 4 + k) * gridDim.x + blockIdx.x] = r[k];
         return;
     }
+    if (RM == RM_TEAM) {
+        team_reduce_store(r, NV, out, rc);
+        return;
+    }
     __shared__ bool last;
+    const int nb = (int)gridDim.x;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; k++) rc.partials[k * gridDim.x + blockIdx.x] = r[k];
+        for (int k = 0; k < NV; k++) rc.partials[k * nb + blockIdx.x] = r[k];
         __threadfence();
         unsigned t = atomicAdd(rc.counter, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned)nb - 1);
     }
     g.sync();
     if (last && threadIdx.x < 32) {
@@ -254,8 +288,7 @@ __device__ __forceinline__ void reduce_store(const A (&v)[NV], double *const (&o
 #pragma unroll
         for (int k = 0; k < NV; k++) {
             double y = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-                y += __ldcg(&rc.partials[k * gridDim.x + b]);
+            for (int b = threadIdx.x; b < nb; b += 32) y += __ldcg(&rc.partials[k * nb + b]);
             y = warp_sum(y);
             if (threadIdx.x == 0 && out[k]) *out[k] = y;
         }
@@ -637,7 +670,7 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
         double *out[1] = {&L.sc[SC_RR0 + i]};
         reduce_store<1, RM, T>(v, out, rc, op.red_pb, g);
     }
-    if ((RM == RM_BLOCK || blockIdx.x == 0) && threadIdx.x == 0)
+    if ((RM == RM_BLOCK || (RM == RM_TEAM ? rc.rank == 0 : blockIdx.x == 0)) && threadIdx.x == 0)
         L.sc[SC_STOP0 + i] = stopped ? 1.0 : 0.0;
 }
 

@@ -78,4 +78,6 @@ def test_batch_setup_rejects_bad_arguments_before_touching_the_gpu(libpath):
     assert L.amg_batch_setup(2, ctypes.cast(ro, ctypes.c_void_p), ctypes.byref(A), xp, xp,
                              ctypes.byref(o), None, ctypes.byref(b)) == amg.ERR_UNSUPPORTED
     assert L.amg_batch_solve(None, None, 1e-8, None, None, None, None, None) == amg.ERR_INVALID_ARG
+    assert L.amg_batch_set_teams(None, 0) == amg.ERR_INVALID_ARG
+    assert L.amg_batch_teams(None, None) == amg.ERR_INVALID_ARG
     L.amg_batch_free(None)

@@ -113,3 +113,52 @@ def test_batch_device_buffers_and_zero_rhs(amg):
     xh, ith, _, _ = B.solve(rhs, 1e-8)  # host buffers: the same numbers
     assert np.array_equal(xh, x) and np.array_equal(ith, it)
     B.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_teams_match_oracle_and_one_cta(amg, oracle_mod, prec):
+    # an autotuned batch sizes teams of CTAs for its largest systems: with these few systems
+    # on a full grid every system above 4 rows per thread gets a team
+    probs = [p1_poisson(**s) for s in SPECS] + [p1_poisson(n=257, jitter=0.2, seed=9, rhs="normal")]
+    cp = amg.FP32 if prec == "fp32" else amg.FP64
+    B = amg.Batch.from_problems(probs, cycle_prec=cp)
+    rhs = np.concatenate([p.b for p in probs])
+    tol = 1e-8
+    x, it, rr, st = B.solve(rhs, tol)
+    teams = B.teams()
+    assert teams.max() > 1 and teams.min() >= 1 and teams.max() <= 8
+    assert teams[-1] == teams.max()  # the largest system has the largest team
+    off = B.row_off
+    for k, p in enumerate(probs):
+        slack = 10 if k < len(SPECS) and SPECS[k].get("graded") else 3
+        _check_system(amg, oracle_mod, p, x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, slack)
+    # the same bits again (team sums in rank order)
+    x2, it2, _, _ = B.solve(rhs, tol)
+    assert np.array_equal(x2, x) and np.array_equal(it2, it)
+    # one CTA per system: the same solutions up to rounding, about the same iterations
+    B.set_teams(1)
+    x1, it1, _, st1 = B.solve(rhs, tol)
+    assert (st1 == amg.OK).all() and (B.teams() == 1).all()
+    for k in range(len(probs)):
+        xs, xt = x1[off[k]:off[k + 1]], x[off[k]:off[k + 1]]
+        assert np.linalg.norm(xs - xt) <= 1e-6 * np.linalg.norm(xs)
+        assert abs(int(it1[k]) - int(it[k])) <= 1
+    # a cap on the team size
+    B.set_teams(2)
+    x3, _, _, st3 = B.solve(rhs, tol)
+    assert (st3 == amg.OK).all() and B.teams().max() == 2
+    B.close()
+
+
+def test_fixed_shape_has_no_teams(amg):
+    probs = [p1_poisson(**s) for s in SPECS[:3]]
+    hs = [amg.Hierarchy.from_problem(p, cycle_prec=amg.FP32) for p in probs]
+    B = amg.Batch.over(hs, threads=1024)
+    B.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    assert (B.teams() == 1).all()
+    B.set_teams(4)  # allowed explicitly: the batch's systems then form teams
+    _, _, _, st = B.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    assert (st == amg.OK).all() and B.teams().max() > 1
+    B.close()
+    for h in hs:
+        h.close()
