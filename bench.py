@@ -289,6 +289,7 @@ def run_batched(args, world, flush, dev, stream):
         barrier(world)
         t = max_over_ranks(world, sum(lat))
         info = B.info()
+        team = B.teams()
         B.close()
         if not (sts == amg.OK).all():
             raise RuntimeError(f"batched {name}: statuses {sorted(set(sts.tolist()))}")
@@ -302,6 +303,8 @@ def run_batched(args, world, flush, dev, stream):
             "iters": [int(its.min()), int(its.max())], "relres_max": float(rrs.max()),
             "launch_shape": {"threads": info["threads"], "ctas": info["ctas"],
                              "tuned_ms": [round(v, 2) for v in info["tuned_ms"]]},
+            "teams": {"systems": int((team > 1).sum()), "ctas": int(team[team > 1].sum()),
+                      "largest": int(team.max())},
             "device_bytes": info["bytes"],
         }
     # the plain FP64 method, one system at a time (every 16th system, hierarchies resident)
@@ -324,7 +327,8 @@ def run_batched(args, world, flush, dev, stream):
     return {
         "workload": f"{len(probs)} jittered P1 Poisson systems, n x n nodes, n log-uniform in "
                     f"[45, 450] ({sum(p.n for p in probs)} unknowns)",
-        "method": "FP32 AMLI-cycle, FP64 flexible-CG outer, one CTA per system",
+        "method": "FP32 AMLI-cycle, FP64 flexible-CG outer, one CTA (or a team of CTAs for "
+                  "the largest systems) per system",
         **res.pop("fp32"),
         "fp64_cycle_batched": res["fp64"],
         "fp64_plain_sequential": {

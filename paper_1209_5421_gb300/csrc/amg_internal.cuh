@@ -67,6 +67,8 @@ struct Level {
     Sell A;
     std::vector<int> color_rows;    // host [ncolors+1]: pi-row range of each colour
     std::vector<int64_t> color_nnz; // host [ncolors]: stored entries of each colour's rows
+    unsigned long long *d_color_nnz = nullptr;  // the same on the device, read back at the
+                                                // end of setup
     std::vector<int> color_blocks;  // host [ncolors+1] (finest level): block range per colour
     int nblocks = 0;
     int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block

@@ -280,17 +280,20 @@ __global__ void k_slice_width(int n, int nslices, const int *__restrict__ len, i
 }
 
 // out[0] = max of v[0..n) (one block)
+// *out = max(*out, v[0..n)) for v >= 0 (*out zeroed by the caller): block maxima, then one
+// integer atomicMax per block (exact in any order)
 __global__ void k_max_int(int n, const int *__restrict__ v, int *__restrict__ out) {
     __shared__ int part[kT];
     int m = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = max(m, v[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, v[i]);
     part[threadIdx.x] = m;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) part[threadIdx.x] = max(part[threadIdx.x], part[threadIdx.x + o]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = part[0];
+    if (threadIdx.x == 0 && part[0] > 0) atomicMax(out, part[0]);
 }
 
 // sl[s] = s * slots for s <= nslices (every slice `slots` = 32 w entries)
@@ -498,6 +501,7 @@ __global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, floa
     if (in_smem)
         for (int e = t; e < n * n; e += T) a[e] = ainv[e];  // the dense matrix arrives in ainv
     __syncthreads();
+    const int lane = t & 31, warp = t >> 5, nwarp = T >> 5;
     for (int j = 0; j < n; j++) {
         if (t == 0) {
             double d = a[(size_t)j * n + j];
@@ -509,9 +513,10 @@ __global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, floa
         double djj = a[(size_t)j * n + j];
         for (int i = j + 1 + t; i < n; i += T) a[(size_t)i * n + j] /= djj;
         __syncthreads();
-        for (int i = j + 1 + t; i < n; i += T) {
-            double lij = a[(size_t)i * n + j];
-            for (int k = j + 1; k <= i; k++) a[(size_t)i * n + k] -= lij * a[(size_t)k * n + j];
+        // trailing update of the lower triangle, a warp per row (each entry once per j)
+        for (int i = j + 1 + warp; i < n; i += nwarp) {
+            const double lij = a[(size_t)i * n + j];
+            for (int k = j + 1 + lane; k <= i; k += 32) a[(size_t)i * n + k] -= lij * a[(size_t)k * n + j];
         }
         __syncthreads();
     }
@@ -529,14 +534,23 @@ __global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, floa
         }
     }
     __syncthreads();
-    for (int e = t; e < n * n; e += T) {
-        int i = e / n, j = e % n;
+    // A^{-1} = W^t W: entry (i, j), i >= j, and its mirror (the same sum: products commute)
+    const int tri = n * (n + 1) / 2;
+    for (int q = t; q < tri; q += T) {
+        int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);  // q = i (i+1) / 2 + j
+        while (i * (i + 1) / 2 > q) i--;
+        while ((i + 1) * (i + 2) / 2 <= q) i++;
+        const int j = q - i * (i + 1) / 2;
         double s = 0.0;
-        for (int k = max(i, j); k < n; k++) s += w[(size_t)k * n + i] * w[(size_t)k * n + j];
-        ainv[e] = s;
+        for (int k = i; k < n; k++) s += w[(size_t)k * n + i] * w[(size_t)k * n + j];
         const float hi = (float)s;  // FP32 cycle: high and low parts, s ~ hi + lo
-        ainv32[e] = hi;
-        ainv32[(size_t)n * n + e] = (float)(s - (double)hi);
+        const float lo = (float)(s - (double)hi);
+        for (int m = 0; m < (i == j ? 1 : 2); m++) {
+            const size_t e = m == 0 ? (size_t)i * n + j : (size_t)j * n + i;
+            ainv[e] = s;
+            ainv32[e] = hi;
+            ainv32[(size_t)n * n + e] = lo;
+        }
     }
 }
 
@@ -557,22 +571,45 @@ std::vector<int> read_ints(const int *d, int n, cudaStream_t s) {
     return v;
 }
 
+// stored entries of each colour's rows into lv.d_color_nnz (read back by read_color_nnz)
 void color_nnz(amg_hierarchy *h, Level &lv, const int *len) {
     cudaStream_t s = h->stream;
     const int nc = (int)lv.color_rows.size() - 1;
     Scratch tmp(s);
     int *cr = tmp.get<int>(nc + 1);
-    unsigned long long *out = tmp.get<unsigned long long>(nc);
+    lv.d_color_nnz = halloc<unsigned long long>(h, std::max(1, nc));
     AMG_CUDA(cudaMemcpyAsync(cr, lv.color_rows.data(), sizeof(int) * (nc + 1),
                              cudaMemcpyHostToDevice, s));
-    AMG_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long) * nc, s));
+    AMG_CUDA(cudaMemsetAsync(lv.d_color_nnz, 0, sizeof(unsigned long long) * nc, s));
     const int per = std::max(1, std::min(64, nblocks_for(lv.n, kT) / std::max(1, nc)));
-    k_color_nnz<<<dim3(nc, per), kT, 0, s>>>(len, cr, out);
+    k_color_nnz<<<dim3(nc, per), kT, 0, s>>>(len, cr, lv.d_color_nnz);
     AMG_LAUNCH_CHECK();
-    std::vector<unsigned long long> v(nc);
-    AMG_CUDA(cudaMemcpyAsync(v.data(), out, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost, s));
+}
+
+// every level's colour counts in one pass at the end of setup (one host round trip); a
+// coarse level's stored entries are their sum
+void read_color_nnz(amg_hierarchy *h) {
+    cudaStream_t s = h->stream;
+    std::vector<std::vector<unsigned long long>> v(h->nlev);
+    for (int l = 0; l < h->nlev; l++) {
+        Level &lv = h->lev[l];
+        if (!lv.d_color_nnz) continue;
+        v[l].resize(lv.color_rows.size() - 1);
+        AMG_CUDA(cudaMemcpyAsync(v[l].data(), lv.d_color_nnz,
+                                 sizeof(unsigned long long) * v[l].size(),
+                                 cudaMemcpyDeviceToHost, s));
+    }
     AMG_CUDA(cudaStreamSynchronize(s));
-    lv.color_nnz.assign(v.begin(), v.end());
+    for (int l = 0; l < h->nlev; l++) {
+        Level &lv = h->lev[l];
+        if (!lv.d_color_nnz) continue;
+        lv.color_nnz.assign(v[l].begin(), v[l].end());
+        if (l > 0) {
+            int64_t tot = 0;
+            for (unsigned long long c : v[l]) tot += (int64_t)c;
+            lv.A.stored = tot;
+        }
+    }
 }
 
 int bits_for(int64_t maxval) {  // bits to hold values in [0, maxval]
@@ -595,13 +632,22 @@ int64_t slice_pointers(amg_hierarchy *h, Sell &A, int n, const int *len, bool un
     k_slice_width<<<nblocks_for((int64_t)A.nslices * 32, kT), kT, 0, s>>>(n, A.nslices, len, sw);
     AMG_LAUNCH_CHECK();
     exclusive_scan(sw, A.sl_ptr, A.nslices, A.sl_ptr + A.nslices, s);
-    A.padded = read_int(A.sl_ptr + A.nslices, s);
     A.uw = 0;
-    if (uniform) {
-        int *d_max = tmp.get<int>(1);
-        k_max_int<<<1, kT, 0, s>>>(A.nslices, sw, d_max);
+    int wmax = 0;
+    if (uniform) {  // the padded size and the widest slice in one read
+        int *d_pw = tmp.get<int>(2);
+        AMG_CUDA(cudaMemcpyAsync(d_pw, A.sl_ptr + A.nslices, sizeof(int),
+                                 cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA(cudaMemsetAsync(d_pw + 1, 0, sizeof(int), s));
+        k_max_int<<<std::min(nblocks_for(A.nslices, kT), 152), kT, 0, s>>>(A.nslices, sw, d_pw + 1);
         AMG_LAUNCH_CHECK();
-        const int wmax = read_int(d_max, s) / 32;
+        const std::vector<int> pw = read_ints(d_pw, 2, s);
+        A.padded = pw[0];
+        wmax = pw[1] / 32;
+    } else {
+        A.padded = read_int(A.sl_ptr + A.nslices, s);
+    }
+    if (uniform) {
         const int64_t up = (int64_t)A.nslices * 32 * wmax;
         if (wmax > 0 && up <= INT32_MAX && (wmax <= 9 || up * 4 <= A.padded * 5)) {
             k_uniform_slices<<<nblocks_for(A.nslices + 1, kT), kT, 0, s>>>(A.nslices, 32 * wmax,
@@ -689,11 +735,7 @@ void galerkin(amg_hierarchy *h, Level &f, Level &c, bool fine) {
     int *len = tmp.get<int>(c.n);
     if (fine) launch_rap<true>(h, f, c, false, len);
     else launch_rap<false>(h, f, c, false, len);
-    int *d_tot = tmp.get<int>(1);
-    int *scanned = tmp.get<int>(c.n);
-    exclusive_scan(len, scanned, c.n, d_tot, s);
-    c.A.stored = read_int(d_tot, s);
-    slice_pointers(h, c.A, c.n, len, true);
+    slice_pointers(h, c.A, c.n, len, true);  // (stored entries: read_color_nnz)
     color_nnz(h, c, len);
     if (fine) launch_rap<true>(h, f, c, true, nullptr);
     else launch_rap<false>(h, f, c, true, nullptr);
@@ -717,14 +759,14 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
                                           160 * 1024));
             attr = true;
         }
-        k_chol_inverse<<<1, 256, smem, s>>>(n, nullptr, nullptr, lv.Ainv, lv.Ainv32, h->err_flag);
+        k_chol_inverse<<<1, 1024, smem, s>>>(n, nullptr, nullptr, lv.Ainv, lv.Ainv32, h->err_flag);
     } else {
         double *a = tmp.get<double>((size_t)n * n);
         double *w = tmp.get<double>((size_t)n * n);
         AMG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * n * n, s));
         k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val, a);
         AMG_LAUNCH_CHECK();
-        k_chol_inverse<<<1, 256, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
+        k_chol_inverse<<<1, 1024, 0, s>>>(n, a, w, lv.Ainv, lv.Ainv32, h->err_flag);
     }
     AMG_LAUNCH_CHECK();
 }
@@ -958,6 +1000,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         }
         coarsest_inverse(h, h->lev[nlev - 1]);
     }
+    read_color_nnz(h);
     err = read_int(h->err_flag, s);
     if (err & 8) throw Error{AMG_ERR_BAD_MATRIX, "coarsest operator is not positive definite"};
     if (err & 4) throw Error{AMG_ERR_CUDA, "internal error: stencil offset beyond the span"};
