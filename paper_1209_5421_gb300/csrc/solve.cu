@@ -681,20 +681,32 @@ __global__ void k_spmv(GLev<double> L, const double *__restrict__ z, double *__r
     }
 }
 
-// out[i] = (w, V[i]) for i < m: every block loops over i; the last block reduces every i
-__global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__restrict__ w,
-                                                      double *const *__restrict__ V, int m,
-                                                      double *out, RedCtx rc) {
-    __shared__ bool last;
-    for (int i = 0; i < m; i++) {
-        const double *v = V[i];
-        double a[1] = {0.0}, r[1];
-        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-            a[0] += w[k] * v[k];
-        block_sum<1, double>(a, r, BlockGroup{});
-        if (threadIdx.x == 0) rc.partials[(size_t)i * gridDim.x + blockIdx.x] = r[0];
-        __syncthreads();  // the reduction scratch is reused by the next i
+// Dots of w with the basis vectors V[0..m), kDotChunk vectors per sweep over the rows: each
+// thread keeps one grid-stride partial sum per vector (in row order), each block reduces them
+// vector by vector, and the last block to finish sums the block partials in block order.
+constexpr int kDotChunk = 8;
+
+__device__ __forceinline__ void mdot_chunk(int n, const double *__restrict__ w,
+                                           double *const *__restrict__ V, int c0, int mc,
+                                           double *partials) {
+    const double *vp[kDotChunk];
+#pragma unroll
+    for (int i = 0; i < kDotChunk; i++) vp[i] = i < mc ? V[c0 + i] : nullptr;
+    double a[kDotChunk] = {}, r[kDotChunk];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int i = 0; i < kDotChunk; i++)
+            if (i < mc) a[i] += wk * vp[i][k];
     }
+    block_sum<kDotChunk, double>(a, r, BlockGroup{});
+    if (threadIdx.x == 0)
+        for (int i = 0; i < mc; i++) partials[(size_t)(c0 + i) * gridDim.x + blockIdx.x] = r[i];
+    __syncthreads();  // the reduction scratch is reused by the next chunk
+}
+
+__device__ __forceinline__ void mdot_finish(int m, double *out, const RedCtx &rc) {
+    __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned t = atomicAdd(rc.counter, 1u);
@@ -713,6 +725,32 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__res
         }
     }
     if (threadIdx.x == 0) *rc.counter = 0u;
+}
+
+// out[i] = (w, V[i]) for i < m
+__global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__restrict__ w,
+                                                      double *const *__restrict__ V, int m,
+                                                      double *out, RedCtx rc) {
+    for (int c0 = 0; c0 < m; c0 += kDotChunk)
+        mdot_chunk(n, w, V, c0, min(kDotChunk, m - c0), rc.partials);
+    mdot_finish(m, out, rc);
+}
+
+// The second Gram-Schmidt pass's dots fused with the first pass's subtraction (both are
+// row-local): w -= sum_i c[i] V[i], then out[i] = (w, V[i]) for i < m. Each row's new w is
+// written by the thread that reads it again in the later chunks.
+__global__ void __launch_bounds__(kRedThreads) k_orth_mdot(int n, double *__restrict__ w,
+                                                           double *const *__restrict__ V, int m,
+                                                           const double *__restrict__ c,
+                                                           double *out, RedCtx rc) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        double x = w[k];
+        for (int i = 0; i < m; i++) x -= c[i] * V[i][k];
+        w[k] = x;
+    }
+    for (int c0 = 0; c0 < m; c0 += kDotChunk)
+        mdot_chunk(n, w, V, c0, min(kDotChunk, m - c0), rc.partials);
+    mdot_finish(m, out, rc);
 }
 
 // w -= sum_i c[i] V[i]; (w, w) -> *nrm2
@@ -1564,10 +1602,8 @@ static GLev<double> fine_view(amg_hierarchy *h) {
     return L;
 }
 
-static void check_device_error(amg_hierarchy *h) {
-    int err = 0;
-    AMG_CUDA(cudaMemcpyAsync(&err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    AMG_CUDA(cudaStreamSynchronize(h->stream));
+// the cycle kernel's error flag, read by the caller
+static void raise_device_error(amg_hierarchy *h, int err) {
     if (err & kErrTimeout) {
         // the kernel left its op loop: clear the flag and the barrier state for the next launch
         AMG_CUDA(cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
@@ -1575,6 +1611,13 @@ static void check_device_error(amg_hierarchy *h) {
         AMG_CUDA(cudaStreamSynchronize(h->stream));
         throw Error{AMG_ERR_TIMEOUT, "a grid barrier of the cycle kernel timed out"};
     }
+}
+
+static void check_device_error(amg_hierarchy *h) {
+    int err = 0;
+    AMG_CUDA(cudaMemcpyAsync(&err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));
+    raise_device_error(h, err);
 }
 
 // one application of B^_0 to h->ro (FP64) into h->zo (FP64)
@@ -1733,7 +1776,8 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
     double **dV = h->dP;          // V[i] = P[i], i <= m
     double **dZ = h->dP + m + 1;  // Z[j] = P[m + 1 + j]
     double *w = h->to;
-    double *dh = h->osc + OS_ZQ;  // device scratch for m+2 scalars
+    double *dh = h->osc + OS_ZQ;           // first pass's dots and the norm: m + 2 scalars
+    double *dh2 = h->osc + OS_ZQ + m + 2;  // second pass's dots: m + 1 (maxit >= 2m + 1)
     GLev<double> Lf = fine_view(h);
     k_gather<<<nblocks_for(n, 256), 256, 0, s>>>(n, F.nat, b_nat, h->bo);
     AMG_LAUNCH_CHECK();
@@ -1750,7 +1794,7 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
     const double nd = n, nnzf = (double)F.A.stored;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     std::vector<double> hv(std::max(m + 2, 8));
-    double *dy = h->osc + OS_ZQ + maxit;  // coefficients for the update
+    double *dy = h->osc + OS_ZQ + maxit + 4;  // coefficients for the update (m <= maxit)
     auto read_scalars = [&](const double *d, int count, double *out) {
         AMG_CUDA(cudaMemcpyAsync(h->h_pinned, d, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
         AMG_CUDA(cudaStreamSynchronize(s));
@@ -1782,19 +1826,33 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
             k_spmv<<<nblocks_for(n, 256), 256, 0, s>>>(Lf, h->P[m + 1 + j], w);
             AMG_LAUNCH_CHECK();
             if (prof) h->prof->end(rec, s);
-            for (int pass = 0; pass < 2; pass++) {
-                if (prof) rec = h->prof->begin(K_FGMRES_MDOT, 0, 8.0 * nd * (j + 2), s);
-                k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, rc);
-                AMG_LAUNCH_CHECK();
-                if (prof) h->prof->end(rec, s);
-                if (prof) rec = h->prof->begin(K_FGMRES_ORTH, 0, 8.0 * nd * (j + 3), s);
-                k_orth_sub<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, dh + j + 1, rc);
-                AMG_LAUNCH_CHECK();
-                if (prof) h->prof->end(rec, s);
-                read_scalars(dh, j + 2, hv.data());
-                for (int i = 0; i <= j; i++) H[(size_t)i * m + j] = (pass ? H[(size_t)i * m + j] : 0.0) + hv[i];
+            // classical Gram-Schmidt twice: h1 = V^t w, w -= V h1, h2 = V^t w, w -= V h2
+            if (prof) rec = h->prof->begin(K_FGMRES_MDOT, 0, 8.0 * nd * (j + 2), s);
+            k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, rc);
+            AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s);
+            if (prof) rec = h->prof->begin(K_FGMRES_ORTH, 0, 8.0 * nd * (j + 3), s);
+            k_orth_mdot<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh, dh2, rc);
+            AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s);
+            if (prof) rec = h->prof->begin(K_FGMRES_ORTH, 0, 8.0 * nd * (j + 3), s);
+            k_orth_sub<<<red_grid(n), kRedThreads, 0, s>>>(n, w, dV, j + 1, dh2, dh + j + 1, rc);
+            AMG_LAUNCH_CHECK();
+            if (prof) h->prof->end(rec, s);
+            {  // h1, the norm, h2 and the cycle's error flag: one round trip
+                int err = 0;
+                AMG_CUDA(cudaMemcpyAsync(h->h_pinned, dh, sizeof(double) * (j + 2),
+                                         cudaMemcpyDeviceToHost, s));
+                AMG_CUDA(cudaMemcpyAsync(h->h_pinned + m + 2, dh2, sizeof(double) * (j + 1),
+                                         cudaMemcpyDeviceToHost, s));
+                if (h->nlev > 1)
+                    AMG_CUDA(cudaMemcpyAsync(&err, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+                AMG_CUDA(cudaStreamSynchronize(s));
+                raise_device_error(h, err);
+                for (int i = 0; i < j + 2; i++) hv[i] = h->h_pinned[i];
+                for (int i = 0; i <= j; i++)
+                    H[(size_t)i * m + j] = (0.0 + hv[i]) + h->h_pinned[m + 2 + i];
             }
-            if (h->nlev > 1) check_device_error(h);
             if (prof) {
                 h->prof->harvest();
                 if (h->nlev > 1) {
