@@ -49,13 +49,18 @@ struct Op {
 
 enum : int { V_RHS = 0, V_E, V_R, V_P0 };  // V_P0 + i = p_i
 
-// view of one level; I = column index type (int in HBM, uint16 in the shared-memory tail)
-template <class T, class I>
+// view of one level; I = column index type (int in HBM, uint16 in the shared-memory tail);
+// B = 1 compiles the lane-parallel block smoother of finest levels with multi-row blocks
+// (a separate kernel instance, so that the code of the others stays as it is)
+template <class T, class I, int B = 0>
 struct LevelDev {
     using val_t = T;
     using idx_t = I;
+    static constexpr int coop = B;
     int n;
     int fine;                       // 1 on the finest level (block smoother, bptr)
+    int bg;                         // finest level: lanes that share a block (kBlockLanes), or
+                                    // 0: one thread per block
     int w;                          // > 0: every slice has width w (sl not read)
     const int *sl;
     const I *col;
@@ -83,6 +88,8 @@ struct StagedLevel {
     using val_t = T;
     using idx_t = unsigned short;
     static constexpr int fine = 0;  // point smoother (staged levels are coarse)
+    static constexpr int bg = 0;
+    static constexpr int coop = 0;
     int n, w;
     const unsigned short *col;
     const T *val;
@@ -100,8 +107,9 @@ struct StagedLevel {
 };
 
 // first slot and slot count of row i
-template <class T, class I>
-__device__ __forceinline__ void row_span(const LevelDev<T, I> &L, int i, int &base, int &width) {
+template <class T, class I, int B>
+__device__ __forceinline__ void row_span(const LevelDev<T, I, B> &L, int i, int &base,
+                                         int &width) {
     const int s = i >> 5;
     if (L.w > 0) {
         width = L.w;
@@ -408,10 +416,125 @@ __device__ void op_zero(const LV &L, typename LV::val_t *u, int tid, int nth) {
     for (int i = tid; i < L.n; i += nth) u[i] = 0;
 }
 
+// Block smoother with kBlockLanes lanes per block (finest level, blocks of several rows, as
+// the octree's 2x2x2-node aggregates): lane q owns row r0 + q. Phase 1 (all lanes at once)
+// gathers the row's terms whose values are final for this row: columns outside the block
+// and block rows the sweep reaches after it (still old); the coefficients of block rows the
+// sweep reaches before it are kept by local index. Phase 2 walks the block's rows in sweep
+// order: the owner finishes its row, the new value goes to the other lanes by a shuffle, and
+// each adds its coefficient times that value. The same Gauss-Seidel update as one thread per
+// block, summed in another order. Blocks of more than kBlockLanes rows (none on the octree
+// workloads) are swept by the group's first lane.
+constexpr int kBlockLanes = 16;
+constexpr int kBlockEarly = 8;  // coefficients of earlier block rows kept per row
+
+template <class LV>
+__device__ __forceinline__ void gs_block_seq(const LV &L, int b, bool backward,
+                                             const typename LV::val_t *f, typename LV::val_t *u) {
+    const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
+    if (!backward)
+        for (int i = r0; i < r1; i++) gs_row(L, i, f, u);
+    else
+        for (int i = r1 - 1; i >= r0; i--) gs_row(L, i, f, u);
+}
+
+template <class LV>
+__device__ void op_gs_blocks_coop(const LV &L, const Op &op, const typename LV::val_t *f,
+                                  typename LV::val_t *u, int tid, int nth) {
+    using T = typename LV::val_t;
+    using I = typename LV::idx_t;
+    constexpr int G = kBlockLanes;
+    const int q = tid & (G - 1);
+    const unsigned gmask = 0xFFFFu << ((threadIdx.x & 31) & 16);  // this group's 16 lanes
+    const int glane0 = (threadIdx.x & 31) & 16;
+    const bool bwd = op.backward != 0;
+    for (int base = op.i0; base < op.i1; base += nth / G) {
+        const int b = base + tid / G;
+        int r0 = 0, k = 0;
+        if (b < op.i1) {
+            r0 = L.bptr[b];
+            k = L.bptr[b + 1] - r0;
+        }
+        if (k > G) {  // the same for the whole group
+            if (q == 0) gs_block_seq(L, b, bwd, f, u);
+            continue;
+        }
+        const bool has = q < k;
+        const int i = r0 + q;
+        T acc = 0, fi = 0, di = 0;
+        T early[kBlockEarly];
+        unsigned lidx = 0;  // local index of early[t], 4 bits each (t < nearly)
+#pragma unroll
+        for (int t = 0; t < kBlockEarly; t++) early[t] = 0;
+        int nearly = 0;
+        bool overflow = false;
+        if (has) {
+            fi = f[i];
+            di = L.dinv[i];
+            int rb, width;
+            row_span(L, i, rb, width);
+            for (int kb = 1; kb < width; kb += kRowBatch) {
+                I c[kRowBatch];
+                T a[kRowBatch];
+#pragma unroll
+                for (int j = 0; j < kRowBatch; j++) {
+                    const int kk = kb + j;
+                    c[j] = kk < width ? L.col[rb + 32 * kk] : (I)-1;
+                    a[j] = kk < width ? L.val[rb + 32 * kk] : T(0);
+                }
+                T xv[kRowBatch];
+#pragma unroll
+                for (int j = 0; j < kRowBatch; j++) {
+                    xv[j] = T(0);
+                    if (col_ok(c[j])) {
+                        const int li = (int)c[j] - r0;
+                        const bool early_row = li >= 0 && li < k && (bwd ? li > q : li < q);
+                        if (!early_row) {
+                            xv[j] = u[c[j]];
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < kBlockEarly; t++)
+                                if (t == nearly) early[t] = a[j];
+                            if (nearly < kBlockEarly) lidx |= (unsigned)li << (4 * nearly);
+                            else overflow = true;
+                            nearly++;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kRowBatch; j++) acc += a[j] * xv[j];
+            }
+        }
+        // more than kBlockEarly earlier block rows in a row: the group's first lane sweeps it
+        if (__any_sync(gmask, overflow)) {
+            if (q == 0) gs_block_seq(L, b, bwd, f, u);
+            continue;
+        }
+        int kmax = k;  // the same in the group
+        for (int s = 0; s < kmax; s++) {
+            const int j = bwd ? kmax - 1 - s : s;  // block row updated at this step
+            T vj = (has && q == j) ? (fi - acc) * di : T(0);
+            vj = __shfl_sync(gmask, vj, glane0 + j);
+            if (has && q == j) u[i] = vj;
+            if (has) {
+#pragma unroll
+                for (int t = 0; t < kBlockEarly; t++)
+                    if (t < nearly && ((lidx >> (4 * t)) & 15u) == (unsigned)j) acc += early[t] * vj;
+            }
+        }
+    }
+}
+
 // one colour: independent blocks (finest level, rows of a block in sweep order) or rows
 template <class LV>
 __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
                       typename LV::val_t *u, int tid, int nth) {
+    if constexpr (LV::coop) {
+        if (L.fine && L.bg > 0) {
+            op_gs_blocks_coop(L, op, f, u, tid, nth);
+            return;
+        }
+    }
     for (int b = op.i0 + tid; b < op.i1; b += nth) {
         if (L.fine) {
             const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
@@ -436,6 +559,26 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             int nth, typename LV::val_t *un = nullptr,
                             const typename LV::val_t *dinv_n = nullptr, int f0 = 0, int f1 = 0) {
     using T = typename LV::val_t;
+    if constexpr (LV::coop) {  // kBlockLanes lanes per aggregate: a row each, then a shuffle sum
+        if (L.fine && L.bg > 0) {
+            constexpr int G = kBlockLanes;
+            const int q = tid & (G - 1);
+            for (int base = 0; base < L.nnext; base += nth / G) {
+                const int R = base + tid / G;
+                T v = 0;
+                if (R < L.nnext)
+                    for (int i = L.bptr[R] + q; i < L.bptr[R + 1]; i += G)
+                        v += row_residual(L, i, f, u);
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (R < L.nnext && q == 0) {
+                    fc[R] = v;
+                    if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
+                }
+            }
+            return;
+        }
+    }
     if (L.fine) {
         for (int R = tid; R < L.nnext; R += nth) {
             T acc = 0;

@@ -342,6 +342,7 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
                 SLev<T> &S = *reinterpret_cast<SLev<T> *>(tail_gview);
                 S.n = G.n;
                 S.fine = 0;
+                S.bg = 0;
                 S.w = G.w;
                 S.sl = G.sl;
                 S.col = G.col16;
@@ -434,8 +435,8 @@ __device__ void run_tail(const CycleArgs<T> &a) {
 // sum the per-CTA partials of the previous op (every CTA, identical order) into sc; one
 // warp does it, in FP64 for the FP64 cycle and in FP32 for the FP32 cycle (whose per-CTA
 // partials are FP32 sums)
-template <class T>
-__device__ __forceinline__ void finalize(const CycleArgs<T> &a, const GLev<T> *tab, const Op &op) {
+template <class T, class TAB>
+__device__ __forceinline__ void finalize(const CycleArgs<T> &a, const TAB *tab, const Op &op) {
     if (threadIdx.x < 32) {
         const int G = gridDim.x;
         double *sc = tab[op.fin_level].sc;
@@ -459,9 +460,11 @@ __device__ __forceinline__ void finalize(const CycleArgs<T> &a, const GLev<T> *t
     __syncthreads();
 }
 
-template <class T, int W>
+// B = 1: finest-level blocks of several rows take the lane-parallel block smoother
+template <class T, int W, int B>
 __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
-    __shared__ GLev<T> gtab[kMaxLevels];
+    using GL = LevelDev<T, int, B>;  // the same layout as GLev<T>
+    __shared__ GL gtab[kMaxLevels];
     __shared__ unsigned long long target;
     __shared__ int abort_flag;
     if (threadIdx.x == 0) {
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
         abort_flag = 0;
     }
     {  // the level table, read by every op, lives in shared memory
-        const int words = a.lay.nlev * (int)(sizeof(GLev<T>) / sizeof(int));
+        const int words = a.lay.nlev * (int)(sizeof(GL) / sizeof(int));
         for (int i = threadIdx.x; i < words; i += blockDim.x)
             ((int *)gtab)[i] = ((const int *)a.tab)[i];
     }
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
         if (op.kind == OP_TAIL) {
             if (blockIdx.x == 0) run_tail<T, W>(a);
         } else if (op.kind != OP_NOP) {
-            run_op<GLev<T>, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
+            run_op<GL, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
         }
         if (!grid_barrier(a.bar, a.err, target, abort_flag)) break;
         if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
@@ -943,6 +946,7 @@ struct EngineBase {
     TailLayout lay{};
     size_t smem = 0;
     int grid = 0;
+    int coop = 0;  // the cycle kernel instance with the lane-parallel block smoother
     std::vector<Op> hprog, htail;
     double tail_bytes = 0, cycle_bytes = 0;
     unsigned long long *ts = nullptr;
@@ -963,6 +967,14 @@ int red_grid(int64_t n) {
 }
 
 size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// finest-level blocks of six or more rows on average (the octree's 2x2x2-node aggregates):
+// the lane-parallel block smoother (op_gs_blocks_coop) and restriction. Smaller blocks (a few
+// rows, as on a quadtree with several nodes per cell) keep one thread per block: with
+// kBlockLanes lanes each, most lanes would idle and the sweep would need more passes.
+bool coop_blocks(const Level &lv) {
+    return lv.nblocks > 0 && 6 * (int64_t)lv.nblocks <= (int64_t)lv.n;
+}
 
 bool is_reduction(const Op &op) {
     return op.kind == OP_MULTIDOT || op.kind == OP_SPMV_DOT || (op.kind == OP_UPDATE && !op.last);
@@ -1149,6 +1161,8 @@ void fill_tables(amg_hierarchy *h) {
         std::memset(&d, 0, sizeof d);
         d.n = lv.n;
         d.fine = (l == 0) ? 1 : 0;
+        // blocks of several rows (octree aggregates): a lane per row (op_gs_blocks_coop)
+        d.bg = (l == 0 && coop_blocks(lv)) ? kBlockLanes : 0;
         d.w = lv.A.uw;
         d.sl = lv.A.sl_ptr;
         d.col = lv.A.col;
@@ -1290,8 +1304,9 @@ int max_tail_bytes() {
 }
 
 template <class T>
-void *cycle_kernel(int W) {
-    return W == 9 ? (void *)k_cycle<T, 9> : (void *)k_cycle<T, 0>;
+void *cycle_kernel(int W, int B) {
+    if (B) return W == 9 ? (void *)k_cycle<T, 9, 1> : (void *)k_cycle<T, 0, 1>;
+    return W == 9 ? (void *)k_cycle<T, 9, 0> : (void *)k_cycle<T, 0, 0>;
 }
 
 template <class T>
@@ -1303,11 +1318,13 @@ void build_engine(amg_hierarchy *h) {
     AMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     AMG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     size_t static_smem = 0;
-    for (int W : {0, 9}) {
-        cudaFuncAttributes fa;
-        AMG_CUDA(cudaFuncGetAttributes(&fa, cycle_kernel<T>(W)));
-        static_smem = std::max(static_smem, fa.sharedSizeBytes);
-    }
+    for (int W : {0, 9})
+        for (int B : {0, 1}) {
+            cudaFuncAttributes fa;
+            AMG_CUDA(cudaFuncGetAttributes(&fa, cycle_kernel<T>(W, B)));
+            static_smem = std::max(static_smem, fa.sharedSizeBytes);
+        }
+    E->coop = coop_blocks(h->lev[0]) ? 1 : 0;
     const long budget = std::min<long>((long)optin - (long)static_smem - 1024,
                                        (long)max_tail_bytes());
     // the tail: the finest coarse level from which everything fits in shared memory, or
@@ -1366,7 +1383,7 @@ void build_engine(amg_hierarchy *h) {
     AMG_CUDA(cudaMemcpyAsync(E->prog, E->hprog.data(), sizeof(Op) * E->hprog.size(),
                              cudaMemcpyHostToDevice, s));
     E->smem = tl < h->nlev ? (size_t)E->lay.bytes : 0;
-    void *kern = cycle_kernel<T>(E->lay.W);
+    void *kern = cycle_kernel<T>(E->lay.W, E->coop);
     // the kernel's dynamic shared-memory limit is a property of the function, shared by every
     // hierarchy of the process: set it to the device maximum (never lower it below what
     // another hierarchy's launches use); each launch passes its own size
@@ -1453,7 +1470,7 @@ void launch_cycle(amg_hierarchy *h) {
         rec = h->prof->begin(K_CYCLE, 0, E->cycle_bytes, s);
     }
     void *args[] = {&a};
-    AMG_CUDA(cudaLaunchCooperativeKernel(cycle_kernel<T>(E->lay.W), dim3(E->grid),
+    AMG_CUDA(cudaLaunchCooperativeKernel(cycle_kernel<T>(E->lay.W, E->coop), dim3(E->grid),
                                          dim3(kPThreads), args, E->smem, s));
     AMG_LAUNCH_CHECK();
     if (prof) h->prof->end(rec, s);
