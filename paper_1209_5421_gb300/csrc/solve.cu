@@ -26,7 +26,12 @@ using GLev = LevelDev<T, int>;                 // level in HBM
 template <class T>
 using SLev = LevelDev<T, unsigned short>;      // level staged in shared memory
 
-constexpr int kPThreads = 1024;     // persistent kernel CTA size (one CTA per SM)
+// persistent kernel CTA size (one CTA per SM): the FP64 cycle runs with fewer threads and
+// twice the registers each, as its ops at the 64-register cap of 1024 threads spill
+constexpr int kPThreads = 1024;
+constexpr int kPThreads64 = 512;
+template <class T>
+constexpr int cycle_threads() { return sizeof(T) == 8 ? kPThreads64 : kPThreads; }
 constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
 
 
@@ -462,7 +467,7 @@ __device__ __forceinline__ void finalize(const CycleArgs<T> &a, const TAB *tab, 
 
 // B = 1: finest-level blocks of several rows take the lane-parallel block smoother
 template <class T, int W, int B>
-__global__ void __launch_bounds__(kPThreads, 1) k_cycle(CycleArgs<T> a) {
+__global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a) {
     using GL = LevelDev<T, int, B>;  // the same layout as GLev<T>
     __shared__ GL gtab[kMaxLevels];
     __shared__ unsigned long long target;
@@ -1280,10 +1285,10 @@ bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
     int nmax = 0;
     for (int l = l0; l < h->nlev; l++)
         if (!Y.lv[l].gmem) nmax = std::max(nmax, Y.lv[l].n);
-    Y.narrow = std::min(1024, std::max(128, (nmax / 4 + 31) / 32 * 32));
+    Y.narrow = std::min(vb == 8 ? kPThreads64 : kPThreads, std::max(128, (nmax / 4 + 31) / 32 * 32));
     if (const char *e = getenv("AMG_TAIL_NARROW")) {  // tuning knob: threads of the narrow group
         const int v = atoi(e);
-        if (v >= 32 && v <= 1024 && v % 32 == 0) Y.narrow = v;
+        if (v >= 32 && v <= (vb == 8 ? kPThreads64 : kPThreads) && v % 32 == 0) Y.narrow = v;
     }
     Y.sc = take(sizeof(double) * SC_N * (size_t)(h->nlev - l0));
     Y.bytes = (int)off;
@@ -1390,7 +1395,8 @@ void build_engine(amg_hierarchy *h) {
     AMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)std::max<long>(0, (long)optin - (long)static_smem)));
     int per_sm = 0;
-    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, E->smem));
+    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cycle_threads<T>(),
+                                                           E->smem));
     if (per_sm < 1) throw Error{AMG_ERR_CUDA, "persistent cycle kernel cannot be resident"};
     E->grid = nsm;  // one CTA per SM (co-resident: cooperative launch)
     E->ts = halloc<unsigned long long>(h, E->hprog.size() + 1);
@@ -1471,7 +1477,7 @@ void launch_cycle(amg_hierarchy *h) {
     }
     void *args[] = {&a};
     AMG_CUDA(cudaLaunchCooperativeKernel(cycle_kernel<T>(E->lay.W, E->coop), dim3(E->grid),
-                                         dim3(kPThreads), args, E->smem, s));
+                                         dim3(cycle_threads<T>()), args, E->smem, s));
     AMG_LAUNCH_CHECK();
     if (prof) h->prof->end(rec, s);
 }
