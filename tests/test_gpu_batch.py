@@ -162,3 +162,21 @@ def test_fixed_shape_has_no_teams(amg):
     B.close()
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_with_a_single_unknown_system(amg, prec):
+    # a one-unknown system (one level, exact solve) beside a large one that forms a team
+    probs = [p1_poisson(n=3, jitter=0.2, seed=1, rhs="normal"),
+             p1_poisson(n=129, jitter=0.2, seed=2, rhs="normal")]
+    cp = amg.FP32 if prec == "fp32" else amg.FP64
+    B = amg.Batch.from_problems(probs, cycle_prec=cp)
+    x, it, rr, st = B.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    assert (st == amg.OK).all()
+    off = B.row_off
+    assert x[0] == pytest.approx(probs[0].b[0] / probs[0].val[0], rel=1e-12)
+    A = probs[1].to_scipy()
+    x1 = x[off[1]:off[2]]
+    assert np.linalg.norm(probs[1].b - A @ x1) / np.linalg.norm(probs[1].b) <= 1e-8
+    assert B.teams()[1] > 1 and B.teams()[0] == 1
+    B.close()

@@ -143,3 +143,32 @@ def test_octree_served(amg):
         assert S.stats()["setups"] == 1
     finally:
         S.close()
+
+
+@pytest.mark.parametrize("n", [3, 5])
+def test_octree_single_level_and_single_unknown(amg, oracle_mod, n):
+    # 1 and 27 unknowns: one level, the exact dense solve
+    p = p1_poisson_3d(n, seed=n)
+    G = amg.Hierarchy.from_problem(p)
+    assert G.nlev == 1 and G.dim == 3
+    x, it, rr, st = G.solve(p.b, 1e-12)
+    assert st == amg.OK and it == 1
+    xs = np.linalg.solve(p.to_scipy().toarray(), p.b)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+    xo, _, _, _ = oracle_mod.Hierarchy.from_problem(p).solve(p.b, 1e-12)
+    assert np.linalg.norm(x - xo) <= 1e-12 * np.linalg.norm(xo)
+
+
+def test_octree_invalid_inputs(amg):
+    p = p1_poisson_3d(9, seed=1)
+    z = p.z.copy()
+    z[3] = np.nan
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy(p.rowptr, p.col, p.val, p.x, p.y, z=z)
+    assert e.value.status == amg.ERR_INVALID_ARG
+    with pytest.raises(amg.AmgError) as e:  # an empty z extent
+        amg.Hierarchy(p.rowptr, p.col, p.val, p.x, p.y, z=p.z, bbox=(0, 1, 0, 1, 0.5, 0.5))
+    assert e.value.status == amg.ERR_INVALID_ARG
+    with pytest.raises(amg.AmgError) as e:  # octree depth above 10 (2^30 cells)
+        amg.Hierarchy(p.rowptr, p.col, p.val, p.x, p.y, z=p.z, aux_level=11)
+    assert e.value.status == amg.ERR_UNSUPPORTED
