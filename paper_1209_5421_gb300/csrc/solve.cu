@@ -98,6 +98,7 @@ extern __shared__ __align__(16) unsigned char amg_smem[];
 
 struct TailCtl {
     int tl, nlev, narrow, kc, sc_off;
+    int top_w;  // slice width of the HBM-resident top level when uniform, else 0
     int *err;
     unsigned long long *tprof;
     long long t0;
@@ -105,6 +106,10 @@ struct TailCtl {
 __shared__ TailCtl tail_ctl;
 __shared__ TailLevelLayout tail_lay[kMaxLevels];
 __shared__ __align__(16) unsigned char tail_gview[sizeof(SLev<double>)];  // SLev<T> of the top
+// The same top level as a StagedLevel<T, W> whose arrays are in HBM (uniform slice width):
+// its phases then run the code the staged levels run, so the tail executes one copy of the
+// phase code instead of two (the tail's time goes largely to instruction fetch)
+__shared__ __align__(16) unsigned char tail_sview[sizeof(StagedLevel<double, 0>)];
 
 template <class T, int W>
 __device__ __forceinline__ StagedLevel<T, W> staged_level(int l) {
@@ -273,8 +278,9 @@ template <class T, int W>
 __device__ void tail_btilde(bool inplace) {
     const int tl = tail_ctl.tl, nlev = tail_ctl.nlev, kc = tail_ctl.kc, narrow = tail_ctl.narrow;
     const int tid = threadIdx.x;
-    const WarpGroup ng{narrow};
-    const SLev<T> &top = *reinterpret_cast<const SLev<T> *>(tail_gview);
+    const SLev<T> &top_gv = *reinterpret_cast<const SLev<T> *>(tail_gview);
+    const StagedLevel<T, W> &topv = *reinterpret_cast<const StagedLevel<T, W> *>(tail_sview);
+    const bool top_staged_code = tail_ctl.top_w > 0 && (W == 0 || tail_ctl.top_w == W);
     int step[kMaxLevels] = {};
     int l = tl, ph = PH_ENTER;
     bool prev_top = true;  // the caller's barrier
@@ -285,11 +291,18 @@ __device__ void tail_btilde(bool inplace) {
             if (!prev_top) __syncthreads();  // the narrow warps' phases are complete
             prev_top = true;
             const int nth = blockDim.x;
-            if (ph == PH_PRE) phase_pre<T, W>(top, BlockGroup{}, nth, l, i);
-            else if (ph == PH_POST) phase_post<T, W>(top, BlockGroup{}, nth, l, i);
+            if (top_staged_code) {  // every thread: barrier 1 over the whole CTA
+                const WarpGroup all{nth};
+                if (ph == PH_PRE) phase_pre<T, W>(topv, all, nth, l, i);
+                else if (ph == PH_POST) phase_post<T, W>(topv, all, nth, l, i);
+            } else {
+                if (ph == PH_PRE) phase_pre<T, W>(top_gv, BlockGroup{}, nth, l, i);
+                else if (ph == PH_POST) phase_post<T, W>(top_gv, BlockGroup{}, nth, l, i);
+            }
         } else {
             prev_top = false;
             if (tid < narrow) {
+                const WarpGroup ng{narrow};
                 const StagedLevel<T, W> L = staged_level<T, W>(l);
                 if (ph == PH_ENTER && coarsest) phase_coarse(L, ng, narrow, l);
                 else if (ph == PH_PRE) phase_pre<T, W>(L, ng, narrow, l, i);
@@ -336,6 +349,7 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
         tail_ctl.narrow = Y.narrow;
         tail_ctl.kc = Y.kc;
         tail_ctl.sc_off = Y.sc;
+        tail_ctl.top_w = 0;
         tail_ctl.err = a.err;
         tail_ctl.tprof = a.tprof;
     }
@@ -371,6 +385,28 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
                 }
                 S.sc = (double *)(amg_smem + Y.sc) + (size_t)(l - Y.tl) * SC_N;
                 S.nnext = G.nnext;
+                StagedLevel<T, 0> &V = *reinterpret_cast<StagedLevel<T, 0> *>(tail_sview);
+                V.n = G.n;
+                V.w = G.w;
+                V.col = G.col16;
+                V.val = G.val;
+                V.dinv = G.dinv;
+                V.bptr = nullptr;
+                V.parent = G.parent;
+                V.children = S.children;
+                V.children2 = S.children2;
+                V.Ainv = nullptr;
+                V.Ainv2 = nullptr;
+                V.rhs = G.rhs;
+                V.e = G.e;
+                V.r = G.r;
+                for (int k = 0; k < kMaxKcycle; k++) {
+                    V.p[k] = G.p[k];
+                    V.q[k] = G.q[k];
+                }
+                V.sc = S.sc;
+                V.nnext = G.nnext;
+                tail_ctl.top_w = G.w;  // 0 unless every slice has one width
             }
             continue;
         }
