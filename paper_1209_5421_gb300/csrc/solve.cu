@@ -759,20 +759,21 @@ __device__ __forceinline__ void mdot_finish(int m, double *out, const RedCtx &rc
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x < 32) {
-        for (int i = 0; i < m; i++) {
-            double y = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-                y += __ldcg(&rc.partials[(size_t)i * gridDim.x + b]);
-            y = warp_sum(y);
-            if (threadIdx.x == 0) out[i] = y;
-        }
+    // vector i by warp i mod (warps): each sum in the same order as one warp summing them all
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < m; i += nw) {
+        double y = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            y += __ldcg(&rc.partials[(size_t)i * gridDim.x + b]);
+        y = warp_sum(y);
+        if (lane == 0) out[i] = y;
     }
+    __syncthreads();  // every warp's partial reads before the counter is re-armed
     if (threadIdx.x == 0) *rc.counter = 0u;
 }
 
 // out[i] = (w, V[i]) for i < m
-__global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__restrict__ w,
+__global__ void __launch_bounds__(kRedThreads, 4) k_mdot(int n, const double *__restrict__ w,
                                                       double *const *__restrict__ V, int m,
                                                       double *out, RedCtx rc) {
     for (int c0 = 0; c0 < m; c0 += kDotChunk)
@@ -783,7 +784,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(int n, const double *__res
 // The second Gram-Schmidt pass's dots fused with the first pass's subtraction (both are
 // row-local): w -= sum_i c[i] V[i], then out[i] = (w, V[i]) for i < m. Each row's new w is
 // written by the thread that reads it again in the later chunks.
-__global__ void __launch_bounds__(kRedThreads) k_orth_mdot(int n, double *__restrict__ w,
+__global__ void __launch_bounds__(kRedThreads, 4) k_orth_mdot(int n, double *__restrict__ w,
                                                            double *const *__restrict__ V, int m,
                                                            const double *__restrict__ c,
                                                            double *out, RedCtx rc) {
