@@ -324,8 +324,9 @@ __device__ void solve_one(const BatchProb<T> &P, const BatchCycle<T> &cyc, const
     const int n = P.n;  // every row loop: from team_tid() in steps of team_nth()
     double *bo = P.bo, *xo = P.xo, *ro = P.ro, *zo = P.zo, *to = P.to;
     T *crhs = cyc.tab[0].rhs, *ce = cyc.tab[0].e;
-    // (z, q_j) and (p_j, q_j) of the kept directions, held by every CTA of the team
-    __shared__ double zq[kBatchCap], pqh[kBatchCap];
+    // (z, q_j) and (p_j, q_j) of the kept directions, held by every CTA of the team, and
+    // their quotients (divided once per step, not per row: FP64 division is long here)
+    __shared__ double zq[kBatchCap], pqh[kBatchCap], cq[kBatchCap];
     double bb = 0.0;
     for (int i = team_tid(), nth = team_nth(); i < n; i += nth) {
         const double v = b[P.off + P.nat[i]];
@@ -368,10 +369,12 @@ __device__ void solve_one(const BatchProb<T> &P, const BatchCycle<T> &cyc, const
                     for (int j = 0; j < 4 && j0 + j < k; j++) zq[j0 + j] = r[j];
             }
             __syncthreads();
+            for (int j = threadIdx.x; j < k; j += blockDim.x) cq[j] = zq[j] / pqh[j];
+            __syncthreads();
             // p_k = z - sum_j (z, q_j) / (p_j, q_j) p_j
             for (int i = team_tid(), nth = team_nth(); i < n; i += nth) {
                 double acc = zo[i];
-                for (int j = 0; j < k; j++) acc -= (zq[j] / pqh[j]) * P.P[(size_t)j * n + i];
+                for (int j = 0; j < k; j++) acc -= cq[j] * P.P[(size_t)j * n + i];
                 pk[i] = acc;
             }
             team_sync();

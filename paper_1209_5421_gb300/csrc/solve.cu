@@ -611,22 +611,32 @@ __global__ void __launch_bounds__(kRedThreads) k_true_residual(GLev<double> L,
 // osc[OS_RP] = (r, p_i), osc[OS_TT] = (t, t), osc[OS_ZQ + j] = (z, A p_j); (p_j, A p_j) in opq
 enum : int { OS_BB = 0, OS_RR = 1, OS_STOP = 2, OS_RP = 4, OS_TT = 5, OS_ZQ = 8 };
 
-// (z, q_j) for all j < it: each block loops over j; the last block reduces every j
-__global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const double *__restrict__ z,
-                                                                double *const *__restrict__ Q,
-                                                                const int *__restrict__ it_ptr,
-                                                                double *osc, RedCtx rc) {
-    const int it = *it_ptr;
-    __shared__ bool last;
-    for (int j = 0; j < it; j++) {
-        const double *q = Q[j];
-        double a[1] = {0.0}, r[1];
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-            a[0] += z[i] * q[i];
-        block_sum<1, double>(a, r, BlockGroup{});
-        if (threadIdx.x == 0) rc.partials[(size_t)j * gridDim.x + blockIdx.x] = r[0];
-        __syncthreads();  // the reduction scratch is reused by the next j
+// Dots of w with the basis vectors V[0..m), kDotChunk vectors per sweep over the rows: each
+// thread keeps one grid-stride partial sum per vector (in row order), each block reduces them
+// vector by vector, and the last block to finish sums the block partials in block order.
+constexpr int kDotChunk = 8;
+
+__device__ __forceinline__ void mdot_chunk(int n, const double *__restrict__ w,
+                                           double *const *__restrict__ V, int c0, int mc,
+                                           double *partials) {
+    const double *vp[kDotChunk];
+#pragma unroll
+    for (int i = 0; i < kDotChunk; i++) vp[i] = i < mc ? V[c0 + i] : nullptr;
+    double a[kDotChunk] = {}, r[kDotChunk];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double wk = w[k];
+#pragma unroll
+        for (int i = 0; i < kDotChunk; i++)
+            if (i < mc) a[i] += wk * vp[i][k];
     }
+    block_sum<kDotChunk, double>(a, r, BlockGroup{});
+    if (threadIdx.x == 0)
+        for (int i = 0; i < mc; i++) partials[(size_t)(c0 + i) * gridDim.x + blockIdx.x] = r[i];
+    __syncthreads();  // the reduction scratch is reused by the next chunk
+}
+
+__device__ __forceinline__ void mdot_finish(int m, double *out, const RedCtx &rc) {
+    __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned t = atomicAdd(rc.counter, 1u);
@@ -635,27 +645,47 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_multidot(int n, const dou
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x < 32) {
-        for (int j = 0; j < it; j++) {
-            double y = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-                y += __ldcg(&rc.partials[(size_t)j * gridDim.x + b]);
-            y = warp_sum(y);
-            if (threadIdx.x == 0) osc[OS_ZQ + j] = y;
-        }
+    // vector i by warp i mod (warps): each sum in the same order as one warp summing them all
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < m; i += nw) {
+        double y = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            y += __ldcg(&rc.partials[(size_t)i * gridDim.x + b]);
+        y = warp_sum(y);
+        if (lane == 0) out[i] = y;
     }
+    __syncthreads();  // every warp's partial reads before the counter is re-armed
     if (threadIdx.x == 0) *rc.counter = 0u;
 }
 
+// (z, q_j) for all j < it: each block loops over j; the last block reduces every j
+__global__ void __launch_bounds__(kRedThreads, 4)
+    k_outer_multidot(int n, const double *__restrict__ z, double *const *__restrict__ Q,
+                     const int *__restrict__ it_ptr, double *osc, RedCtx rc) {
+    const int it = *it_ptr;
+    for (int c0 = 0; c0 < it; c0 += kDotChunk)
+        mdot_chunk(n, z, Q, c0, min(kDotChunk, it - c0), rc.partials);
+    mdot_finish(it, osc + OS_ZQ, rc);
+}
+
 // p_it = z - sum_j (z, q_j) / (p_j, q_j) p_j   (Alg. 1 step 2 on the finest level)
+// The coefficients are divided once per block (FP64 division is a long instruction sequence
+// on this GPU), the same values as dividing per row.
+constexpr int kOrthCoef = 256;
+
 __global__ void k_outer_orth(int n, const double *__restrict__ z, double *const *__restrict__ P,
                              const int *__restrict__ it_ptr, const double *__restrict__ osc,
                              const double *__restrict__ opq) {
     const int it = *it_ptr;
+    __shared__ double cf[kOrthCoef];
+    for (int j = threadIdx.x; j < it && j < kOrthCoef; j += blockDim.x)
+        cf[j] = -osc[OS_ZQ + j] / opq[j];
+    __syncthreads();
     double *p = P[it];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc = z[i];
-        for (int j = 0; j < it; j++) acc += (-osc[OS_ZQ + j] / opq[j]) * P[j][i];
+        for (int j = 0; j < it; j++)
+            acc += (j < kOrthCoef ? cf[j] : -osc[OS_ZQ + j] / opq[j]) * P[j][i];
         p[i] = acc;
     }
 }
@@ -723,53 +753,6 @@ __global__ void k_spmv(GLev<double> L, const double *__restrict__ z, double *__r
         const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
         w[row] = row_dot(L, base, 0, width, z);
     }
-}
-
-// Dots of w with the basis vectors V[0..m), kDotChunk vectors per sweep over the rows: each
-// thread keeps one grid-stride partial sum per vector (in row order), each block reduces them
-// vector by vector, and the last block to finish sums the block partials in block order.
-constexpr int kDotChunk = 8;
-
-__device__ __forceinline__ void mdot_chunk(int n, const double *__restrict__ w,
-                                           double *const *__restrict__ V, int c0, int mc,
-                                           double *partials) {
-    const double *vp[kDotChunk];
-#pragma unroll
-    for (int i = 0; i < kDotChunk; i++) vp[i] = i < mc ? V[c0 + i] : nullptr;
-    double a[kDotChunk] = {}, r[kDotChunk];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const double wk = w[k];
-#pragma unroll
-        for (int i = 0; i < kDotChunk; i++)
-            if (i < mc) a[i] += wk * vp[i][k];
-    }
-    block_sum<kDotChunk, double>(a, r, BlockGroup{});
-    if (threadIdx.x == 0)
-        for (int i = 0; i < mc; i++) partials[(size_t)(c0 + i) * gridDim.x + blockIdx.x] = r[i];
-    __syncthreads();  // the reduction scratch is reused by the next chunk
-}
-
-__device__ __forceinline__ void mdot_finish(int m, double *out, const RedCtx &rc) {
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned t = atomicAdd(rc.counter, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // vector i by warp i mod (warps): each sum in the same order as one warp summing them all
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < m; i += nw) {
-        double y = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32)
-            y += __ldcg(&rc.partials[(size_t)i * gridDim.x + b]);
-        y = warp_sum(y);
-        if (lane == 0) out[i] = y;
-    }
-    __syncthreads();  // every warp's partial reads before the counter is re-armed
-    if (threadIdx.x == 0) *rc.counter = 0u;
 }
 
 // out[i] = (w, V[i]) for i < m
