@@ -229,6 +229,10 @@ int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns);
  *             1 = one CTA per system (the default with a fixed shape: a system's result then
  *             does not depend on the other systems), 2..8 = sized as above, at most max_team.
  * A batch whose shape is chosen by timing times its shapes again on the next solve.
+ * Teams expect the batch's kernel to have the GPU to itself (its CTAs resident together): when
+ * several batches are solved at the same time on different streams, give them a fixed shape
+ * or max_team = 1 (a team whose members cannot all run waits until its barrier's limit, and
+ * that system ends with AMG_ERR_TIMEOUT).
  * Errors: AMG_ERR_INVALID_ARG (NULL, max_team outside 0..8).
  */
 int amg_batch_set_teams(amg_batch *bt, int32_t max_team);
