@@ -348,7 +348,7 @@ def run_octree(args, world, flush, dev, stream):
     from paper_1209_5421_gb300 import amg
     from paper_1209_5421_gb300.meshes import p1_poisson_3d
 
-    prob = p1_poisson_3d(args.octree_n, seed=0)
+    prob = p1_poisson_3d(args.octree_n, seed=0)  # (cube_129 in meshes.WORKLOADS at 129)
     td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
     A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
     z = td(prob.z)

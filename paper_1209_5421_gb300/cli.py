@@ -30,7 +30,8 @@ def main(argv=None) -> int:
     A = [dev(t) for t in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
     b = dev(prob.b)
     x = torch.empty_like(b)
-    opts = dict(aux_level=aux, cycle_prec=amg.FP32 if a.prec == "fp32" else amg.FP64,
+    z = dev(prob.z) if getattr(prob, "z", None) is not None else None  # octree (3D)
+    opts = dict(aux_level=aux, z=z, cycle_prec=amg.FP32 if a.prec == "fp32" else amg.FP64,
                 outer=amg.OUTER_FGMRES if a.outer == "fgmres" else amg.OUTER_FCG)
     status = 0
     for _ in range(a.repeat):

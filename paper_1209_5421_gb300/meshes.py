@@ -236,6 +236,9 @@ WORKLOADS = {
     # disk of radius 0.5 cut from 1921x1921 nodes (jitter 0.2h): about 2.89M unknowns, the
     # size of the paper's smaller disk example; empty auxiliary cells in the corners; L auto
     "disk_1921": dict(disk=True, n=1921, jitter=0.2, seed=0, rhs="normal", aux_level=0),
+    # 3D: 129^3-node Kuhn tetrahedral grid of the unit cube (jitter 0.15h), 2,048,383
+    # unknowns, octree depth auto (= 6)
+    "cube_129": dict(cube=True, n=129, seed=0, rhs="normal", aux_level=0),
 }
 
 
@@ -246,6 +249,8 @@ def workload(name: str, **overrides) -> tuple[Problem, int]:
     aux = spec.pop("aux_level")
     if spec.pop("disk", False):
         return disk_poisson(name=name, **spec), aux
+    if spec.pop("cube", False):
+        return p1_poisson_3d(name=name, **spec), aux
     return p1_poisson(name=name, **spec), aux
 
 
