@@ -180,3 +180,25 @@ def test_batch_with_a_single_unknown_system(amg, prec):
     assert np.linalg.norm(probs[1].b - A @ x1) / np.linalg.norm(probs[1].b) <= 1e-8
     assert B.teams()[1] > 1 and B.teams()[0] == 1
     B.close()
+
+
+def test_full_batch_workload(amg, oracle_mod):
+    # the benchmark's batched configuration at full size: 256 systems (13M unknowns), FP32
+    # cycle, autotuned launch shape with teams. Every system meets the FP64 true residual;
+    # every 32nd system is compared with the oracle's solution one by one.
+    from paper_1209_5421_gb300.meshes import batch_workload
+
+    probs = batch_workload()
+    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP32)
+    tol = 1e-8
+    x, it, rr, st = B.solve(np.concatenate([p.b for p in probs]), tol)
+    assert (st == amg.OK).all()
+    assert B.teams().max() > 1
+    off = B.row_off
+    for k, p in enumerate(probs):
+        xk = x[off[k]:off[k + 1]]
+        A = p.to_scipy()
+        assert np.linalg.norm(p.b - A @ xk) / np.linalg.norm(p.b) <= tol, k
+    for k in range(0, len(probs), 32):
+        _check_system(amg, oracle_mod, probs[k], x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, 3)
+    B.close()

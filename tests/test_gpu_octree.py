@@ -172,3 +172,24 @@ def test_octree_invalid_inputs(amg):
     with pytest.raises(amg.AmgError) as e:  # octree depth above 10 (2^30 cells)
         amg.Hierarchy(p.rowptr, p.col, p.val, p.x, p.y, z=p.z, aux_level=11)
     assert e.value.status == amg.ERR_UNSUPPORTED
+
+
+def test_octree_full_size_cube_129(amg, oracle_mod):
+    # the benchmark's 3D workload at full size (2,048,383 unknowns), FP32 cycle with FGMRES as
+    # the bench times it: the hierarchy against the oracle's (sizes, cells, colours,
+    # aggregates bit-exact; operators row-scaled within 1e-12), then the solve
+    from paper_1209_5421_gb300.meshes import workload
+
+    p, aux = workload("cube_129")
+    G = amg.Hierarchy.from_problem(p, aux_level=aux, cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES)
+    O = oracle_mod.Hierarchy.from_problem(p, aux_level=aux)
+    _compare(G, O)
+    tol = 1e-8
+    x, it, rr, st = G.solve(p.b, tol)
+    xo, ito, _, sto = O.solve(p.b, tol)
+    assert st == amg.OK and sto == oracle_mod.OK
+    A = p.to_scipy()
+    assert np.linalg.norm(p.b - A @ x) / np.linalg.norm(p.b) <= tol
+    assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert it <= ito + 3, (it, ito)
+    G.close()
