@@ -724,7 +724,10 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_update(int n, double *con
     const int it = *it_ptr;
     const double pq = opq[it];
     const bool bad = !(pq > 0.0) || !isfinite(pq);
-    const double alpha = bad ? 0.0 : osc[OS_RP] / pq;
+    __shared__ double alpha_s;  // one FP64 division per block, not per thread
+    if (threadIdx.x == 0) alpha_s = bad ? 0.0 : osc[OS_RP] / pq;
+    __syncthreads();
+    const double alpha = alpha_s;
     const double *p = P[it];
     const double *q = Q[it];
     double v[1] = {0.0};
