@@ -526,7 +526,12 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
     constexpr int kOpWords = (int)(sizeof(Op) / sizeof(int));
     if (threadIdx.x < kOpWords) ((int *)&sop[0])[threadIdx.x] = ((const int *)a.prog)[threadIdx.x];
     __syncthreads();
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnth = gridDim.x * blockDim.x;
+    // rows go to warps in 32-row chunks with the CTA index fastest, so an op over a few
+    // thousand rows (the coarse grid-wide levels) spreads over every SM instead of filling the
+    // first few CTAs; a warp's rows stay consecutive (coalesced slots, lane = row mod 32)
+    const int gtid = (((int)threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x) * 32 +
+                     ((int)threadIdx.x & 31);
+    const int gnth = gridDim.x * blockDim.x;
     const RedCtx rc{a.partials, nullptr};
     for (int k = 0; k < a.nops; k++) {
         const Op &op = sop[k & 1];
