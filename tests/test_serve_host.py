@@ -1,0 +1,252 @@
+"""The serving loop's host logic on the CPU, with the GPU work replaced by fakes.
+
+The real `Server` runs (its setup thread, batch workers and large-lane thread, admission,
+eviction and queues); only the hierarchy and batch objects are stand-ins that solve exactly
+with scipy, report a device size, and record when they run. This checks the scheduling
+invariants without a GPU:
+  * every request gets the solution of its own system, through the lane its size selects;
+  * admission: with the setup estimate above the real size the resident bytes never exceed
+    the budget and idle hierarchies are evicted least recently used first; real sizes above
+    the estimate, and growth during solves, are charged and evicted back under the budget;
+    a matrix larger than the budget is refused;
+  * a large-lane solve never overlaps a batch solve or a setup (it has the GPU to itself);
+  * an unknown matrix is reported by drain().
+The same server on the GPU is tested in test_gpu_serve.py.
+"""
+import contextlib
+import threading
+import time
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from paper_1209_5421_gb300 import amg
+from paper_1209_5421_gb300.meshes import p1_poisson
+
+BYTES_PER_UNKNOWN = 1000  # the fakes' device size (below the server's setup estimate)
+
+
+class Log:
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.intervals = []  # (kind, t0, t1)
+        self.closed = []     # sizes of closed hierarchies, in order
+
+    @contextlib.contextmanager
+    def span(self, kind, hold=0.003):
+        t0 = time.perf_counter()
+        time.sleep(hold)  # long enough for overlaps to show
+        yield
+        with self.lock:
+            self.intervals.append((kind, t0, time.perf_counter()))
+
+
+def _solve(rowptr, col, val, b):
+    n = len(rowptr) - 1
+    return spla.spsolve(sp.csr_matrix((val, col, rowptr), shape=(n, n)).tocsc(), b)
+
+
+def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0):
+    class FakeHierarchy:
+        def __init__(self, rowptr, col, val, x, y, z=None, cycle_prec=None, outer=None):
+            with log.span("setup"):
+                self.A = (np.asarray(rowptr), np.asarray(col), np.asarray(val))
+                self.n = len(rowptr) - 1
+                self.nbytes = bytes_per_unknown * self.n
+
+        def solve(self, b, tol, stream=None):
+            with log.span("large"):
+                x = _solve(*self.A, b.numpy())
+            self.nbytes += grow_per_solve  # as the outer iteration's directions are allocated
+            return torch.from_numpy(x), 1, 0.0, amg.OK
+
+        def close(self):
+            with log.lock:
+                log.closed.append(self.n)
+
+    class FakeBatch:
+        def __init__(self, hs):
+            self.hs = hs
+            self.row_off = np.zeros(len(hs) + 1, np.int64)
+            self.row_off[1:] = np.cumsum([h.n for h in hs])
+
+        @classmethod
+        def over(cls, hierarchies, threads=0, stream=None):
+            return cls(list(hierarchies))
+
+        def solve(self, rhs, tol, stream=None):
+            with log.span("batch"):
+                r = rhs.numpy()
+                x = np.concatenate([_solve(*h.A, r[self.row_off[k]:self.row_off[k + 1]])
+                                    for k, h in enumerate(self.hs)])
+            for h in self.hs:
+                h.nbytes += grow_per_solve
+            k = len(self.hs)
+            return torch.from_numpy(x), np.ones(k, int), np.zeros(k), np.zeros(k, int)
+
+        def close(self):
+            pass
+
+    return FakeHierarchy, FakeBatch
+
+
+@pytest.fixture
+def server_cls(monkeypatch):
+    import torch
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    from paper_1209_5421_gb300.serve import Server
+
+    log = Log()
+
+    def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, **kw):
+        H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve)
+        monkeypatch.setattr(amg, "Hierarchy", H)
+        monkeypatch.setattr(amg, "Batch", B)
+        S = Server(**kw)
+        S.dev = torch.device("cpu")  # before the first request: the fakes run on the host
+        return S
+
+    return make, log
+
+
+def _consistent(S):
+    """The charged bytes are the resident hierarchies' current bytes."""
+    return S.used == sum(e.h.nbytes for e in S.res.values()) == sum(e.nbytes for e in S.res.values())
+
+
+def _problems(sizes):
+    return {f"m{k}": p1_poisson(n, jitter=0.2, seed=20 + k, rhs="normal")
+            for k, n in enumerate(sizes)}
+
+
+def _register(S, probs):
+    for key, p in probs.items():
+        S.register(key, p.rowptr, p.col, p.val, p.x, p.y)
+
+
+def _overlaps(log, a, b):
+    A = [(t0, t1) for k, t0, t1 in log.intervals if k == a]
+    B = [(t0, t1) for k, t0, t1 in log.intervals if k == b]
+    return [(x, y) for x in A for y in B if x[0] < y[1] and y[0] < x[1]]
+
+
+def test_results_lanes_and_exclusive_large_lane(server_cls):
+    make, log = server_cls
+    probs = _problems([9, 17, 12, 33, 14, 29])  # 49 .. 961 unknowns
+    large = 500  # the 33 x 33 and 29 x 29 node systems take the large lane
+    S = make(workers=3, large_unknowns=large)
+    _register(S, probs)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(40):
+        key = f"m{rng.integers(len(probs))}"
+        reqs.append((key, S.submit(key, rng.standard_normal(probs[key].n))))
+        if i % 7 == 0:
+            time.sleep(0.002)
+    S.drain(timeout=120)
+    st = S.stats()
+    S.close()
+    assert st["completed"] == len(reqs)
+    assert st["setups"] == len({k for k, _ in reqs}) and st["evictions"] == 0
+    for key, r in reqs:
+        p = probs[key]
+        assert r.done.is_set() and r.status == amg.OK
+        assert r.lane == ("large" if p.n > large else "batch"), (key, r.lane)
+        np.testing.assert_allclose(r.x, _solve(p.rowptr, p.col, p.val, r.b), rtol=0, atol=1e-12)
+    assert any(k == "large" for k, _, _ in log.intervals)
+    assert not _overlaps(log, "large", "batch")
+    assert not _overlaps(log, "large", "setup")
+
+
+def test_budget_admission_lru_eviction(server_cls):
+    from paper_1209_5421_gb300.serve import setup_estimate
+
+    make, log = server_cls
+    probs = {f"m{k}": p1_poisson(n, jitter=0.2, seed=40 + k, rhs="normal")
+             for k, n in enumerate([20, 21, 22, 21])}  # 324 .. 400 unknowns
+    real = {k: BYTES_PER_UNKNOWN * p.n for k, p in probs.items()}
+    est = {k: setup_estimate(p.n, len(p.col)) for k, p in probs.items()}
+    assert all(est[k] > real[k] for k in probs)  # the estimate is an upper bound here
+    # any two residents leave room for a setup's estimate, no three do
+    budget = 2 * max(real.values()) + max(est.values())
+    assert 3 * min(real.values()) + min(est.values()) > budget
+    S = make(workers=2, budget_bytes=budget, large_unknowns=10 ** 6)
+    _register(S, probs)
+    for key in ["m0", "m1", "m0", "m2", "m3", "m1"]:  # one at a time: LRU = submission order
+        r = S.submit(key, np.ones(probs[key].n))
+        S.drain(timeout=60)
+        assert r.status == amg.OK
+        assert _consistent(S) and S.used <= budget
+    st = S.stats()
+    S.close()
+    assert st["max_resident_bytes"] <= budget
+    # m3 needs room with m1, m0, m2 resident: m1 goes (m0 was used after it); then m1 needs
+    # room with m0, m2, m3 resident: m0 goes
+    assert st["evictions"] == 2 and log.closed[:2] == [probs["m1"].n, probs["m0"].n]
+    assert st["setups"] == 5
+
+
+def test_real_size_above_the_estimate_is_evicted_back_under_the_budget(server_cls):
+    from paper_1209_5421_gb300.serve import setup_estimate
+
+    make, _ = server_cls
+    probs = _problems([20, 21, 22, 23])
+    bpu = 3000  # real bytes per unknown, above the estimate
+    assert all(setup_estimate(p.n, len(p.col)) < bpu * p.n for p in probs.values())
+    # m3's estimate fits beside m2 but its real size does not: the server must evict m2 (idle)
+    # after m3's setup
+    budget = bpu * (probs["m2"].n + probs["m3"].n) - 1
+    assert bpu * probs["m2"].n + setup_estimate(probs["m3"].n, len(probs["m3"].col)) <= budget
+    S = make(bytes_per_unknown=bpu, workers=2, budget_bytes=budget, large_unknowns=10 ** 6)
+    _register(S, probs)
+    for key in ["m0", "m1", "m2", "m3", "m0"]:
+        r = S.submit(key, np.ones(probs[key].n))
+        S.drain(timeout=60)
+        assert r.status == amg.OK
+        assert key in S.res  # the hierarchy just set up stays
+        assert _consistent(S) and S.used <= budget
+    st = S.stats()
+    S.close()
+    assert st["evictions"] >= 3  # m0 and m1 at admission, m2 after m3's setup
+
+
+@pytest.mark.parametrize("large", [10, 10 ** 6])
+def test_growth_during_solves_is_charged(server_cls, large):
+    make, _ = server_cls
+    probs = _problems([9, 12, 15])
+    grow = 5000
+    S = make(grow_per_solve=grow, workers=2, large_unknowns=large)
+    _register(S, probs)
+    for i in range(9):
+        key = f"m{i % 3}"
+        S.submit(key, np.ones(probs[key].n))
+    S.drain(timeout=60)
+    assert _consistent(S)
+    base = sum(BYTES_PER_UNKNOWN * p.n for p in probs.values())
+    assert S.used == base + 9 * grow and S.max_used >= S.used
+    S.close()
+
+
+def test_matrix_larger_than_the_budget_is_refused(server_cls):
+    make, _ = server_cls
+    p = p1_poisson(30, jitter=0.2, seed=1, rhs="normal")
+    S = make(workers=1, budget_bytes=1000)
+    S.register("big", p.rowptr, p.col, p.val, p.x, p.y)
+    S.submit("big", p.b)
+    with pytest.raises(RuntimeError, match="does not fit"):
+        S.drain(timeout=30)
+    S.close()
+
+
+def test_unknown_matrix_is_reported(server_cls):
+    make, _ = server_cls
+    S = make(workers=1)
+    S.submit("nobody", np.ones(4))
+    with pytest.raises(RuntimeError, match="unknown matrix"):
+        S.drain(timeout=30)
+    S.close()
