@@ -319,6 +319,9 @@ int amg_smooth(amg_hierarchy *h, int level, int backward, const double *f, doubl
  * (values, 0 padding), written here column-major (entry (i, k) at [k * rows + i]).
  * diag_first = 1 moves each row's diagonal entry to slot 0 (as the paper's solver stores
  * it); 0 keeps the CSR order. Device kernel; all arrays are device or host memory.
+ * rowptr must be non-decreasing from rowptr[0] = 0, and col and val must hold rowptr[rows]
+ * entries: the packer reads that many and does not validate rowptr (unlike amg_setup, which
+ * validates the whole matrix on the device); the Python binding checks host arrays.
  * Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries.
  */
 int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, const double *val,
@@ -337,6 +340,7 @@ int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, cons
  *     make that first call before any stream capture.
  *   - Every call on a device shares the array: calls that overlap on the GPU (other streams
  *     or host threads) race and must be ordered by the caller.
+ *   - The same precondition on rowptr as amg_csr_to_ell.
  *   - Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries; the call waits for
  *     its kernels to finish.
  */

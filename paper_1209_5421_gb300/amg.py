@@ -153,9 +153,44 @@ def _check(status: int, what: str):
         raise AmgError(status, f"{what}: {lib().amg_last_error().decode()}")
 
 
-def _as(a, dtype):
-    if isinstance(a, np.ndarray):
-        return np.ascontiguousarray(a, dtype=dtype)
+_TORCH_DTYPE = {np.dtype(np.int32): "torch.int32", np.dtype(np.float64): "torch.float64"}
+
+
+def _is_tensor(a) -> bool:
+    return hasattr(a, "data_ptr") and not isinstance(a, np.ndarray)
+
+
+def _count(a) -> int:
+    return int(a.numel()) if _is_tensor(a) else int(a.size)
+
+
+def _as(a, dtype, n=None, what="array"):
+    """An input array for a C call. numpy arrays (and other array-likes) become contiguous
+    arrays of `dtype`; a torch tensor is passed as it is and must already have that dtype (the
+    library reads its bytes as `dtype`). n: the number of entries the call reads. A raw
+    pointer carries no length, so a shorter buffer would be read past its end: checked here."""
+    if _is_tensor(a):
+        if str(a.dtype) != _TORCH_DTYPE[np.dtype(dtype)]:
+            raise TypeError(f"{what}: a tensor of {a.dtype}; the library reads "
+                            f"{_TORCH_DTYPE[np.dtype(dtype)]}")
+    else:
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if n is not None and _count(a) != n:
+        raise ValueError(f"{what}: {_count(a)} entries, expected {n}")
+    return a
+
+
+def _out(a, dtype, n, what):
+    """A caller-provided output buffer (written in place, so never converted): `n` entries of
+    `dtype`, contiguous."""
+    if _is_tensor(a):
+        if str(a.dtype) != _TORCH_DTYPE[np.dtype(dtype)]:
+            raise TypeError(f"{what}: a tensor of {a.dtype}, expected "
+                            f"{_TORCH_DTYPE[np.dtype(dtype)]}")
+    elif not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype):
+        raise TypeError(f"{what}: expected a numpy array or tensor of {np.dtype(dtype)}")
+    if _count(a) != n:
+        raise ValueError(f"{what}: {_count(a)} entries, expected {n}")
     return a
 
 
@@ -171,12 +206,16 @@ class Hierarchy:
                  bbox=None, stream=None, z=None):
         """z given: the octree (3D) variant (amg_setup3); bbox then has 6 entries."""
         L = lib()
-        self._keep = (_as(rowptr, np.int32), _as(col, np.int32), _as(val, np.float64),
-                      _as(x, np.float64), _as(y, np.float64))
-        zz = _as(z, np.float64) if z is not None else None
-        rp, cl, vl, xx, yy = self._keep
-        n = len(rp) - 1
-        nnz = len(cl)
+        rp = _as(rowptr, np.int32, what="rowptr")
+        n = _count(rp) - 1
+        if n < 0:
+            raise ValueError("rowptr: no entries (a CSR matrix of n rows has n + 1)")
+        cl = _as(col, np.int32, what="col")
+        nnz = _count(cl)
+        vl = _as(val, np.float64, nnz, "val")
+        xx, yy = _as(x, np.float64, n, "x"), _as(y, np.float64, n, "y")
+        zz = _as(z, np.float64, n, "z") if z is not None else None
+        self._keep = (rp, cl, vl, xx, yy, zz)  # alive until the call returns
         A = Csr(n, nnz, _ptr(rp), _ptr(cl), _ptr(vl))
         o = Options()
         L.amg_options_default(C.byref(o))
@@ -231,9 +270,11 @@ class Hierarchy:
 
     def solve(self, b, tol=1e-8, x=None, stream=None, check=False):
         """x = A^{-1} b. Returns (x, iters, relres, status). x: numpy if b is numpy."""
-        b = _as(b, np.float64)
+        b = _as(b, np.float64, self.n, "b")
         if x is None:
             x = np.empty(self.n) if isinstance(b, np.ndarray) else b.new_empty(self.n)
+        else:
+            _out(x, np.float64, self.n, "x")
         it = C.c_int()
         rr = C.c_double()
         st = lib().amg_solve(self.h, _ptr(b), tol, _ptr(x), C.byref(it), C.byref(rr),
@@ -320,15 +361,16 @@ class Hierarchy:
         return out
 
     def apply_cycle(self, level: int, f, stream=None):
-        f = _as(f, np.float64)
-        z = np.empty(len(f)) if isinstance(f, np.ndarray) else f.new_empty(len(f))
+        f = _as(f, np.float64, self.level_info(level)["n"], "f")
+        z = np.empty(_count(f)) if isinstance(f, np.ndarray) else f.new_empty(_count(f))
         _check(lib().amg_apply_cycle(self.h, level, _ptr(f), _ptr(z), _stream(stream)),
                "amg_apply_cycle")
         return z
 
     def smooth(self, level: int, f, u, backward=False, stream=None):
-        f = _as(f, np.float64)
-        u = _as(u, np.float64).copy()
+        n = self.level_info(level)["n"]
+        f = _as(f, np.float64, n, "f")
+        u = _as(u, np.float64, n, "u").copy()
         _check(lib().amg_smooth(self.h, level, int(backward), _ptr(f), _ptr(u), _stream(stream)),
                "amg_smooth")
         return u
@@ -336,8 +378,12 @@ class Hierarchy:
 
 def csr_to_ell(rowptr, col, val, width, diag_first=True, stream=None):
     """The paper's ELL format (Sec. 4.1): column-major Aj (cols, -1 pad), Ax (vals, 0 pad)."""
-    rowptr, col, val = _as(rowptr, np.int32), _as(col, np.int32), _as(val, np.float64)
-    rows = len(rowptr) - 1
+    rowptr, col = _as(rowptr, np.int32, what="rowptr"), _as(col, np.int32, what="col")
+    val = _as(val, np.float64, _count(col), "val")
+    rows = _count(rowptr) - 1
+    if isinstance(rowptr, np.ndarray) and rows >= 0:  # the packer trusts rowptr: check it
+        if rowptr[0] != 0 or (np.diff(rowptr) < 0).any() or rowptr[-1] > _count(col):
+            raise ValueError("rowptr must rise from 0 to at most len(col)")
     Aj = np.empty(rows * width, np.int32)
     Ax = np.empty(rows * width)
     _check(lib().amg_csr_to_ell(rows, _ptr(rowptr), _ptr(col), _ptr(val), width,
@@ -358,6 +404,11 @@ class Batch:
         L = lib()
         sizes = [len(p[0]) - 1 for p in problems]
         nnzs = [len(p[1]) for p in problems]
+        for k, p in enumerate(problems):
+            if sizes[k] < 0 or len(p[2]) != nnzs[k] or len(p[3]) != sizes[k] \
+                    or len(p[4]) != sizes[k]:
+                raise ValueError(f"system {k}: rowptr needs n + 1 entries, val as many as col, "
+                                 "x and y n each")
         row_off = np.zeros(len(problems) + 1, np.int64)
         row_off[1:] = np.cumsum(sizes)
         nz_off = np.zeros(len(problems) + 1, np.int64)
@@ -435,9 +486,11 @@ class Batch:
     def solve(self, rhs, tol=1e-8, x=None, stream=None):
         """All systems: rhs concatenated (numpy or device tensor). Returns (x, iters, relres,
         status) with per-system numpy arrays; the call's own status is max-severity first."""
-        rhs = _as(rhs, np.float64)
+        rhs = _as(rhs, np.float64, self.n, "rhs")
         if x is None:
             x = np.empty(self.n) if isinstance(rhs, np.ndarray) else rhs.new_empty(self.n)
+        else:
+            _out(x, np.float64, self.n, "x")
         it = np.zeros(self.nprob, np.int32)
         rr = np.zeros(self.nprob, np.float64)
         st = np.zeros(self.nprob, np.int32)
