@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "amg_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
+# A prebuilt oracle library to load instead (the mutation test points this at builds of the
+# oracle with one planted mistake each, to show that the pins catch it); unset in normal use.
+LIB_OVERRIDE_ENV = "AMG_ORACLE_LIB"
 
 OK, ERR_INVALID_ARG, ERR_BAD_MATRIX, ERR_OOM, ERR_NOT_CONVERGED, ERR_BREAKDOWN = 0, 1, 2, 3, 5, 6
 
@@ -25,13 +28,20 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc: -O2, no FMA contraction, IEEE division."""
+    if os.environ.get(LIB_OVERRIDE_ENV):
+        return os.environ[LIB_OVERRIDE_ENV]
     os.makedirs(BUILD_DIR, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-std=c99", "-o", tmp, SRC, "-lm"])
+        compile_oracle(SRC, tmp)
         os.replace(tmp, LIB)
     return LIB
+
+
+def compile_oracle(src: str, out: str):
+    """gcc -O2, no FMA contraction, IEEE division: the flags every build of the oracle uses."""
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                           "-shared", "-std=c99", "-o", out, src, "-lm"])
 
 
 class Opts(C.Structure):

@@ -1,0 +1,153 @@
+"""The oracle's pins catch plausible mistakes: each one planted in a copy of the oracle fails
+at least one pin.
+
+Every mutant below is a copy of oracle/amg_oracle.c with one mistake of the kind a
+restatement of the paper could make (a transposed operand, a dropped term, a wrong sign or
+index, an off-by-one, the paper's own over-simple claims taken literally). Each copy is
+compiled with the oracle's flags and the pin files (tests/test_oracle_*.py) run against it in
+a subprocess, through the oracle loader's library override. A pin must fail (pytest exit
+status 1: a test failed, not a crash). A build of the unmodified source through the same path
+must pass, so the failures come from the mistakes.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+from oracle import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = [os.path.join("tests", f) for f in ("test_oracle_aggregation.py", "test_oracle_galerkin.py",
+                                          "test_oracle_smoother.py", "test_oracle_cycle.py",
+                                          "test_oracle_disk.py", "test_oracle_octree.py")]
+
+# name -> (text in the oracle, replacement): each text occurs exactly once
+MUTANTS = {
+    # Sec. 3.2 / 4.2 binning: x and y exchanged in the cell coordinates
+    "bin_x_y_exchanged": (
+        "        f->t1[j] = cell_index_1d(x[j], h->bbox[0], h->bbox[1], L);\n"
+        "        f->t2[j] = cell_index_1d(y[j], h->bbox[2], h->bbox[3], L);",
+        "        f->t1[j] = cell_index_1d(y[j], h->bbox[2], h->bbox[3], L);\n"
+        "        f->t2[j] = cell_index_1d(x[j], h->bbox[0], h->bbox[1], L);"),
+    # eq. subregion: rounding up instead of down (off by one cell)
+    "bin_rounds_up": (
+        "    return (int)floor(s);",
+        "    return (int)ceil(s) < w ? (int)ceil(s) : w - 1;"),
+    # Sec. 3.1 depth rule: 4^L < N instead of 4^L <= N
+    "depth_strict": (
+        "    while (N >= (1LL << (2 * (L + 1)))) L++;",
+        "    while (N > (1LL << (2 * (L + 1)))) L++;"),
+    # Sec. 4.2 parent cell with t1 and t2 exchanged (the text's transposed form, reading R2)
+    "parent_transposed": (
+        "            cid[i] = (c3 * w + c2) * w + c1;",
+        "            cid[i] = (c3 * w + c1) * w + c2;"),
+    # Sec. 2 / Sec. 5: empty cells kept as (empty) aggregates instead of compacted away
+    "empty_cells_kept": (
+        "        for (long long c = 0; c < ncell; c++) num[c] = num[c] ? nc++ : -1;",
+        "        for (long long c = 0; c < ncell; c++) num[c] = nc++;"),
+    # eq. acsum: the diagonal entries dropped from the Galerkin sums
+    "galerkin_drops_diagonal": (
+        "                buf[k].v = f->val[p];",
+        "                buf[k].v = f->col[p] == i ? 0.0 : f->val[p];"),
+    # eq. acsum: every contribution summed into the row's own aggregate (column index lost)
+    "galerkin_wrong_column": (
+        "                buf[k].c = f->agg[f->col[p]];",
+        "                buf[k].c = f->agg[i];"),
+    # Sec. 4.5 taken literally: four colours whatever the span (fails reading R5)
+    "four_colours_always": (
+        "    lv->m = lv->span + 1 > 2 ? lv->span + 1 : 2;",
+        "    lv->m = 2;"),
+    # reading R5: the span measured in t1 only
+    "span_ignores_t2": (
+        "            if (d2 > s) s = d2;",
+        "            (void)d2;"),
+    # Sec. 6 octree colouring with m instead of m^2 for the third coordinate
+    "octree_colour_weight": (
+        "        if (lv->t3) lv->color[i] += lv->m * lv->m * (lv->t3[i] % lv->m);",
+        "        if (lv->t3) lv->color[i] += lv->m * (lv->t3[i] % lv->m);"),
+    # Gauss-Seidel update with the wrong sign on the off-diagonal terms
+    "gs_sign": (
+        "        else s -= lv->val[p] * u[j];",
+        "        else s += lv->val[p] * u[j];"),
+    # reading R14: the post-smoother sweeps in the forward order (not the adjoint R^t)
+    "backward_sweep_forward": (
+        "        for (int p = lv->n - 1; p >= 0; p--) gs_row(lv, lv->perm[p], f, u);",
+        "        for (int p = 0; p < lv->n; p++) gs_row(lv, lv->perm[p], f, u);"),
+    # Alg. 2: f restricted instead of the residual f - A u1
+    "restricts_f_not_residual": (
+        "    for (int i = 0; i < n; i++) r[i] = f[i] - r[i];",
+        "    for (int i = 0; i < n; i++) r[i] = f[i];"),
+    # Alg. 2: u2 = P e instead of u1 + P e
+    "prolongation_overwrites": (
+        "    for (int i = 0; i < n; i++) z[i] += e[lv->agg[i]];",
+        "    for (int i = 0; i < n; i++) z[i] = e[lv->agg[i]];"),
+    # Alg. 2: the post-smoothing step dropped
+    "no_post_smoothing": (
+        "    smooth(lv, 1, f, z);\n    free(r);",
+        "    free(r);"),
+    # Alg. 1: the orthogonalisation coefficient with the wrong sign
+    "alg1_beta_sign": (
+        "            double beta = -dot(n, z, q + (size_t)j * n) / pAp[j];",
+        "            double beta = dot(n, z, q + (size_t)j * n) / pAp[j];"),
+    # Alg. 1: alpha from (r, r) instead of (r, p)
+    "alg1_alpha": (
+        "        double alpha = dot(n, r, pi) / pAp[it];\n"
+        "        for (int i = 0; i < n; i++) u[i] += alpha * pi[i];",
+        "        double alpha = dot(n, r, r) / pAp[it];\n"
+        "        for (int i = 0; i < n; i++) u[i] += alpha * pi[i];"),
+    # outer flexible CG: the orthogonalisation coefficient with the wrong sign
+    "outer_beta_sign": (
+        "            double beta = -dot(n, z, Q[j]) / pAp[j];",
+        "            double beta = dot(n, z, Q[j]) / pAp[j];"),
+    # coarsest exact solve: the backward substitution reads L instead of L^t
+    "cholesky_transposed": (
+        "        for (int k = i + 1; k < n; k++) s -= a[(size_t)k * n + i] * u[k];",
+        "        for (int k = i + 1; k < n; k++) s -= a[(size_t)i * n + k] * u[k];"),
+}
+
+
+def _build(name, text, tmp):
+    src = open(oracle.SRC).read()
+    if text is not None:
+        old, new = text
+        assert src.count(old) == 1, f"{name}: the mutated text must occur once in the oracle"
+        src = src.replace(old, new)
+    c = os.path.join(tmp, f"{name}.c")
+    with open(c, "w") as f:
+        f.write(src)
+    so = os.path.join(tmp, f"lib{name}.so")
+    oracle.compile_oracle(c, so)
+    return so
+
+
+def _run_pins(so):
+    env = dict(os.environ, **{oracle.LIB_OVERRIDE_ENV: so})
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"  # the runs go in parallel: one BLAS thread each
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-m", "not gpu",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=900)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    tmp = str(tmp_path_factory.mktemp("mutants"))
+    cases = {"unmodified": None, **MUTANTS}
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+        libs = dict(zip(cases, ex.map(lambda kv: _build(kv[0], kv[1], tmp), cases.items())))
+        runs = dict(zip(cases, ex.map(_run_pins, [libs[k] for k in cases])))
+    return runs
+
+
+def test_unmodified_oracle_passes_through_the_same_path(results):
+    rc, out = results["unmodified"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(results, name):
+    rc, out = results[name]
+    assert rc == 1, f"{name}: pins exit status {rc} (1 = a pin failed)\n{out}"

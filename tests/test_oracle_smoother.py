@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from paper_1209_5421_gb300.meshes import p1_poisson
+from paper_1209_5421_gb300.meshes import five_point_grid, p1_poisson
 
 CASES = [
     dict(n=17, jitter=0.2, seed=0),
@@ -46,6 +46,28 @@ def test_span_colours_and_order(oracle_mod, case):
         if l == 0:
             cell = lv.t1 + lv.cellw * lv.t2
             assert np.all((cell[rows] == cell[lv.col]) == ~other)
+
+
+@pytest.mark.parametrize("vertical", [True, False])
+def test_span_counts_both_coordinates(oracle_mod, vertical):
+    """Reading R5 with the span set by one coordinate alone: a 5-point grid whose neighbours
+    lie three auxiliary cells apart in one direction and one cell apart in the other
+    (explicit box [0,1]^2, 2^5 cells per side). The span is 3 whichever direction carries it,
+    so m = 4 (16 colours), and no two coupled unknowns share a colour."""
+    M, L = 8, 5
+    prob = five_point_grid(M)
+    i = np.arange(M * M) % M
+    j = np.arange(M * M) // M
+    near, far = (i + 0.5) / 2 ** L, (3 * j + 0.5) / 2 ** L
+    x, y = (near, far) if vertical else (far, near)
+    h = oracle_mod.Hierarchy(prob.rowptr, prob.col, prob.val, x, y, aux_level=L,
+                             bbox=(0.0, 1.0, 0.0, 1.0), coarsest_max=4)
+    lv = h.level(0)
+    assert lv.span == 3 and lv.m == 4
+    np.testing.assert_array_equal(lv.color, lv.t1 % 4 + 4 * (lv.t2 % 4))
+    rows = np.repeat(np.arange(lv.n), np.diff(lv.rowptr))
+    off = rows != lv.col
+    assert np.all(lv.color[rows][off] != lv.color[lv.col][off])
 
 
 def test_uniform_span_one_gives_four_colours(oracle_mod):
