@@ -56,6 +56,23 @@ def test_binning_matches_exact_boxes(oracle_mod, L):
     assert cell[np.argmax(y)] // w == w - 1
 
 
+def test_setup_box_is_each_coordinates_extent(oracle_mod):
+    """Sec. 3.1 eq. ab12 in the setup path: the auxiliary box is the extent of each coordinate
+    separately. On a mesh stretched to x in [0.5, 3.5] and shifted to y in [-2, -1], the box is
+    numpy's min / max of each coordinate, and every unknown's level-L cell is its exact eq.
+    subregion box within that extent."""
+    prob = p1_poisson(33, jitter=0.2, seed=4)
+    x, y = 3.0 * prob.x + 0.5, prob.y - 2.0
+    L = 4
+    h = oracle_mod.Hierarchy(prob.rowptr, prob.col, prob.val, x, y, aux_level=L,
+                             coarsest_max=16)
+    np.testing.assert_array_equal(h.bbox, [x.min(), x.max(), y.min(), y.max()])
+    lv = h.level(0)
+    for j in range(len(x)):
+        assert lv.t1[j] == _exact_cell(x[j], x.min(), x.max(), L)[0], j
+        assert lv.t2[j] == _exact_cell(y[j], y.min(), y.max(), L)[0], j
+
+
 def test_uniform_grid_aggregates_are_2x2_blocks(oracle_mod):
     # Sec. 5 (uniform grid): aggregation coincides with geometric coarsening
     L = 4

@@ -105,6 +105,34 @@ MUTANTS = {
     "cholesky_transposed": (
         "        for (int k = i + 1; k < n; k++) s -= a[(size_t)k * n + i] * u[k];",
         "        for (int k = i + 1; k < n; k++) s -= a[(size_t)i * n + k] * u[k];"),
+    # coarsest factorisation: the diagonal update with the wrong sign
+    "cholesky_diagonal_sign": (
+        "        for (int k = 0; k < j; k++) d -= a[(size_t)j * n + k] * a[(size_t)j * n + k];",
+        "        for (int k = 0; k < j; k++) d += a[(size_t)j * n + k] * a[(size_t)j * n + k];"),
+    # Sec. 3.1 eq. ab12: the box's upper x bound taken from y
+    "box_upper_x_from_y": (
+        "            if (x[j] > b1) b1 = x[j];",
+        "            if (y[j] > b1) b1 = y[j];"),
+    # octree binning: z measured against the y extent of the box
+    "octree_z_in_y_box": (
+        "        if (dim == 3) f->t3[j] = cell_index_1d(z[j], h->bbox[4], h->bbox[5], L);",
+        "        if (dim == 3) f->t3[j] = cell_index_1d(z[j], h->bbox[2], h->bbox[3], L);"),
+    # octree depth: 4^L <= N (the quadtree rule) instead of 8^L <= N
+    "octree_depth_rule": (
+        "    while (N >= (1LL << (3 * (L + 1)))) L++;",
+        "    while (N >= (1LL << (2 * (L + 1)))) L++;"),
+    # sweep order pi: rows in index order within a colour, not grouped by block (fine level)
+    "sweep_ignores_blocks": (
+        "    for (int i = 0; i < n; i++) tmp[cnt[blockkey[i]]++] = i;",
+        "    for (int i = 0; i < n; i++) tmp[i] = i;"),
+    # Alg. 2 restriction: P^t r summed into the wrong coarse row (off by one aggregate)
+    "restriction_shifted": (
+        "    for (int i = 0; i < n; i++) fc[lv->agg[i]] += r[i];",
+        "    for (int i = 0; i < n; i++) fc[(lv->agg[i] + 1) % cl->n] += r[i];"),
+    # reading R11: one Alg. 1 step on every level (a V-cycle) whatever kcycle_n says
+    "kcycle_one_step": (
+        "    int steps = h->opt.kcycle_n;",
+        "    int steps = 1;"),
 }
 
 

@@ -66,6 +66,24 @@ def test_octree_binning_matches_exact_boxes(oracle_mod, L):
     assert cell[np.argmax(z)] // (w * w) == w - 1  # the closed upper face belongs to the last cell
 
 
+def test_octree_setup_box_is_each_coordinates_extent(oracle_mod):
+    """Sec. 3.1 eq. ab12 in three coordinates, in the setup path: on a mesh whose coordinates
+    have three different extents (x in [0, 1], y in [1, 3], z in [-1, 2]) the box is numpy's
+    min / max of each coordinate, and every unknown's level-L cell is its exact eq. subregion
+    box within those extents."""
+    p = p1_poisson_3d(9, seed=5)
+    x, y, z = p.x, 2.0 * p.y + 1.0, 3.0 * p.z - 1.0
+    L = 2
+    h = oracle_mod.Hierarchy(p.rowptr, p.col, p.val, x, y, z=z, aux_level=L, coarsest_max=8)
+    np.testing.assert_array_equal(h.bbox, [x.min(), x.max(), y.min(), y.max()])
+    np.testing.assert_array_equal(h.zbox, [z.min(), z.max()])
+    lv = h.level(0)
+    for j in range(len(x)):
+        t = [_exact_cell(v, lo, hi, L) for v, lo, hi in
+             ((x[j], x.min(), x.max()), (y[j], y.min(), y.max()), (z[j], z.min(), z.max()))]
+        assert (lv.t1[j], lv.t2[j], lv.t3[j]) == tuple(t), j
+
+
 @pytest.mark.parametrize("n", [9, 17])
 def test_octree_aggregation_galerkin_colours(oracle_mod, n):
     p = p1_poisson_3d(n, seed=n)
