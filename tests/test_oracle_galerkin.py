@@ -43,6 +43,30 @@ def test_galerkin_equals_triple_product(oracle_mod, case):
         assert (c.to_scipy() != 0).sum() <= pat.sum()
 
 
+@pytest.mark.parametrize("case", CASES + [dict(n=33, jitter=0.0, seed=0)])
+def test_stored_pattern_is_every_contributed_pair(oracle_mod, case):
+    """Readings R6 / R7 / R17: a coarse operator stores every pair (R, C) that receives a
+    contribution of eq. acsum, also when the sum is exactly zero. The expected structure is
+    that of P^t S P, with S holding a one for every stored fine entry (a sum of ones cannot
+    cancel). The unjittered mesh has exactly-zero couplings on its diagonal edges, so there
+    the coarse levels store exact zeros."""
+    prob = p1_poisson(**case)
+    h = oracle_mod.Hierarchy.from_problem(prob, coarsest_max=4)
+    zeros = 0
+    for l in range(h.nlev - 1):
+        f = h.level(l)
+        c = h.level(l + 1)
+        P = _P(f.agg, c.n)
+        S = sp.csr_matrix((np.ones(len(f.col)), f.col, f.rowptr), shape=(f.n, f.n))
+        E = (P.T @ S @ P).tocsr()
+        E.sort_indices()
+        np.testing.assert_array_equal(c.rowptr, E.indptr)
+        np.testing.assert_array_equal(c.col, E.indices)
+        zeros += int((c.val == 0.0).sum())
+    if case["jitter"] == 0.0:
+        assert zeros > 0
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_coarse_operators_symmetric(oracle_mod, case):
     prob = p1_poisson(**case)

@@ -129,6 +129,15 @@ MUTANTS = {
     "restriction_shifted": (
         "    for (int i = 0; i < n; i++) fc[lv->agg[i]] += r[i];",
         "    for (int i = 0; i < n; i++) fc[(lv->agg[i] + 1) % cl->n] += r[i];"),
+    # readings R6 / R17: Galerkin sums that cancel to exactly zero dropped from the pattern
+    "galerkin_drops_exact_zeros": (
+        "            c->col[out] = buf[a].c;\n            c->val[out] = s;\n            out++;",
+        "            if (s != 0.0) {\n            c->col[out] = buf[a].c;\n"
+        "            c->val[out] = s;\n            out++; }"),
+    # the coarsest level: coarsening continues while n >= coarsest_max instead of n >
+    "coarsest_threshold": (
+        "    while (h->lev[h->nlev - 1].n > opt->coarsest_max) {",
+        "    while (h->lev[h->nlev - 1].n >= opt->coarsest_max) {"),
     # reading R11: one Alg. 1 step on every level (a V-cycle) whatever kcycle_n says
     "kcycle_one_step": (
         "    int steps = h->opt.kcycle_n;",
