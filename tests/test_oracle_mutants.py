@@ -67,6 +67,14 @@ MUTANTS = {
     "octree_colour_weight": (
         "        if (lv->t3) lv->color[i] += lv->m * lv->m * (lv->t3[i] % lv->m);",
         "        if (lv->t3) lv->color[i] += lv->m * (lv->t3[i] % lv->m);"),
+    # octree span: the third coordinate's offsets left out
+    "octree_span_ignores_t3": (
+        "                if (d3 > s) s = d3;",
+        "                (void)d3;"),
+    # octree coarse cells: t3 of a coarse row read as its t2
+    "octree_coarse_t3": (
+        "                if (dim == 3) cl->t3[num[c]] = (int)(c / ((long long)w * w));",
+        "                if (dim == 3) cl->t3[num[c]] = (int)((c / w) % w);"),
     # Gauss-Seidel update with the wrong sign on the off-diagonal terms
     "gs_sign": (
         "        else s -= lv->val[p] * u[j];",

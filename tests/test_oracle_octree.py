@@ -84,6 +84,32 @@ def test_octree_setup_box_is_each_coordinates_extent(oracle_mod):
         assert (lv.t1[j], lv.t2[j], lv.t3[j]) == tuple(t), j
 
 
+@pytest.mark.parametrize("far", [0, 1, 2])
+def test_octree_span_counts_every_coordinate(oracle_mod, far):
+    """Reading R5 in 3D (R23) with the span set by one coordinate alone: a 7-point grid of 4^3
+    unknowns whose neighbours lie three auxiliary cells apart along axis `far` and one cell
+    apart along the other two (explicit box [0,1]^3, 2^4 cells per side). The span is 3
+    whichever axis carries it, so m = 4 (64 colours), and no two coupled unknowns share a
+    colour."""
+    M, L = 4, 4
+    T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(M, M))
+    I = sp.identity(M)
+    A = (sp.kron(sp.kron(I, I), T) + sp.kron(sp.kron(I, T), I) + sp.kron(sp.kron(T, I), I)).tocsr()
+    A.eliminate_zeros()  # kron stores the zero blocks, and a stored entry is a coupling
+    A.sort_indices()
+    k = np.arange(M ** 3)
+    idx = [k % M, (k // M) % M, k // (M * M)]  # x fastest, as the matrix is ordered
+    xyz = [(3 * c + 0.5) / 2 ** L if d == far else (c + 0.5) / 2 ** L for d, c in enumerate(idx)]
+    h = oracle_mod.Hierarchy(A.indptr, A.indices, A.data, xyz[0], xyz[1], z=xyz[2], aux_level=L,
+                             bbox=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), coarsest_max=4)
+    lv = h.level(0)
+    assert lv.span == 3 and lv.m == 4
+    np.testing.assert_array_equal(lv.color, lv.t1 % 4 + 4 * (lv.t2 % 4) + 16 * (lv.t3 % 4))
+    rows = np.repeat(np.arange(lv.n), np.diff(lv.rowptr))
+    off = rows != lv.col
+    assert np.all(lv.color[rows][off] != lv.color[lv.col][off])
+
+
 @pytest.mark.parametrize("n", [9, 17])
 def test_octree_aggregation_galerkin_colours(oracle_mod, n):
     p = p1_poisson_3d(n, seed=n)
