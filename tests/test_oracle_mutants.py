@@ -109,6 +109,10 @@ MUTANTS = {
     "outer_beta_sign": (
         "            double beta = -dot(n, z, Q[j]) / pAp[j];",
         "            double beta = dot(n, z, Q[j]) / pAp[j];"),
+    # reading R13: the outer iteration stops on the absolute residual, not relative to ||b||
+    "outer_stop_absolute": (
+        "        rel = sqrt(dot(n, r, r)) / bn;\n        if (!isfinite(rel))",
+        "        rel = sqrt(dot(n, r, r));\n        if (!isfinite(rel))"),
     # coarsest exact solve: the backward substitution reads L instead of L^t
     "cholesky_transposed": (
         "        for (int k = i + 1; k < n; k++) s -= a[(size_t)k * n + i] * u[k];",
