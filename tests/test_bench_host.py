@@ -127,3 +127,27 @@ def test_batch_is_one_block_diagonal_csr(monkeypatch):
     np.testing.assert_array_equal(s["x"], np.concatenate([p.x for p in probs]))
     np.testing.assert_array_equal(s["y"], np.concatenate([p.y for p in probs]))
     B.b = None  # nothing to free in the stand-in
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle, timed on the host cores) prints one JSON line
+    with the contract's keys: the same metric, unit and direction as the GPU arm, its own
+    cpu_baseline, and an e2e entry with no host-device traffic."""
+    import subprocess
+
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                        "quasi_uniform_65", "--steps", "2", "--warmup", "3"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"].startswith("solves/s")
+    assert d["unit"] == "solves/s" and d["higher_is_better"] is True
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 2, 3)
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["vs_baseline"] is None
+    assert d["config"]["workload"] == "quasi_uniform_65" and d["config"]["iters"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
