@@ -6,7 +6,8 @@
   taken on (hash of csrc/), else null;
 * bench.measured_peak_hbm: the measured copy bandwidth, or the stated fallback;
 * amg.Batch: the systems are concatenated into one block-diagonal CSR with row offsets, the
-  layout amg_batch_setup takes; checked by reading back what reaches a stand-in library.
+  layout amg_batch_setup takes; checked by reading back what reaches a stand-in library;
+* bench.py --impl reference: the oracle arm's JSON line, end to end on a small workload.
 """
 import ctypes as C
 import json
