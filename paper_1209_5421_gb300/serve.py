@@ -22,6 +22,8 @@ Setups run on a separate thread (each on the hierarchy's own stream).
 
 Every system is computed by code whose result does not depend on the other work in flight:
 in the batch lane by one CTA of fixed size, in the large lane by the single-system kernel.
+A matrix the library rejects at setup (not SPD, invalid CSR, no device memory) ends its own
+requests with the library's status (lane "setup", no x); the server goes on with the others.
 """
 from __future__ import annotations
 
@@ -103,6 +105,7 @@ class Server:
         self.completed: list[Request] = []
         self.evictions = 0
         self.setups = 0
+        self.setup_failures = 0  # matrices the library rejected (their requests failed)
         self.batches = 0
         self.errors: list[str] = []
         # setups and large-lane solves never overlap: the grid-wide kernel wants every SM
@@ -170,7 +173,8 @@ class Server:
         return {"completed": len(lat), "solves_per_s": len(lat) / (t1 - t0),
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "setups": self.setups, "evictions": self.evictions, "batches": self.batches,
+                "setups": self.setups, "setup_failures": self.setup_failures,
+                "evictions": self.evictions, "batches": self.batches,
                 "max_resident_bytes": self.max_used, "budget_bytes": self.budget,
                 "large_lane": sum(r.lane == "large" for r in self.completed)}
 
@@ -255,6 +259,7 @@ class Server:
                     return
                 if r.key not in self.setting_up:
                     continue
+            h = None
             try:
                 with self.grid_lock:
                     h = amg.Hierarchy(*m[:5], z=m[5], cycle_prec=self.prec,
@@ -262,6 +267,23 @@ class Server:
                     if n <= self.large:  # the cycle copies and batched workspace, allocated now
                         amg.Batch.over([h], threads=1024).close()
                 nbytes = h.nbytes
+            except (amg.AmgError, ValueError, TypeError) as e:
+                # the library (or the binding) rejects this matrix: its requests end with that
+                # status and the server goes on with the others
+                if h is not None:
+                    h.close()
+                status = e.status if isinstance(e, amg.AmgError) else amg.ERR_INVALID_ARG
+                with self.cv:
+                    self.setting_up.discard(r.key)
+                    self.used -= est
+                    failed = [r] + [q for q in self.need_setup if q.key == r.key]
+                    for q in failed[1:]:
+                        self.need_setup.remove(q)
+                    for q in failed:
+                        self._finish(q, None, 0, float("nan"), status, "setup")
+                    self.setup_failures += 1
+                    self.cv.notify_all()
+                continue
             except Exception as e:  # noqa: BLE001
                 self._fail(f"setup of {r.key!r}: {e}")
                 return

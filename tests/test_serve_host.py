@@ -51,6 +51,8 @@ def _solve(rowptr, col, val, b):
 def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0):
     class FakeHierarchy:
         def __init__(self, rowptr, col, val, x, y, z=None, cycle_prec=None, outer=None):
+            if np.asarray(val)[0] <= 0:  # as the library's check of the diagonal
+                raise amg.AmgError(amg.ERR_BAD_MATRIX, "amg_setup: stand-in rejects the matrix")
             with log.span("setup"):
                 self.A = (np.asarray(rowptr), np.asarray(col), np.asarray(val))
                 self.n = len(rowptr) - 1
@@ -230,6 +232,31 @@ def test_growth_during_solves_is_charged(server_cls, large):
     base = sum(BYTES_PER_UNKNOWN * p.n for p in probs.values())
     assert S.used == base + 9 * grow and S.max_used >= S.used
     S.close()
+
+
+def test_rejected_matrix_fails_only_its_own_requests(server_cls):
+    make, _ = server_cls
+    probs = _problems([9, 12, 15])
+    bad = probs["m1"]
+    val = bad.val.copy()
+    val[0] = -1.0  # not SPD: the library refuses it
+    S = make(workers=2)
+    for key, p in probs.items():
+        S.register(key, p.rowptr, p.col, val if key == "m1" else p.val, p.x, p.y)
+    reqs = [(k, S.submit(k, np.ones(probs[k].n))) for k in ["m0", "m1", "m2", "m1", "m0"]]
+    S.drain(timeout=60)
+    later = S.submit("m2", np.ones(probs["m2"].n))  # the server still serves afterwards
+    S.drain(timeout=60)
+    st = S.stats()
+    assert _consistent(S)  # nothing stays charged for the rejected matrix
+    S.close()
+    for key, r in reqs + [("m2", later)]:
+        assert r.done.is_set()
+        if key == "m1":
+            assert r.status == amg.ERR_BAD_MATRIX and r.lane == "setup" and r.x is None
+        else:
+            assert r.status == amg.OK and r.x is not None
+    assert st["setup_failures"] >= 1 and st["setups"] == 2
 
 
 def test_matrix_larger_than_the_budget_is_refused(server_cls):
