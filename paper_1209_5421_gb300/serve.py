@@ -22,8 +22,10 @@ Setups run on a separate thread (each on the hierarchy's own stream).
 
 Every system is computed by code whose result does not depend on the other work in flight:
 in the batch lane by one CTA of fixed size, in the large lane by the single-system kernel.
-A matrix the library rejects at setup (not SPD, invalid CSR, no device memory) ends its own
-requests with the library's status (lane "setup", no x); the server goes on with the others.
+A request the server cannot set up ends alone, with a status (lane "setup", no x), and the
+server goes on with the others: a matrix the library rejects (not SPD, invalid CSR, no device
+memory) with the library's status, a matrix larger than the whole budget with ERR_OOM, a key
+that was never registered with ERR_INVALID_ARG.
 """
 from __future__ import annotations
 
@@ -105,7 +107,7 @@ class Server:
         self.completed: list[Request] = []
         self.evictions = 0
         self.setups = 0
-        self.setup_failures = 0  # matrices the library rejected (their requests failed)
+        self.setup_failures = 0  # matrices that could not be set up (their requests failed)
         self.batches = 0
         self.errors: list[str] = []
         # setups and large-lane solves never overlap: the grid-wide kernel wants every SM
@@ -165,18 +167,22 @@ class Server:
         self.res.clear()
 
     def stats(self) -> dict:
-        lat = sorted(r.latency for r in self.completed)
+        """Throughput and latency over the requests that returned a solution; requests that
+        ended at setup (lane "setup") are counted apart, as `failed`."""
+        solved = [r for r in self.completed if r.x is not None]
+        failed = len(self.completed) - len(solved)
+        lat = sorted(r.latency for r in solved)
         if not lat:
-            return {"completed": 0}
-        t0 = min(r.t_arrival for r in self.completed)
-        t1 = max(r.t_done for r in self.completed)
-        return {"completed": len(lat), "solves_per_s": len(lat) / (t1 - t0),
+            return {"completed": 0, "failed": failed}
+        t0 = min(r.t_arrival for r in solved)
+        t1 = max(r.t_done for r in solved)
+        return {"completed": len(lat), "failed": failed, "solves_per_s": len(lat) / (t1 - t0),
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
                 "setups": self.setups, "setup_failures": self.setup_failures,
                 "evictions": self.evictions, "batches": self.batches,
                 "max_resident_bytes": self.max_used, "budget_bytes": self.budget,
-                "large_lane": sum(r.lane == "large" for r in self.completed)}
+                "large_lane": sum(r.lane == "large" for r in solved)}
 
     # ---- internals --------------------------------------------------------------------
     def _fail(self, msg: str):
@@ -189,6 +195,17 @@ class Server:
         r.t_done = time.perf_counter()
         r.done.set()
         self.completed.append(r)
+
+    def _fail_key(self, key, status: int, first: Request | None = None):
+        """End every queued request for matrix `key` (and `first`, already dequeued) with
+        `status`, lane "setup", no x (caller holds cv)."""
+        failed = ([first] if first is not None else []) + [q for q in self.need_setup
+                                                           if q.key == key]
+        for q in failed:
+            if q is not first:
+                self.need_setup.remove(q)
+            self._finish(q, None, 0, float("nan"), status, "setup")
+        self.setup_failures += 1
 
     def _recharge(self, ent: _Resident):
         """Charge a resident hierarchy's current bytes (a solve may have grown them) and evict
@@ -236,17 +253,16 @@ class Server:
                     self.cv.notify_all()
                     continue
                 m = self.matrices.get(r.key)
-                if m is None:
+                if m is None:  # never registered: this request fails, the server goes on
                     self.need_setup.popleft()
-                    self.errors.append(f"unknown matrix {r.key!r}")
+                    self._finish(r, None, 0, float("nan"), amg.ERR_INVALID_ARG, "setup")
                     self.cv.notify_all()
                     continue
                 n = len(m[0]) - 1
                 est = setup_estimate(n, len(m[1]))  # replaced by the real bytes after setup
                 while not self.stop and not self._admit(est):
-                    if est > self.budget:
-                        self.need_setup.popleft()
-                        self.errors.append(f"matrix {r.key!r} does not fit the budget")
+                    if est > self.budget:  # can never fit: its requests fail, the rest go on
+                        self._fail_key(r.key, amg.ERR_OOM)
                         self.cv.notify_all()
                         break
                     self.cv.wait(0.01)  # wait for hierarchies to become idle
@@ -276,12 +292,7 @@ class Server:
                 with self.cv:
                     self.setting_up.discard(r.key)
                     self.used -= est
-                    failed = [r] + [q for q in self.need_setup if q.key == r.key]
-                    for q in failed[1:]:
-                        self.need_setup.remove(q)
-                    for q in failed:
-                        self._finish(q, None, 0, float("nan"), status, "setup")
-                    self.setup_failures += 1
+                    self._fail_key(r.key, status, first=r)
                     self.cv.notify_all()
                 continue
             except Exception as e:  # noqa: BLE001

@@ -8,9 +8,10 @@ invariants without a GPU:
   * admission: with the setup estimate above the real size the resident bytes never exceed
     the budget and idle hierarchies are evicted least recently used first; real sizes above
     the estimate, and growth during solves, are charged and evicted back under the budget;
-    a matrix larger than the budget is refused;
+    a matrix larger than the whole budget fails its own requests;
   * a large-lane solve never overlaps a batch solve or a setup (it has the GPU to itself);
-  * an unknown matrix is reported by drain().
+  * a request the server cannot set up (unknown key, rejected or oversized matrix) ends alone
+    with a status, and the others are served.
 The same server on the GPU is tested in test_gpu_serve.py.
 """
 import contextlib
@@ -257,23 +258,35 @@ def test_rejected_matrix_fails_only_its_own_requests(server_cls):
         else:
             assert r.status == amg.OK and r.x is not None
     assert st["setup_failures"] >= 1 and st["setups"] == 2
+    assert st["failed"] == 2 and st["completed"] == 4  # throughput counts solved requests only
 
 
 def test_matrix_larger_than_the_budget_is_refused(server_cls):
     make, _ = server_cls
-    p = p1_poisson(30, jitter=0.2, seed=1, rhs="normal")
-    S = make(workers=1, budget_bytes=1000)
-    S.register("big", p.rowptr, p.col, p.val, p.x, p.y)
-    S.submit("big", p.b)
-    with pytest.raises(RuntimeError, match="does not fit"):
-        S.drain(timeout=30)
+    big = p1_poisson(30, jitter=0.2, seed=1, rhs="normal")
+    small = p1_poisson(6, jitter=0.2, seed=2, rhs="normal")
+    from paper_1209_5421_gb300.serve import setup_estimate
+
+    budget = setup_estimate(small.n, len(small.col)) + 1000  # room for the small one only
+    S = make(workers=1, budget_bytes=budget)
+    S.register("big", big.rowptr, big.col, big.val, big.x, big.y)
+    S.register("small", small.rowptr, small.col, small.val, small.x, small.y)
+    r1, r2 = S.submit("big", big.b), S.submit("big", big.b)
+    r3 = S.submit("small", small.b)
+    S.drain(timeout=30)
     S.close()
+    assert r1.status == r2.status == amg.ERR_OOM and r1.lane == "setup" and r1.x is None
+    assert r3.status == amg.OK
 
 
-def test_unknown_matrix_is_reported(server_cls):
+def test_unknown_matrix_fails_its_request(server_cls):
     make, _ = server_cls
+    p = p1_poisson(6, jitter=0.2, seed=2, rhs="normal")
     S = make(workers=1)
-    S.submit("nobody", np.ones(4))
-    with pytest.raises(RuntimeError, match="unknown matrix"):
-        S.drain(timeout=30)
+    S.register("known", p.rowptr, p.col, p.val, p.x, p.y)
+    r1 = S.submit("nobody", np.ones(4))
+    r2 = S.submit("known", p.b)
+    S.drain(timeout=30)
     S.close()
+    assert r1.status == amg.ERR_INVALID_ARG and r1.lane == "setup" and r1.x is None
+    assert r2.status == amg.OK
