@@ -9,6 +9,8 @@ invariants without a GPU:
     the budget and idle hierarchies are evicted least recently used first; real sizes above
     the estimate, and growth during solves, are charged and evicted back under the budget;
     a matrix larger than the whole budget fails its own requests;
+  * continuous batching: a request that arrives while a batch runs starts beside it on a free
+    worker (with one worker it can only follow);
   * a large-lane solve never overlaps a batch solve or a setup (it has the GPU to itself);
   * a request the server cannot set up (unknown key, rejected or oversized matrix) ends alone
     with a status, and the others are served.
@@ -34,13 +36,17 @@ class Log:
         self.lock = threading.Lock()
         self.intervals = []  # (kind, t0, t1)
         self.closed = []     # sizes of closed hierarchies, in order
+        self.running = {}    # kind -> spans in progress
 
     @contextlib.contextmanager
     def span(self, kind, hold=0.003):
         t0 = time.perf_counter()
+        with self.lock:
+            self.running[kind] = self.running.get(kind, 0) + 1
         time.sleep(hold)  # long enough for overlaps to show
         yield
         with self.lock:
+            self.running[kind] -= 1
             self.intervals.append((kind, t0, time.perf_counter()))
 
 
@@ -49,7 +55,8 @@ def _solve(rowptr, col, val, b):
     return spla.spsolve(sp.csr_matrix((val, col, rowptr), shape=(n, n)).tocsc(), b)
 
 
-def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0):
+def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0,
+               batch_hold=0.003):
     class FakeHierarchy:
         def __init__(self, rowptr, col, val, x, y, z=None, cycle_prec=None, outer=None):
             if np.asarray(val)[0] <= 0:  # as the library's check of the diagonal
@@ -80,7 +87,7 @@ def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0
             return cls(list(hierarchies))
 
         def solve(self, rhs, tol, stream=None):
-            with log.span("batch"):
+            with log.span("batch", hold=batch_hold):
                 r = rhs.numpy()
                 x = np.concatenate([_solve(*h.A, r[self.row_off[k]:self.row_off[k + 1]])
                                     for k, h in enumerate(self.hs)])
@@ -106,8 +113,8 @@ def server_cls(monkeypatch):
 
     log = Log()
 
-    def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, **kw):
-        H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve)
+    def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, batch_hold=0.003, **kw):
+        H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve, batch_hold)
         monkeypatch.setattr(amg, "Hierarchy", H)
         monkeypatch.setattr(amg, "Batch", B)
         S = Server(**kw)
@@ -164,6 +171,31 @@ def test_results_lanes_and_exclusive_large_lane(server_cls):
     assert any(k == "large" for k, _, _ in log.intervals)
     assert not _overlaps(log, "large", "batch")
     assert not _overlaps(log, "large", "setup")
+
+
+@pytest.mark.parametrize("workers", [1, 2])
+def test_arrivals_during_a_batch_start_beside_it(server_cls, workers):
+    """Continuous batching: a request that becomes ready while a batch is on the GPU starts in
+    a launch of its own on a free worker, overlapping the running one, instead of waiting for
+    it. With one worker (the control) the second batch can only follow the first."""
+    make, log = server_cls
+    probs = _problems([9, 12])
+    S = make(workers=workers, batch_hold=0.3, large_unknowns=10 ** 6)
+    _register(S, probs)
+    r0 = S.submit("m0", np.ones(probs["m0"].n))
+    t0 = time.perf_counter()
+    while not log.running.get("batch") and time.perf_counter() - t0 < 30:
+        time.sleep(0.002)  # until m0's batch is on the (stand-in) GPU
+    assert log.running.get("batch") == 1
+    r1 = S.submit("m1", np.ones(probs["m1"].n))
+    S.drain(timeout=60)
+    S.close()
+    assert r0.status == r1.status == amg.OK and r0.lane == r1.lane == "batch"
+    batches = [(t0, t1) for k, t0, t1 in log.intervals if k == "batch"]
+    assert len(batches) == 2
+    overlap = _overlaps(log, "batch", "batch")
+    overlapping = [(a, b) for a, b in overlap if a != b]
+    assert bool(overlapping) == (workers > 1), batches
 
 
 def test_budget_admission_lru_eviction(server_cls):
