@@ -11,12 +11,16 @@ invariants without a GPU:
     a matrix larger than the whole budget fails its own requests;
   * continuous batching: a request that arrives while a batch runs starts beside it on a free
     worker (with one worker it can only follow);
-  * a large-lane solve never overlaps a batch solve or a setup (it has the GPU to itself);
+  * a large-lane solve never overlaps a batch solve or a setup, whichever comes first (it has
+    the GPU to itself);
   * a request the server cannot set up (unknown key, rejected or oversized matrix) ends alone
     with a status, and the others are served.
 The same server on the GPU is tested in test_gpu_serve.py.
 """
 import contextlib
+import importlib.util
+import os
+import sys
 import threading
 import time
 
@@ -29,6 +33,21 @@ from paper_1209_5421_gb300 import amg
 from paper_1209_5421_gb300.meshes import p1_poisson
 
 BYTES_PER_UNKNOWN = 1000  # the fakes' device size (below the server's setup estimate)
+# a copy of serve.py to test instead of the package's (test_serve_mutants.py plants mistakes)
+SERVE_UNDER_TEST = "AMG_SERVE_UNDER_TEST"
+
+
+def serve_module():
+    path = os.environ.get(SERVE_UNDER_TEST)
+    if not path:
+        from paper_1209_5421_gb300 import serve
+        return serve
+    spec = importlib.util.spec_from_file_location("paper_1209_5421_gb300._serve_under_test", path)
+    mod = importlib.util.module_from_spec(spec)
+    mod.__package__ = "paper_1209_5421_gb300"  # its relative imports: the package's modules
+    sys.modules[spec.name] = mod  # dataclasses look their module up there
+    spec.loader.exec_module(mod)
+    return mod
 
 
 class Log:
@@ -56,7 +75,7 @@ def _solve(rowptr, col, val, b):
 
 
 def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0,
-               batch_hold=0.003):
+               batch_hold=0.003, large_hold=0.003):
     class FakeHierarchy:
         def __init__(self, rowptr, col, val, x, y, z=None, cycle_prec=None, outer=None):
             if np.asarray(val)[0] <= 0:  # as the library's check of the diagonal
@@ -67,7 +86,7 @@ def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0
                 self.nbytes = bytes_per_unknown * self.n
 
         def solve(self, b, tol, stream=None):
-            with log.span("large"):
+            with log.span("large", hold=large_hold):
                 x = _solve(*self.A, b.numpy())
             self.nbytes += grow_per_solve  # as the outer iteration's directions are allocated
             return torch.from_numpy(x), 1, 0.0, amg.OK
@@ -84,6 +103,8 @@ def make_fakes(torch, log, bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0
 
         @classmethod
         def over(cls, hierarchies, threads=0, stream=None):
+            # a system's batched workspace belongs to its hierarchy: one system, one slot
+            assert len({id(h) for h in hierarchies}) == len(hierarchies), "a system twice"
             return cls(list(hierarchies))
 
         def solve(self, rhs, tol, stream=None):
@@ -109,19 +130,24 @@ def server_cls(monkeypatch):
     monkeypatch.setattr(torch.cuda, "set_device", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
-    from paper_1209_5421_gb300.serve import Server
+    Server = serve_module().Server
 
     log = Log()
+    made = []
 
-    def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, batch_hold=0.003, **kw):
-        H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve, batch_hold)
+    def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, batch_hold=0.003,
+             large_hold=0.003, **kw):
+        H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve, batch_hold, large_hold)
         monkeypatch.setattr(amg, "Hierarchy", H)
         monkeypatch.setattr(amg, "Batch", B)
         S = Server(**kw)
         S.dev = torch.device("cpu")  # before the first request: the fakes run on the host
+        made.append(S)
         return S
 
-    return make, log
+    yield make, log
+    for S in made:  # also when the test failed: no server thread outlives its test
+        S.close()
 
 
 def _consistent(S):
@@ -198,8 +224,43 @@ def test_arrivals_during_a_batch_start_beside_it(server_cls, workers):
     assert bool(overlapping) == (workers > 1), batches
 
 
+def _wait_running(log, kind):
+    t0 = time.perf_counter()
+    while not log.running.get(kind) and time.perf_counter() - t0 < 30:
+        time.sleep(0.002)
+    assert log.running.get(kind) == 1, kind
+
+
+@pytest.mark.parametrize("first", ["batch", "large"])
+def test_large_lane_has_the_gpu_to_itself(server_cls, first):
+    """A large-lane request that arrives while a batch runs waits for it to finish; while a
+    large solve runs, neither a batch of a resident matrix nor a new matrix's setup starts:
+    the large solve never overlaps either."""
+    make, log = server_cls
+    probs = _problems([9, 14, 10])  # 49 and 64 unknowns: batch lane; 144: large lane
+    S = make(workers=2, large_unknowns=100, batch_hold=0.25, large_hold=0.25)
+    _register(S, probs)
+    ones = {k: np.ones(p.n) for k, p in probs.items()}
+    if first == "batch":
+        reqs = [S.submit("m0", ones["m0"])]
+        _wait_running(log, "batch")
+        reqs.append(S.submit("m1", ones["m1"]))  # large, while the batch runs
+    else:
+        reqs = [S.submit("m0", ones["m0"])]
+        S.drain(timeout=60)  # m0 resident: its next request could start at once
+        reqs.append(S.submit("m1", ones["m1"]))
+        _wait_running(log, "large")
+        reqs += [S.submit("m0", ones["m0"]), S.submit("m2", ones["m2"])]  # batch; new setup
+    S.drain(timeout=60)
+    S.close()
+    assert all(r.status == amg.OK for r in reqs)
+    assert {r.lane for r in reqs} == {"batch", "large"}
+    assert not _overlaps(log, "large", "batch")
+    assert not _overlaps(log, "large", "setup")
+
+
 def test_budget_admission_lru_eviction(server_cls):
-    from paper_1209_5421_gb300.serve import setup_estimate
+    setup_estimate = serve_module().setup_estimate
 
     make, log = server_cls
     probs = {f"m{k}": p1_poisson(n, jitter=0.2, seed=40 + k, rhs="normal")
@@ -227,7 +288,7 @@ def test_budget_admission_lru_eviction(server_cls):
 
 
 def test_real_size_above_the_estimate_is_evicted_back_under_the_budget(server_cls):
-    from paper_1209_5421_gb300.serve import setup_estimate
+    setup_estimate = serve_module().setup_estimate
 
     make, _ = server_cls
     probs = _problems([20, 21, 22, 23])
@@ -297,7 +358,7 @@ def test_matrix_larger_than_the_budget_is_refused(server_cls):
     make, _ = server_cls
     big = p1_poisson(30, jitter=0.2, seed=1, rhs="normal")
     small = p1_poisson(6, jitter=0.2, seed=2, rhs="normal")
-    from paper_1209_5421_gb300.serve import setup_estimate
+    setup_estimate = serve_module().setup_estimate
 
     budget = setup_estimate(small.n, len(small.col)) + 1000  # room for the small one only
     S = make(workers=1, budget_bytes=budget)
