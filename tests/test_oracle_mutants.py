@@ -75,6 +75,14 @@ MUTANTS = {
     "octree_coarse_t3": (
         "                if (dim == 3) cl->t3[num[c]] = (int)(c / ((long long)w * w));",
         "                if (dim == 3) cl->t3[num[c]] = (int)((c / w) % w);"),
+    # Sec. 4.5 colour formula with t1 and t2 exchanged
+    "colour_transposed": (
+        "        lv->color[i] = (lv->t1[i] % lv->m) + lv->m * (lv->t2[i] % lv->m);",
+        "        lv->color[i] = (lv->t2[i] % lv->m) + lv->m * (lv->t1[i] % lv->m);"),
+    # R_k: the forward sweep run in the reversed order
+    "forward_sweep_reversed": (
+        "    if (!backward)\n        for (int p = 0; p < lv->n; p++) gs_row(lv, lv->perm[p], f, u);",
+        "    if (!backward)\n        for (int p = lv->n - 1; p >= 0; p--) gs_row(lv, lv->perm[p], f, u);"),
     # Gauss-Seidel update with the wrong sign on the off-diagonal terms
     "gs_sign": (
         "        else s -= lv->val[p] * u[j];",
