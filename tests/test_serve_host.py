@@ -152,7 +152,8 @@ def server_cls(monkeypatch):
 
 def _consistent(S):
     """The charged bytes are the resident hierarchies' current bytes."""
-    return S.used == sum(e.h.nbytes for e in S.res.values()) == sum(e.nbytes for e in S.res.values())
+    ents = list(S.res.values())
+    return S.used == sum(e.h.nbytes for e in ents) == sum(e.nbytes for e in ents)
 
 
 def _problems(sizes):
