@@ -49,7 +49,11 @@ def _check_system(amg, oracle_mod, prob, x, it, rr, st, tol, slack):
     xo, ito, _, _ = O.solve(prob.b, tol)
     err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
     assert err <= 1e-6, err
-    assert it <= ito + slack, (it, ito)
+    if slack is None:
+        # the plain FP64 method: the same flexible CG as the oracle, so within one iteration
+        assert abs(int(it) - int(ito)) <= 1, (it, ito)
+    else:
+        assert it <= ito + slack, (it, ito)
     return err
 
 
@@ -66,7 +70,9 @@ def test_batch_matches_oracle(amg, oracle_mod, prec):
     assert info["ctas"] >= 1 and info["bytes"] > 0
     off = B.row_off
     for k, p in enumerate(probs):
-        slack = 10 if SPECS[k].get("graded") else 3
+        # FP32 cycles: the rounding of the cycle may cost a few iterations more than the
+        # FP64 oracle's; the FP64 cycle is held to the oracle's count within one
+        slack = None if prec == "fp64" else (10 if SPECS[k].get("graded") else 3)
         _check_system(amg, oracle_mod, p, x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, slack)
     # a second solve replays the captured launch: same bits
     x2, it2, _, _ = B.solve(rhs, tol)
@@ -130,7 +136,7 @@ def test_teams_match_oracle_and_one_cta(amg, oracle_mod, prec):
     assert teams[-1] == teams.max()  # the largest system has the largest team
     off = B.row_off
     for k, p in enumerate(probs):
-        slack = 10 if k < len(SPECS) and SPECS[k].get("graded") else 3
+        slack = None if prec == "fp64" else (10 if k < len(SPECS) and SPECS[k].get("graded") else 3)
         _check_system(amg, oracle_mod, p, x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, slack)
     # the same bits again (team sums in rank order)
     x2, it2, _, _ = B.solve(rhs, tol)
