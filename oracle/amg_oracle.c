@@ -43,6 +43,8 @@ typedef struct {
     int no_factor;     /* 1: skip the coarsest Cholesky (inspect operators of singular A) */
     int dim;           /* 2 (quadtree, default when 0) or 3 (octree, Sec. 3.1 / Sec. 6) */
     double zbox[2];    /* a3, b3 (dim 3 with has_bbox) */
+    int nu_pre;        /* Gauss-Seidel sweeps of the pre-smoothing (reading R10); 0 = 1 */
+    int nu_post;       /* sweeps of the post-smoothing; 0 = 1 */
 } oamg_opts;
 
 typedef struct {
@@ -316,7 +318,7 @@ static int setup_impl(int n, const int *rowptr, const int *col, const double *va
         return OAMG_ERR_INVALID_ARG;
     if (opt->dim != 0 && opt->dim != 2 && opt->dim != 3) return OAMG_ERR_INVALID_ARG;
     if (opt->coarsest_max < 1 || opt->kcycle_n < 1 || opt->aux_level < 0 ||
-        opt->aux_level > (dim == 3 ? 10 : 15))
+        opt->aux_level > (dim == 3 ? 10 : 15) || opt->nu_pre < 0 || opt->nu_post < 0)
         return OAMG_ERR_INVALID_ARG;
     int st = check_csr(n, rowptr, col, val);
     if (st) return st;
@@ -326,6 +328,8 @@ static int setup_impl(int n, const int *rowptr, const int *col, const double *va
 
     oamg_h *h = (oamg_h *)xcalloc(1, sizeof(oamg_h));
     h->opt = *opt;
+    if (h->opt.nu_pre == 0) h->opt.nu_pre = 1;
+    if (h->opt.nu_post == 0) h->opt.nu_post = 1;
     h->dim = dim;
     /* eq. ab12: a1 = min x, b1 = max x, a2 = min y, b2 = max y (and a3, b3 for z) */
     if (opt->has_bbox) {
@@ -525,9 +529,10 @@ static void bhat(const oamg_h *h, int l, const double *f, double *z) {
     double *r = (double *)malloc(sizeof(double) * (size_t)n);
     double *fc = (double *)xcalloc((size_t)cl->n, sizeof(double));
     double *e = (double *)xcalloc((size_t)cl->n, sizeof(double));
-    /* pre-smoothing u1 = R_k f, from zero */
+    /* pre-smoothing u1 = R_k f, from zero; with nu_pre > 1 the smoother R_k is nu_pre
+     * forward sweeps, each started from the result of the one before (reading R10) */
     for (int i = 0; i < n; i++) z[i] = 0.0;
-    smooth(lv, 0, f, z);
+    for (int s = 0; s < h->opt.nu_pre; s++) smooth(lv, 0, f, z);
     /* coarse-grid correction: fc = P^t (f - A u1) (Sec. 4.3 restriction) */
     spmv(lv, z, r);
     for (int i = 0; i < n; i++) r[i] = f[i] - r[i];
@@ -535,8 +540,9 @@ static void bhat(const oamg_h *h, int l, const double *f, double *z) {
     btilde(h, l + 1, fc, e);
     /* u2 = u1 + P e (Sec. 4.3 prolongation) */
     for (int i = 0; i < n; i++) z[i] += e[lv->agg[i]];
-    /* post-smoothing: u2 + R_k^t (f - A u2) = one backward sweep started from u2 */
-    smooth(lv, 1, f, z);
+    /* post-smoothing: u2 + R_k^t (f - A u2) = one backward sweep started from u2 (nu_post
+     * backward sweeps in a row with nu_post > 1, the adjoint of the pre-smoothing's) */
+    for (int s = 0; s < h->opt.nu_post; s++) smooth(lv, 1, f, z);
     free(r);
     free(fc);
     free(e);

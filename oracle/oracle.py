@@ -47,7 +47,8 @@ def compile_oracle(src: str, out: str):
 class Opts(C.Structure):
     _fields_ = [("aux_level", C.c_int), ("coarsest_max", C.c_int), ("kcycle_n", C.c_int),
                 ("max_iters", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4),
-                ("no_factor", C.c_int), ("dim", C.c_int), ("zbox", C.c_double * 2)]
+                ("no_factor", C.c_int), ("dim", C.c_int), ("zbox", C.c_double * 2),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int)]
 
 
 def lib():
@@ -151,14 +152,16 @@ class Hierarchy:
     """Oracle setup (Sec. 3-4 of the paper) for one matrix + node coordinates."""
 
     def __init__(self, rowptr, col, val, x, y, aux_level=0, coarsest_max=64, kcycle_n=2,
-                 max_iters=200, bbox=None, no_factor=False, z=None):
-        """z given: the octree (3D) variant; bbox then has 6 entries a1,b1,a2,b2,a3,b3."""
+                 max_iters=200, bbox=None, no_factor=False, z=None, nu_pre=1, nu_post=1):
+        """z given: the octree (3D) variant; bbox then has 6 entries a1,b1,a2,b2,a3,b3.
+        nu_pre / nu_post: Gauss-Seidel sweeps of the pre- / post-smoothing (reading R10)."""
         L = lib()
         self._keep = (_i32(rowptr), _i32(col), _f64(val), _f64(x), _f64(y))
         bb = tuple(bbox) if bbox is not None else (0.0,) * 6
         o = Opts(aux_level, coarsest_max, kcycle_n, max_iters, 0 if bbox is None else 1,
                  (C.c_double * 4)(*bb[:4]), int(no_factor), 3 if z is not None else 2,
-                 (C.c_double * 2)(*(bb[4:6] if len(bb) >= 6 else (0.0, 0.0))))
+                 (C.c_double * 2)(*(bb[4:6] if len(bb) >= 6 else (0.0, 0.0))), int(nu_pre),
+                 int(nu_post))
         h = C.c_void_p()
         n = len(self._keep[0]) - 1
         if z is not None:

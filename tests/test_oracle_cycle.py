@@ -40,6 +40,62 @@ def _dense_two_level(h):
     return A, B
 
 
+@pytest.mark.parametrize("nu", [(2, 2), (2, 1), (1, 3)])
+def test_two_level_cycle_with_several_sweeps(oracle_mod, nu):
+    """nu_pre forward and nu_post backward sweeps (reading R10 made a parameter): Alg. 2 is
+    then B = (I - E) A^{-1} with the error propagation E = (I - M^t A)^nu_post (I - C A)
+    (I - M A)^nu_pre of the textbook two-grid method (a different formula from the
+    step-by-step cycle); symmetric when nu_pre = nu_post."""
+    prob = p1_poisson(n=17, jitter=0.2, seed=3)
+    h = _two_level(oracle_mod, prob, nu_pre=nu[0], nu_post=nu[1])
+    A, _ = _dense_two_level(h)
+    f = h.level(0)
+    c = h.level(1)
+    n = f.n
+    P = np.zeros((n, c.n))
+    P[np.arange(n), f.agg] = 1.0
+    Q = np.eye(n)[f.perm]
+    Ap = Q @ A @ Q.T
+    M = Q.T @ np.linalg.inv(np.tril(Ap)) @ Q
+    Mt = Q.T @ np.linalg.inv(np.triu(Ap)) @ Q
+    I = np.eye(n)
+    C = P @ np.linalg.inv(c.to_scipy().toarray()) @ P.T
+    mp = np.linalg.matrix_power
+    E = mp(I - Mt @ A, nu[1]) @ (I - C @ A) @ mp(I - M @ A, nu[0])
+    B = np.linalg.solve(A.T, (I - E).T).T  # (I - E) A^{-1}
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        v = rng.standard_normal(n)
+        np.testing.assert_allclose(h.bhat(0, v), B @ v, rtol=0, atol=1e-10 * np.abs(B @ v).max())
+    sym = np.abs(B - B.T).max() / np.abs(B).max()
+    if nu[0] == nu[1]:
+        assert sym < 1e-10
+    else:
+        assert sym > 1e-6  # the pre- and post-smoothing differ: not symmetric
+    # one sweep each is the operator of the default cycle
+    h1 = _two_level(oracle_mod, prob)
+    v = rng.standard_normal(n)
+    assert not np.allclose(h.bhat(0, v), h1.bhat(0, v), rtol=1e-6, atol=0)
+
+
+def test_several_sweeps_solve_matches_direct(oracle_mod):
+    prob = p1_poisson(n=17, jitter=0.2, seed=6, rhs="normal")
+    A = prob.to_scipy().toarray()
+    xd = np.linalg.solve(A, prob.b)
+    it1 = None
+    for nu in ((1, 1), (2, 2), (3, 3)):
+        h = oracle_mod.Hierarchy.from_problem(prob, aux_level=3, coarsest_max=16, nu_pre=nu[0],
+                                              nu_post=nu[1])
+        assert h.nlev >= 3
+        x, it, rr, st = h.solve(prob.b, 1e-14)
+        assert st == oracle_mod.OK
+        assert np.linalg.norm(x - xd) <= 1e-12 * np.linalg.norm(xd)
+        x8, it8, _, _ = h.solve(prob.b, 1e-8)
+        if it1 is not None:
+            assert it8 <= it1  # more smoothing never needs more iterations here
+        it1 = it8
+
+
 @pytest.mark.parametrize("case", [dict(n=17, jitter=0.2, seed=0),
                                   dict(n=19, jitter=0.1, graded=True, kappa_blocks=16, seed=1)])
 def test_two_level_cycle_is_the_dense_operator(oracle_mod, case):

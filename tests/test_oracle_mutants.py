@@ -101,8 +101,17 @@ MUTANTS = {
         "    for (int i = 0; i < n; i++) z[i] = e[lv->agg[i]];"),
     # Alg. 2: the post-smoothing step dropped
     "no_post_smoothing": (
-        "    smooth(lv, 1, f, z);\n    free(r);",
-        "    free(r);"),
+        "    for (int s = 0; s < h->opt.nu_post; s++) smooth(lv, 1, f, z);",
+        ""),
+    # reading R10 as a parameter: the post-smoothing's sweep count taken from nu_pre
+    "post_sweeps_from_nu_pre": (
+        "    for (int s = 0; s < h->opt.nu_post; s++) smooth(lv, 1, f, z);",
+        "    for (int s = 0; s < h->opt.nu_pre; s++) smooth(lv, 1, f, z);"),
+    # every pre-smoothing sweep restarted from zero (the sweeps do not compose)
+    "pre_sweeps_restart_from_zero": (
+        "    for (int s = 0; s < h->opt.nu_pre; s++) smooth(lv, 0, f, z);",
+        "    for (int s = 0; s < h->opt.nu_pre; s++) {\n"
+        "        for (int i = 0; i < n; i++) z[i] = 0.0;\n        smooth(lv, 0, f, z);\n    }"),
     # Alg. 1: the orthogonalisation coefficient with the wrong sign
     "alg1_beta_sign": (
         "            double beta = -dot(n, z, q + (size_t)j * n) / pAp[j];",
