@@ -55,12 +55,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-graded", action="store_true")
     ap.add_argument("--batch-systems", type=int, default=256)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-octree", action="store_true")
     ap.add_argument("--octree-n", type=int, default=129)
-    ap.add_argument("--serve-rate", type=float, default=100.0)
-    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-rates", default="10,50,100,200,500,1000,2000")
+    ap.add_argument("--serve-requests", type=int, default=48)
     return ap.parse_args()
 
 
@@ -207,7 +209,13 @@ def cpu_oracle_baseline(prob, aux, tol, budget_s=30.0):
     t1 = time.perf_counter()
     x, it, rr, st = O.solve(prob.b, tol)
     t2 = time.perf_counter()
-    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": it, "relres": rr, "status": st}
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": it, "relres": rr, "status": st,
+            "x": x}
+
+
+def rel_err(x, xo):
+    """||x - x_oracle|| / ||x_oracle|| (the error against the FP64 oracle's solution)."""
+    return float(np.linalg.norm(x - xo) / np.linalg.norm(xo))
 
 
 # ---------------------------------------------------------------------------------------
@@ -390,53 +398,214 @@ def run_octree(args, world, flush, dev, stream):
     return out
 
 
-def run_served(args, local):
-    """The served form: a Poisson stream of solve requests at `serve_rate` req/s into the
-    continuous-batching server (HBM budget 150 GB). Matrices: 32 jittered P1 Poisson systems,
-    unknowns log-uniform in [1e3, 1e6]; 30% of the requests reuse a matrix already seen with a
-    new N(0,1) right-hand side, the others bring the next new matrix (while any is left).
-    Latency = completion - arrival (host clock), over all requests."""
+def time_config(args, world, flush, stream, A, b, x, opts, steps, warmup):
+    """Setup + solve steps of one configuration: per-step CUDA events around the setup and
+    around the solve (L2 flushed before every step, outside the events)."""
+    import torch
+
+    from paper_1209_5421_gb300 import amg
+
+    def step(mid=None):
+        h = amg.Hierarchy(*A, **opts)
+        if mid is not None:
+            mid.record(stream)
+        _, it, rr, st = h.solve(b, args.tol, x=x)
+        h.close()
+        if st != amg.OK:
+            raise RuntimeError(f"solve failed: status {st}, relres {rr}")
+        return it, rr
+
+    for _ in range(warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    its, rrs = [], []
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        it, rr = step(ev[k][1])
+        ev[k][2].record(stream)
+        its.append(it)
+        rrs.append(rr)
+    torch.cuda.synchronize()
+    barrier(world)
+    lat = [e[0].elapsed_time(e[2]) for e in ev]
+    total = max_over_ranks(world, sum(lat))
+    return {"value": round(world * steps / (total / 1e3), 3), "unit": "solves/s",
+            "ms_per_step": round(total / steps, 3),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                           "p99": round(float(np.percentile(lat, 99)), 3)},
+            "setup_ms": round(statistics.median(e[0].elapsed_time(e[1]) for e in ev), 3),
+            "solve_ms": round(statistics.median(e[1].elapsed_time(e[2]) for e in ev), 3),
+            "iters": its[-1], "relres": float(max(rrs)), "steps": steps}
+
+
+def golden_oracle_iters(name, tol):
+    """The FP64 oracle's outer iterations for a workload, from the stored golden counts."""
+    p = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
+    try:
+        for line in open(p):
+            f = line.split()
+            if f and not line.startswith("#") and f[0] == name and float(f[1]) == tol:
+                return int(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def run_small_latency(args, world, flush, dev, stream):
+    """The 65 x 65-node jittered P1 Poisson (3,969 unknowns, load vector of f = 1, auxiliary
+    grid 64 x 64), the plain FP64 method (FP64 cycle, flexible-CG outer), one system per step:
+    the latency case. Error against the FP64 oracle's solution of the same system."""
+    import torch
+
+    from oracle import oracle
+    from paper_1209_5421_gb300 import amg
+    from paper_1209_5421_gb300.meshes import workload
+
+    prob, aux = workload("quasi_uniform_65")
+    td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
+    A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
+    b = td(prob.b)
+    x = torch.empty_like(b)
+    res = time_config(args, world, flush, stream, A, b, x,
+                      dict(aux_level=aux, cycle_prec=amg.FP64, outer=amg.OUTER_FCG),
+                      steps=max(20, args.steps), warmup=max(3, args.warmup))
+    xg = x.cpu().numpy()
+    oracle.build()
+    O = oracle.Hierarchy.from_problem(prob, aux_level=aux)
+    xo, ito, _, _ = O.solve(prob.b, args.tol)
+    return {"workload": "quasi_uniform_65", "unknowns": prob.n, "nnz": prob.nnz,
+            "aux_level": aux, "method": "FP64 AMLI-cycle, flexible-CG outer (plain method)",
+            **res, "iters_oracle": ito, "err_vs_oracle": rel_err(xg, xo)}
+
+
+def run_graded(args, world, flush, dev, stream):
+    """The graded workload: 1449 x 1449-node P1 Poisson with x -> x^2, y -> y^2, jitter 0.1h
+    and kappa log-uniform in [0.1, 10] on 16 x 16 blocks (2,093,809 unknowns, L = 10 by the
+    depth rule): FP32 cycle with FP64 FGMRES, and the plain FP64 method beside it; the
+    oracle's iteration count from the stored golden counts; per-op rates of the finest
+    level's block Gauss-Seidel colours from a profiling pass."""
+    import torch
+
+    from paper_1209_5421_gb300 import amg
+    from paper_1209_5421_gb300.meshes import workload
+
+    prob, aux = workload("graded_1449")
+    td = lambda a: torch.as_tensor(a).to(dev)  # noqa: E731
+    A = [td(a) for a in (prob.rowptr, prob.col, prob.val, prob.x, prob.y)]
+    b = td(prob.b)
+    x = torch.empty_like(b)
+    steps = max(2, min(args.steps, 4))
+    out = {"workload": "graded_1449", "unknowns": prob.n, "nnz": prob.nnz,
+           "iters_oracle": golden_oracle_iters("graded_1449", args.tol)}
+    for name, o in (("fp32_fgmres", dict(aux_level=aux, cycle_prec=amg.FP32,
+                                         outer=amg.OUTER_FGMRES)),
+                    ("fp64_fcg", dict(aux_level=aux, cycle_prec=amg.FP64, outer=amg.OUTER_FCG))):
+        out[name] = time_config(args, world, flush, stream, A, b, x, o, steps=steps,
+                                warmup=max(1, min(args.warmup, 2)))
+    if not args.no_profile:
+        h = amg.Hierarchy(*A, aux_level=aux, cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES)
+        h.profile(2)
+        flush.fill_(0.0)
+        h.solve(b, args.tol, x=x)
+        ks = h.profile_read()
+        nl = h.nlev
+        info = [h.level_info(l) for l in range(nl)]
+        agg = h.level(0)["agg"]
+        h.close()
+        out["levels"] = nl
+        # the finest level's block Gauss-Seidel: unknowns per aggregate (one thread a block)
+        per = np.bincount(agg)
+        out["fine_block_rows"] = {"max": int(per.max()), "mean": round(float(per.mean()), 2),
+                                  "blocks": int(len(per))}
+        out["kernels"] = sorted(
+            [{"name": k["name"], "launches": k["launches"], "ms": round(k["ms"], 4),
+              "GBps": round(k["bytes"] / (k["ms"] / 1e3) / 1e9, 1) if k["ms"] > 0 else None}
+             for k in ks], key=lambda d: -d["ms"])[:10]
+        out["level_rows"] = [int(i["n"]) for i in info]
+    return out
+
+
+def serve_matrices(count=24, seed=11):
+    """The served stream's matrices: `count` P1 Poisson systems with unknowns log-uniform in
+    [1e3, 4e6], alternately quasi-uniform (jitter 0.2h) and graded (x -> x^2, y -> y^2,
+    jitter 0.1h, kappa on 16 x 16 blocks), each with its own mesh seed."""
     from paper_1209_5421_gb300.meshes import p1_poisson
+
+    rng = np.random.default_rng(seed)
+    unknowns = np.exp(rng.uniform(np.log(1e3), np.log(4e6), count))
+    sides = np.rint(np.sqrt(unknowns)).astype(int) + 2
+    mats = []
+    for k, m in enumerate(sides):
+        if k % 2:
+            mats.append(p1_poisson(int(m), jitter=0.1, graded=True, kappa_blocks=16,
+                                   seed=100 + k, rhs="normal"))
+        else:
+            mats.append(p1_poisson(int(m), jitter=0.2, seed=100 + k, rhs="normal"))
+    return mats
+
+
+def run_served_rate(args, local, mats, rate, nreq, seed):
+    """One rate of the served form: a fresh server, a Poisson stream of `nreq` requests at
+    `rate` req/s; 30% of the requests reuse a matrix already seen with a new N(0,1) rhs, the
+    others bring the next new matrix (while any is left). Latency = completion - arrival."""
     from paper_1209_5421_gb300.serve import Server
 
-    rng = np.random.default_rng(11)
-    sides = np.rint(np.sqrt(np.exp(rng.uniform(np.log(1e3), np.log(1e6), 32)))).astype(int) + 2
-    mats = [p1_poisson(int(m), jitter=0.2, seed=100 + k, rhs="normal") for k, m in enumerate(sides)]
+    rng = np.random.default_rng(seed)
     S = Server(budget_bytes=150 << 30, device=local)
     for k, p in enumerate(mats):
         S.register(k, p.rowptr, p.col, p.val, p.x, p.y)
     seen, nxt, reqs = [], 0, []
-    for i in range(args.serve_requests):
+    for i in range(nreq):
         if seen and (rng.random() < 0.3 or nxt == len(mats)):
             key = seen[rng.integers(len(seen))]
         else:
             key = nxt
             nxt += 1
             seen.append(key)
-        reqs.append((key, rng.standard_normal(mats[key].n), float(rng.exponential(1.0 / args.serve_rate))))
+        reqs.append((key, rng.standard_normal(mats[key].n), float(rng.exponential(1.0 / rate))))
     t0 = time.perf_counter()
     handles = []
     for key, b, gap in reqs:
         handles.append(S.submit(key, b, args.tol))
         time.sleep(gap)
+    offered_s = time.perf_counter() - t0
     S.drain()
     wall = time.perf_counter() - t0
     st = S.stats()
     S.close()
     bad = [r.status for r in handles if r.status != 0]
     if bad:
-        raise RuntimeError(f"served: failed statuses {sorted(set(bad))}")
+        raise RuntimeError(f"served at {rate} req/s: failed statuses {sorted(set(bad))}")
+    return {"rate_offered": rate, "offered_req_per_s": round(nreq / offered_s, 2),
+            "value": round(st["solves_per_s"], 2), "unit": "solves/s",
+            "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2)},
+            "requests": nreq, "wall_s": round(wall, 2), "setups": st["setups"],
+            "evictions": st["evictions"], "batches": st["batches"],
+            "large_lane_solves": st["large_lane"],
+            "max_resident_bytes": st["max_resident_bytes"],
+            "relres_max": max(r.relres for r in handles)}
+
+
+def run_served(args, local):
+    """The served form, swept over offered rates: the same matrices (quasi-uniform and graded,
+    1e3..4e6 unknowns) and a fresh continuous-batching server per rate (HBM budget 150 GB)."""
+    mats = serve_matrices()
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    per_rate = [run_served_rate(args, local, mats, r, args.serve_requests, 11 + k)
+                for k, r in enumerate(rates)]
     return {
-        "workload": f"{len(reqs)} requests, Poisson arrivals at {args.serve_rate:g} req/s; "
-                    f"{len(mats)} matrices of 1e3..1e6 unknowns (log-uniform), 30% reuse",
+        "workload": f"{args.serve_requests} requests per rate, Poisson arrivals; "
+                    f"{len(mats)} matrices of 1e3..4e6 unknowns (log-uniform), quasi-uniform "
+                    "and graded alternately, 30% reuse",
         "method": "FP32 AMLI-cycle; batch lane FP64 flexible CG (one CTA per system), "
                   "large lane (> 250k unknowns) FP64 FGMRES on the whole GPU",
-        "value": round(st["solves_per_s"], 2), "unit": "solves/s",
-        "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2)},
-        "wall_s": round(wall, 2), "setups": st["setups"], "evictions": st["evictions"],
-        "batches": st["batches"], "large_lane_solves": st["large_lane"],
-        "max_resident_bytes": st["max_resident_bytes"], "budget_bytes": st["budget_bytes"],
-        "relres_max": max(r.relres for r in handles),
+        "unknowns": [int(m.n) for m in mats],
+        "budget_bytes": 150 << 30,
+        "rates": per_rate,
     }
 
 
@@ -461,8 +630,10 @@ def run_ours(args, world, rank, local):
 
     launch_total = [0]
 
-    def step(o=opts):
+    def step(o=opts, mid=None):
         h = amg.Hierarchy(*A, **o)
+        if mid is not None:  # setup returns once its work is done: the setup / solve split
+            mid.record(stream)
         _, it, rr, st = h.solve(b, args.tol, x=x)
         su, so = h.launch_counts()
         launch_total[0] += su + so
@@ -477,6 +648,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     launch_total[0] = 0
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     iters = []
     barrier(world)
@@ -485,12 +657,15 @@ def run_ours(args, world, rank, local):
         for k in range(args.steps):
             flush.fill_(float(k))
             starts[k].record(stream)
-            it, rr = step()
+            it, rr = step(mid=mids[k])
             ends[k].record(stream)
             iters.append(it)
         torch.cuda.synchronize()
     barrier(world)
     lat = [s.elapsed_time(e) for s, e in zip(starts, ends)]  # ms
+    setup_ms = statistics.median(s.elapsed_time(m) for s, m in zip(starts, mids))
+    solve_ms = statistics.median(m.elapsed_time(e) for m, e in zip(mids, ends))
+    x_head = x.cpu().numpy().copy()
     total_ms = max_over_ranks(world, sum(lat))
     value = world * args.steps / (total_ms / 1e3)
     launches_timed = launch_total[0]
@@ -518,6 +693,7 @@ def run_ours(args, world, rank, local):
         fp64_line = {"value": round(world * args.steps / (t64 / 1e3), 3), "unit": "solves/s",
                      "ms_per_step": round(t64 / args.steps, 3), "iters": its64[-1],
                      "method": "FP64 AMLI-cycle, flexible-CG outer"}
+        x64 = x.cpu().numpy().copy()
 
     # ---- e2e: the C ABI with pinned host buffers (H2D of inputs, D2H of x inside the step)
     e2e = None
@@ -575,6 +751,8 @@ def run_ours(args, world, rank, local):
                     "ms_per_launch": dom["ms"] / dom["launches"],
                     "launches_in_solve": dom["launches"]}
 
+    small = None if args.no_small else run_small_latency(args, world, flush, dev, stream)
+    graded = None if args.no_graded else run_graded(args, world, flush, dev, stream)
     batched = None if args.no_batch else run_batched(args, world, flush, dev, stream)
     served = None if (args.no_serve or rank != 0) else run_served(args, local)
     octree = None if args.no_octree else run_octree(args, world, flush, dev, stream)
@@ -582,12 +760,17 @@ def run_ours(args, world, rank, local):
     out = None
     if rank == 0:
         cpu = None
+        err_vs_oracle = None
         if not args.no_cpu and world == 1:
             c = cpu_oracle_baseline(prob, aux, args.tol)
             tot = c["setup_s"] + c["solve_s"]
             cpu = {"value": 1.0 / tot, "unit": "solves/s", "cores": 1, "kind": "oracle",
                    "sample": f"one full oracle setup+solve of {args.workload} "
                              f"({c['iters']} iterations, {tot:.1f} s)"}
+            err_vs_oracle = rel_err(x_head, c["x"])
+            if fp64_line is not None:
+                fp64_line["err_vs_oracle"] = rel_err(x64, c["x"])
+                fp64_line["iters_oracle"] = c["iters"]
         lat_sorted = sorted(lat)
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
@@ -603,6 +786,9 @@ def run_ours(args, world, rank, local):
                        "aux_level": aux, "tol": args.tol, "iters": iters[-1],
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas{world}"},
+            "setup_ms": round(setup_ms, 3), "solve_ms": round(solve_ms, 3),
+            "iters": iters[-1],
+            "err_vs_oracle": err_vs_oracle,
             "latency_ms": {"p50": round(float(np.percentile(lat_sorted, 50)), 3),
                            "p99": round(float(np.percentile(lat_sorted, 99)), 3)},
             "clocks": clk.summary(),
@@ -611,6 +797,8 @@ def run_ours(args, world, rank, local):
             "fp64_plain": fp64_line,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "small_fp64": small,
+            "graded": graded,
             "batched": batched,
             "served": served,
             "octree": octree,

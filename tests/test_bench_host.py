@@ -153,3 +153,14 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_golden_oracle_iterations_and_error():
+    # the stored oracle counts (written by tests/golden/make_oracle_counts.py) are read back by
+    # workload and tolerance; the error against the oracle is relative to its solution
+    assert bench.golden_oracle_iters("graded_1449", 1e-8) == 126
+    assert bench.golden_oracle_iters("quasi_uniform_65", 1e-8) == 10
+    assert bench.golden_oracle_iters("graded_1449", 1e-6) is None
+    assert bench.golden_oracle_iters("nope", 1e-8) is None
+    xo = np.array([3.0, 4.0])
+    assert bench.rel_err(np.array([3.0, 4.5]), xo) == pytest.approx(0.1)
