@@ -84,6 +84,9 @@ typedef struct {
                            coordinates' min/max (eq. ab12) [0] */
     double bbox[4];     /* a1, b1, a2, b2 */
     double zbox[2];     /* a3, b3: the box's third side (amg_setup3 with has_bbox) */
+    int nu_pre;         /* Gauss-Seidel sweeps of the pre-smoothing R_k of Alg. 2 on every
+                           level, the first from zero [1]; 1..4 (0 = 1) */
+    int nu_post;        /* backward sweeps of the post-smoothing R_k^t [1]; 1..4 (0 = 1) */
 } amg_options;
 
 typedef struct amg_hierarchy amg_hierarchy;
@@ -172,8 +175,8 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
 
 /*
  * A batch over hierarchies that already exist (built by amg_setup or amg_batch_setup; all
- * with the same cycle_prec and kcycle_n; borrowed: they must outlive the batch, and a
- * hierarchy must not be solved by two calls at the same time). System p is hs[p]; its rows in
+ * with the same cycle_prec, kcycle_n, nu_pre and nu_post; borrowed: they must outlive the
+ * batch, and a hierarchy must not be solved by two calls at the same time). System p is hs[p]; its rows in
  * the concatenated vectors follow those of hs[0..p-1]. threads: 0 = choose the launch shape
  * by timing on the first solve, with teams of CTAs for the largest systems (see
  * amg_batch_set_teams); 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs per
@@ -330,8 +333,9 @@ int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, cons
 /*
  * amg_csr_to_ell without any allocation, for callers that cannot allocate device memory
  * when they call in -- for example because another allocator already owns all of the GPU's
- * memory, or because a latency-critical loop forbids allocation calls. No counterpart in the
- * paper: it is the ELL packing of Sec. 4.1 (same arguments and results as amg_csr_to_ell).
+ * memory, or because a latency-critical loop forbids allocation calls. The paper has no
+ * counterpart of this entry point; it takes the same arguments and gives the same results as
+ * amg_csr_to_ell.
  *   - All arrays must be device memory (host arrays would need staging buffers):
  *     otherwise AMG_ERR_INVALID_ARG.
  *   - Its scratch is a fixed array inside the library (about 64 KiB per GPU, held until the
@@ -340,9 +344,12 @@ int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, cons
  *     make that first call before any stream capture.
  *   - Every call on a device shares the array: calls that overlap on the GPU (other streams
  *     or host threads) race and must be ordered by the caller.
+ *   - Every call synchronises: it reads the overflow count back into host memory and waits
+ *     on `stream` (cudaStreamSynchronize) before it returns.
  *   - The same precondition on rowptr as amg_csr_to_ell.
- *   - Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries; the call waits for
- *     its kernels to finish.
+ *   - Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries. Every failure sets
+ *     the text amg_last_error returns; a CUDA error left pending by other code on the calling
+ *     thread is not taken for this call's.
  */
 int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const int32_t *col,
                            const double *val, int32_t width, int diag_first, int32_t *Aj,
@@ -377,6 +384,44 @@ int amg_profile_read(const amg_hierarchy *h, int capacity, int32_t *kind, int32_
 
 /* Static name of a kernel kind reported by amg_profile_read. */
 const char *amg_kernel_name(int kind);
+
+/* ---------------------------------------------------------------------------------------
+ * Fault injection, for tests of the error paths. The paper has no counterpart. Every fault
+ * is made on the host side or by a bounded wait that runs out: the GPU is never made to
+ * fault, trap or hang, and the context stays usable.
+ * ------------------------------------------------------------------------------------- */
+
+/*
+ * Barrier fault of h's cycle kernel for the following solves (until reset with 0, 0): every
+ * grid barrier of the persistent kernel gives up after limit_ns nanoseconds (0 = the default
+ * 2 s), and the first barrier of each launch waits for `extra` arrivals more than the grid
+ * makes, so that it runs out (0 = none). The solve then returns AMG_ERR_TIMEOUT and leaves h
+ * ready for the next solve. Errors: AMG_ERR_INVALID_ARG for NULL or negative arguments.
+ */
+int amg_debug_barrier_fault(amg_hierarchy *h, int64_t limit_ns, int32_t extra);
+
+/*
+ * The same for the team barriers of a batch (systems solved by a team of CTAs): their waits
+ * give up after limit_ns (0 = 2 s), and with extra > 0 every team's first barrier runs out.
+ * Those systems report AMG_ERR_TIMEOUT; systems solved by one CTA are unaffected. The next
+ * solve re-captures the launch with the new arguments.
+ */
+int amg_debug_batch_barrier_fault(amg_batch *bt, int64_t limit_ns, int32_t extra);
+
+/*
+ * Allocation fault: with k > 0 the k-th device allocation the library makes from now on (any
+ * thread, any call) fails as if the device were out of memory, so the call making it returns
+ * AMG_ERR_OOM after releasing what it had allocated; later allocations succeed again. k = 0
+ * disarms it. Errors: AMG_ERR_INVALID_ARG for k < 0.
+ */
+int amg_debug_fail_allocation(int64_t k);
+
+/*
+ * Bytes currently allocated from `device`'s default stream-ordered memory pool, which every
+ * device allocation of the library uses (freed blocks return to it once their stream reaches
+ * the free: synchronise first). A leak check compares it before and after a call.
+ */
+int amg_debug_pool_bytes_in_use(int32_t device, int64_t *bytes);
 
 #ifdef __cplusplus
 }

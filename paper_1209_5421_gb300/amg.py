@@ -38,7 +38,7 @@ class Options(C.Structure):
     _fields_ = [("aux_level", C.c_int), ("coarsest_max", C.c_int), ("kcycle_n", C.c_int),
                 ("max_iters", C.c_int), ("outer", C.c_int), ("cycle_prec", C.c_int),
                 ("fgmres_restart", C.c_int), ("has_bbox", C.c_int), ("bbox", C.c_double * 4),
-                ("zbox", C.c_double * 2)]
+                ("zbox", C.c_double * 2), ("nu_pre", C.c_int), ("nu_post", C.c_int)]
 
 
 _lib = None
@@ -114,8 +114,29 @@ def lib():
                   "amg_profile_enable",
                   "amg_profile_read"):
             getattr(L, f).restype = C.c_int
+        L.amg_debug_barrier_fault.argtypes = [P, C.c_int64, C.c_int32]
+        L.amg_debug_barrier_fault.restype = C.c_int
+        L.amg_debug_batch_barrier_fault.argtypes = [P, C.c_int64, C.c_int32]
+        L.amg_debug_batch_barrier_fault.restype = C.c_int
+        L.amg_debug_fail_allocation.argtypes = [C.c_int64]
+        L.amg_debug_fail_allocation.restype = C.c_int
+        L.amg_debug_pool_bytes_in_use.argtypes = [C.c_int32, C.POINTER(C.c_int64)]
+        L.amg_debug_pool_bytes_in_use.restype = C.c_int
         _lib = L
     return _lib
+
+
+def debug_fail_allocation(k: int):
+    """Make the k-th device allocation of the library from now on fail (0: disarm)."""
+    _check(lib().amg_debug_fail_allocation(int(k)), "amg_debug_fail_allocation")
+
+
+def pool_bytes_in_use(device: int = 0) -> int:
+    """Bytes allocated from the device's default memory pool (the library's allocations)."""
+    v = C.c_int64()
+    _check(lib().amg_debug_pool_bytes_in_use(int(device), C.byref(v)),
+           "amg_debug_pool_bytes_in_use")
+    return v.value
 
 
 def _ptr(a) -> int | None:
@@ -203,8 +224,9 @@ class Hierarchy:
 
     def __init__(self, rowptr, col, val, x, y, aux_level=0, coarsest_max=64, kcycle_n=2,
                  max_iters=200, cycle_prec=FP64, outer=OUTER_FCG, fgmres_restart=30,
-                 bbox=None, stream=None, z=None):
-        """z given: the octree (3D) variant (amg_setup3); bbox then has 6 entries."""
+                 bbox=None, stream=None, z=None, nu_pre=1, nu_post=1):
+        """z given: the octree (3D) variant (amg_setup3); bbox then has 6 entries.
+        nu_pre / nu_post: Gauss-Seidel sweeps of the pre- / post-smoothing."""
         L = lib()
         rp = _as(rowptr, np.int32, what="rowptr")
         n = _count(rp) - 1
@@ -221,6 +243,7 @@ class Hierarchy:
         L.amg_options_default(C.byref(o))
         o.aux_level, o.coarsest_max, o.kcycle_n, o.max_iters = aux_level, coarsest_max, kcycle_n, max_iters
         o.cycle_prec, o.outer, o.fgmres_restart = cycle_prec, outer, fgmres_restart
+        o.nu_pre, o.nu_post = nu_pre, nu_post
         if bbox is not None:
             o.has_bbox = 1
             for k in range(4):
@@ -338,6 +361,11 @@ class Hierarchy:
         _check(lib().amg_launch_counts(self.h, _ptr(s), _ptr(v)), "amg_launch_counts")
         return int(s[0]), int(v[0])
 
+    def debug_barrier_fault(self, limit_ns: int = 0, extra: int = 0):
+        """Host-set barrier fault of the cycle kernel for the following solves (0, 0: off)."""
+        _check(lib().amg_debug_barrier_fault(self.h, int(limit_ns), int(extra)),
+               "amg_debug_barrier_fault")
+
     def profile(self, enable: bool | int = True):
         """0/False: off; 1/True: per-kernel and per-op timing, tail ops one by one; 2: the
         same with the shared-memory tail timed as a whole (no per-op work added to it)."""
@@ -400,7 +428,7 @@ class Batch:
     """
 
     def __init__(self, problems, aux_level=0, coarsest_max=64, kcycle_n=2, max_iters=200,
-                 cycle_prec=FP64, stream=None, device=None):
+                 cycle_prec=FP64, stream=None, device=None, nu_pre=1, nu_post=1):
         L = lib()
         sizes = [len(p[0]) - 1 for p in problems]
         nnzs = [len(p[1]) for p in problems]
@@ -434,6 +462,7 @@ class Batch:
         L.amg_options_default(C.byref(o))
         o.aux_level, o.coarsest_max, o.kcycle_n, o.max_iters = aux_level, coarsest_max, kcycle_n, max_iters
         o.cycle_prec, o.outer = cycle_prec, OUTER_FCG
+        o.nu_pre, o.nu_post = nu_pre, nu_post
         b = C.c_void_p()
         st = L.amg_batch_setup(self.nprob, row_off.ctypes.data, C.byref(A), _ptr(xx), _ptr(yy),
                                C.byref(o), _stream(stream), C.byref(b))
@@ -496,9 +525,15 @@ class Batch:
         st = np.zeros(self.nprob, np.int32)
         r = lib().amg_batch_solve(self.b, _ptr(rhs), tol, _ptr(x), it.ctypes.data,
                                   rr.ctypes.data, st.ctypes.data, _stream(stream))
-        if r not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        # per-system outcomes come back in `status`; other failures raise
+        if r not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
             _check(r, "amg_batch_solve")
         return x, it, rr, st
+
+    def debug_barrier_fault(self, limit_ns: int = 0, extra: int = 0):
+        """Host-set fault of the team barriers for the following solves (0, 0: off)."""
+        _check(lib().amg_debug_batch_barrier_fault(self.b, int(limit_ns), int(extra)),
+               "amg_debug_batch_barrier_fault")
 
     def info(self) -> dict:
         n = C.c_int32()

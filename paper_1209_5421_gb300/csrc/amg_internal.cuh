@@ -24,6 +24,7 @@ namespace amg {
 
 constexpr int kSliceH = 32;        // sliced-ELL slice height (one warp)
 constexpr int kMaxKcycle = 4;      // largest supported kcycle_n
+constexpr int kMaxSweeps = 4;      // largest supported nu_pre / nu_post
 constexpr int kMaxLevels = 20;
 constexpr int kRedBlocks = 608;    // blocks of the deterministic reductions (4 x 152 SMs)
 constexpr int kRedThreads = 256;
@@ -152,6 +153,9 @@ struct amg_hierarchy {
     // diagnostics: per-op CUDA-event profiling and launch counts (solve.cu)
     amg::Profiler *prof = nullptr;
     int64_t setup_launches = 0, solve_launches = 0;
+    // host-set barrier fault of the cycle kernel (amg_debug_barrier_fault): 0 = none
+    int64_t dbg_bar_limit_ns = 0;
+    int dbg_bar_extra = 0;
 };
 
 namespace amg {
@@ -171,6 +175,9 @@ struct Error {
         }                                                                                \
     } while (0)
 
+// records `what` as the text amg_last_error returns on this host thread; returns status
+int set_last_error(int status, const char *what);
+
 // every kernel launch is followed by AMG_LAUNCH_CHECK, which also counts it
 extern thread_local int64_t g_launches;
 #define AMG_LAUNCH_CHECK()            \
@@ -185,12 +192,22 @@ inline int nblocks_for(int64_t n, int threads) {
 }
 
 // ---- allocation (stream-ordered, tracked by the hierarchy) ----------------------------
+// Every device allocation of the library goes through device_alloc. A host-set fault
+// (amg_debug_fail_allocation) makes the k-th one from then on fail as if the device had no
+// memory left: it throws the library's out-of-memory error without calling CUDA.
+bool fail_this_allocation();  // capi.cu: counts down the armed fault
+inline void device_alloc(void **p, size_t bytes, cudaStream_t s) {
+    if (fail_this_allocation())
+        throw Error{AMG_ERR_OOM, "device allocation failed (host-set fault)"};
+    AMG_CUDA(cudaMallocAsync(p, bytes, s));
+}
+
 template <class T>
 T *halloc(amg_hierarchy *h, size_t count) {
     void *p = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    AMG_CUDA(cudaMallocAsync(&p, bytes, h->stream));
+    device_alloc(&p, bytes, h->stream);
     h->allocs.push_back(p);
     h->bytes += bytes;
     return (T *)p;
@@ -206,7 +223,7 @@ struct Scratch {
         void *p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
-        AMG_CUDA(cudaMallocAsync(&p, bytes, s));
+        device_alloc(&p, bytes, s);
         ptrs.push_back(p);
         return (T *)p;
     }
@@ -270,6 +287,10 @@ void batch_timeline(const BatchEngine *E, int64_t *start_ns, int64_t *end_ns);
 void batch_set_teams(BatchEngine *E, int max_team);
 // CTAs of each system's team in the chosen launch shape (host array; -1 before a solve)
 void batch_teams(const BatchEngine *E, int *team);
+// host-set fault of the team barriers for the following solves: limit_ns > 0 replaces the
+// wait limit, extra > 0 makes every team's first barrier wait for that many more arrivals
+// than its members make (so it runs out); 0, 0 restores the defaults
+void batch_barrier_fault(BatchEngine *E, int64_t limit_ns, int extra);
 void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
                   double *u_nat);
 

@@ -60,6 +60,7 @@ struct Team {
     double *part;              // outer sums [2][4][K], then the cycle reductions [4][K]
     unsigned int *cnt;         // arrivals of the cycle's reductions (RM_TEAM)
     unsigned long long target;
+    unsigned long long limit_ns;  // wait limit of the team barrier
     int parity;                // buffer of the next outer sum
     int abort;                 // a barrier wait ran out: no further waits
 };
@@ -77,7 +78,7 @@ __device__ __noinline__ void team_wait() {
         if ((++spins & 1023) == 0) {
             if (t0 == 0) {
                 t0 = global_ns();
-            } else if (global_ns() - t0 > kBarrierLimitNs) {
+            } else if (global_ns() - t0 > bt_team.limit_ns) {
                 bt_team.abort = 1;
                 return;
             }
@@ -163,6 +164,7 @@ struct BatchCycle {
     const int *colors;
     const int *cofs, *ncol;
     int nlev, kc;
+    int nu_pre, nu_post;  // smoothing sweeps
 };
 
 // first non-empty colour [r0, r1) of level l >= 1
@@ -195,13 +197,15 @@ __device__ __forceinline__ void bc_pre(const BatchCycle<T> &c, int l, int i) {
         while (col < nc && cr[col + 1] == cr[col]) col++;
         col++;
     }
-    for (; col < nc; col++) {
-        if (cr[col + 1] == cr[col]) continue;
-        op.i0 = cr[col];
-        op.i1 = cr[col + 1];
-        op_gs(L, op, f, z, tid, nth);
-        team_sync();
-    }
+    // the first sweep's remaining colours, then nu_pre - 1 further forward sweeps
+    for (int sw = 0, c1 = col; sw < c.nu_pre; sw++, c1 = 0)
+        for (col = c1; col < nc; col++) {
+            if (cr[col + 1] == cr[col]) continue;
+            op.i0 = cr[col];
+            op.i1 = cr[col + 1];
+            op_gs(L, op, f, z, tid, nth);
+            team_sync();
+        }
     const BLev<T> &N = c.tab[l + 1];
     if (l + 1 < c.nlev - 1) {  // the next level smooths: its first colour from zero too
         int f0, f1;
@@ -225,13 +229,14 @@ __device__ __forceinline__ void bc_post(const BatchCycle<T> &c, int l, int i) {
     team_sync();
     Op op = batch_op();
     op.backward = 1;
-    for (int col = c.ncol[l] - 1; col >= 0; col--) {
-        if (cr[col + 1] == cr[col]) continue;
-        op.i0 = cr[col];
-        op.i1 = cr[col + 1];
-        op_gs(L, op, f, z, tid, nth);
-        team_sync();
-    }
+    for (int sw = 0; sw < c.nu_post; sw++)
+        for (int col = c.ncol[l] - 1; col >= 0; col--) {
+            if (cr[col + 1] == cr[col]) continue;
+            op.i0 = cr[col];
+            op.i1 = cr[col + 1];
+            op_gs(L, op, f, z, tid, nth);
+            team_sync();
+        }
     if (l == 0) return;
     const RedCtx rc = team_rc();
     op = batch_op();
@@ -443,10 +448,11 @@ __device__ void solve_one(const BatchProb<T> &P, const BatchCycle<T> &cyc, const
 template <class T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_batch(const BatchProb<T> *__restrict__ probs, const int4 *__restrict__ slots, int nslots,
-        int *next, int kc, const double *__restrict__ b, double *__restrict__ x, double tol,
-        int maxit, int *iters, double *relres, int *status, unsigned long long *t_start,
-        unsigned long long *t_end, unsigned long long *team_bar, double *team_part,
-        unsigned int *team_cnt) {
+        int *next, int kc, int nu, const double *__restrict__ b, double *__restrict__ x,
+        double tol, int maxit, int *iters, double *relres, int *status,
+        unsigned long long *t_start, unsigned long long *t_end, unsigned long long *team_bar,
+        double *team_part, unsigned int *team_cnt, unsigned long long bar_limit_ns,
+        int bar_extra) {
     __shared__ BatchProb<T> sp;
     __shared__ BLev<T> stab[kMaxLevels];
     __shared__ int q;
@@ -463,7 +469,8 @@ k_batch(const BatchProb<T> *__restrict__ probs, const int4 *__restrict__ slots, 
             bt_team.bar = team_bar + p;
             bt_team.part = team_part + (size_t)p * kTeamPart;
             bt_team.cnt = team_cnt + p;
-            bt_team.target = 0;
+            bt_team.target = (unsigned long long)bar_extra;  // > 0 only under a host-set fault
+            bt_team.limit_ns = bar_limit_ns;
             bt_team.parity = 0;
             bt_team.abort = 0;
         }
@@ -479,7 +486,8 @@ k_batch(const BatchProb<T> *__restrict__ probs, const int4 *__restrict__ slots, 
                 ((int *)stab)[i] = ((const int *)sp.tab)[i];
         }
         __syncthreads();
-        BatchCycle<T> cyc{stab, sp.colors, sp.cofs, sp.ncol, sp.nlev, kc};
+        // nu: nu_pre + 256 nu_post
+        BatchCycle<T> cyc{stab, sp.colors, sp.cofs, sp.ncol, sp.nlev, kc, nu & 255, nu >> 8};
         if (threadIdx.x == 0 && sl.y == 0) t_start[p] = global_ns();
         solve_one(sp, cyc, b, x, tol, maxit, iters, relres, status, p);
         if (threadIdx.x == 0 && sl.y == 0) t_end[p] = global_ns();
@@ -513,6 +521,10 @@ struct BatchEngine {
     int64_t N = 0;
     bool fp32 = false;
     int kc = 2, maxit = 200;
+    int nu = 1 + 256;  // nu_pre + 256 nu_post
+    // host-set team-barrier fault (amg_debug_batch_barrier_fault): 0 = none
+    int64_t dbg_bar_limit_ns = 0;
+    int dbg_bar_extra = 0;
     cudaStream_t stream = nullptr;
     std::vector<void *> allocs;
     void *probs = nullptr;  // BatchProb<T>[nprob]
@@ -543,7 +555,7 @@ struct BatchEngine {
 template <class U>
 U *balloc(BatchEngine *E, size_t count) {
     void *p = nullptr;
-    AMG_CUDA(cudaMallocAsync(&p, std::max<size_t>(16, count * sizeof(U)), E->stream));
+    device_alloc(&p, std::max<size_t>(16, count * sizeof(U)), E->stream);
     E->allocs.push_back(p);
     E->bytes += count * sizeof(U);
     return (U *)p;
@@ -672,6 +684,7 @@ BatchEngine *batch_create(const std::vector<amg_hierarchy *> &hs, const std::vec
         const amg_options &o = hs[0]->opt;
         E->fp32 = o.cycle_prec == AMG_FP32;
         E->kc = o.kcycle_n;
+        E->nu = o.nu_pre + 256 * o.nu_post;
         E->maxit = o.max_iters;
         for (amg_hierarchy *h : hs) {
             AMG_CUDA(cudaStreamSynchronize(h->stream));
@@ -721,11 +734,14 @@ static void launch_batch(BatchEngine *E, int shape, const double *b, double *x, 
     AMG_CUDA(cudaMemsetAsync(E->team_bar, 0, sizeof(unsigned long long) * E->nprob, E->stream));
     AMG_CUDA(cudaMemsetAsync(E->team_cnt, 0, sizeof(unsigned int) * E->nprob, E->stream));
     void *kern = E->fp32 ? batch_kernel<float>(shape) : batch_kernel<double>(shape);
-    int nslots = E->nslots[shape], kc = E->kc, maxit = E->maxit;
-    void *args[] = {&E->probs,  &E->slots[shape], &nslots,     &E->next,    &kc,
+    int nslots = E->nslots[shape], kc = E->kc, nu = E->nu, maxit = E->maxit;
+    unsigned long long limit_ns =
+        E->dbg_bar_limit_ns > 0 ? (unsigned long long)E->dbg_bar_limit_ns : kBarrierLimitNs;
+    int extra = E->dbg_bar_extra;
+    void *args[] = {&E->probs,  &E->slots[shape], &nslots,     &E->next,    &kc,  &nu,
                     &b,         &x,               &tol,        &maxit,      &E->iters,
                     &E->relres, &E->status,       &E->t_start, &E->t_end,   &E->team_bar,
-                    &E->team_part, &E->team_cnt};
+                    &E->team_part, &E->team_cnt, &limit_ns, &extra};
     AMG_CUDA(cudaLaunchKernel(kern, dim3(E->grid[shape]), dim3(kShapes[shape].threads), args, 0,
                               E->stream));
     AMG_LAUNCH_CHECK();
@@ -816,6 +832,12 @@ void batch_set_teams(BatchEngine *E, int max_team) {
         if (E->grid[s] > 0) build_slots(E, s);
     if (E->tuned) E->shape = -1;  // the shapes' times change with the teams
     E->g_shape = -1;              // recapture the launch
+}
+
+void batch_barrier_fault(BatchEngine *E, int64_t limit_ns, int extra) {
+    E->dbg_bar_limit_ns = limit_ns;
+    E->dbg_bar_extra = extra;
+    E->g_shape = -1;  // recapture the launch with the new arguments
 }
 
 void batch_teams(const BatchEngine *E, int *team) {

@@ -1,6 +1,7 @@
 // C ABI of the library (include/amg.h): argument checks, host/device staging, ownership,
 // status codes; no exception crosses the interface.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -20,6 +21,25 @@ int fail(int status, const std::string &what) {
     g_last_error = what;
     return status;
 }
+
+}  // namespace
+
+namespace amg {
+int set_last_error(int status, const char *what) { return fail(status, what); }
+
+// host-set allocation fault: 0 = off, k > 0 = the k-th device allocation from now fails
+static std::atomic<int64_t> g_fail_alloc_countdown{0};
+bool fail_this_allocation() {
+    int64_t k = g_fail_alloc_countdown.load(std::memory_order_relaxed);
+    while (k > 0) {
+        if (g_fail_alloc_countdown.compare_exchange_weak(k, k - 1, std::memory_order_relaxed))
+            return k == 1;
+    }
+    return false;
+}
+}  // namespace amg
+
+namespace {
 
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
@@ -127,6 +147,8 @@ void amg_options_default(amg_options *o) {
     o->has_bbox = 0;
     o->bbox[0] = o->bbox[1] = o->bbox[2] = o->bbox[3] = 0.0;
     o->zbox[0] = o->zbox[1] = 0.0;
+    o->nu_pre = 1;
+    o->nu_post = 1;
 }
 
 const char *amg_status_string(int s) {
@@ -164,6 +186,8 @@ int check_options(const amg_options &o) {
         return fail(AMG_ERR_INVALID_ARG, "fgmres_restart");
     if (o.has_bbox && !(o.bbox[1] > o.bbox[0] && o.bbox[3] > o.bbox[2]))
         return fail(AMG_ERR_INVALID_ARG, "bbox must have b1 > a1 and b2 > a2");
+    if (o.nu_pre < 0 || o.nu_pre > amg::kMaxSweeps || o.nu_post < 0 || o.nu_post > amg::kMaxSweeps)
+        return fail(AMG_ERR_UNSUPPORTED, "nu_pre and nu_post must be 0..4 (0 = 1)");
     return AMG_OK;
 }
 
@@ -174,6 +198,8 @@ amg_hierarchy *setup_device(const amg_csr &Ad, const double *xd, const double *y
     try {
         h = new amg_hierarchy();
         h->opt = o;
+        if (h->opt.nu_pre == 0) h->opt.nu_pre = 1;
+        if (h->opt.nu_post == 0) h->opt.nu_post = 1;
         h->N = Ad.n;
         h->dim = zd ? 3 : 2;
         AMG_CUDA(cudaGetDevice(&h->device));
@@ -412,8 +438,10 @@ int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, v
         return fail(AMG_ERR_INVALID_ARG, "threads must be 0, 1024, 512 or 256");
     for (int p = 0; p < nprob; p++) {
         if (!hs[p]) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
-        if (hs[p]->opt.cycle_prec != hs[0]->opt.cycle_prec || hs[p]->opt.kcycle_n != hs[0]->opt.kcycle_n)
-            return fail(AMG_ERR_INVALID_ARG, "every hierarchy needs the same cycle_prec and kcycle_n");
+        if (hs[p]->opt.cycle_prec != hs[0]->opt.cycle_prec || hs[p]->opt.kcycle_n != hs[0]->opt.kcycle_n ||
+            hs[p]->opt.nu_pre != hs[0]->opt.nu_pre || hs[p]->opt.nu_post != hs[0]->opt.nu_post)
+            return fail(AMG_ERR_INVALID_ARG,
+                        "every hierarchy needs the same cycle_prec, kcycle_n, nu_pre and nu_post");
         for (int q = 0; q < p; q++)
             if (hs[q] == hs[p]) return fail(AMG_ERR_INVALID_ARG, "a hierarchy appears twice");
     }
@@ -508,6 +536,41 @@ int amg_batch_set_teams(amg_batch *bt, int32_t max_team) {
         return AMG_OK;
     }
     AMG_CATCH
+}
+
+int amg_debug_barrier_fault(amg_hierarchy *h, int64_t limit_ns, int32_t extra) {
+    if (!h) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
+    if (limit_ns < 0 || extra < 0) return fail(AMG_ERR_INVALID_ARG, "negative limit or arrivals");
+    h->dbg_bar_limit_ns = limit_ns;
+    h->dbg_bar_extra = extra;
+    return AMG_OK;
+}
+
+int amg_debug_batch_barrier_fault(amg_batch *bt, int64_t limit_ns, int32_t extra) {
+    if (!bt) return fail(AMG_ERR_INVALID_ARG, "NULL batch");
+    if (limit_ns < 0 || extra < 0) return fail(AMG_ERR_INVALID_ARG, "negative limit or arrivals");
+    amg::batch_barrier_fault(bt->eng, limit_ns, extra);
+    return AMG_OK;
+}
+
+int amg_debug_fail_allocation(int64_t k) {
+    if (k < 0) return fail(AMG_ERR_INVALID_ARG, "k must be >= 0");
+    amg::g_fail_alloc_countdown.store(k);
+    return AMG_OK;
+}
+
+int amg_debug_pool_bytes_in_use(int32_t device, int64_t *bytes) {
+    if (!bytes) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    cudaMemPool_t pool;
+    cudaError_t e = cudaDeviceGetDefaultMemPool(&pool, device);
+    uint64_t used = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *bytes = (int64_t)used;
+    return AMG_OK;
 }
 
 int amg_batch_teams(const amg_batch *bt, int32_t *team) {

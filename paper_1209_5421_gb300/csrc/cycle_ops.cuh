@@ -335,7 +335,8 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsig
 }
 
 __device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err,
-                                             unsigned long long &target, int &abort_flag) {
+                                             unsigned long long &target, int &abort_flag,
+                                             unsigned long long limit_ns = kBarrierLimitNs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
@@ -346,7 +347,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long *count, int *err
             if ((++spins & 1023) == 0) {
                 if (t0 == 0) {
                     t0 = global_ns();
-                } else if (global_ns() - t0 > kBarrierLimitNs || (ld_volatile_int(err) & kErrTimeout)) {
+                } else if (global_ns() - t0 > limit_ns || (ld_volatile_int(err) & kErrTimeout)) {
                     atomicOr(err, kErrTimeout);
                     abort_flag = 1;
                     break;

@@ -12,6 +12,8 @@
 // slot and the combining kernel overwrites the total, so nothing has to be cleared between
 // calls, but calls whose kernels overlap on the GPU (different streams, or different host
 // threads) race on it and must be ordered by the caller.
+#include <stdio.h>
+
 #include <mutex>
 
 #include "amg_internal.cuh"
@@ -110,36 +112,62 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_noalloc_total(int nblocks, 
     if (threadIdx.x == 0) scratch[kNoAllocMaxBlocks] = part[0];
 }
 
+// a CUDA error of this call: its text becomes amg_last_error's, the error is cleared
+int cuda_fail(cudaError_t e, const char *where) {
+    static thread_local char msg[192];
+    snprintf(msg, sizeof msg, "%s: %s", where, cudaGetErrorString(e));
+    cudaGetLastError();
+    return amg::set_last_error(AMG_ERR_CUDA, msg);
+}
+
 }  // namespace
 
 extern "C" int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const int32_t *col,
                                       const double *val, int32_t width, int diag_first,
                                       int32_t *Aj, double *Ax, void *stream) {
-    if (rows <= 0 || width < 0 || !rowptr || !col || !val || !Aj || !Ax) return AMG_ERR_INVALID_ARG;
-    if (rows > kNoAllocMaxRows) return AMG_ERR_UNSUPPORTED;  // beyond the static scratch
+    if (rows <= 0 || width < 0 || !rowptr || !col || !val || !Aj || !Ax)
+        return amg::set_last_error(AMG_ERR_INVALID_ARG, "bad argument");
+    if (rows > kNoAllocMaxRows)  // beyond the static scratch
+        return amg::set_last_error(AMG_ERR_UNSUPPORTED,
+                                   "rows above the allocation-free packer's limit (4,194,304)");
     if (!on_device(rowptr) || !on_device(col) || !on_device(val) || !on_device(Aj) ||
-        !on_device(Ax))
-        return AMG_ERR_INVALID_ARG;  // host arrays would need staging buffers
+        !on_device(Ax))  // host arrays would need staging buffers
+        return amg::set_last_error(AMG_ERR_INVALID_ARG,
+                                   "the allocation-free packer takes device arrays only");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return AMG_ERR_CUDA;
-    }
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     int *scratch = nullptr;
     int st = scratch_address(dev, &scratch);
-    if (st != AMG_OK) return st;
+    if (st == AMG_ERR_UNSUPPORTED)
+        return amg::set_last_error(st, "device ordinal above the packer's device table");
+    if (st != AMG_OK) return amg::set_last_error(st, "cudaGetSymbolAddress of the packer's scratch failed");
     cudaStream_t s = (cudaStream_t)stream;
     const int nblocks = (rows + kNoAllocThreads - 1) / kNoAllocThreads;
-    k_csr_to_ell_noalloc<<<nblocks, kNoAllocThreads, 0, s>>>(rows, rowptr, col, val, width,
-                                                             diag_first, Aj, Ax, scratch);
-    k_noalloc_total<<<1, kNoAllocThreads, 0, s>>>(nblocks, scratch);
-    int over = 0;
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(&over, scratch + kNoAllocMaxBlocks, sizeof(int), cudaMemcpyDeviceToHost,
-                        s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return AMG_ERR_CUDA;
+    // cudaLaunchKernel returns the status of its own launch, so an error left pending on this
+    // thread by other code is neither taken for this call's nor cleared here
+    {
+        int r = rows, w = width, df = diag_first;
+        const int *rp = rowptr, *cl = col;
+        const double *vl = val;
+        int *aj = Aj, *sc = scratch;
+        double *ax = Ax;
+        void *args[] = {&r, &rp, &cl, &vl, &w, &df, &aj, &ax, &sc};
+        e = cudaLaunchKernel((const void *)k_csr_to_ell_noalloc, dim3(nblocks),
+                             dim3(kNoAllocThreads), args, 0, s);
+        if (e != cudaSuccess) return cuda_fail(e, "packing kernel launch");
+        int nb = nblocks;
+        void *args2[] = {&nb, &sc};
+        e = cudaLaunchKernel((const void *)k_noalloc_total, dim3(1), dim3(kNoAllocThreads), args2,
+                             0, s);
+        if (e != cudaSuccess) return cuda_fail(e, "count kernel launch");
     }
-    return over ? AMG_ERR_INVALID_ARG : AMG_OK;  // some row has more than `width` entries
+    int over = 0;
+    e = cudaMemcpyAsync(&over, scratch + kNoAllocMaxBlocks, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the overflow count");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (over)  // some row has more than `width` entries
+        return amg::set_last_error(AMG_ERR_INVALID_ARG, "a row has more entries than width");
+    return AMG_OK;
 }

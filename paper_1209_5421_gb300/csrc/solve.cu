@@ -49,6 +49,7 @@ struct TailLayout {
     int nlev;
     int narrow;  // threads (whole warps) that run the ops of the staged levels
     int kc;      // Alg. 1 steps (kcycle_n)
+    int nu_pre, nu_post;  // smoothing sweeps
     int W;       // slice width of every staged level when fixed (9), else 0
     int bytes;
     int sc;      // the tail levels' Alg. 1 scalars, SC_N doubles per level
@@ -71,6 +72,10 @@ struct CycleArgs {
     unsigned long long *ts;      // per-op end timestamps (profiling) or null
     unsigned long long *tprof;   // tail: [16 level + kind] cycles, [kTprofCount + 16 level +
                                  // kind] count (profiling) or null
+    // host-set barrier fault (amg_debug_barrier_fault): wait limit of every grid barrier, and
+    // arrivals the first barrier waits for beyond the grid's (0: none)
+    unsigned long long bar_limit_ns;
+    int bar_extra;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -98,6 +103,7 @@ extern __shared__ __align__(16) unsigned char amg_smem[];
 
 struct TailCtl {
     int tl, nlev, narrow, kc, sc_off;
+    int nu_pre, nu_post;
     int top_w;  // slice width of the HBM-resident top level when uniform, else 0
     int *err;
     unsigned long long *tprof;
@@ -200,14 +206,16 @@ __device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int 
         g.sync();
         tail_mark(l, OP_GS_FIRST);
     }
-    for (c++; c < nc; c++) {
-        if (cr[c + 1] == cr[c]) continue;
-        op.i0 = cr[c];
-        op.i1 = cr[c + 1];
-        op_gs(L, op, f, z, tid, nth);
-        g.sync();
-        tail_mark(l, OP_GS);
-    }
+    // the first sweep's remaining colours, then nu_pre - 1 further forward sweeps
+    for (int sw = 0, c1 = c + 1; sw < tail_ctl.nu_pre; sw++, c1 = 0)
+        for (c = c1; c < nc; c++) {
+            if (cr[c + 1] == cr[c]) continue;
+            op.i0 = cr[c];
+            op.i1 = cr[c + 1];
+            op_gs(L, op, f, z, tid, nth);
+            g.sync();
+            tail_mark(l, OP_GS);
+        }
     const StagedLevel<T, W> N = staged_level<T, W>(l + 1);
     if (tail_lay[l + 1].Ainv < 0) {  // the next level smooths: its first colour too
         int f0, f1;
@@ -232,14 +240,15 @@ __device__ __forceinline__ void phase_post(const LV &L, const G &g, int nth, int
     const int *cr = (const int *)(amg_smem + tail_lay[l].colors);
     Op op = tail_op();
     op.backward = 1;
-    for (int c = tail_lay[l].ncolors - 1; c >= 0; c--) {
-        if (cr[c + 1] == cr[c]) continue;
-        op.i0 = cr[c];
-        op.i1 = cr[c + 1];
-        op_gs(L, op, f, z, tid, nth);
-        g.sync();
-        tail_mark(l, OP_GS);
-    }
+    for (int sw = 0; sw < tail_ctl.nu_post; sw++)
+        for (int c = tail_lay[l].ncolors - 1; c >= 0; c--) {
+            if (cr[c + 1] == cr[c]) continue;
+            op.i0 = cr[c];
+            op.i1 = cr[c + 1];
+            op_gs(L, op, f, z, tid, nth);
+            g.sync();
+            tail_mark(l, OP_GS);
+        }
     const RedCtx rc{nullptr, nullptr};
     const int kc = tail_ctl.kc;
     op = tail_op();
@@ -348,6 +357,8 @@ __device__ void stage_tail(const CycleArgs<T> &a) {
         tail_ctl.nlev = Y.nlev;
         tail_ctl.narrow = Y.narrow;
         tail_ctl.kc = Y.kc;
+        tail_ctl.nu_pre = Y.nu_pre;
+        tail_ctl.nu_post = Y.nu_post;
         tail_ctl.sc_off = Y.sc;
         tail_ctl.top_w = 0;
         tail_ctl.err = a.err;
@@ -509,7 +520,7 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
     __shared__ unsigned long long target;
     __shared__ int abort_flag;
     if (threadIdx.x == 0) {
-        target = 0;
+        target = (unsigned long long)a.bar_extra;  // > 0 only under a host-set barrier fault
         abort_flag = 0;
     }
     {  // the level table, read by every op, lives in shared memory
@@ -545,7 +556,7 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
         } else if (op.kind != OP_NOP) {
             run_op<GL, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
         }
-        if (!grid_barrier(a.bar, a.err, target, abort_flag)) break;
+        if (!grid_barrier(a.bar, a.err, target, abort_flag, a.bar_limit_ns)) break;
         if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
     }
 }
@@ -1070,15 +1081,17 @@ struct Builder {
             }
             c0++;
         }
-        for (int c = c0; c < nc; c++) {
-            if (ranges[c + 1] == ranges[c]) continue;
-            Op g = mk(OP_GS, l);
-            g.i0 = ranges[c];
-            g.i1 = ranges[c + 1];
-            g.fsel = fsel;
-            g.usel = zsel;
-            emit(g);
-        }
+        // the first sweep's remaining colours, then nu_pre - 1 further forward sweeps
+        for (int sw = 0; sw < h->opt.nu_pre; sw++)
+            for (int c = sw == 0 ? c0 : 0; c < nc; c++) {
+                if (ranges[c + 1] == ranges[c]) continue;
+                Op g = mk(OP_GS, l);
+                g.i0 = ranges[c];
+                g.i1 = ranges[c + 1];
+                g.fsel = fsel;
+                g.usel = zsel;
+                emit(g);
+            }
         Op rs = mk(OP_RESTRICT, l);  // next.rhs = P^t (f - A u1)
         rs.fsel = fsel;
         rs.usel = zsel;
@@ -1092,16 +1105,17 @@ struct Builder {
         Op pr = mk(OP_PROLONG, l);   // u2 = u1 + P e
         pr.usel = zsel;
         emit(pr);
-        for (int c = nc - 1; c >= 0; c--) {  // post-smoothing: colours descending
-            if (ranges[c + 1] == ranges[c]) continue;
-            Op g = mk(OP_GS, l);
-            g.i0 = ranges[c];
-            g.i1 = ranges[c + 1];
-            g.backward = 1;
-            g.fsel = fsel;
-            g.usel = zsel;
-            emit(g);
-        }
+        for (int sw = 0; sw < h->opt.nu_post; sw++)  // post-smoothing: colours descending
+            for (int c = nc - 1; c >= 0; c--) {
+                if (ranges[c + 1] == ranges[c]) continue;
+                Op g = mk(OP_GS, l);
+                g.i0 = ranges[c];
+                g.i1 = ranges[c + 1];
+                g.backward = 1;
+                g.fsel = fsel;
+                g.usel = zsel;
+                emit(g);
+            }
     }
 
     // e = B~_l [rhs] (Alg. 1 with kcycle_n steps; exact on the coarsest level). first_done:
@@ -1255,6 +1269,8 @@ bool tail_layout(amg_hierarchy *h, int l0, int vb, bool top_in_gmem,
     Y.tl = l0;
     Y.nlev = h->nlev;
     Y.kc = h->opt.kcycle_n;
+    Y.nu_pre = h->opt.nu_pre;
+    Y.nu_post = h->opt.nu_post;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         int o = (int)off;
@@ -1439,14 +1455,14 @@ void alloc_vecs(amg_hierarchy *h) {
         Vecs<T> &v = vecs<T>(lv);
         int n = lv.n;
         if (l > 0) {
-            v.rhs = halloc<T>(h, n);
-            v.e = halloc<T>(h, n);
+            if (!v.rhs) v.rhs = halloc<T>(h, n);
+            if (!v.e) v.e = halloc<T>(h, n);
         }
         if (l > 0 && !lv.coarsest) {
-            v.r = halloc<T>(h, n);
+            if (!v.r) v.r = halloc<T>(h, n);
             for (int i = 0; i < h->opt.kcycle_n; i++) {
-                v.p[i] = halloc<T>(h, n);
-                v.q[i] = halloc<T>(h, n);
+                if (!v.p[i]) v.p[i] = halloc<T>(h, n);
+                if (!v.q[i]) v.q[i] = halloc<T>(h, n);
             }
         }
     }
@@ -1455,22 +1471,28 @@ void alloc_vecs(amg_hierarchy *h) {
 void ensure_fp32(amg_hierarchy *h) {
     if (h->fp32_ready) return;
     cudaStream_t s = h->stream;
+    // every step keeps what an earlier, failed attempt already allocated (an allocation can
+    // fail part-way; the next solve then completes the set)
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
-        lv.A.val32 = halloc<float>(h, lv.A.padded);
+        if (lv.A.val32) continue;
+        float *v = halloc<float>(h, lv.A.padded);
         k_convert<double, float><<<nblocks_for(lv.A.padded, 256), 256, 0, s>>>(
-            (int)lv.A.padded, lv.A.val, lv.A.val32);
+            (int)lv.A.padded, lv.A.val, v);
         AMG_LAUNCH_CHECK();
+        lv.A.val32 = v;
     }
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
-        lv.dinv32 = halloc<float>(h, lv.n);
-        k_inv_diag<float><<<nblocks_for(lv.n, 256), 256, 0, s>>>(lv.n, lv.A.sl_ptr, lv.A.val, lv.dinv32);
+        if (lv.dinv32) continue;
+        float *d = halloc<float>(h, lv.n);
+        k_inv_diag<float><<<nblocks_for(lv.n, 256), 256, 0, s>>>(lv.n, lv.A.sl_ptr, lv.A.val, d);
         AMG_LAUNCH_CHECK();
+        lv.dinv32 = d;
     }
     alloc_vecs<float>(h);
-    h->r32 = halloc<float>(h, h->N);
-    h->z32 = halloc<float>(h, h->N);
+    if (!h->r32) h->r32 = halloc<float>(h, h->N);
+    if (!h->z32) h->z32 = halloc<float>(h, h->N);
     h->lev[0].v32.rhs = h->r32;
     h->lev[0].v32.e = h->z32;
     fill_tables<float>(h);
@@ -1494,6 +1516,9 @@ void launch_cycle(amg_hierarchy *h) {
     a.partials = h->cyc_partials;
     a.bar = h->bar;
     a.err = h->err_flag;
+    a.bar_limit_ns = h->dbg_bar_limit_ns > 0 ? (unsigned long long)h->dbg_bar_limit_ns
+                                             : kBarrierLimitNs;
+    a.bar_extra = h->dbg_bar_extra;
     AMG_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), s));
     a.ts = prof ? E->ts + 1 : nullptr;
     a.tprof = (prof && h->prof->tail_ops) ? E->tprof : nullptr;
@@ -1631,9 +1656,11 @@ static void ensure_directions(amg_hierarchy *h, int count) {
     int old = (int)h->P.size();
     if (count <= old) return;
     int target = std::min(h->opt.max_iters, ((count + chunk - 1) / chunk) * chunk);
-    for (int j = old; j < target; j++) {
-        h->P.push_back(halloc<double>(h, n));
-        h->Q.push_back(halloc<double>(h, n));
+    for (int j = old; j < target; j++) {  // both allocated before either is kept: P and Q
+        double *p = halloc<double>(h, n);    // stay the same length if an allocation fails
+        double *q = halloc<double>(h, n);
+        h->P.push_back(p);
+        h->Q.push_back(q);
     }
     AMG_CUDA(cudaMemcpyAsync(h->dP, h->P.data(), sizeof(double *) * target, cudaMemcpyHostToDevice,
                              h->stream));

@@ -80,6 +80,27 @@ def test_batch_matches_oracle(amg, oracle_mod, prec):
     B.close()
 
 
+def test_batch_several_sweeps_matches_oracle(amg, oracle_mod):
+    # two sweeps each way on every level (reading R10 as a parameter), the plain FP64 method:
+    # within one iteration of the oracle's count with the same sweeps
+    probs = [p1_poisson(**s) for s in SPECS[:4]]
+    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP64, nu_pre=2, nu_post=2)
+    rhs = np.concatenate([p.b for p in probs])
+    tol = 1e-8
+    x, it, rr, st = B.solve(rhs, tol)
+    off = B.row_off
+    for k, p in enumerate(probs):
+        assert st[k] == amg.OK
+        A = p.to_scipy()
+        xk = x[off[k]:off[k + 1]]
+        assert np.linalg.norm(p.b - A @ xk) / np.linalg.norm(p.b) <= tol
+        O = oracle_mod.Hierarchy.from_problem(p, nu_pre=2, nu_post=2)
+        xo, ito, _, _ = O.solve(p.b, tol)
+        assert abs(int(it[k]) - int(ito)) <= 1, (k, it[k], ito)
+        assert np.linalg.norm(xk - xo) <= 1e-6 * np.linalg.norm(xo)
+    B.close()
+
+
 def test_system_alone_and_in_the_batch(amg):
     probs = [p1_poisson(**s) for s in SPECS]
     tol = 1e-8

@@ -77,6 +77,10 @@ CASES = {
                         dict(aux_level=5, coarsest_max=16)),
     "kcycle3": (dict(n=41, jitter=0.2, seed=4, rhs="normal"), dict(kcycle_n=3, coarsest_max=4)),
     "kcycle1": (dict(n=41, jitter=0.2, seed=5, rhs="normal"), dict(kcycle_n=1)),
+    # several smoothing sweeps (reading R10 as a parameter): 9,025 unknowns, so the finest
+    # level runs grid-wide and the rest in the shared-memory tail; and a tail-only case
+    "nu2": (dict(n=97, jitter=0.2, seed=6, rhs="normal"), dict(nu_pre=2, nu_post=2)),
+    "nu31": (dict(n=41, jitter=0.2, seed=7, rhs="normal"), dict(nu_pre=3, nu_post=1)),
 }
 
 
@@ -114,7 +118,7 @@ def test_solve_parity(amg, oracle_mod, name):
     assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("name", ["jitter33", "graded65_kappa", "kcycle3"])
+@pytest.mark.parametrize("name", ["jitter33", "graded65_kappa", "kcycle3", "nu2", "nu31"])
 def test_smoother_and_cycle_parity(amg, oracle_mod, name):
     prob, opts = _problem(name)
     G = amg.Hierarchy.from_problem(prob, **opts)
@@ -132,6 +136,28 @@ def test_smoother_and_cycle_parity(amg, oracle_mod, name):
         zg = G.apply_cycle(l, f)
         zo = O.bhat(l, f)
         assert np.linalg.norm(zg - zo) <= 1e-11 * np.linalg.norm(zo), (l, np.linalg.norm(zg - zo) / np.linalg.norm(zo))
+
+
+def test_several_sweeps_fp32_cycle(amg, oracle_mod):
+    # the FP32 cycle with two sweeps each way, FGMRES outer: meets the tolerance in FP64 and
+    # agrees with the FP64 oracle's solution of the same preconditioned method
+    prob, opts = _problem("nu2")
+    G = amg.Hierarchy.from_problem(prob, cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES, **opts)
+    O = oracle_mod.Hierarchy.from_problem(prob, **opts)
+    tol = 1e-8
+    xg, itg, rrg, stg = G.solve(prob.b, tol)
+    xo, ito, _, sto = O.solve(prob.b, tol)
+    assert stg == amg.OK and sto == oracle_mod.OK
+    A = prob.to_scipy()
+    assert np.linalg.norm(prob.b - A @ xg) / np.linalg.norm(prob.b) <= tol
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert itg <= ito + 3, (itg, ito)
+    # more sweeps than the default: fewer (or as many) outer iterations
+    G1 = amg.Hierarchy.from_problem(prob, cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES)
+    _, it1, _, st1 = G1.solve(prob.b, tol)
+    assert st1 == amg.OK and itg <= it1
+    G.close()
+    G1.close()
 
 
 def test_uniform_grid_and_explicit_box(amg, oracle_mod):

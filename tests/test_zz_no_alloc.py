@@ -84,3 +84,77 @@ def test_limits_and_host_arrays_rejected(lib):
     st = L.amg_csr_to_ell_noalloc(prob.n, prob.rowptr.ctypes.data, prob.col.ctypes.data,
                                   prob.val.ctypes.data, 5, 1, Aj.ctypes.data, Ax.ctypes.data, None)
     assert st == lib.ERR_INVALID_ARG
+
+
+def _golden_ell():
+    import os
+
+    d = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "ell_example.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        d[k] = [float(t) for t in v]
+    return d
+
+
+def test_paper_worked_example(lib):
+    # the ELL example printed with the packing (3 x 4 matrix, K = 3, column-major Aj / Ax)
+    L = lib.lib()
+    g = _golden_ell()
+    rp = np.array(g["rowptr"], np.int32)
+    cl = np.array(g["col"], np.int32)
+    vl = np.array(g["val"])
+    width = int(g["width"][0])
+    for _ in range(2):  # two calls in a row: the shared scratch carries nothing over
+        st, Aj, Ax = _pack(lib, L.amg_csr_to_ell_noalloc, rp, cl, vl, width, False)
+        assert st == lib.OK
+        np.testing.assert_array_equal(Aj, np.array(g["Aj"], np.int32))
+        np.testing.assert_array_equal(Ax, np.array(g["Ax"]))
+
+
+def test_overflow_in_a_late_block_only(lib):
+    # more than one 256-row block, and only a row of the last block is too long: the count of
+    # that block must reach the total (every block's count is summed)
+    L = lib.lib()
+    prob = p1_poisson(40, jitter=0.2, seed=4)  # 38^2 = 1444 rows: 6 blocks
+    assert prob.n > 5 * 256
+    deg = np.diff(prob.rowptr)
+    width = int(deg.max())
+    # a matrix whose only rows of `width` entries lie in the last block: drop the last entry
+    # of every such row before it
+    cut = 5 * 256
+    short = np.zeros(prob.n, bool)
+    short[:cut] = deg[:cut] == width
+    keep = np.ones(len(prob.col), bool)
+    keep[prob.rowptr[1:][short] - 1] = False
+    rowptr = np.concatenate([[0], np.cumsum(deg - short)]).astype(np.int32)
+    col, val = prob.col[keep], prob.val[keep]
+    d2 = np.diff(rowptr)
+    assert d2[:cut].max() < width and d2[cut:].max() == width
+    st, _, _ = _pack(lib, L.amg_csr_to_ell_noalloc, rowptr, col, val, width - 1, 1)
+    assert st == lib.ERR_INVALID_ARG
+    assert b"width" in L.amg_last_error()
+    st, Aj, Ax = _pack(lib, L.amg_csr_to_ell_noalloc, rowptr, col, val, width, 1)
+    assert st == lib.OK
+    st0, Aj0, Ax0 = _pack(lib, L.amg_csr_to_ell, rowptr, col, val, width, 1)
+    assert st0 == lib.OK
+    np.testing.assert_array_equal(Aj, Aj0)
+    np.testing.assert_array_equal(Ax, Ax0)
+
+
+def test_failures_set_the_error_text(lib):
+    import torch
+
+    L = lib.lib()
+    tiny = torch.zeros(4, dtype=torch.int32, device="cuda")
+    tinyd = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = L.amg_csr_to_ell_noalloc(4194305, tiny.data_ptr(), tiny.data_ptr(), tinyd.data_ptr(), 1,
+                                  1, tiny.data_ptr(), tinyd.data_ptr(), None)
+    assert st == lib.ERR_UNSUPPORTED and b"4,194,304" in L.amg_last_error()
+    prob = p1_poisson(9)
+    Aj = np.empty(prob.n * 5, np.int32)
+    Ax = np.empty(prob.n * 5)
+    st = L.amg_csr_to_ell_noalloc(prob.n, prob.rowptr.ctypes.data, prob.col.ctypes.data,
+                                  prob.val.ctypes.data, 5, 1, Aj.ctypes.data, Ax.ctypes.data, None)
+    assert st == lib.ERR_INVALID_ARG and b"device arrays" in L.amg_last_error()
