@@ -42,6 +42,27 @@ enum : int {
     SC_N = 24
 };
 
+// Big aggregates of the finest level (graded meshes put thousands of unknowns in one
+// auxiliary cell): their Gauss-Seidel sweep runs on a warp (blocks of up to kWarpBlockRows
+// rows) or a whole CTA, in level order. The level of a row in a forward sweep is 1 + the
+// largest level of the rows of its block it depends on (coupled rows earlier in the sweep),
+// 0 if none; rows of one level are independent, and every earlier coupled row has a lower
+// level, so sweeping level by level reads exactly the values the sequential sweep reads:
+// the same result, bit for bit. The backward sweep has its own levels (dependencies on
+// later rows).
+constexpr int kBigBlockRows = 16;
+constexpr int kWarpBlockRows = 128;
+struct BigSched {
+    int nbig;
+    const int *ids;              // [nbig] big block ids: colour by colour (block order), and
+                                 // inside a colour the warp-sized blocks first
+    const int *lofs_f, *lofs_b;  // [nbig + 1]: block k's level boundaries start at lp_*[lofs_*[k]]
+    const int *lp_f, *lp_b;      // level boundaries: positions in ent_* (level j of block k is
+                                 // ent_*[lp[lofs[k] + j] .. lp[lofs[k] + j + 1]))
+    const int4 *ent_f, *ent_b;   // rows of every big block in level order: (pi row, first
+                                 // slot, slot count, 0)
+};
+
 struct Sell {
     int n = 0;
     int nslices = 0;
@@ -73,6 +94,11 @@ struct Level {
     std::vector<int> color_blocks;  // host [ncolors+1] (finest level): block range per colour
     int nblocks = 0;
     int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block
+    // finest level: blocks of more than kBigBlockRows rows, swept by whole CTAs in level order
+    int nbig = 0;
+    const BigSched *big_dev = nullptr;  // device copy of the schedule
+    std::vector<int> color_big;     // host [ncolors+1]: each colour's range of big blocks
+    std::vector<int> color_bigc;    // host [ncolors]: where each colour's CTA-sized ones start
     int *parent = nullptr;  // [n] pi-row of the next coarser level
     int4 *children = nullptr;  // level >= 2: [n] children pi-rows in level-1 by quadrant
     int4 *children2 = nullptr; // octree: children 4..7 (octant (t1&1) + 2 (t2&1) + 4 (t3&1))

@@ -6,6 +6,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "amg_internal.cuh"
@@ -401,18 +402,70 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
         if (nz[0] != 0 || nz[nprob] != A->nnz)
             throw Error{AMG_ERR_BAD_MATRIX, "rowptr does not run from 0 to nnz"};
         bt->row_off.assign(row_off, row_off + nprob + 1);
-        for (int p = 0; p < nprob; p++) {
-            const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
-            const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
-            if (nnz < n) throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
-            Scratch loc(us);
-            int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
-            k_localize_rows<<<(n + 256) / 256, 256, 0, us>>>(n, rp + r0, z0, lrp);
-            k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
-            AMG_CUDA(cudaGetLastError());
-            amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
-            bt->hs.push_back(setup_device(Ap, xd + r0, yd + r0, nullptr, o, stream));
-        }
+        for (int p = 0; p < nprob; p++)
+            if (nz[p + 1] - nz[p] < (int)(row_off[p + 1] - row_off[p]))
+                throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
+        // The systems' setups are independent chains of small kernels and host round trips
+        // (latency-bound), so several run at once: worker threads take systems in turn, each
+        // on its own stream (ordered after the caller's), largest systems first.
+        bt->hs.assign(nprob, nullptr);
+        cudaEvent_t ready;
+        AMG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        AMG_CUDA(cudaEventRecord(ready, us));  // the staged inputs
+        std::vector<int> order(nprob);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return row_off[a + 1] - row_off[a] > row_off[b + 1] - row_off[b];
+        });
+        std::atomic<int> next{0};
+        std::mutex err_m;
+        Error first{AMG_OK, ""};
+        const int dev = bt->device;
+        auto worker = [&]() {
+            cudaStream_t ws = nullptr;
+            try {
+                AMG_CUDA(cudaSetDevice(dev));
+                AMG_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+                AMG_CUDA(cudaStreamWaitEvent(ws, ready, 0));
+                for (int t; (t = next.fetch_add(1)) < nprob;) {
+                    {
+                        std::lock_guard<std::mutex> g(err_m);
+                        if (first.status != AMG_OK) break;  // another system failed: stop
+                    }
+                    const int p = order[t];
+                    const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
+                    const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
+                    Scratch loc(ws);
+                    int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
+                    k_localize_rows<<<(n + 256) / 256, 256, 0, ws>>>(n, rp + r0, z0, lrp);
+                    k_localize_cols<<<(nnz + 255) / 256, 256, 0, ws>>>(nnz, cl + z0, r0, lcl);
+                    AMG_CUDA(cudaGetLastError());
+                    amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
+                    // returns after its work is done, so the localized arrays may be freed
+                    bt->hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, ws);
+                }
+            } catch (const Error &e) {
+                std::lock_guard<std::mutex> g(err_m);
+                if (first.status == AMG_OK) first = e;
+            } catch (const std::bad_alloc &) {
+                std::lock_guard<std::mutex> g(err_m);
+                if (first.status == AMG_OK) first = Error{AMG_ERR_OOM, "host allocation failed"};
+            } catch (...) {
+                std::lock_guard<std::mutex> g(err_m);
+                if (first.status == AMG_OK) first = Error{AMG_ERR_CUDA, "unexpected internal exception"};
+            }
+            if (ws) {
+                cudaStreamSynchronize(ws);
+                cudaStreamDestroy(ws);
+            }
+        };
+        const int nw = std::max(1, std::min({nprob, 16, (int)std::thread::hardware_concurrency()}));
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nw; w++) pool.emplace_back(worker);
+        worker();
+        for (std::thread &t : pool) t.join();
+        cudaEventDestroy(ready);
+        if (first.status != AMG_OK) throw first;
         bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, 0);
         AMG_CUDA(cudaStreamSynchronize(us));
         *out = bt;

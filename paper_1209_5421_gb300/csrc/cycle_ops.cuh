@@ -25,6 +25,9 @@ enum OpKind : int {
     OP_TAIL,          // persistent program: CTA 0 runs the tail program in shared memory
     OP_NOP,           // persistent program: only the prologue (finalise a reduction)
     OP_GS_FIRST,      // point GS from zero, first colour: u_i = f_i / a_ii on [i0, i1), 0 elsewhere
+    OP_RESID,         // first pass of a split restriction: q_step = f - A u (row by row)
+    OP_GATHER,        // second pass: next.rhs[R] = sum of q_step over R's children
+    OP_NKINDS
 };
 
 struct Op {
@@ -45,7 +48,13 @@ struct Op {
     // RESTRICT for B^ of the next level (u = next.p_0, f = next.rhs), UPDATE (not last) for
     // the next Alg. 1 step (u = p_{i+1}, f = r)
     int fuse, f0, f1;
+    // finest level, grid-wide executors: big blocks (aggregates of more than kBigBlockRows
+    // unknowns) [bb0, bb1) of L.big->ids, swept by warps ([bb0, bbc)) and whole CTAs ([bbc,
+    // bb1)) for GS (this colour's), summed by CTAs for RESTRICT (all); 0, 0, 0 = none (every
+    // block is one thread's, as in the batch and tail executors)
+    int bb0, bbc, bb1;
 };
+
 
 enum : int { V_RHS = 0, V_E, V_R, V_P0 };  // V_P0 + i = p_i
 
@@ -68,6 +77,7 @@ struct LevelDev {
     const T *dinv;                  // 1 / a_ii (smoother)
     const unsigned short *col16;    // 16-bit copy of col (levels read by the tail from HBM)
     const int *bptr;
+    const BigSched *big;            // finest level: the big blocks' sweep schedule, or NULL
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
     const int4 *children2;          // octree: their children 4..7 (NULL on a quadtree)
@@ -95,6 +105,7 @@ struct StagedLevel {
     const T *val;
     const T *dinv;
     const int *bptr;                // unused (fine = 0)
+    static constexpr const BigSched *big = nullptr;
     const int *parent;
     const int4 *children;           // children of the NEXT coarser level's rows
     const int4 *children2;          // octree: their children 4..7 (NULL on a quadtree)
@@ -441,7 +452,7 @@ __device__ __forceinline__ void gs_block_seq(const LV &L, int b, bool backward,
 
 template <class LV>
 __device__ void op_gs_blocks_coop(const LV &L, const Op &op, const typename LV::val_t *f,
-                                  typename LV::val_t *u, int tid, int nth) {
+                                  typename LV::val_t *u, int tid, int nth, bool skip_big) {
     using T = typename LV::val_t;
     using I = typename LV::idx_t;
     constexpr int G = kBlockLanes;
@@ -457,7 +468,7 @@ __device__ void op_gs_blocks_coop(const LV &L, const Op &op, const typename LV::
             k = L.bptr[b + 1] - r0;
         }
         if (k > G) {  // the same for the whole group
-            if (q == 0) gs_block_seq(L, b, bwd, f, u);
+            if (q == 0 && !(skip_big && k > kBigBlockRows)) gs_block_seq(L, b, bwd, f, u);
             continue;
         }
         const bool has = q < k;
@@ -526,19 +537,70 @@ __device__ void op_gs_blocks_coop(const LV &L, const Op &op, const typename LV::
     }
 }
 
-// one colour: independent blocks (finest level, rows of a block in sweep order) or rows
+// Gauss-Seidel update of row i whose slots start at `base` (gs_row without the slice lookup)
 template <class LV>
+__device__ __forceinline__ void gs_row_at(const LV &L, int i, int base, int width,
+                                          const typename LV::val_t *f, typename LV::val_t *u) {
+    u[i] = (f[i] - row_dot(L, base, 1, width, u)) * L.dinv[i];
+}
+
+// the big blocks of one colour in level order: [op.bb0, op.bbc) one warp each (__syncwarp
+// between levels), [op.bbc, op.bb1) one CTA each (CTA barrier between levels). tid, nth:
+// the executor's global thread index and count (whole warps). Every thread of the grid calls
+// this.
+template <class LV>
+__device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::val_t *f,
+                                 typename LV::val_t *u, int tid, int nth) {
+    const BigSched *S = L.big;
+    const bool bwd = op.backward != 0;
+    const int *lofs = bwd ? S->lofs_b : S->lofs_f;
+    const int *lp = bwd ? S->lp_b : S->lp_f;
+    const int4 *ent = bwd ? S->ent_b : S->ent_f;
+    const int lane = tid & 31;
+    for (int k = op.bb0 + (tid >> 5); k < op.bbc; k += nth >> 5) {  // warp-sized blocks
+        const int l1 = lofs[k + 1];
+        for (int j = lofs[k]; j < l1; j++) {
+            const int b = lp[j + 1];
+            for (int p = lp[j] + lane; p < b; p += 32) {
+                const int4 e = ent[p];
+                gs_row_at(L, e.x, e.y, e.z, f, u);
+            }
+            __syncwarp();  // this level's values are read by the next level's rows
+        }
+    }
+    for (int k = op.bbc + (int)blockIdx.x; k < op.bb1; k += (int)gridDim.x) {  // larger blocks
+        const int l1 = lofs[k + 1];
+        for (int j = lofs[k]; j < l1; j++) {
+            const int b = lp[j + 1];
+            for (int p = lp[j] + (int)threadIdx.x; p < b; p += (int)blockDim.x) {
+                const int4 e = ent[p];
+                gs_row_at(L, e.x, e.y, e.z, f, u);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// one colour: independent blocks (finest level, rows of a block in sweep order) or rows.
+// BIG (the grid-wide executors, whose programs set op.bb0, op.bb1): the colour's big blocks
+// are left to the CTA phase at the end. Other executors never see big-block ranges and do
+// not compile that phase (nor its shared memory).
+template <class LV, bool BIG = false>
 __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
                       typename LV::val_t *u, int tid, int nth) {
+    const bool big = BIG && L.fine && op.bb1 > op.bb0;
     if constexpr (LV::coop) {
         if (L.fine && L.bg > 0) {
-            op_gs_blocks_coop(L, op, f, u, tid, nth);
+            op_gs_blocks_coop(L, op, f, u, tid, nth, big);
+            if constexpr (BIG)
+                if (big) op_gs_big_blocks(L, op, f, u, tid, nth);
             return;
         }
     }
     for (int b = op.i0 + tid; b < op.i1; b += nth) {
         if (L.fine) {
             const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
+            if (big && r1 - r0 > kBigBlockRows) continue;  // a CTA's, below
             if (!op.backward)
                 for (int i = r0; i < r1; i++) gs_row(L, i, f, u);
             else
@@ -547,6 +609,8 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
             gs_row(L, b, f, u);
         }
     }
+    if constexpr (BIG)
+        if (big) op_gs_big_blocks(L, op, f, u, tid, nth);
 }
 
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
@@ -554,11 +618,57 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
 // explicit form), one lane per child and a shuffle tree (nth must be a multiple of 32)
 // With un non-null, the next level's smoothing starts here as well (Op::fuse):
 // un[R] = fc[R] / a_RR on the next level's first colour [f0, f1), 0 elsewhere.
+// fc of the finest level's big blocks: a warp per block of up to kWarpBlockRows rows, a CTA
+// per larger block; the rows' residuals summed per lane (thread), then over the warp (CTA)
+// in a fixed order. tid, nth: the executor's global thread index and count (whole warps).
+// Every thread of the grid calls this.
+template <class LV>
+__device__ void restrict_big_blocks(const LV &L, const typename LV::val_t *f,
+                                    const typename LV::val_t *u, typename LV::val_t *fc,
+                                    typename LV::val_t *un, const typename LV::val_t *dinv_n,
+                                    int f0, int f1, int tid, int nth) {
+    using T = typename LV::val_t;
+    const BigSched *S = L.big;
+    const int lane = tid & 31;
+    for (int k = tid >> 5; k < S->nbig; k += nth >> 5) {
+        const int R = S->ids[k];
+        const int r0 = L.bptr[R], r1 = L.bptr[R + 1];
+        if (r1 - r0 > kWarpBlockRows) continue;  // a CTA's, below
+        T v = 0;
+        for (int i = r0 + lane; i < r1; i += 32) v += row_residual(L, i, f, u);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            fc[R] = v;
+            if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
+        }
+    }
+    for (int k = (int)blockIdx.x; k < S->nbig; k += (int)gridDim.x) {
+        const int R = S->ids[k];
+        const int r0 = L.bptr[R], r1 = L.bptr[R + 1];
+        if (r1 - r0 <= kWarpBlockRows) continue;  // a warp's, above
+        T v[1] = {T(0)};
+        for (int i = r0 + (int)threadIdx.x; i < r1; i += (int)blockDim.x)
+            v[0] += row_residual(L, i, f, u);
+        double r[1];
+        block_sum<1, T>(v, r, BlockGroup{});
+        if (threadIdx.x == 0) {
+            const T sum = (T)r[0];
+            fc[R] = sum;
+            if (un) un[R] = (R >= f0 && R < f1) ? sum * dinv_n[R] : T(0);
+        }
+        __syncthreads();  // the reduction scratch is used again by the next block
+    }
+}
+
+// big = true (grid-wide executors, finest level with big blocks): blocks of more than
+// kBigBlockRows rows are summed by whole CTAs at the end
 template <class LV>
 __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             const typename LV::val_t *u, typename LV::val_t *fc, int tid,
                             int nth, typename LV::val_t *un = nullptr,
-                            const typename LV::val_t *dinv_n = nullptr, int f0 = 0, int f1 = 0) {
+                            const typename LV::val_t *dinv_n = nullptr, int f0 = 0, int f1 = 0,
+                            bool big = false) {
     using T = typename LV::val_t;
     if constexpr (LV::coop) {  // kBlockLanes lanes per aggregate: a row each, then a shuffle sum
         if (L.fine && L.bg > 0) {
@@ -567,26 +677,32 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
             for (int base = 0; base < L.nnext; base += nth / G) {
                 const int R = base + tid / G;
                 T v = 0;
-                if (R < L.nnext)
+                bool mine = R < L.nnext;
+                if (mine && big && L.bptr[R + 1] - L.bptr[R] > kBigBlockRows) mine = false;
+                if (mine)
                     for (int i = L.bptr[R] + q; i < L.bptr[R + 1]; i += G)
                         v += row_residual(L, i, f, u);
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (R < L.nnext && q == 0) {
+                if (mine && q == 0) {
                     fc[R] = v;
                     if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
                 }
             }
+            if (big) restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth);
             return;
         }
     }
     if (L.fine) {
         for (int R = tid; R < L.nnext; R += nth) {
+            const int r0 = L.bptr[R], r1 = L.bptr[R + 1];
+            if (big && r1 - r0 > kBigBlockRows) continue;  // a CTA's, below
             T acc = 0;
-            for (int i = L.bptr[R]; i < L.bptr[R + 1]; i++) acc += row_residual(L, i, f, u);
+            for (int i = r0; i < r1; i++) acc += row_residual(L, i, f, u);
             fc[R] = acc;
             if (un) un[R] = (R >= f0 && R < f1) ? acc * dinv_n[R] : T(0);
         }
+        if (big) restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth);
         return;
     }
     const bool oct = L.children2 != nullptr;
@@ -608,6 +724,41 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
             fc[R] = v;
             if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
         }
+    }
+}
+
+// The restriction of a coarse level in two passes, for executors where the children of
+// consecutive coarse rows are far apart (they lie in different colours): t = f - A u row by
+// row (consecutive rows, contiguous slots), then fc[R] = the sum of t over R's children.
+// The sum is taken in op_restrict's order ((t0 + t1) + (t2 + t3), octree + ((t4 + t5) +
+// (t6 + t7)), missing children as 0), so both forms give the same bits.
+template <class LV>
+__device__ void op_resid(const LV &L, const typename LV::val_t *f, const typename LV::val_t *u,
+                         typename LV::val_t *t, int tid, int nth) {
+    for (int i = tid; i < L.n; i += nth) t[i] = row_residual(L, i, f, u);
+}
+
+template <class LV>
+__device__ void op_gather_children(const LV &L, const typename LV::val_t *t,
+                                   typename LV::val_t *fc, int tid, int nth,
+                                   typename LV::val_t *un = nullptr,
+                                   const typename LV::val_t *dinv_n = nullptr, int f0 = 0,
+                                   int f1 = 0) {
+    using T = typename LV::val_t;
+    const bool oct = L.children2 != nullptr;
+    for (int R = tid; R < L.nnext; R += nth) {
+        const int4 ch = L.children[R];
+        const T a0 = ch.x >= 0 ? t[ch.x] : T(0), a1 = ch.y >= 0 ? t[ch.y] : T(0);
+        const T a2 = ch.z >= 0 ? t[ch.z] : T(0), a3 = ch.w >= 0 ? t[ch.w] : T(0);
+        T v = (a0 + a1) + (a2 + a3);
+        if (oct) {
+            const int4 c2 = L.children2[R];
+            const T b0 = c2.x >= 0 ? t[c2.x] : T(0), b1 = c2.y >= 0 ? t[c2.y] : T(0);
+            const T b2 = c2.z >= 0 ? t[c2.z] : T(0), b3 = c2.w >= 0 ? t[c2.w] : T(0);
+            v = v + ((b0 + b1) + (b2 + b3));
+        }
+        fc[R] = v;
+        if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
     }
 }
 
@@ -653,15 +804,16 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
     // the lanes of a warp read 32 / g rows at once: lane `sub` of a row reads columns
     // sub + g t, t < T, starting at t = its row group in the warp, so that rows whose stride
     // is a multiple of the 32 shared-memory banks do not read the same banks in the same step
-    const int T_ = (n + g - 1) / g, rot = (tid & 31) / g;
+    const int T_ = (n + g - 1) / g, rot = ((tid & 31) / g) % T_;
     for (int base = 0; base < n; base += rows_per_pass) {
         const int i = base + tid / g;
         if constexpr (sizeof(T) == 4) {
             float s = 0.f, c = 0.f;  // running sum, sum of all rounding errors
             if (i < n) {
                 const float *ah = L.Ainv2 + (size_t)i * n, *al = ah + (size_t)n * n;
-                for (int tt = 0; tt < T_; tt++) {
-                    const int j = sub + g * ((tt + rot) % T_);
+                // column group tt' = (tt + rot) mod T_, wrapped by a compare (no division)
+                for (int tt = 0, tw = rot; tt < T_; tt++, tw = (tw + 1 == T_) ? 0 : tw + 1) {
+                    const int j = sub + g * tw;
                     if (j >= n) continue;
                     const float x = L.rhs[j];
                     const float ph = __fmul_rn(ah[j], x);
@@ -685,8 +837,8 @@ __device__ void op_coarse(const LV &L, int tid, int nth) {
             double s = 0.0;
             if (i < n) {
                 const double *a = L.Ainv + (size_t)i * n;
-                for (int tt = 0; tt < T_; tt++) {
-                    const int j = sub + g * ((tt + rot) % T_);
+                for (int tt = 0, tw = rot; tt < T_; tt++, tw = (tw + 1 == T_) ? 0 : tw + 1) {
+                    const int j = sub + g * tw;
                     if (j < n) s += a[j] * (double)L.rhs[j];
                 }
             }
@@ -825,12 +977,21 @@ __device__ __forceinline__ void run_op_on(const LV &L, const Next &next, const O
                                           const RedCtx &rc, int tid, int nth, const G &g) {
     switch (op.kind) {
         case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
-        case OP_GS: op_gs(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
+        case OP_GS: op_gs<LV, true>(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_GS_FIRST: op_gs_first(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_RESTRICT: {
             const auto &N = next();
             op_restrict(L, vec_of(L, op.fsel), vec_of(L, op.usel), N.rhs, tid, nth,
-                        op.fuse ? N.p[0] : nullptr, N.dinv, op.f0, op.f1);
+                        op.fuse ? N.p[0] : nullptr, N.dinv, op.f0, op.f1, op.bb1 > op.bb0);
+            break;
+        }
+        case OP_RESID:
+            op_resid(L, vec_of(L, op.fsel), vec_of(L, op.usel), pick(L.q, op.step), tid, nth);
+            break;
+        case OP_GATHER: {
+            const auto &N = next();
+            op_gather_children(L, pick(L.q, op.step), N.rhs, tid, nth, op.fuse ? N.p[0] : nullptr,
+                               N.dinv, op.f0, op.f1);
             break;
         }
         case OP_PROLONG: op_prolong(L, next().e, vec_of(L, op.usel), tid, nth); break;

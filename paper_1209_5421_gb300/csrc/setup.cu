@@ -6,6 +6,7 @@
 //   segmented reduction into stencil slots (eq. acsum / c-sum) -> coarsest exact inverse.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "amg_internal.cuh"
 
@@ -555,6 +556,60 @@ __global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, floa
 }
 
 // ---------------------------------------------------------------------------------------
+// big blocks of the finest level: flag[b] = 1 for blocks of more than kBigBlockRows rows
+__global__ void k_big_flag(int nb, const int *__restrict__ bptr, int *__restrict__ flag) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) flag[b] = (bptr[b + 1] - bptr[b] > kBigBlockRows) ? 1 : 0;
+}
+__global__ void k_big_compact(int nb, const int *__restrict__ flag, const int *__restrict__ pos,
+                              const int *__restrict__ bptr, int *__restrict__ ids,
+                              int2 *__restrict__ range) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb && flag[b]) {
+        ids[pos[b]] = b;
+        range[pos[b]] = make_int2(bptr[b], bptr[b + 1]);
+    }
+}
+
+// sweep levels of one big block per CTA: lf(i) = 1 + max lf(j) over the coupled rows j < i of
+// the block (0 if none), lb(i) the same over j > i. Monotone rounds from 0 until nothing
+// changes reach the longest dependency path (the fixed point) in at most depth + 1 rounds;
+// values read while others write in the same round only delay convergence. Bounded by the
+// block's row count.
+__global__ void k_big_levels(const int2 *__restrict__ range, const int *__restrict__ rofs,
+                             const int *__restrict__ sl, const int *__restrict__ col,
+                             int *lf, int *lb) {
+    const int k = blockIdx.x;
+    const int r0 = range[k].x, m = range[k].y - range[k].x, off = rofs[k];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        lf[off + i] = 0;
+        lb[off + i] = 0;
+    }
+    __syncthreads();
+    for (int round = 0; round <= m + 1; round++) {
+        int changed = 0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int row = r0 + i, a = sl[row >> 5], w = (sl[(row >> 5) + 1] - a) >> 5;
+            int vf = 0, vb = 0;
+            for (int t = 0; t < w; t++) {
+                const int j = col[a + 32 * t + (row & 31)] - r0;
+                if (j < 0 || j >= m || j == i) continue;
+                if (j < i) vf = max(vf, ((volatile int *)lf)[off + j] + 1);
+                else vb = max(vb, ((volatile int *)lb)[off + j] + 1);
+            }
+            if (vf != lf[off + i]) {
+                lf[off + i] = vf;
+                changed = 1;
+            }
+            if (vb != lb[off + i]) {
+                lb[off + i] = vb;
+                changed = 1;
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+}
+
 int read_int(const int *d, cudaStream_t s) {
     int v = 0;
     AMG_CUDA(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -741,6 +796,108 @@ void galerkin(amg_hierarchy *h, Level &f, Level &c, bool fine) {
     else launch_rap<false>(h, f, c, true, nullptr);
 }
 
+// the finest level's big blocks and their level-ordered sweep schedules (forward and
+// backward); the levels come from the device, the orders are built here
+void build_big_blocks(amg_hierarchy *h, Level &F) {
+    cudaStream_t s = h->stream;
+    const int nb = F.nblocks;
+    const int ncol = (int)F.color_blocks.size() - 1;
+    Scratch tmp(s);
+    int *flag = tmp.get<int>(nb), *pos = tmp.get<int>(nb), *tot = tmp.get<int>(1);
+    k_big_flag<<<nblocks_for(nb, 256), 256, 0, s>>>(nb, F.bptr, flag);
+    AMG_LAUNCH_CHECK();
+    exclusive_scan(flag, pos, nb, tot, s);
+    const int nbig = read_int(tot, s);
+    F.nbig = nbig;
+    F.color_big.assign(ncol + 1, 0);
+    F.color_bigc.assign(ncol, 0);
+    if (nbig == 0) return;
+    int *ids_asc = tmp.get<int>(nbig);
+    int2 *range_asc = tmp.get<int2>(nbig);
+    k_big_compact<<<nblocks_for(nb, 256), 256, 0, s>>>(nb, flag, pos, F.bptr, ids_asc, range_asc);
+    AMG_LAUNCH_CHECK();
+    std::vector<int> hid = read_ints(ids_asc, nbig, s);
+    std::vector<int2> hra(nbig);
+    AMG_CUDA(cudaMemcpyAsync(hra.data(), range_asc, sizeof(int2) * nbig, cudaMemcpyDeviceToHost, s));
+    std::vector<int> sl = read_ints(F.A.sl_ptr, F.A.nslices + 1, s);
+    // colour by colour (ids ascending: colours are block ranges), warp-sized blocks first
+    std::vector<int> ord;
+    ord.reserve(nbig);
+    for (int c = 0; c < ncol; c++) {
+        const int a = (int)(std::lower_bound(hid.begin(), hid.end(), F.color_blocks[c]) - hid.begin());
+        const int b = (int)(std::lower_bound(hid.begin(), hid.end(), F.color_blocks[c + 1]) - hid.begin());
+        F.color_big[c] = (int)ord.size();
+        for (int k = a; k < b; k++)
+            if (hra[k].y - hra[k].x <= kWarpBlockRows) ord.push_back(k);
+        F.color_bigc[c] = (int)ord.size();
+        for (int k = a; k < b; k++)
+            if (hra[k].y - hra[k].x > kWarpBlockRows) ord.push_back(k);
+    }
+    F.color_big[ncol] = (int)ord.size();
+    std::vector<int> ids(nbig), rofs(nbig + 1, 0);
+    std::vector<int2> hr(nbig);
+    for (int k = 0; k < nbig; k++) {
+        ids[k] = hid[ord[k]];
+        hr[k] = hra[ord[k]];
+        rofs[k + 1] = rofs[k] + (hr[k].y - hr[k].x);
+    }
+    const int R = rofs[nbig];
+    int2 *range = tmp.get<int2>(nbig);
+    int *d_rofs = tmp.get<int>(nbig + 1), *lf = tmp.get<int>(R), *lb = tmp.get<int>(R);
+    AMG_CUDA(cudaMemcpyAsync(range, hr.data(), sizeof(int2) * nbig, cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemcpyAsync(d_rofs, rofs.data(), sizeof(int) * (nbig + 1),
+                             cudaMemcpyHostToDevice, s));
+    k_big_levels<<<nbig, 256, 0, s>>>(range, d_rofs, F.A.sl_ptr, F.A.col, lf, lb);
+    AMG_LAUNCH_CHECK();
+    std::vector<int> hf = read_ints(lf, R, s), hb = read_ints(lb, R, s);
+    // counting sort of each block's rows by level (rows ascending inside a level); an entry
+    // carries the row's first slot and slot count, so the sweep reads no slice pointer
+    std::vector<int4> ent_f(R), ent_b(R);
+    std::vector<int> lofs_f(nbig + 1), lofs_b(nbig + 1), lp_f, lp_b;
+    auto order = [&](const std::vector<int> &lv, std::vector<int4> &ent, std::vector<int> &lofs,
+                     std::vector<int> &lp) {
+        for (int k = 0; k < nbig; k++) {
+            const int a = rofs[k], m = rofs[k + 1] - a, r0 = hr[k].x;
+            int depth = 0;
+            for (int i = 0; i < m; i++) depth = std::max(depth, lv[a + i] + 1);
+            std::vector<int> cnt(depth + 1, 0);
+            for (int i = 0; i < m; i++) cnt[lv[a + i] + 1]++;
+            for (int j = 0; j < depth; j++) cnt[j + 1] += cnt[j];
+            lofs[k] = (int)lp.size();
+            for (int j = 0; j < depth; j++) lp.push_back(a + cnt[j]);
+            std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+            for (int i = 0; i < m; i++) {
+                const int row = r0 + i, sa = sl[row >> 5];
+                ent[a + fill[lv[a + i]]++] =
+                    make_int4(row, sa + (row & 31), (sl[(row >> 5) + 1] - sa) >> 5, 0);
+            }
+        }
+        lofs[nbig] = (int)lp.size();
+        lp.push_back(R);
+    };
+    order(hf, ent_f, lofs_f, lp_f);
+    order(hb, ent_b, lofs_b, lp_b);
+    auto up = [&](const auto &v) {
+        using E = typename std::decay_t<decltype(v)>::value_type;
+        E *d = halloc<E>(h, v.size());
+        AMG_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(E) * v.size(), cudaMemcpyHostToDevice, s));
+        return (const E *)d;
+    };
+    BigSched S;
+    S.nbig = nbig;
+    S.ids = up(ids);
+    S.lofs_f = up(lofs_f);
+    S.lofs_b = up(lofs_b);
+    S.lp_f = up(lp_f);
+    S.lp_b = up(lp_b);
+    S.ent_f = up(ent_f);
+    S.ent_b = up(ent_b);
+    BigSched *d = halloc<BigSched>(h, 1);
+    AMG_CUDA(cudaMemcpyAsync(d, &S, sizeof S, cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaStreamSynchronize(s));  // the host vectors above are locals
+    F.big_dev = d;
+}
+
 void coarsest_inverse(amg_hierarchy *h, Level &lv) {
     cudaStream_t s = h->stream;
     int n = lv.n;
@@ -753,12 +910,13 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
         k_dense_from_sell<<<nblocks_for(n, kT), kT, 0, s>>>(n, lv.A.sl_ptr, lv.A.col, lv.A.val,
                                                           lv.Ainv);
         AMG_LAUNCH_CHECK();
-        static bool attr = false;  // opt in to more than 48 KB once per process
-        if (!attr) {
+        // opt in to more than 48 KB once per process (thread-safe: setups may run in parallel)
+        static const bool attr = [] {
             AMG_CUDA(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           160 * 1024));
-            attr = true;
-        }
+            return true;
+        }();
+        (void)attr;
         k_chol_inverse<<<1, 1024, smem, s>>>(n, nullptr, nullptr, lv.Ainv, lv.Ainv32, h->err_flag);
     } else {
         double *a = tmp.get<double>((size_t)n * n);
@@ -968,6 +1126,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         AMG_LAUNCH_CHECK();
         F.A.stored = Ain.nnz;
         color_nnz(h, F, len);
+        build_big_blocks(h, F);
 
         // ---- A_1 = P^t A P
         galerkin(h, F, C1, true);

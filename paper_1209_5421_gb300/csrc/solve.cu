@@ -33,6 +33,10 @@ constexpr int kPThreads64 = 512;
 template <class T>
 constexpr int cycle_threads() { return sizeof(T) == 8 ? kPThreads64 : kPThreads; }
 constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
+// coarse levels of at least this many rows restrict in two grid-wide passes (OP_RESID,
+// OP_GATHER): their rows' children lie in different colours, far apart in HBM, and the
+// one-pass form's four-lane gathers read scattered slots
+constexpr int kSplitRestrictRows = 131072;
 
 
 // shared-memory image of the tail levels (byte offsets into the dynamic shared memory)
@@ -76,6 +80,8 @@ struct CycleArgs {
     // arrivals the first barrier waits for beyond the grid's (0: none)
     unsigned long long bar_limit_ns;
     int bar_extra;
+    // the finest level's input and output vectors when not the table's (FGMRES basis vectors)
+    T *rhs0, *e0;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -216,13 +222,19 @@ __device__ __forceinline__ void phase_pre(const LV &L, const G &g, int nth, int 
             g.sync();
             tail_mark(l, OP_GS);
         }
+    // next.rhs = P^t (f - A u1) in two passes: the residual row by row into q_i (free until
+    // step i's SpMV writes it), then the children sums
+    T *t = pick(L.q, i);
+    op_resid(L, f, z, t, tid, nth);
+    g.sync();
+    tail_mark(l, OP_RESID);
     const StagedLevel<T, W> N = staged_level<T, W>(l + 1);
     if (tail_lay[l + 1].Ainv < 0) {  // the next level smooths: its first colour too
         int f0, f1;
         tail_first_colour(l + 1, f0, f1);
-        op_restrict(L, f, z, N.rhs, tid, nth, N.p[0], N.dinv, f0, f1);
+        op_gather_children(L, t, N.rhs, tid, nth, N.p[0], N.dinv, f0, f1);
     } else {
-        op_restrict(L, f, z, N.rhs, tid, nth);
+        op_gather_children(L, t, N.rhs, tid, nth);
     }
     g.sync();
     tail_mark(l, OP_RESTRICT);
@@ -527,6 +539,11 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
         const int words = a.lay.nlev * (int)(sizeof(GL) / sizeof(int));
         for (int i = threadIdx.x; i < words; i += blockDim.x)
             ((int *)gtab)[i] = ((const int *)a.tab)[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (a.rhs0) gtab[0].rhs = a.rhs0;
+        if (a.e0) gtab[0].e = a.e0;
     }
     if (blockIdx.x == 0 && a.lay.tl < a.lay.nlev) stage_tail(a);
     __syncthreads();
@@ -835,7 +852,7 @@ __global__ void k_lincomb(int n, double *__restrict__ x, double *const *__restri
 // diagnostics: per-kernel timing and algorithmic bytes
 thread_local int64_t g_launches = 0;
 
-enum : int { K_CYCLE = 12, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
+enum : int { K_CYCLE = OP_NKINDS, K_OUTER_MULTIDOT, K_OUTER_ORTH, K_OUTER_SPMV_DOT, K_OUTER_UPDATE,
              K_TRUE_RESIDUAL, K_FGMRES_SPMV, K_FGMRES_MDOT, K_FGMRES_ORTH, K_NUM };
 constexpr int K_IN_CYCLE = 100;  // + op kind: an op timed inside the persistent kernel
 constexpr int K_IN_TAIL = 200;   // + op kind: an op timed inside the shared-memory tail
@@ -844,23 +861,26 @@ const char *kernel_name(int kind) {
     static const char *names[K_NUM] = {"zero", "gs_colour", "resid_restrict", "prolong_correct",
                                        "coarse_solve", "alg1_multidot", "alg1_orth",
                                        "alg1_spmv_dot", "alg1_update", "tail_cta", "barrier_only",
-                                       "gs_first_colour",
+                                       "gs_first_colour", "residual", "restrict_gather",
                                        "cycle_persistent", "outer_multidot", "outer_orth",
                                        "outer_spmv_dot", "outer_update", "true_residual",
                                        "fgmres_spmv", "fgmres_mdot", "fgmres_orth_sub"};
-    static const char *incycle[12] = {"in_cycle:zero", "in_cycle:gs_colour",
-                                      "in_cycle:resid_restrict", "in_cycle:prolong_correct",
-                                      "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
-                                      "in_cycle:alg1_orth", "in_cycle:alg1_spmv_dot",
-                                      "in_cycle:alg1_update", "in_cycle:tail_cta",
-                                      "in_cycle:barrier_only", "in_cycle:gs_first_colour"};
-    static const char *intail[12] = {"in_tail:zero", "in_tail:gs_colour", "in_tail:resid_restrict",
-                                     "in_tail:prolong_correct", "in_tail:coarse_solve",
-                                     "in_tail:alg1_multidot", "in_tail:alg1_orth",
-                                     "in_tail:alg1_spmv_dot", "in_tail:alg1_update", "in_tail:?",
-                                     "in_tail:?", "in_tail:gs_first_colour"};
-    if (kind >= K_IN_CYCLE && kind < K_IN_CYCLE + 12) return incycle[kind - K_IN_CYCLE];
-    if (kind >= K_IN_TAIL && kind < K_IN_TAIL + 12) return intail[kind - K_IN_TAIL];
+    static const char *incycle[OP_NKINDS] = {"in_cycle:zero", "in_cycle:gs_colour",
+                                             "in_cycle:resid_restrict", "in_cycle:prolong_correct",
+                                             "in_cycle:coarse_solve", "in_cycle:alg1_multidot",
+                                             "in_cycle:alg1_orth", "in_cycle:alg1_spmv_dot",
+                                             "in_cycle:alg1_update", "in_cycle:tail_cta",
+                                             "in_cycle:barrier_only", "in_cycle:gs_first_colour",
+                                             "in_cycle:residual", "in_cycle:restrict_gather"};
+    static const char *intail[OP_NKINDS] = {"in_tail:zero", "in_tail:gs_colour",
+                                            "in_tail:resid_restrict", "in_tail:prolong_correct",
+                                            "in_tail:coarse_solve", "in_tail:alg1_multidot",
+                                            "in_tail:alg1_orth", "in_tail:alg1_spmv_dot",
+                                            "in_tail:alg1_update", "in_tail:?", "in_tail:?",
+                                            "in_tail:gs_first_colour", "in_tail:residual",
+                                            "in_tail:restrict_gather"};
+    if (kind >= K_IN_CYCLE && kind < K_IN_CYCLE + OP_NKINDS) return incycle[kind - K_IN_CYCLE];
+    if (kind >= K_IN_TAIL && kind < K_IN_TAIL + OP_NKINDS) return intail[kind - K_IN_TAIL];
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "unknown";
 }
 
@@ -970,6 +990,10 @@ static double op_bytes(const amg_hierarchy *h, const Op &op, int w) {
         }
         case OP_RESTRICT:
             return nnz * (4 + w) + 2.0 * w * n + w * nn + (op.level == 0 ? 4.0 * nn : 16.0 * nn);
+        // the two passes of a split restriction: the restriction's bytes, shared out (the
+        // intermediate residual vector is the split's own traffic, not the method's)
+        case OP_RESID: return nnz * (4 + w) + 2.0 * w * n;
+        case OP_GATHER: return w * nn + 16.0 * nn;
         case OP_PROLONG: return 2.0 * w * n + 4.0 * n + w * nn;
         case OP_COARSE: return w * n * n + 2.0 * w * n;
         case OP_MULTIDOT: return w * n * (1 + op.step);
@@ -1058,6 +1082,15 @@ struct Builder {
         return l >= 1 && l < h->nlev && l != stop_level && !h->lev[l].coarsest;
     }
 
+    // the big blocks of colour c on the finest level go to whole CTAs (grid-wide programs)
+    void big_range(int l, int c, Op &g) const {
+        const Level &lv = h->lev[l];
+        if (l != 0 || lv.nbig == 0) return;
+        g.bb0 = lv.color_big[c];
+        g.bbc = lv.color_bigc[c];
+        g.bb1 = lv.color_big[c + 1];
+    }
+
     // z = B^_l [f] (Alg. 2). first_done: the first colour of the pre-smoothing was already
     // done by the op before (a fused RESTRICT or UPDATE)
     void bhat(int l, int fsel, int zsel, bool first_done = false) {
@@ -1090,15 +1123,28 @@ struct Builder {
                 g.i1 = ranges[c + 1];
                 g.fsel = fsel;
                 g.usel = zsel;
+                big_range(l, c, g);
                 emit(g);
             }
         Op rs = mk(OP_RESTRICT, l);  // next.rhs = P^t (f - A u1)
         rs.fsel = fsel;
         rs.usel = zsel;
+        if (l == 0 && lv.nbig > 0) rs.bb1 = lv.nbig;  // every big block, by whole CTAs
         const bool fuse = starts_with_first_colour(l + 1);
         if (fuse) {  // and the next level's first colour from zero
             rs.fuse = 1;
             first_colour(l + 1, rs.f0, rs.f1);
+        }
+        if (l >= 1 && lv.n >= kSplitRestrictRows) {
+            // a large coarse level: the residual row by row into q_step, then the children
+            // sums (coalesced slots instead of a gather over four colours' rows)
+            Op rr = mk(OP_RESID, l);
+            rr.fsel = fsel;
+            rr.usel = zsel;
+            rr.step = zsel - V_P0;
+            emit(rr);
+            rs.kind = OP_GATHER;
+            rs.step = zsel - V_P0;
         }
         emit(rs);
         btilde(l + 1, fuse);         // next.e = B~_{k-1}[next.rhs]
@@ -1114,6 +1160,7 @@ struct Builder {
                 g.backward = 1;
                 g.fsel = fsel;
                 g.usel = zsel;
+                big_range(l, c, g);
                 emit(g);
             }
     }
@@ -1219,6 +1266,7 @@ void fill_tables(amg_hierarchy *h) {
         else d.dinv = (const T *)lv.dinv32;
         d.col16 = lv.col16;
         d.bptr = lv.bptr;
+        d.big = (l == 0) ? lv.big_dev : nullptr;
         d.parent = lv.parent;
         d.children = (l + 1 < h->nlev) ? h->lev[l + 1].children : nullptr;
         d.children2 = (l + 1 < h->nlev) ? h->lev[l + 1].children2 : nullptr;
@@ -1502,12 +1550,14 @@ void ensure_fp32(amg_hierarchy *h) {
 
 // one launch of the persistent kernel: z = B^_0 [r] on level 0's table buffers
 template <class T>
-void launch_cycle(amg_hierarchy *h) {
+void launch_cycle(amg_hierarchy *h, T *rhs0 = nullptr, T *e0 = nullptr) {
     EngineBase *E = engine_slot<T>(h);
     cudaStream_t s = h->stream;
     const bool prof = profiling(h);
     CycleArgs<T> a;
     a.tab = dtab<T>(h);
+    a.rhs0 = rhs0;
+    a.e0 = e0;
     a.prog = E->prog;
     a.nops = E->nops;
     a.tail_colors = E->tail_colors;
@@ -1699,24 +1749,33 @@ static void check_device_error(amg_hierarchy *h) {
 }
 
 // one application of B^_0 to h->ro (FP64) into h->zo (FP64)
-static void apply_preconditioner(amg_hierarchy *h) {
+// out = B^_0 [in] (FP64 vectors; in = h->ro, out = h->zo unless given: the FGMRES basis
+// passes its vectors directly)
+static void apply_preconditioner(amg_hierarchy *h, const double *in = nullptr,
+                                 double *out = nullptr) {
     cudaStream_t s = h->stream;
     const int n = (int)h->N;
-    if (h->nlev == 1) {  // exact solve on the only level
+    if (!in) in = h->ro;
+    if (!out) out = h->zo;
+    if (h->nlev == 1) {  // exact solve on the only level (table vectors ro -> zo)
+        if (in != h->ro)
+            AMG_CUDA(cudaMemcpyAsync(h->ro, in, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         Op op = Builder::mk(OP_COARSE, 0);
         RedCtx rc{h->red_partials, h->red_counter};
         k_op<double><<<1, kRedThreads, 0, s>>>(dtab<double>(h), op, rc);
         AMG_LAUNCH_CHECK();
+        if (out != h->zo)
+            AMG_CUDA(cudaMemcpyAsync(out, h->zo, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         return;
     }
     if (h->opt.cycle_prec == AMG_FP32) {
-        k_convert<double, float><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->ro, h->r32);
+        k_convert<double, float><<<nblocks_for(n, 256), 256, 0, s>>>(n, in, h->r32);
         AMG_LAUNCH_CHECK();
         launch_cycle<float>(h);
-        k_convert<float, double><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->z32, h->zo);
+        k_convert<float, double><<<nblocks_for(n, 256), 256, 0, s>>>(n, h->z32, out);
         AMG_LAUNCH_CHECK();
     } else {
-        launch_cycle<double>(h);
+        launch_cycle<double>(h, const_cast<double *>(in), out);
     }
 }
 
@@ -1895,9 +1954,7 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
         bool done = false;
         for (; j < m && it < maxit; j++) {
             // Z[j] = B^[V[j]]
-            AMG_CUDA(cudaMemcpyAsync(h->ro, h->P[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            apply_preconditioner(h);
-            AMG_CUDA(cudaMemcpyAsync(h->P[m + 1 + j], h->zo, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            apply_preconditioner(h, h->P[j], h->P[m + 1 + j]);
             // w = A Z[j], orthogonalised twice against V[0..j]
             Profiler::Rec rec{};
             if (prof) rec = h->prof->begin(K_FGMRES_SPMV, 0, 12.0 * nnzf + 16.0 * nd, s);
@@ -2067,6 +2124,7 @@ void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat
         g.backward = backward;
         g.fsel = V_RHS;
         g.usel = V_E;
+        Builder{h, nullptr, h->nlev}.big_range(level, c, g);
         k_op<double><<<nblocks_for(g.i1 - g.i0, kRedThreads), kRedThreads, 0, s>>>(dtab<double>(h), g, rc);
         AMG_LAUNCH_CHECK();
     }
