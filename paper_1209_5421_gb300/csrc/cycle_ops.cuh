@@ -537,6 +537,56 @@ __device__ void op_gs_blocks_coop(const LV &L, const Op &op, const typename LV::
     }
 }
 
+// asynchronous prefetch of [p, p + bytes) into L2 (cp.async.bulk.prefetch), trimmed inward to
+// 16-byte boundaries so that it never reaches outside the range
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+    uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    while (a < e) {
+        const unsigned chunk = (unsigned)((e - a) < 32768 ? (e - a) : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(chunk) : "memory");
+        a += chunk;
+    }
+}
+
+// L2 prefetch of what big block k's sweep reads: its level-ordered entries, its rows' slots
+// (contiguous slices: the block's rows are consecutive) and its rows' f, 1/a_ii and u
+template <class LV>
+__device__ void prefetch_big_block(const LV &L, const int *lofs, const int *lp, const int4 *ent,
+                                   int k, const typename LV::val_t *f,
+                                   const typename LV::val_t *u) {
+    using T = typename LV::val_t;
+    const BigSched *S = L.big;
+    const int blk = S->ids[k];
+    const int r0 = L.bptr[blk], r1 = L.bptr[blk + 1];
+    const int e0 = lp[lofs[k]], e1 = lp[lofs[k + 1]];
+    prefetch_l2(ent + e0, sizeof(int4) * (size_t)(e1 - e0));
+    const int s0 = L.sl[r0 >> 5], s1 = L.sl[((r1 - 1) >> 5) + 1];
+    prefetch_l2(L.col + s0, sizeof(typename LV::idx_t) * (size_t)(s1 - s0));
+    prefetch_l2(L.val + s0, sizeof(T) * (size_t)(s1 - s0));
+    prefetch_l2(f + r0, sizeof(T) * (size_t)(r1 - r0));
+    prefetch_l2(L.dinv + r0, sizeof(T) * (size_t)(r1 - r0));
+    prefetch_l2(u + r0, sizeof(T) * (size_t)(r1 - r0));
+}
+
+// every big-block task's data on its way to L2 (one lane per warp task, one thread per CTA
+// task), issued before the op's other work so that the level chains wait on L2, not DRAM
+template <class LV>
+__device__ void prefetch_big_tasks(const LV &L, const Op &op, const typename LV::val_t *f,
+                                   const typename LV::val_t *u, int tid, int nth) {
+    const BigSched *S = L.big;
+    const bool bwd = op.backward != 0;
+    const int *lofs = bwd ? S->lofs_b : S->lofs_f;
+    const int *lp = bwd ? S->lp_b : S->lp_f;
+    const int4 *ent = bwd ? S->ent_b : S->ent_f;
+    if ((tid & 31) == 0)
+        for (int k = op.bb0 + (tid >> 5); k < op.bbc; k += nth >> 5)
+            prefetch_big_block(L, lofs, lp, ent, k, f, u);
+    if (threadIdx.x == 0)
+        for (int k = op.bbc + (int)blockIdx.x; k < op.bb1; k += (int)gridDim.x)
+            prefetch_big_block(L, lofs, lp, ent, k, f, u);
+}
+
 // Gauss-Seidel update of row i whose slots start at `base` (gs_row without the slice lookup)
 template <class LV>
 __device__ __forceinline__ void gs_row_at(const LV &L, int i, int base, int width,
@@ -589,6 +639,8 @@ template <class LV, bool BIG = false>
 __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
                       typename LV::val_t *u, int tid, int nth) {
     const bool big = BIG && L.fine && op.bb1 > op.bb0;
+    if constexpr (BIG)
+        if (big) prefetch_big_tasks(L, op, f, u, tid, nth);
     if constexpr (LV::coop) {
         if (L.fine && L.bg > 0) {
             op_gs_blocks_coop(L, op, f, u, tid, nth, big);

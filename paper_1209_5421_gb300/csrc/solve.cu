@@ -36,7 +36,7 @@ constexpr int kTailRowsMax = 4096;  // levels larger than this are never staged
 // coarse levels of at least this many rows restrict in two grid-wide passes (OP_RESID,
 // OP_GATHER): their rows' children lie in different colours, far apart in HBM, and the
 // one-pass form's four-lane gathers read scattered slots
-constexpr int kSplitRestrictRows = 131072;
+constexpr int kSplitRestrictRows = 524288;
 
 
 // shared-memory image of the tail levels (byte offsets into the dynamic shared memory)
