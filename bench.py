@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--octree-n", type=int, default=129)
     ap.add_argument("--serve-rates", default="10,50,100,200,500,1000,2000")
     ap.add_argument("--serve-requests", type=int, default=48)
+    # systems above this many unknowns take the large lane (the grid-wide solver, alone on
+    # the GPU); smaller ones share the batch lane, one CTA each
+    ap.add_argument("--serve-large", type=int, default=50_000)
     return ap.parse_args()
 
 
@@ -555,7 +558,7 @@ def run_served_rate(args, local, mats, rate, nreq, seed):
     from paper_1209_5421_gb300.serve import Server
 
     rng = np.random.default_rng(seed)
-    S = Server(budget_bytes=150 << 30, device=local)
+    S = Server(budget_bytes=150 << 30, device=local, large_unknowns=args.serve_large)
     for k, p in enumerate(mats):
         S.register(k, p.rowptr, p.col, p.val, p.x, p.y)
     seen, nxt, reqs = [], 0, []
@@ -602,8 +605,9 @@ def run_served(args, local):
                     f"{len(mats)} matrices of 1e3..4e6 unknowns (log-uniform), quasi-uniform "
                     "and graded alternately, 30% reuse",
         "method": "FP32 AMLI-cycle; batch lane FP64 flexible CG (one CTA per system), "
-                  "large lane (> 250k unknowns) FP64 FGMRES on the whole GPU",
+                  f"large lane (> {args.serve_large} unknowns) FP64 FGMRES on the whole GPU",
         "unknowns": [int(m.n) for m in mats],
+        "large_lane_unknowns": args.serve_large,
         "budget_bytes": 150 << 30,
         "rates": per_rate,
     }

@@ -417,6 +417,15 @@ int amg_debug_batch_barrier_fault(amg_batch *bt, int64_t limit_ns, int32_t extra
 int amg_debug_fail_allocation(int64_t k);
 
 /*
+ * Index checks: in a library built with -DAMG_BOUNDS_CHECK (`python -m
+ * paper_1209_5421_gb300.build --bounds-check`), every gather of the cycle's and the batch
+ * kernel's ops checks its index against the vector's length; an index outside it is skipped
+ * and sets a flag. *flags receives the flags set since the last call (0: none) and clears
+ * them. Errors: AMG_ERR_UNSUPPORTED in a library built without the checks (the default).
+ */
+int amg_debug_bounds_flags(int32_t *flags);
+
+/*
  * Bytes currently allocated from `device`'s default stream-ordered memory pool, which every
  * device allocation of the library uses (freed blocks return to it once their stream reaches
  * the free: synchronise first). A leak check compares it before and after a call.

@@ -13,7 +13,9 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libamg_gb300.so")
+# AMG_GB300_LIBRARY selects another build of the library (the bounds-checking variant
+# libamg_gb300_bc.so in its tests)
+LIB_PATH = os.environ.get("AMG_GB300_LIBRARY") or os.path.join(HERE, "libamg_gb300.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "amg.h")
 
 OK = 0
@@ -122,6 +124,8 @@ def lib():
         L.amg_debug_fail_allocation.restype = C.c_int
         L.amg_debug_pool_bytes_in_use.argtypes = [C.c_int32, C.POINTER(C.c_int64)]
         L.amg_debug_pool_bytes_in_use.restype = C.c_int
+        L.amg_debug_bounds_flags.argtypes = [C.POINTER(C.c_int32)]
+        L.amg_debug_bounds_flags.restype = C.c_int
         _lib = L
     return _lib
 
@@ -129,6 +133,14 @@ def lib():
 def debug_fail_allocation(k: int):
     """Make the k-th device allocation of the library from now on fail (0: disarm)."""
     _check(lib().amg_debug_fail_allocation(int(k)), "amg_debug_fail_allocation")
+
+
+def bounds_flags() -> int:
+    """Index-check flags of the bounds-checking build since the last call (raises
+    AmgError(ERR_UNSUPPORTED) in the normal build)."""
+    v = C.c_int32()
+    _check(lib().amg_debug_bounds_flags(C.byref(v)), "amg_debug_bounds_flags")
+    return v.value
 
 
 def pool_bytes_in_use(device: int = 0) -> int:
@@ -270,8 +282,20 @@ class Hierarchy:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().amg_free(self.h)
+            if not getattr(self, "_view", False):
+                lib().amg_free(self.h)
             self.h = None
+
+    @classmethod
+    def view(cls, handle: int, n: int, owner):
+        """A Hierarchy over a handle owned elsewhere (a batch's system): never freed here;
+        `owner` is kept alive while the view is."""
+        self = cls.__new__(cls)
+        self.h = C.c_void_p(handle)
+        self.n = n
+        self._view = True
+        self._owner = owner
+        return self
 
     @property
     def dim(self) -> int:
@@ -529,6 +553,13 @@ class Batch:
         if r not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_TIMEOUT):
             _check(r, "amg_batch_solve")
         return x, it, rr, st
+
+    def system(self, p: int) -> "Hierarchy":
+        """System p's hierarchy (owned by the batch) as a non-owning Hierarchy view."""
+        h = lib().amg_batch_system(self.b, int(p))
+        if not h:
+            raise AmgError(ERR_INVALID_ARG, f"no system {p}")
+        return Hierarchy.view(h, int(self.row_off[p + 1] - self.row_off[p]), self)
 
     def debug_barrier_fault(self, limit_ns: int = 0, extra: int = 0):
         """Host-set fault of the team barriers for the following solves (0, 0: off)."""

@@ -319,5 +319,9 @@ void batch_teams(const BatchEngine *E, int *team);
 void batch_barrier_fault(BatchEngine *E, int64_t limit_ns, int extra);
 void smooth_level(amg_hierarchy *h, int level, int backward, const double *f_nat,
                   double *u_nat);
+// the bounds-checking build's flags of solve.cu's and batch.cu's kernels, read and cleared
+// (-1: the library was built without index checks)
+int bounds_flags_solve();
+int bounds_flags_batch();
 
 }  // namespace amg

@@ -840,6 +840,8 @@ void batch_barrier_fault(BatchEngine *E, int64_t limit_ns, int extra) {
     E->g_shape = -1;  // recapture the launch with the new arguments
 }
 
+int bounds_flags_batch() { return bounds_flag_read_clear(); }
+
 void batch_teams(const BatchEngine *E, int *team) {
     for (int p = 0; p < E->nprob; p++) team[p] = E->shape < 0 ? -1 : E->team[E->shape][p];
 }

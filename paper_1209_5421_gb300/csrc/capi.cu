@@ -612,6 +612,14 @@ int amg_debug_fail_allocation(int64_t k) {
     return AMG_OK;
 }
 
+int amg_debug_bounds_flags(int32_t *flags) {
+    if (!flags) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    const int a = amg::bounds_flags_solve(), b = amg::bounds_flags_batch();
+    if (a < 0 || b < 0) return fail(AMG_ERR_UNSUPPORTED, "built without index checks");
+    *flags = a | b;
+    return AMG_OK;
+}
+
 int amg_debug_pool_bytes_in_use(int32_t device, int64_t *bytes) {
     if (!bytes) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
     cudaMemPool_t pool;

@@ -138,6 +138,32 @@ __device__ __forceinline__ void row_span(const StagedLevel<T, W> &L, int i, int 
     base = (i >> 5) * 32 * width + (i & 31);
 }
 
+// Index checks of the bounds-checking build (compiled with -DAMG_BOUNDS_CHECK): an index of
+// a gather outside [0, n) sets this translation unit's flag (amg_debug_bounds_flags reads it)
+// and the access is skipped, so a bad index is reported instead of read. The normal build
+// checks nothing here: setup builds every index and validates the input matrix.
+#ifdef AMG_BOUNDS_CHECK
+static __device__ unsigned int g_bounds_err;
+__device__ __forceinline__ bool idx_ok(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return true;
+    atomicOr(&g_bounds_err, 1u);
+    return false;
+}
+// this translation unit's flag, read and cleared (host; -1 when the flag is not built)
+static inline int bounds_flag_read_clear() {
+    unsigned int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_err, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_bounds_err, &zero, sizeof zero) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int)v;
+}
+#else
+__device__ __forceinline__ constexpr bool idx_ok(int, int) { return true; }
+static inline int bounds_flag_read_clear() { return -1; }
+#endif
+
 __device__ __forceinline__ bool col_ok(int c) { return c >= 0; }
 __device__ __forceinline__ bool col_ok(unsigned short c) { return c != (unsigned short)0xFFFF; }
 
@@ -395,7 +421,8 @@ __device__ __forceinline__ typename LV::val_t row_dot(const LV &L, int base, int
         }
         T xv[kRowBatch];
 #pragma unroll
-        for (int j = 0; j < kRowBatch; j++) xv[j] = col_ok(c[j]) ? x[c[j]] : T(0);
+        for (int j = 0; j < kRowBatch; j++)
+            xv[j] = (col_ok(c[j]) && idx_ok((int)c[j], L.n)) ? x[c[j]] : T(0);
 #pragma unroll
         for (int j = 0; j < kRowBatch; j++) acc += a[j] * xv[j];
     }
@@ -767,7 +794,7 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
             const int4 ch = (q < 4 ? L.children : L.children2)[R];
             const int qq = q & 3;
             const int c = qq == 0 ? ch.x : qq == 1 ? ch.y : qq == 2 ? ch.z : ch.w;
-            if (c >= 0) v = row_residual(L, c, f, u);
+            if (c >= 0 && idx_ok(c, L.n)) v = row_residual(L, c, f, u);
         }
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -800,13 +827,12 @@ __device__ void op_gather_children(const LV &L, const typename LV::val_t *t,
     const bool oct = L.children2 != nullptr;
     for (int R = tid; R < L.nnext; R += nth) {
         const int4 ch = L.children[R];
-        const T a0 = ch.x >= 0 ? t[ch.x] : T(0), a1 = ch.y >= 0 ? t[ch.y] : T(0);
-        const T a2 = ch.z >= 0 ? t[ch.z] : T(0), a3 = ch.w >= 0 ? t[ch.w] : T(0);
+        auto at = [&](int c) { return (c >= 0 && idx_ok(c, L.n)) ? t[c] : T(0); };
+        const T a0 = at(ch.x), a1 = at(ch.y), a2 = at(ch.z), a3 = at(ch.w);
         T v = (a0 + a1) + (a2 + a3);
         if (oct) {
             const int4 c2 = L.children2[R];
-            const T b0 = c2.x >= 0 ? t[c2.x] : T(0), b1 = c2.y >= 0 ? t[c2.y] : T(0);
-            const T b2 = c2.z >= 0 ? t[c2.z] : T(0), b3 = c2.w >= 0 ? t[c2.w] : T(0);
+            const T b0 = at(c2.x), b1 = at(c2.y), b2 = at(c2.z), b3 = at(c2.w);
             v = v + ((b0 + b1) + (b2 + b3));
         }
         fc[R] = v;
@@ -826,7 +852,10 @@ __device__ void op_gs_first(const LV &L, const Op &op, const typename LV::val_t 
 template <class LV>
 __device__ void op_prolong(const LV &L, const typename LV::val_t *e, typename LV::val_t *u,
                            int tid, int nth) {
-    for (int i = tid; i < L.n; i += nth) u[i] += e[L.parent[i]];
+    for (int i = tid; i < L.n; i += nth) {
+        const int pr = L.parent[i];
+        if (idx_ok(pr, L.nnext)) u[i] += e[pr];
+    }
 }
 
 // e = A^{-1} rhs with the dense inverse of the coarsest level, g lanes per row (g = largest

@@ -1694,6 +1694,8 @@ void allocate_solve_workspace(amg_hierarchy *h) {
     if (h->nlev > 1) build_engine<double>(h);
 }
 
+int bounds_flags_solve() { return bounds_flag_read_clear(); }
+
 void free_engines(amg_hierarchy *h) {
     delete h->eng64;
     delete h->eng32;

@@ -229,3 +229,23 @@ def test_full_batch_workload(amg, oracle_mod):
     for k in range(0, len(probs), 32):
         _check_system(amg, oracle_mod, probs[k], x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol, 3)
     B.close()
+
+
+def test_batched_setup_matches_single_setups(amg):
+    # amg_batch_setup builds the systems' hierarchies on worker threads, largest first: each
+    # must be the hierarchy the single-system setup builds, bit for bit (levels, operators,
+    # aggregates, colours)
+    probs = [p1_poisson(**s) for s in SPECS] + [p1_poisson(n=129, jitter=0.1, graded=True,
+                                                           kappa_blocks=16, seed=11)]
+    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP64)
+    for k, p in enumerate(probs):
+        Gb = B.system(k)
+        Gs = amg.Hierarchy.from_problem(p)
+        assert Gb.nlev == Gs.nlev, k
+        for l in range(Gs.nlev):
+            assert Gb.level_info(l) == Gs.level_info(l), (k, l)
+            lb, ls = Gb.level(l), Gs.level(l)
+            for key in ls:
+                np.testing.assert_array_equal(lb[key], ls[key], err_msg=f"system {k} level {l} {key}")
+        Gs.close()
+    B.close()
