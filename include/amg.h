@@ -175,16 +175,17 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
 
 /*
  * A batch over hierarchies that already exist (built by amg_setup or amg_batch_setup; all
- * with the same cycle_prec, kcycle_n, nu_pre and nu_post; borrowed: they must outlive the
+ * with the same cycle_prec, kcycle_n, nu_pre, nu_post and max_iters; borrowed: they must outlive the
  * batch, and a hierarchy must not be solved by two calls at the same time). System p is hs[p]; its rows in
  * the concatenated vectors follow those of hs[0..p-1]. threads: 0 = choose the launch shape
  * by timing on the first solve, with teams of CTAs for the largest systems (see
  * amg_batch_set_teams); 1024, 512 or 256 = that many threads per CTA (1, 2 or 4 CTAs per
  * SM), one CTA per system. With a fixed shape a system's result does not depend on the
- * other systems of the batch (each system is computed by one CTA in a fixed order). The first batched solve of a
- * hierarchy allocates its outer-iteration workspace (64 FP64 directions, about 1 KB per
- * unknown), owned by the hierarchy and counted by amg_hierarchy_bytes.
- * Errors: AMG_ERR_INVALID_ARG (NULL, mixed precisions, a repeated hierarchy, other threads),
+ * other systems of the batch (each system is computed by one CTA in a fixed order). The batch allocates each
+ * hierarchy's outer-iteration workspace: 32 FP64 directions and their images at first
+ * (about 0.5 KB per unknown), the same directions amg_solve uses, owned by the hierarchy and
+ * counted by amg_hierarchy_bytes.
+ * Errors: AMG_ERR_INVALID_ARG (NULL, mixed options, a repeated hierarchy, other threads),
  * AMG_ERR_OOM, AMG_ERR_CUDA.
  */
 int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, void *stream,
@@ -197,8 +198,11 @@ int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, v
  * and status (as amg_solve would return it); each may be NULL. The first call also times the
  * candidate launch shapes on this batch (every timed solve is a complete solve) and keeps
  * the fastest; the launch sequence is captured in a CUDA graph and replayed while b, x and
- * tol stay the same. Returns AMG_OK if every system converged, else the first non-OK system
- * status in system order.
+ * tol stay the same. The outer iteration keeps every direction (flexible CG with full
+ * A-orthogonalisation, as amg_solve): a system that fills its allocated directions gets
+ * twice as many (at most max_iters) and continues in a further launch, so its iterates are
+ * those of an unbounded workspace. Returns AMG_OK if every system converged, else the first
+ * non-OK system status in system order.
  */
 int amg_batch_solve(amg_batch *bt, const double *b, double tol, double *x, int32_t *iters,
                     double *relres, int32_t *status, void *stream);

@@ -122,11 +122,11 @@ struct EngineBase;
 // outer-iteration workspace of a hierarchy solved inside a batch (batch.cu); allocated on the
 // hierarchy's first batched solve and owned by it
 struct BatchWs {
-    int cap = 0;                    // directions kept before a restart
     double *bo = nullptr, *xo = nullptr, *to = nullptr;
-    double *P = nullptr, *Q = nullptr;
+    double *pq = nullptr;           // (p_j, q_j) of the outer directions (the hierarchy's P, Q)
     int *colors = nullptr;          // colour ranges of every level, concatenated
     int cofs[kMaxLevels] = {}, ncol[kMaxLevels] = {};
+    int4 *bigr = nullptr;           // finest level's colours: their big blocks (bb0, bbc, bb1)
 };
 
 }  // namespace amg
@@ -287,6 +287,9 @@ int solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
           double *relres);
 void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double *z_nat);
 void prepare_cycle(amg_hierarchy *h);
+// outer directions P[j], Q[j] (and the device tables dP, dQ) for j < count at least, in
+// chunks, at most max_iters; returns the number allocated. Synchronises h->stream.
+int ensure_directions(amg_hierarchy *h, int count);
 const void *level_table(const amg_hierarchy *h, bool fp32);
 
 // ---- batched solves (batch.cu) ------------------------------------------------------------

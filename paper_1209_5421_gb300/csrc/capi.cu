@@ -492,7 +492,8 @@ int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, v
     for (int p = 0; p < nprob; p++) {
         if (!hs[p]) return fail(AMG_ERR_INVALID_ARG, "NULL hierarchy");
         if (hs[p]->opt.cycle_prec != hs[0]->opt.cycle_prec || hs[p]->opt.kcycle_n != hs[0]->opt.kcycle_n ||
-            hs[p]->opt.nu_pre != hs[0]->opt.nu_pre || hs[p]->opt.nu_post != hs[0]->opt.nu_post)
+            hs[p]->opt.nu_pre != hs[0]->opt.nu_pre || hs[p]->opt.nu_post != hs[0]->opt.nu_post ||
+            hs[p]->opt.max_iters != hs[0]->opt.max_iters)
             return fail(AMG_ERR_INVALID_ARG,
                         "every hierarchy needs the same cycle_prec, kcycle_n, nu_pre and nu_post");
         for (int q = 0; q < p; q++)

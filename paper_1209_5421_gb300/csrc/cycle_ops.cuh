@@ -600,7 +600,8 @@ __device__ void prefetch_big_block(const LV &L, const int *lofs, const int *lp, 
 // task), issued before the op's other work so that the level chains wait on L2, not DRAM
 template <class LV>
 __device__ void prefetch_big_tasks(const LV &L, const Op &op, const typename LV::val_t *f,
-                                   const typename LV::val_t *u, int tid, int nth) {
+                                   const typename LV::val_t *u, int tid, int nth, int crank,
+                                   int ccount) {
     const BigSched *S = L.big;
     const bool bwd = op.backward != 0;
     const int *lofs = bwd ? S->lofs_b : S->lofs_f;
@@ -610,7 +611,7 @@ __device__ void prefetch_big_tasks(const LV &L, const Op &op, const typename LV:
         for (int k = op.bb0 + (tid >> 5); k < op.bbc; k += nth >> 5)
             prefetch_big_block(L, lofs, lp, ent, k, f, u);
     if (threadIdx.x == 0)
-        for (int k = op.bbc + (int)blockIdx.x; k < op.bb1; k += (int)gridDim.x)
+        for (int k = op.bbc + crank; k < op.bb1; k += ccount)
             prefetch_big_block(L, lofs, lp, ent, k, f, u);
 }
 
@@ -623,11 +624,13 @@ __device__ __forceinline__ void gs_row_at(const LV &L, int i, int base, int widt
 
 // the big blocks of one colour in level order: [op.bb0, op.bbc) one warp each (__syncwarp
 // between levels), [op.bbc, op.bb1) one CTA each (CTA barrier between levels). tid, nth:
-// the executor's global thread index and count (whole warps). Every thread of the grid calls
-// this.
+// the executor's thread index and count (whole warps); crank, ccount: this CTA's index among
+// the executor's CTAs and their number (the grid's, or a batch team's). Every thread of the
+// executor calls this.
 template <class LV>
 __device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::val_t *f,
-                                 typename LV::val_t *u, int tid, int nth) {
+                                 typename LV::val_t *u, int tid, int nth, int crank,
+                                 int ccount) {
     const BigSched *S = L.big;
     const bool bwd = op.backward != 0;
     const int *lofs = bwd ? S->lofs_b : S->lofs_f;
@@ -645,7 +648,7 @@ __device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::v
             __syncwarp();  // this level's values are read by the next level's rows
         }
     }
-    for (int k = op.bbc + (int)blockIdx.x; k < op.bb1; k += (int)gridDim.x) {  // larger blocks
+    for (int k = op.bbc + crank; k < op.bb1; k += ccount) {  // larger blocks
         const int l1 = lofs[k + 1];
         for (int j = lofs[k]; j < l1; j++) {
             const int b = lp[j + 1];
@@ -664,15 +667,24 @@ __device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::v
 // not compile that phase (nor its shared memory).
 template <class LV, bool BIG = false>
 __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
-                      typename LV::val_t *u, int tid, int nth) {
+                      typename LV::val_t *u, int tid, int nth, int crank = -1,
+                      int ccount = -1) {
     const bool big = BIG && L.fine && op.bb1 > op.bb0;
-    if constexpr (BIG)
-        if (big) prefetch_big_tasks(L, op, f, u, tid, nth);
+    if constexpr (BIG) {
+        if (crank < 0) {  // the grid's CTAs
+            crank = (int)blockIdx.x;
+            ccount = (int)gridDim.x;
+        }
+        if (big) prefetch_big_tasks(L, op, f, u, tid, nth, crank, ccount);
+    } else {
+        (void)crank;
+        (void)ccount;
+    }
     if constexpr (LV::coop) {
         if (L.fine && L.bg > 0) {
             op_gs_blocks_coop(L, op, f, u, tid, nth, big);
             if constexpr (BIG)
-                if (big) op_gs_big_blocks(L, op, f, u, tid, nth);
+                if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount);
             return;
         }
     }
@@ -689,7 +701,7 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
         }
     }
     if constexpr (BIG)
-        if (big) op_gs_big_blocks(L, op, f, u, tid, nth);
+        if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount);
 }
 
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
@@ -705,7 +717,7 @@ template <class LV>
 __device__ void restrict_big_blocks(const LV &L, const typename LV::val_t *f,
                                     const typename LV::val_t *u, typename LV::val_t *fc,
                                     typename LV::val_t *un, const typename LV::val_t *dinv_n,
-                                    int f0, int f1, int tid, int nth) {
+                                    int f0, int f1, int tid, int nth, int crank, int ccount) {
     using T = typename LV::val_t;
     const BigSched *S = L.big;
     const int lane = tid & 31;
@@ -722,7 +734,7 @@ __device__ void restrict_big_blocks(const LV &L, const typename LV::val_t *f,
             if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
         }
     }
-    for (int k = (int)blockIdx.x; k < S->nbig; k += (int)gridDim.x) {
+    for (int k = crank; k < S->nbig; k += ccount) {
         const int R = S->ids[k];
         const int r0 = L.bptr[R], r1 = L.bptr[R + 1];
         if (r1 - r0 <= kWarpBlockRows) continue;  // a warp's, above
@@ -747,8 +759,12 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             const typename LV::val_t *u, typename LV::val_t *fc, int tid,
                             int nth, typename LV::val_t *un = nullptr,
                             const typename LV::val_t *dinv_n = nullptr, int f0 = 0, int f1 = 0,
-                            bool big = false) {
+                            bool big = false, int crank = -1, int ccount = -1) {
     using T = typename LV::val_t;
+    if (crank < 0) {  // the grid's CTAs
+        crank = (int)blockIdx.x;
+        ccount = (int)gridDim.x;
+    }
     if constexpr (LV::coop) {  // kBlockLanes lanes per aggregate: a row each, then a shuffle sum
         if (L.fine && L.bg > 0) {
             constexpr int G = kBlockLanes;
@@ -768,7 +784,8 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                     if (un) un[R] = (R >= f0 && R < f1) ? v * dinv_n[R] : T(0);
                 }
             }
-            if (big) restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth);
+            if (big)
+                restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth, crank, ccount);
             return;
         }
     }
@@ -781,7 +798,8 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
             fc[R] = acc;
             if (un) un[R] = (R >= f0 && R < f1) ? acc * dinv_n[R] : T(0);
         }
-        if (big) restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth);
+        if (big)
+            restrict_big_blocks(L, f, u, fc, un, dinv_n, f0, f1, tid, nth, crank, ccount);
         return;
     }
     const bool oct = L.children2 != nullptr;

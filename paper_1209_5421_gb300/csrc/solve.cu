@@ -1702,11 +1702,11 @@ void free_engines(amg_hierarchy *h) {
     h->eng64 = h->eng32 = nullptr;
 }
 
-static void ensure_directions(amg_hierarchy *h, int count) {
+int ensure_directions(amg_hierarchy *h, int count) {
     const int n = (int)h->N;
     const int chunk = 16;
     int old = (int)h->P.size();
-    if (count <= old) return;
+    if (count <= old) return old;
     int target = std::min(h->opt.max_iters, ((count + chunk - 1) / chunk) * chunk);
     for (int j = old; j < target; j++) {  // both allocated before either is kept: P and Q
         double *p = halloc<double>(h, n);    // stay the same length if an allocation fails
@@ -1718,6 +1718,8 @@ static void ensure_directions(amg_hierarchy *h, int count) {
                              h->stream));
     AMG_CUDA(cudaMemcpyAsync(h->dQ, h->Q.data(), sizeof(double *) * target, cudaMemcpyHostToDevice,
                              h->stream));
+    AMG_CUDA(cudaStreamSynchronize(h->stream));  // the tables are copied from host vectors
+    return target;
 }
 
 static GLev<double> fine_view(amg_hierarchy *h) {

@@ -7,7 +7,8 @@ hierarchies: before its setup an estimate from the matrix's size (above the meas
 2D and 3D hierarchies), after the setup and after every solve its real bytes
 (amg_hierarchy_bytes; a solve can grow them, as the outer Krylov iteration allocates its
 directions on demand). Where the real bytes exceed what was charged, idle hierarchies are
-evicted until the total fits the budget again; the peak is reported as it was.
+evicted until the total fits the budget again; the peak is reported as it was, and so are
+the bytes solves added (`grown_bytes`): the peak stays within the budget plus those.
 
 Two lanes share the GPU:
   * the batch lane: whenever systems are ready, a worker takes all of them (up to
@@ -39,8 +40,9 @@ import numpy as np
 from . import amg
 
 # device bytes per unknown of the batched-solve workspace a hierarchy allocates on its first
-# batched solve (64 FP64 directions and their images, 3 vectors, colour ranges)
-_BATCH_WS_BYTES_PER_UNKNOWN = 8 * (2 * 64 + 3)
+# batched solve (32 FP64 directions and their images, 3 vectors, colour ranges; a system
+# that needs more directions gets them on demand, and the real size replaces the estimate)
+_BATCH_WS_BYTES_PER_UNKNOWN = 8 * (2 * 32 + 3)
 
 
 def setup_estimate(n: int, nnz: int) -> int:
@@ -96,6 +98,7 @@ class Server:
         self.res: OrderedDict = OrderedDict()      # key -> _Resident (LRU order)
         self.used = 0
         self.max_used = 0
+        self.grown = 0  # bytes that solves added to resident hierarchies
         self.cv = threading.Condition()
         self.need_setup: deque = deque()           # requests whose matrix is not resident
         self.ready: deque = deque()                # requests whose hierarchy is resident
@@ -182,6 +185,7 @@ class Server:
                 "setups": self.setups, "setup_failures": self.setup_failures,
                 "evictions": self.evictions, "batches": self.batches,
                 "max_resident_bytes": self.max_used, "budget_bytes": self.budget,
+                "grown_bytes": self.grown,
                 "large_lane": sum(r.lane == "large" for r in solved)}
 
     # ---- internals --------------------------------------------------------------------
@@ -216,6 +220,7 @@ class Server:
             self.errors.append(f"hierarchy bytes: {e}")
             return
         if nbytes != ent.nbytes:
+            self.grown += max(0, nbytes - ent.nbytes)
             self.used += nbytes - ent.nbytes
             ent.nbytes = nbytes
             self.max_used = max(self.max_used, self.used)

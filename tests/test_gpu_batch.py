@@ -249,3 +249,57 @@ def test_batched_setup_matches_single_setups(amg):
                 np.testing.assert_array_equal(lb[key], ls[key], err_msg=f"system {k} level {l} {key}")
         Gs.close()
     B.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graded_systems_big_aggregates(amg, oracle_mod, prec):
+    # graded meshes: aggregates of up to 484 unknowns on the finest level (462 above 16
+    # unknowns, a warp's in level order; 8 above 128, a CTA's). Alone on a CTA, in a team of
+    # CTAs and in teams of at most 2: the FP64 cycle within one iteration of the oracle
+    probs = [p1_poisson(n=257, jitter=0.1, graded=True, kappa_blocks=16, seed=12, rhs="normal"),
+             p1_poisson(n=97, jitter=0.1, graded=True, kappa_blocks=16, seed=2, rhs="normal"),
+             p1_poisson(n=193, jitter=0.1, graded=True, kappa_blocks=16, seed=13, rhs="normal")]
+    for p in probs:
+        agg = oracle_mod.Hierarchy.from_problem(p).level(0).agg
+        assert np.bincount(agg).max() > 128 or p.n < 10000
+    cp = amg.FP32 if prec == "fp32" else amg.FP64
+    B = amg.Batch.from_problems(probs, cycle_prec=cp)
+    rhs = np.concatenate([p.b for p in probs])
+    tol = 1e-8
+    off = B.row_off
+    for cap in (None, 1, 2):
+        if cap is not None:
+            B.set_teams(cap)
+        x, it, rr, st = B.solve(rhs, tol)
+        if cap is None:
+            assert B.teams().max() > 1
+        for k, p in enumerate(probs):
+            slack = None if prec == "fp64" else 10
+            _check_system(amg, oracle_mod, p, x[off[k]:off[k + 1]], it[k], rr[k], st[k], tol,
+                          slack)
+    B.close()
+
+
+def test_directions_grow_to_max_iters(amg, oracle_mod):
+    # a system needing more outer directions than a batch allocates at first (32) gets more in
+    # a further launch and keeps all of them: the same iterates as the oracle's unbounded
+    # flexible CG. With max_iters = 40 it stops there, not converged, with a valid x.
+    p = p1_poisson(n=193, jitter=0.1, graded=True, kappa_blocks=16, seed=13, rhs="normal")
+    q = p1_poisson(n=33, jitter=0.2, seed=3, rhs="normal")
+    B = amg.Batch.from_problems([p, q], cycle_prec=amg.FP64, max_iters=40)
+    x, it, rr, st = B.solve(np.concatenate([p.b, q.b]), 1e-8)
+    assert st[0] == amg.ERR_NOT_CONVERGED and it[0] == 40, (st, it)
+    assert st[1] == amg.OK
+    xp = x[:p.n]
+    true_rel = np.linalg.norm(p.b - p.to_scipy() @ xp) / np.linalg.norm(p.b)
+    assert abs(rr[0] - true_rel) <= 1e-6 * true_rel, (rr[0], true_rel)
+    assert 1e-8 < true_rel < 1.0
+    # the oracle's iterate after 40 steps: the same residual up to rounding
+    O = oracle_mod.Hierarchy.from_problem(p, max_iters=40)
+    xo, ito, rro, _ = O.solve(p.b, 1e-8)
+    assert ito == 40
+    assert abs(true_rel - rro) <= 1e-3 * rro, (true_rel, rro)
+    # a second solve starts with the grown workspace: the same result
+    x2, it2, _, st2 = B.solve(np.concatenate([p.b, q.b]), 1e-8)
+    assert np.array_equal(x2, x) and np.array_equal(it2, it) and np.array_equal(st2, st)
+    B.close()

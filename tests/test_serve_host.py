@@ -326,6 +326,8 @@ def test_growth_during_solves_is_charged(server_cls, large):
     assert _consistent(S)
     base = sum(BYTES_PER_UNKNOWN * p.n for p in probs.values())
     assert S.used == base + 9 * grow and S.max_used >= S.used
+    st = S.stats()
+    assert st["grown_bytes"] == 9 * grow
     S.close()
 
 
