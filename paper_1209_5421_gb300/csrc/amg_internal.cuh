@@ -287,6 +287,9 @@ int solve(amg_hierarchy *h, const double *b, double tol, double *x, int *iters,
           double *relres);
 void apply_cycle_level(amg_hierarchy *h, int level, const double *f_nat, double *z_nat);
 void prepare_cycle(amg_hierarchy *h);
+// what a batched solve needs of a hierarchy beyond its setup: the FP32 cycle's copies (FP32
+// cycle) and the batched-solve workspace; idempotent, synchronises h->stream
+void batch_prepare(amg_hierarchy *h);
 // outer directions P[j], Q[j] (and the device tables dP, dQ) for j < count at least, in
 // chunks, at most max_iters; returns the number allocated. Synchronises h->stream.
 int ensure_directions(amg_hierarchy *h, int count);

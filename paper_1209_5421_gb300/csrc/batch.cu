@@ -129,6 +129,11 @@ const BatchWs &batch_ws(amg_hierarchy *h) {
     return w;
 }
 
+void batch_prepare(amg_hierarchy *h) {
+    prepare_cycle(h);
+    batch_ws(h);
+}
+
 template <class T>
 void build_probs(BatchEngine *E) {
     const int np = E->nprob;

@@ -443,6 +443,7 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
                     amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
                     // returns after its work is done, so the localized arrays may be freed
                     bt->hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, ws);
+                    amg::batch_prepare(bt->hs[p]);  // here, not serially in batch_create
                 }
             } catch (const Error &e) {
                 std::lock_guard<std::mutex> g(err_m);

@@ -1708,11 +1708,13 @@ int ensure_directions(amg_hierarchy *h, int count) {
     int old = (int)h->P.size();
     if (count <= old) return old;
     int target = std::min(h->opt.max_iters, ((count + chunk - 1) / chunk) * chunk);
-    for (int j = old; j < target; j++) {  // both allocated before either is kept: P and Q
-        double *p = halloc<double>(h, n);    // stay the same length if an allocation fails
-        double *q = halloc<double>(h, n);
-        h->P.push_back(p);
-        h->Q.push_back(q);
+    // the new P and Q vectors in one allocation (each 256-byte aligned); if it fails, P and
+    // Q keep their length
+    const size_t stride = ((size_t)n + 31) & ~(size_t)31, m = (size_t)(target - old);
+    double *slab = halloc<double>(h, 2 * m * stride);
+    for (size_t j = 0; j < m; j++) {
+        h->P.push_back(slab + j * stride);
+        h->Q.push_back(slab + (m + j) * stride);
     }
     AMG_CUDA(cudaMemcpyAsync(h->dP, h->P.data(), sizeof(double *) * target, cudaMemcpyHostToDevice,
                              h->stream));
