@@ -60,8 +60,20 @@ struct BigSched {
     const int *lp_f, *lp_b;      // level boundaries: positions in ent_* (level j of block k is
                                  // ent_*[lp[lofs[k] + j] .. lp[lofs[k] + j + 1]))
     const int4 *ent_f, *ent_b;   // rows of every big block in level order: (pi row, first
-                                 // slot, slot count, 0)
+                                 // slot, slot count, offset of the row's off-diagonal slots
+                                 // among the block's, in this order)
 };
+
+// shared-memory bytes of a big block's sweep in shared memory (big_block_smem): rows m,
+// levels nl, off-diagonal slots ns, value size vb; 0 if it cannot be done there (16-bit
+// row, slot and entry indices)
+__host__ __device__ inline size_t big_smem_align(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t big_smem_bytes(int m, int nl, int ns, int vb) {
+    if (m > 65535 || ns > 65535) return 0;
+    return big_smem_align((size_t)3 * m * vb) + big_smem_align((size_t)6 * m) +
+           big_smem_align((size_t)2 * (nl + 1)) + big_smem_align((size_t)2 * ns * vb) +
+           big_smem_align((size_t)2 * ns);
+}
 
 struct Sell {
     int n = 0;
@@ -94,11 +106,15 @@ struct Level {
     std::vector<int> color_blocks;  // host [ncolors+1] (finest level): block range per colour
     int nblocks = 0;
     int *bptr = nullptr;    // finest level: [nblocks+1] pi-row range of each block
-    // finest level: blocks of more than kBigBlockRows rows, swept by whole CTAs in level order
+    // finest level: blocks of more than kBigBlockRows rows, swept in level order by warps
+    // and CTAs
     int nbig = 0;
     const BigSched *big_dev = nullptr;  // device copy of the schedule
     std::vector<int> color_big;     // host [ncolors+1]: each colour's range of big blocks
     std::vector<int> color_bigc;    // host [ncolors]: where each colour's CTA-sized ones start
+    std::vector<size_t> big_smem[2];  // shared memory each CTA-sized big block's sweep
+                                      // needs (big_smem_bytes; FP32, FP64 values)
+    size_t big_smem_warp[2] = {0, 0};  // the most a warp-sized one needs
     int *parent = nullptr;  // [n] pi-row of the next coarser level
     int4 *children = nullptr;  // level >= 2: [n] children pi-rows in level-1 by quadrant
     int4 *children2 = nullptr; // octree: children 4..7 (octant (t1&1) + 2 (t2&1) + 4 (t3&1))

@@ -622,42 +622,168 @@ __device__ __forceinline__ void gs_row_at(const LV &L, int i, int base, int widt
     u[i] = (f[i] - row_dot(L, base, 1, width, u)) * L.dinv[i];
 }
 
-// the big blocks of one colour in level order: [op.bb0, op.bbc) one warp each (__syncwarp
-// between levels), [op.bbc, op.bb1) one CTA each (CTA barrier between levels). tid, nth:
+// Shared memory a grid-wide executor lends to the big blocks' sweeps: p (null on CTAs
+// without it) and its size. With skip0, CTA 0 (whose shared memory holds the tail) takes no
+// big block; the warp-sized blocks go to warps [0, wwarps) of the other CTAs, each with a
+// slice of wslice bytes at p + warp * wslice (wwarps = 0: to every warp, from global memory).
+struct BigScratch {
+    unsigned char *p = nullptr;
+    unsigned bytes = 0;
+    bool skip0 = false;
+    int wwarps = 0;
+    unsigned wslice = 0;
+};
+
+// the threads that sweep one big block together: a CTA, or one warp
+struct CtaGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct LaneGroup {
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+// Big block k swept in shared memory (buf, bytes) by group g. Its rows' couplings are staged
+// first, in one pass over the block with no dependence between rows: each off-diagonal
+// slot's coefficient, and either the current value of a coupled unknown outside the block
+// (this colour does not change it) or the index of one inside; with each row's f and
+// 1/a_ii. The block's unknowns then live in shared memory and the level-ordered sweep reads
+// nothing else: a group barrier between levels, no memory round trip. Every row's sum takes
+// its slots in row_dot's order, with row_dot's zero terms up to the end of its last batch:
+// the same operations, the same bits. Returns false (nothing done) when the block does not
+// fit.
+template <class LV, class G>
+__device__ bool big_block_smem(const LV &L, const int *lofs, const int *lp, const int4 *ent,
+                               int k, const typename LV::val_t *f, typename LV::val_t *u,
+                               unsigned char *buf, size_t bytes, const G &g) {
+    using T = typename LV::val_t;
+    const BigSched *S = L.big;
+    const int blk = S->ids[k];
+    const int r0 = L.bptr[blk], m = L.bptr[blk + 1] - r0;
+    const int l0 = lofs[k], nl = lofs[k + 1] - l0;
+    const int e0 = lp[l0];  // the block's rows: ent[e0, e0 + m), level by level
+    const int4 last = ent[e0 + m - 1];
+    const int ns = last.w + last.z - 1;
+    const size_t need = big_smem_bytes(m, nl, ns, (int)sizeof(T));
+    if (need == 0 || need > bytes) return false;
+    unsigned char *q = buf;
+    T *su = (T *)q;  // the block's unknowns (local index = row - r0)
+    T *ef = su + m, *ed = ef + m;  // per entry: f, 1/a_ii
+    q += big_smem_align((size_t)3 * m * sizeof(T));
+    // per entry: local row, first slot, slot count
+    unsigned short *erow = (unsigned short *)q, *eo = erow + m, *ew = eo + m;
+    q += big_smem_align((size_t)6 * m);
+    unsigned short *slp = (unsigned short *)q;  // level boundaries, relative to e0
+    q += big_smem_align((size_t)2 * (nl + 1));
+    T *sa = (T *)q, *sx = sa + ns;  // per slot: coefficient, outside value
+    q += big_smem_align((size_t)2 * ns * sizeof(T));
+    unsigned short *si = (unsigned short *)q;  // per slot: inside index, 0xFFFF outside
+    const int t = g.rank(), nt = g.size();
+    for (int j = t; j <= nl; j += nt) slp[j] = (unsigned short)(lp[l0 + j] - e0);
+    for (int i = t; i < m; i += nt) {
+        const int4 e = ent[e0 + i];
+        const int row = e.x;
+        erow[i] = (unsigned short)(row - r0);
+        eo[i] = (unsigned short)e.w;
+        ew[i] = (unsigned short)e.z;
+        ef[i] = f[row];
+        ed[i] = L.dinv[row];
+        su[row - r0] = u[row];
+        for (int kk = 1; kk < e.z; kk++) {
+            const auto c = L.col[e.y + 32 * kk];
+            const int s = e.w + kk - 1;
+            sa[s] = L.val[e.y + 32 * kk];
+            unsigned short ix = 0xFFFF;
+            T xv = T(0);
+            if (col_ok(c) && idx_ok((int)c, L.n)) {
+                const int ci = (int)c;
+                if (ci >= r0 && ci < r0 + m) ix = (unsigned short)(ci - r0);
+                else xv = u[ci];
+            }
+            si[s] = ix;
+            sx[s] = xv;
+        }
+    }
+    g.sync();
+    for (int j = 0; j < nl; j++) {
+        const int p1 = slp[j + 1];
+        for (int i = slp[j] + t; i < p1; i += nt) {
+            const int o = (int)eo[i] - 1, w = ew[i];
+            T acc = 0;
+            int kk = 1;
+            for (; kk < w; kk++) {
+                const unsigned short ix = si[o + kk];
+                const T xv = ix != 0xFFFF ? su[ix] : sx[o + kk];
+                acc += sa[o + kk] * xv;
+            }
+            for (const int kend = 1 + (w + kRowBatch - 2) / kRowBatch * kRowBatch; kk < kend; kk++)
+                acc += T(0) * T(0);  // row_dot's zero terms to the end of its batch
+            su[erow[i]] = (ef[i] - acc) * ed[i];
+        }
+        g.sync();
+    }
+    for (int i = t; i < m; i += nt) u[r0 + i] = su[i];
+    g.sync();  // the buffer is used again by the group's next block
+    return true;
+}
+
+// one big block swept from global memory by group g, level by level
+template <class LV, class G>
+__device__ void big_block_global(const LV &L, const int *lofs, const int *lp, const int4 *ent,
+                                 int k, const typename LV::val_t *f, typename LV::val_t *u,
+                                 const G &g) {
+    const int l1 = lofs[k + 1];
+    for (int j = lofs[k]; j < l1; j++) {
+        const int b = lp[j + 1];
+        for (int p = lp[j] + g.rank(); p < b; p += g.size()) {
+            const int4 e = ent[p];
+            gs_row_at(L, e.x, e.y, e.z, f, u);
+        }
+        g.sync();  // this level's values are read by the next level's rows
+    }
+}
+
+// the big blocks of one colour in level order: [op.bb0, op.bbc) one warp each,
+// [op.bbc, op.bb1) one CTA each; in shared memory where the executor lends it (sc). tid, nth:
 // the executor's thread index and count (whole warps); crank, ccount: this CTA's index among
 // the executor's CTAs and their number (the grid's, or a batch team's). Every thread of the
 // executor calls this.
 template <class LV>
 __device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::val_t *f,
                                  typename LV::val_t *u, int tid, int nth, int crank,
-                                 int ccount) {
+                                 int ccount, const BigScratch &sc) {
     const BigSched *S = L.big;
     const bool bwd = op.backward != 0;
     const int *lofs = bwd ? S->lofs_b : S->lofs_f;
     const int *lp = bwd ? S->lp_b : S->lp_f;
     const int4 *ent = bwd ? S->ent_b : S->ent_f;
-    const int lane = tid & 31;
-    for (int k = op.bb0 + (tid >> 5); k < op.bbc; k += nth >> 5) {  // warp-sized blocks
-        const int l1 = lofs[k + 1];
-        for (int j = lofs[k]; j < l1; j++) {
-            const int b = lp[j + 1];
-            for (int p = lp[j] + lane; p < b; p += 32) {
-                const int4 e = ent[p];
-                gs_row_at(L, e.x, e.y, e.z, f, u);
-            }
-            __syncwarp();  // this level's values are read by the next level's rows
+    if (sc.skip0) {  // CTA 0 lends no shared memory: the other CTAs take every big block
+        if (blockIdx.x == 0) return;
+        crank -= 1;
+        ccount -= 1;
+        const int w = (int)threadIdx.x >> 5;
+        if (sc.wwarps > 0 && w < sc.wwarps) {  // warps with a slice: warp-sized blocks
+            unsigned char *slice = sc.p + (size_t)w * sc.wslice;
+            for (int k = op.bb0 + w * ccount + crank; k < op.bbc; k += sc.wwarps * ccount)
+                if (!big_block_smem(L, lofs, lp, ent, k, f, u, slice, sc.wslice, LaneGroup{}))
+                    big_block_global(L, lofs, lp, ent, k, f, u, LaneGroup{});
+        } else if (sc.wwarps == 0) {
+            const int nw = ((int)blockDim.x >> 5) * ccount;
+            for (int k = op.bb0 + w * ccount + crank; k < op.bbc; k += nw)
+                big_block_global(L, lofs, lp, ent, k, f, u, LaneGroup{});
         }
+        __syncthreads();  // the slices are the CTA-sized blocks' buffer next
+    } else {
+        for (int k = op.bb0 + (tid >> 5); k < op.bbc; k += nth >> 5)  // warp-sized blocks
+            big_block_global(L, lofs, lp, ent, k, f, u, LaneGroup{});
     }
     for (int k = op.bbc + crank; k < op.bb1; k += ccount) {  // larger blocks
-        const int l1 = lofs[k + 1];
-        for (int j = lofs[k]; j < l1; j++) {
-            const int b = lp[j + 1];
-            for (int p = lp[j] + (int)threadIdx.x; p < b; p += (int)blockDim.x) {
-                const int4 e = ent[p];
-                gs_row_at(L, e.x, e.y, e.z, f, u);
-            }
-            __syncthreads();
-        }
+        if (sc.p && big_block_smem(L, lofs, lp, ent, k, f, u, sc.p, sc.bytes, CtaGroup{}))
+            continue;
+        big_block_global(L, lofs, lp, ent, k, f, u, CtaGroup{});
     }
 }
 
@@ -668,7 +794,7 @@ __device__ void op_gs_big_blocks(const LV &L, const Op &op, const typename LV::v
 template <class LV, bool BIG = false>
 __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
                       typename LV::val_t *u, int tid, int nth, int crank = -1,
-                      int ccount = -1) {
+                      int ccount = -1, const BigScratch &sc = BigScratch{}) {
     const bool big = BIG && L.fine && op.bb1 > op.bb0;
     if constexpr (BIG) {
         if (crank < 0) {  // the grid's CTAs
@@ -684,14 +810,14 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
         if (L.fine && L.bg > 0) {
             op_gs_blocks_coop(L, op, f, u, tid, nth, big);
             if constexpr (BIG)
-                if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount);
+                if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount, sc);
             return;
         }
     }
     for (int b = op.i0 + tid; b < op.i1; b += nth) {
         if (L.fine) {
             const int r0 = L.bptr[b], r1 = L.bptr[b + 1];
-            if (big && r1 - r0 > kBigBlockRows) continue;  // a CTA's, below
+            if (big && r1 - r0 > kBigBlockRows) continue;  // in level order, below
             if (!op.backward)
                 for (int i = r0; i < r1; i++) gs_row(L, i, f, u);
             else
@@ -701,7 +827,7 @@ __device__ void op_gs(const LV &L, const Op &op, const typename LV::val_t *f,
         }
     }
     if constexpr (BIG)
-        if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount);
+        if (big) op_gs_big_blocks(L, op, f, u, tid, nth, crank, ccount, sc);
 }
 
 // fc = P^t (f - A u): the finest level sums the contiguous block of each aggregate; the
@@ -753,7 +879,7 @@ __device__ void restrict_big_blocks(const LV &L, const typename LV::val_t *f,
 }
 
 // big = true (grid-wide executors, finest level with big blocks): blocks of more than
-// kBigBlockRows rows are summed by whole CTAs at the end
+// kBigBlockRows rows are summed by warps and CTAs at the end (restrict_big_blocks)
 template <class LV>
 __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
                             const typename LV::val_t *u, typename LV::val_t *fc, int tid,
@@ -792,7 +918,7 @@ __device__ void op_restrict(const LV &L, const typename LV::val_t *f,
     if (L.fine) {
         for (int R = tid; R < L.nnext; R += nth) {
             const int r0 = L.bptr[R], r1 = L.bptr[R + 1];
-            if (big && r1 - r0 > kBigBlockRows) continue;  // a CTA's, below
+            if (big && r1 - r0 > kBigBlockRows) continue;  // by warps / CTAs, below
             T acc = 0;
             for (int i = r0; i < r1; i++) acc += row_residual(L, i, f, u);
             fc[R] = acc;
@@ -1073,10 +1199,13 @@ __device__ void op_update(const LV &L, const Op &op, const RedCtx &rc, int tid, 
 // group g; next() gives the view of the next coarser level (only its rhs and e are used)
 template <class LV, int RM, class G, class Next>
 __device__ __forceinline__ void run_op_on(const LV &L, const Next &next, const Op &op,
-                                          const RedCtx &rc, int tid, int nth, const G &g) {
+                                          const RedCtx &rc, int tid, int nth, const G &g,
+                                          const BigScratch &sc = BigScratch{}) {
     switch (op.kind) {
         case OP_ZERO: op_zero(L, vec_of(L, op.usel), tid, nth); break;
-        case OP_GS: op_gs<LV, true>(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
+        case OP_GS:
+            op_gs<LV, true>(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth, -1, -1, sc);
+            break;
         case OP_GS_FIRST: op_gs_first(L, op, vec_of(L, op.fsel), vec_of(L, op.usel), tid, nth); break;
         case OP_RESTRICT: {
             const auto &N = next();
@@ -1106,9 +1235,9 @@ __device__ __forceinline__ void run_op_on(const LV &L, const Next &next, const O
 // run one op on level op.level of a table of views, every thread of the CTA taking part
 template <class LV, int RM>
 __device__ __forceinline__ void run_op(const LV *tab, const Op &op, const RedCtx &rc, int tid,
-                                       int nth) {
+                                       int nth, const BigScratch &sc = BigScratch{}) {
     run_op_on<LV, RM>(tab[op.level], [&]() -> const LV & { return tab[op.level + 1]; }, op, rc,
-                      tid, nth, BlockGroup{});
+                      tid, nth, BlockGroup{}, sc);
 }
 
 }  // namespace amg

@@ -871,6 +871,20 @@ void build_big_blocks(amg_hierarchy *h, Level &F) {
                 ent[a + fill[lv[a + i]]++] =
                     make_int4(row, sa + (row & 31), (sl[(row >> 5) + 1] - sa) >> 5, 0);
             }
+            int ns = 0;  // the rows' off-diagonal slots, numbered in level order
+            for (int i = 0; i < m; i++) {
+                ent[a + i].w = ns;
+                ns += ent[a + i].z - 1;
+            }
+            for (int vb : {4, 8}) {
+                const size_t need = big_smem_bytes(m, depth, ns, vb);
+                if (m > kWarpBlockRows) {
+                    F.big_smem[vb == 8].push_back(need);
+                } else {
+                    size_t &w = F.big_smem_warp[vb == 8];
+                    w = std::max(w, need);
+                }
+            }
         }
         lofs[nbig] = (int)lp.size();
         lp.push_back(R);

@@ -82,6 +82,11 @@ struct CycleArgs {
     int bar_extra;
     // the finest level's input and output vectors when not the table's (FGMRES basis vectors)
     T *rhs0, *e0;
+    // CTAs 1.. lend their dynamic shared memory to the big blocks' sweeps; the warp-sized
+    // ones go to warps [0, big_wwarps) with big_wslice bytes each (0: to every warp, from
+    // global memory)
+    int big_smem, big_wwarps;
+    unsigned big_wslice;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -561,6 +566,16 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
                      ((int)threadIdx.x & 31);
     const int gnth = gridDim.x * blockDim.x;
     const RedCtx rc{a.partials, nullptr};
+    BigScratch sc;
+    if (a.big_smem && gridDim.x > 1) {
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        sc.p = blockIdx.x ? amg_smem : nullptr;  // CTA 0's holds the tail
+        sc.bytes = dyn;
+        sc.skip0 = true;
+        sc.wwarps = a.big_wwarps;
+        sc.wslice = a.big_wslice;
+    }
     for (int k = 0; k < a.nops; k++) {
         const Op &op = sop[k & 1];
         // the next descriptor into the other buffer (last read by op k-1), issued before op k
@@ -571,7 +586,7 @@ __global__ void __launch_bounds__(cycle_threads<T>(), 1) k_cycle(CycleArgs<T> a)
         if (op.kind == OP_TAIL) {
             if (blockIdx.x == 0) run_tail<T, W>(a);
         } else if (op.kind != OP_NOP) {
-            run_op<GL, RM_PARTIAL>(gtab, op, rc, gtid, gnth);
+            run_op<GL, RM_PARTIAL>(gtab, op, rc, gtid, gnth, sc);
         }
         if (!grid_barrier(a.bar, a.err, target, abort_flag, a.bar_limit_ns)) break;
         if (a.ts && blockIdx.x == 0 && threadIdx.x == 0) a.ts[k] = global_ns();
@@ -1015,6 +1030,9 @@ struct EngineBase {
     size_t smem = 0;
     int grid = 0;
     int coop = 0;  // the cycle kernel instance with the lane-parallel block smoother
+    int big_smem = 0;  // CTAs 1.. sweep the big blocks in their shared memory
+    int big_wwarps = 0;  // warps of a CTA with a slice for the warp-sized blocks
+    unsigned big_wslice = 0;
     std::vector<Op> hprog, htail;
     double tail_bytes = 0, cycle_bytes = 0;
     unsigned long long *ts = nullptr;
@@ -1035,6 +1053,7 @@ int red_grid(int64_t n) {
 }
 
 size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 
 // finest-level blocks of six or more rows on average (the octree's 2x2x2-node aggregates):
 // the lane-parallel block smoother (op_gs_blocks_coop) and restriction. Smaller blocks (a few
@@ -1480,6 +1499,35 @@ void build_engine(amg_hierarchy *h) {
     AMG_CUDA(cudaMemcpyAsync(E->prog, E->hprog.data(), sizeof(Op) * E->hprog.size(),
                              cudaMemcpyHostToDevice, s));
     E->smem = tl < h->nlev ? (size_t)E->lay.bytes : 0;
+    // Big blocks: swept in the shared memory of CTAs 1... A CTA-sized block needs as much as
+    // the largest one that fits on the device; the warp-sized ones get a slice each on as
+    // many warps per CTA as the most of them in one colour need (a block that does not fit
+    // takes the global-memory sweep; the forward and backward schedules each count).
+    E->big_smem = 0;
+    E->big_wwarps = 0;
+    E->big_wslice = 0;
+    if (h->lev[0].nbig > 0 && nsm > 1) {
+        const Level &F0 = h->lev[0];
+        const int vsel = sizeof(T) == 8;
+        const size_t avail = (size_t)std::max<long>(0, (long)optin - (long)static_smem - 1024);
+        size_t big = 0;
+        for (size_t need : F0.big_smem[vsel])
+            if (need > 0 && need <= avail) big = std::max(big, need);
+        const size_t wneed = F0.big_smem_warp[vsel];
+        int wtasks = 0;  // warp-sized blocks of the fullest colour
+        for (size_t c = 0; c < F0.color_bigc.size(); c++)
+            wtasks = std::max(wtasks, F0.color_bigc[c] - F0.color_big[c]);
+        if (wneed > 0 && wneed <= avail && wtasks > 0) {
+            const int per_cta = (wtasks + nsm - 2) / (nsm - 1);
+            E->big_wwarps = std::min({cycle_threads<T>() / 32, per_cta, (int)(avail / wneed)});
+            E->big_wslice = (unsigned)wneed;
+        }
+        const size_t smem = std::max(big, (size_t)E->big_wwarps * E->big_wslice);
+        if (smem > 0) {
+            E->big_smem = 1;
+            E->smem = std::max(E->smem, smem);
+        }
+    }
     void *kern = cycle_kernel<T>(E->lay.W, E->coop);
     // the kernel's dynamic shared-memory limit is a property of the function, shared by every
     // hierarchy of the process: set it to the device maximum (never lower it below what
@@ -1569,6 +1617,9 @@ void launch_cycle(amg_hierarchy *h, T *rhs0 = nullptr, T *e0 = nullptr) {
     a.bar_limit_ns = h->dbg_bar_limit_ns > 0 ? (unsigned long long)h->dbg_bar_limit_ns
                                              : kBarrierLimitNs;
     a.bar_extra = h->dbg_bar_extra;
+    a.big_smem = E->big_smem;
+    a.big_wwarps = E->big_wwarps;
+    a.big_wslice = E->big_wslice;
     AMG_CUDA(cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), s));
     a.ts = prof ? E->ts + 1 : nullptr;
     a.tprof = (prof && h->prof->tail_ops) ? E->tprof : nullptr;

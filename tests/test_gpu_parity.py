@@ -81,6 +81,10 @@ CASES = {
     # level runs grid-wide and the rest in the shared-memory tail; and a tail-only case
     "nu2": (dict(n=97, jitter=0.2, seed=6, rhs="normal"), dict(nu_pre=2, nu_post=2)),
     "nu31": (dict(n=41, jitter=0.2, seed=7, rhs="normal"), dict(nu_pre=3, nu_post=1)),
+    # graded with aggregates of up to 484 unknowns: 462 above 16 (swept by warps in level
+    # order), 7 above 128 (by CTAs, in shared memory in the persistent kernel)
+    "graded257_kappa": (dict(n=257, jitter=0.1, graded=True, kappa_blocks=16, seed=12,
+                             rhs="normal"), dict()),
 }
 
 
@@ -118,7 +122,8 @@ def test_solve_parity(amg, oracle_mod, name):
     assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("name", ["jitter33", "graded65_kappa", "kcycle3", "nu2", "nu31"])
+@pytest.mark.parametrize("name", ["jitter33", "graded65_kappa", "kcycle3", "nu2", "nu31",
+                                  "graded257_kappa"])
 def test_smoother_and_cycle_parity(amg, oracle_mod, name):
     prob, opts = _problem(name)
     G = amg.Hierarchy.from_problem(prob, **opts)
@@ -158,6 +163,25 @@ def test_several_sweeps_fp32_cycle(amg, oracle_mod):
     assert st1 == amg.OK and itg <= it1
     G.close()
     G1.close()
+
+
+def test_graded_fp32_cycle_big_blocks(amg, oracle_mod):
+    # the FP32 cycle on the graded case whose largest aggregates are swept by CTAs in shared
+    # memory: meets the tolerance in FP64, agrees with the oracle's solution
+    prob, opts = _problem("graded257_kappa")
+    O = oracle_mod.Hierarchy.from_problem(prob, **opts)
+    agg = O.level(0).agg
+    assert np.bincount(agg).max() > 128
+    G = amg.Hierarchy.from_problem(prob, cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES, **opts)
+    tol = 1e-8
+    xg, itg, rrg, stg = G.solve(prob.b, tol)
+    xo, ito, _, sto = O.solve(prob.b, tol)
+    assert stg == amg.OK and sto == oracle_mod.OK
+    A = prob.to_scipy()
+    assert np.linalg.norm(prob.b - A @ xg) / np.linalg.norm(prob.b) <= tol
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+    assert itg <= ito + 10, (itg, ito)
+    G.close()
 
 
 def test_uniform_grid_and_explicit_box(amg, oracle_mod):
