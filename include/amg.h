@@ -349,7 +349,9 @@ int amg_csr_to_ell(int32_t rows, const int32_t *rowptr, const int32_t *col, cons
  *   - Every call on a device shares the array: calls that overlap on the GPU (other streams
  *     or host threads) race and must be ordered by the caller.
  *   - Every call synchronises: it reads the overflow count back into host memory and waits
- *     on `stream` (cudaStreamSynchronize) before it returns.
+ *     on `stream` (cudaStreamSynchronize) before it returns. A stream that is capturing does
+ *     not allow that, so on such a stream the call returns AMG_ERR_UNSUPPORTED at once,
+ *     before any work, and the caller's capture goes on undisturbed.
  *   - The same precondition on rowptr as amg_csr_to_ell.
  *   - Returns AMG_ERR_INVALID_ARG if a row has more than `width` entries. Every failure sets
  *     the text amg_last_error returns; a CUDA error left pending by other code on the calling

@@ -444,43 +444,66 @@ def csr_to_ell(rowptr, col, val, width, diag_first=True, stream=None):
     return Aj, Ax
 
 
+def concatenate(problems, device=None):
+    """The block-diagonal CSR of many systems, the layout amg_batch_setup takes.
+
+    problems: list of (rowptr, col, val, x, y) of each system (local indexing, host arrays).
+    Returns (row_off, rowptr, col, val, x, y): row_off (host int64, one entry per system and
+    the total) and the concatenated arrays, as torch tensors on `device` if one is given."""
+    sizes = [len(p[0]) - 1 for p in problems]
+    nnzs = [len(p[1]) for p in problems]
+    for k, p in enumerate(problems):
+        if sizes[k] < 0 or len(p[2]) != nnzs[k] or len(p[3]) != sizes[k] \
+                or len(p[4]) != sizes[k]:
+            raise ValueError(f"system {k}: rowptr needs n + 1 entries, val as many as col, "
+                             "x and y n each")
+    row_off = np.zeros(len(problems) + 1, np.int64)
+    row_off[1:] = np.cumsum(sizes)
+    nz_off = np.zeros(len(problems) + 1, np.int64)
+    nz_off[1:] = np.cumsum(nnzs)
+    if row_off[-1] >= 2**31 or nz_off[-1] >= 2**31:
+        raise ValueError("the concatenation needs fewer than 2^31 rows and entries")
+    rp = np.empty(row_off[-1] + 1, np.int32)
+    cl = np.empty(nz_off[-1], np.int32)
+    vl = np.empty(nz_off[-1], np.float64)
+    xx = np.empty(row_off[-1], np.float64)
+    yy = np.empty(row_off[-1], np.float64)
+    for k, p in enumerate(problems):
+        r0, r1, z0, z1 = row_off[k], row_off[k + 1], nz_off[k], nz_off[k + 1]
+        np.add(np.asarray(p[0])[:-1], z0, out=rp[r0:r1], casting="unsafe")
+        np.add(np.asarray(p[1]), r0, out=cl[z0:z1], casting="unsafe")
+        vl[z0:z1] = p[2]
+        xx[r0:r1] = p[3]
+        yy[r0:r1] = p[4]
+    rp[-1] = nz_off[-1]
+    arrays = [rp, cl, vl, xx, yy]
+    if device is not None:
+        import torch
+
+        arrays = [torch.as_tensor(a).to(device) for a in arrays]
+    return (row_off, *arrays)
+
+
 class Batch:
     """amg_batch_setup / amg_batch_solve: many independent systems, one persistent kernel.
 
     problems: list of (rowptr, col, val, x, y) of each system (local indexing, host arrays);
     they are concatenated into one block-diagonal CSR here (the layout the C ABI takes).
+    concatenated: the output of `concatenate` instead of problems (the systems laid out
+    already, on the host or the device).
     """
 
-    def __init__(self, problems, aux_level=0, coarsest_max=64, kcycle_n=2, max_iters=200,
-                 cycle_prec=FP64, stream=None, device=None, nu_pre=1, nu_post=1):
+    def __init__(self, problems=None, aux_level=0, coarsest_max=64, kcycle_n=2, max_iters=200,
+                 cycle_prec=FP64, stream=None, device=None, nu_pre=1, nu_post=1,
+                 concatenated=None):
         L = lib()
-        sizes = [len(p[0]) - 1 for p in problems]
-        nnzs = [len(p[1]) for p in problems]
-        for k, p in enumerate(problems):
-            if sizes[k] < 0 or len(p[2]) != nnzs[k] or len(p[3]) != sizes[k] \
-                    or len(p[4]) != sizes[k]:
-                raise ValueError(f"system {k}: rowptr needs n + 1 entries, val as many as col, "
-                                 "x and y n each")
-        row_off = np.zeros(len(problems) + 1, np.int64)
-        row_off[1:] = np.cumsum(sizes)
-        nz_off = np.zeros(len(problems) + 1, np.int64)
-        nz_off[1:] = np.cumsum(nnzs)
-        rp = np.concatenate([np.asarray(p[0], np.int64)[:-1] + nz_off[k]
-                             for k, p in enumerate(problems)] + [nz_off[-1:]]).astype(np.int32)
-        cl = np.concatenate([np.asarray(p[1], np.int64) + row_off[k]
-                             for k, p in enumerate(problems)]).astype(np.int32)
-        vl = np.concatenate([np.asarray(p[2], np.float64) for p in problems])
-        xx = np.concatenate([np.asarray(p[3], np.float64) for p in problems])
-        yy = np.concatenate([np.asarray(p[4], np.float64) for p in problems])
-        arrays = [rp, cl, vl, xx, yy]
-        if device is not None:
-            import torch
-
-            arrays = [torch.as_tensor(a).to(device) for a in arrays]
-        rp, cl, vl, xx, yy = arrays
+        if concatenated is None:
+            concatenated = concatenate(problems, device)
+        row_off, rp, cl, vl, xx, yy = concatenated
+        row_off = np.asarray(row_off, np.int64)
         self.row_off = row_off
         self.n = int(row_off[-1])
-        self.nprob = len(problems)
+        self.nprob = len(row_off) - 1
         A = Csr(self.n, len(cl), _ptr(rp), _ptr(cl), _ptr(vl))
         o = Options()
         L.amg_options_default(C.byref(o))

@@ -18,8 +18,8 @@ LIB = os.path.join(HERE, "libamg_gb300.so")
 # the bounds-checking variant: index checks in the kernels' gathers (flag, never a trap)
 OBJ_BC = os.path.join(HERE, "_build_bc")
 LIB_BC = os.path.join(HERE, "libamg_gb300_bc.so")
-SOURCES = ["scan_sort.cu", "setup.cu", "solve.cu", "capi.cu", "noalloc.cu", "batch.cu",
-           "batch_graded.cu"]
+SOURCES = ["scan_sort.cu", "setup.cu", "setup_batch.cu", "solve.cu", "capi.cu", "noalloc.cu",
+           "batch.cu", "batch_graded.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,7 @@ constexpr int kMaxLevels = 20;
 constexpr int kRedBlocks = 608;    // blocks of the deterministic reductions (4 x 152 SMs)
 constexpr int kRedThreads = 256;
 constexpr int kMaxCoarsest = 256;  // largest exact coarsest level
+constexpr int kBatchDirs = 32;     // outer directions a batched system starts with (grown on demand)
 
 // scalar slots of a level's device scalar array
 // (one slot per Alg. 1 step where a kernel reads the previous step's value while writing its
@@ -174,6 +176,7 @@ struct amg_hierarchy {
     double *osc = nullptr;             // outer scalars
     int *oit = nullptr;                // device iteration counter
     double *h_pinned = nullptr;        // pinned host scalars
+    bool pinned_owned = true;          // false: h_pinned is part of a batch's pinned block
     // FGMRES state (FP64 basis)
     double *gm_V = nullptr, *gm_Z = nullptr, *gm_H = nullptr;
     int gm_cap = 0;
@@ -255,6 +258,41 @@ T *halloc(amg_hierarchy *h, size_t count) {
     return (T *)p;
 }
 
+// Many small arrays carved from a few large allocations (a bump allocator over chunks): the
+// batched setup's hierarchies take their arrays from the batch's arena, which owns them and
+// frees them with the batch. Every piece is 256-byte aligned.
+struct Arena {
+    cudaStream_t s = nullptr;
+    std::vector<void *> chunks;
+    char *cur = nullptr;
+    size_t left = 0;
+    size_t bytes = 0;  // allocated chunk bytes
+    size_t chunk = size_t(64) << 20;  // chunk size (a larger piece gets a chunk of its own)
+    void *get(size_t b) {
+        b = (std::max<size_t>(b, 16) + 255) & ~size_t(255);
+        if (b > left) {
+            const size_t c = std::max(b, chunk);
+            void *p = nullptr;
+            device_alloc(&p, c, s);
+            chunks.push_back(p);
+            bytes += c;
+            cur = (char *)p;
+            left = c;
+        }
+        void *r = cur;
+        cur += b;
+        left -= b;
+        return r;
+    }
+    void release() {
+        for (void *p : chunks) cudaFreeAsync(p, s);
+        chunks.clear();
+        cur = nullptr;
+        left = 0;
+        bytes = 0;
+    }
+};
+
 // scratch allocation freed by the owner (RAII)
 struct Scratch {
     cudaStream_t s;
@@ -306,6 +344,26 @@ void prepare_cycle(amg_hierarchy *h);
 // what a batched solve needs of a hierarchy beyond its setup: the FP32 cycle's copies (FP32
 // cycle) and the batched-solve workspace; idempotent, synchronises h->stream
 void batch_prepare(amg_hierarchy *h);
+// doubles of the outer iteration's device scalars (h->osc) for max_iters iterations
+size_t outer_scalar_count(int max_iters);
+// host image of h's device level table in the cycle precision fp32 (LevelDev<T, int>[nlev]):
+// what the level table holds once the level arrays exist; returns its size in bytes
+size_t level_table_image(amg_hierarchy *h, bool fp32, std::vector<unsigned char> &out);
+// the finest level's big blocks and their level-ordered sweep schedules (setup.cu)
+void build_fine_big_blocks(amg_hierarchy *h);
+// Batched setup (setup_batch.cu): every hierarchy of hs (created, options and sizes set, no
+// levels yet; system p is rows[p] of the block-diagonal A: rows r0 .. r0 + n, entries
+// nz0 .. nz0 + nnz; x, y device; every system has more than coarsest_max unknowns) is built
+// by one set of multi-system kernels on stream s, with the arrays from `ar` and the pinned
+// scalars of every hierarchy from *pinned (one block, allocated here); then each hierarchy is
+// ready for amg_solve and batched solves like one from amg_setup + batch_prepare. Throws
+// amg::Error.
+struct BatchRows {
+    int r0, n, nz0, nnz;
+};
+void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const double *x,
+                 const double *y, const std::vector<BatchRows> &rows, cudaStream_t s, Arena &ar,
+                 double **pinned);
 // outer directions P[j], Q[j] (and the device tables dP, dQ) for j < count at least, in
 // chunks, at most max_iters; returns the number allocated. Synchronises h->stream.
 int ensure_directions(amg_hierarchy *h, int count);

@@ -13,7 +13,6 @@ namespace amg {
 template <class T>
 using BLev = LevelDev<T, int>;
 
-constexpr int kBatchDirs = 32;   // outer directions a system starts with (grown on demand)
 constexpr int kBatchChunk = 64;  // directions orthogonalised against per pass
 constexpr int kBatchResume = 1000;  // status: the directions are full, the host adds more
 constexpr int kMaxTeam = 8;    // CTAs of one team at most

@@ -6,7 +6,6 @@
 #include <new>
 #include <numeric>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "amg_internal.cuh"
@@ -81,7 +80,7 @@ void destroy(amg_hierarchy *h) {
     amg::profiler_free(h);
     for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
-    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->h_pinned && h->pinned_owned) cudaFreeHost(h->h_pinned);
     if (h->order_ev) cudaEventDestroy(h->order_ev);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -327,6 +326,8 @@ void amg_free(amg_hierarchy *h) { destroy(h); }
 struct amg_batch {
     std::vector<amg_hierarchy *> hs;
     bool owns = true;  // hierarchies built by amg_batch_setup (else borrowed)
+    amg::Arena arena;  // arrays of the hierarchies the batched setup built
+    double *pinned = nullptr;  // their pinned host scalars, one block
     std::vector<int64_t> row_off;
     amg::BatchEngine *eng = nullptr;
     cudaStream_t stream = nullptr;
@@ -342,6 +343,11 @@ void destroy_batch(amg_batch *bt) {
     amg::batch_destroy(bt->eng);
     if (bt->owns)
         for (amg_hierarchy *h : bt->hs) destroy(h);
+    if (bt->stream) {  // after the hierarchies: they hold pieces of the arena
+        bt->arena.release();
+        cudaStreamSynchronize(bt->stream);
+    }
+    if (bt->pinned) cudaFreeHost(bt->pinned);
     if (bt->order_ev) cudaEventDestroy(bt->order_ev);
     if (bt->stream) cudaStreamDestroy(bt->stream);
     delete bt;
@@ -356,6 +362,12 @@ __global__ void k_localize_rows(int n, const int *__restrict__ rowptr, int nz0,
 __global__ void k_localize_cols(int nnz, const int *__restrict__ col, int r0, int *__restrict__ out) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < nnz) out[k] = col[k] - r0;
+}
+// out[p] = rowptr[row_off[p]]: the first entry of every system
+__global__ void k_gather_rowptr(int m, const int *__restrict__ rowptr,
+                                const int64_t *__restrict__ row_off, int *__restrict__ out) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < m) out[p] = rowptr[row_off[p]];
 }
 
 }  // namespace
@@ -394,79 +406,81 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
         const double *vl = to_device(A->val, (size_t)A->nnz, tmp);
         const double *xd = to_device(x, N, tmp);
         const double *yd = to_device(y, N, tmp);
-        // nonzero offset of every system: rowptr[row_off[p]]
+        // nonzero offset of every system: rowptr[row_off[p]], gathered and read back at once
         std::vector<int> nz(nprob + 1);
-        for (int p = 0; p <= nprob; p++)
-            AMG_CUDA(cudaMemcpyAsync(&nz[p], rp + row_off[p], sizeof(int), cudaMemcpyDeviceToHost, us));
-        AMG_CUDA(cudaStreamSynchronize(us));
+        {
+            int64_t *dro = tmp.get<int64_t>((size_t)nprob + 1);
+            int *dnz = tmp.get<int>((size_t)nprob + 1);
+            AMG_CUDA(cudaMemcpyAsync(dro, row_off, sizeof(int64_t) * (nprob + 1),
+                                     cudaMemcpyHostToDevice, us));
+            k_gather_rowptr<<<(nprob + 256) / 256, 256, 0, us>>>(nprob + 1, rp, dro, dnz);
+            AMG_CUDA(cudaGetLastError());
+            AMG_CUDA(cudaMemcpyAsync(nz.data(), dnz, sizeof(int) * (nprob + 1),
+                                     cudaMemcpyDeviceToHost, us));
+            AMG_CUDA(cudaStreamSynchronize(us));
+        }
         if (nz[0] != 0 || nz[nprob] != A->nnz)
             throw Error{AMG_ERR_BAD_MATRIX, "rowptr does not run from 0 to nnz"};
         bt->row_off.assign(row_off, row_off + nprob + 1);
         for (int p = 0; p < nprob; p++)
             if (nz[p + 1] - nz[p] < (int)(row_off[p + 1] - row_off[p]))
                 throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
-        // The systems' setups are independent chains of small kernels and host round trips
-        // (latency-bound), so several run at once: worker threads take systems in turn, each
-        // on its own stream (ordered after the caller's), largest systems first.
+        // Systems of more than coarsest_max unknowns are set up together, by one set of
+        // multi-system kernels (setup_batch.cu); a system small enough to be its own coarsest
+        // level (one level, the exact solve) takes the single-system setup.
         bt->hs.assign(nprob, nullptr);
-        cudaEvent_t ready;
-        AMG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-        AMG_CUDA(cudaEventRecord(ready, us));  // the staged inputs
-        std::vector<int> order(nprob);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return row_off[a + 1] - row_off[a] > row_off[b + 1] - row_off[b];
-        });
-        std::atomic<int> next{0};
-        std::mutex err_m;
-        Error first{AMG_OK, ""};
-        const int dev = bt->device;
-        auto worker = [&]() {
-            cudaStream_t ws = nullptr;
+        std::vector<int> multi;
+        for (int p = 0; p < nprob; p++) {
+            const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
+            if (n > o.coarsest_max) {
+                multi.push_back(p);
+                continue;
+            }
+            const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
+            Scratch loc(us);
+            int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
+            k_localize_rows<<<(n + 256) / 256, 256, 0, us>>>(n, rp + r0, z0, lrp);
+            k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
+            AMG_CUDA(cudaGetLastError());
+            amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
+            bt->hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, us);
+            amg::batch_prepare(bt->hs[p]);
+        }
+        if (!multi.empty()) {
+            std::vector<amg_hierarchy *> mh;
+            std::vector<amg::BatchRows> rows;
+            AMG_CUDA(cudaEventRecord(bt->order_ev, us));  // the staged inputs
+            AMG_CUDA(cudaStreamWaitEvent(bt->stream, bt->order_ev, 0));
+            for (int p : multi) {
+                amg_hierarchy *h = new amg_hierarchy();
+                bt->hs[p] = h;
+                h->opt = o;
+                if (h->opt.nu_pre == 0) h->opt.nu_pre = 1;
+                if (h->opt.nu_post == 0) h->opt.nu_post = 1;
+                h->N = row_off[p + 1] - row_off[p];
+                h->dim = 2;
+                h->device = bt->device;
+                h->stream = bt->stream;  // while the batch builds it
+                mh.push_back(h);
+                rows.push_back(amg::BatchRows{(int)row_off[p], (int)h->N, nz[p], nz[p + 1] - nz[p]});
+            }
+            bt->arena.s = bt->stream;
+            const int64_t l0 = amg::g_launches;
             try {
-                AMG_CUDA(cudaSetDevice(dev));
-                AMG_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
-                AMG_CUDA(cudaStreamWaitEvent(ws, ready, 0));
-                for (int t; (t = next.fetch_add(1)) < nprob;) {
-                    {
-                        std::lock_guard<std::mutex> g(err_m);
-                        if (first.status != AMG_OK) break;  // another system failed: stop
-                    }
-                    const int p = order[t];
-                    const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
-                    const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
-                    Scratch loc(ws);
-                    int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
-                    k_localize_rows<<<(n + 256) / 256, 256, 0, ws>>>(n, rp + r0, z0, lrp);
-                    k_localize_cols<<<(nnz + 255) / 256, 256, 0, ws>>>(nnz, cl + z0, r0, lcl);
-                    AMG_CUDA(cudaGetLastError());
-                    amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
-                    // returns after its work is done, so the localized arrays may be freed
-                    bt->hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, ws);
-                    amg::batch_prepare(bt->hs[p]);  // here, not serially in batch_create
+                amg::build_batch(mh, amg_csr{A->n, A->nnz, rp, cl, vl}, xd, yd, rows, bt->stream,
+                                 bt->arena, &bt->pinned);
+                for (amg_hierarchy *h : mh) {
+                    h->setup_launches = amg::g_launches - l0;  // the whole batch's launches
+                    h->stream = nullptr;
+                    AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+                    AMG_CUDA(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
                 }
-            } catch (const Error &e) {
-                std::lock_guard<std::mutex> g(err_m);
-                if (first.status == AMG_OK) first = e;
-            } catch (const std::bad_alloc &) {
-                std::lock_guard<std::mutex> g(err_m);
-                if (first.status == AMG_OK) first = Error{AMG_ERR_OOM, "host allocation failed"};
             } catch (...) {
-                std::lock_guard<std::mutex> g(err_m);
-                if (first.status == AMG_OK) first = Error{AMG_ERR_CUDA, "unexpected internal exception"};
+                for (amg_hierarchy *h : mh)
+                    if (h->stream == bt->stream) h->stream = nullptr;  // not the hierarchy's own
+                throw;
             }
-            if (ws) {
-                cudaStreamSynchronize(ws);
-                cudaStreamDestroy(ws);
-            }
-        };
-        const int nw = std::max(1, std::min({nprob, 16, (int)std::thread::hardware_concurrency()}));
-        std::vector<std::thread> pool;
-        for (int w = 1; w < nw; w++) pool.emplace_back(worker);
-        worker();
-        for (std::thread &t : pool) t.join();
-        cudaEventDestroy(ready);
-        if (first.status != AMG_OK) throw first;
+        }
         bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, 0);
         AMG_CUDA(cudaStreamSynchronize(us));
         *out = bt;

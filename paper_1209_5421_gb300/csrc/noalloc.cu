@@ -130,6 +130,16 @@ extern "C" int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const
     if (rows > kNoAllocMaxRows)  // beyond the static scratch
         return amg::set_last_error(AMG_ERR_UNSUPPORTED,
                                    "rows above the allocation-free packer's limit (4,194,304)");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call reads its result back and waits on the stream, which a stream under capture
+    // does not allow (and which would end the caller's capture): refuse it untouched
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return amg::set_last_error(AMG_ERR_UNSUPPORTED,
+                                   "the allocation-free packer waits on its stream: not while "
+                                   "the stream is capturing");
     if (!on_device(rowptr) || !on_device(col) || !on_device(val) || !on_device(Aj) ||
         !on_device(Ax))  // host arrays would need staging buffers
         return amg::set_last_error(AMG_ERR_INVALID_ARG,
@@ -142,7 +152,6 @@ extern "C" int amg_csr_to_ell_noalloc(int32_t rows, const int32_t *rowptr, const
     if (st == AMG_ERR_UNSUPPORTED)
         return amg::set_last_error(st, "device ordinal above the packer's device table");
     if (st != AMG_OK) return amg::set_last_error(st, "cudaGetSymbolAddress of the packer's scratch failed");
-    cudaStream_t s = (cudaStream_t)stream;
     const int nblocks = (rows + kNoAllocThreads - 1) / kNoAllocThreads;
     // cudaLaunchKernel returns the status of its own launch, so an error left pending on this
     // thread by other code is neither taken for this call's nor cleared here

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "amg_internal.cuh"
+#include "setup_ops.cuh"
 
 namespace amg {
 namespace {
@@ -24,29 +25,7 @@ __global__ void k_validate(int n, int64_t nnz, const int *__restrict__ rowptr,
                            const double *__restrict__ z, int *err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int flags = 0;
-    int64_t b = rowptr[i], e = rowptr[i + 1];
-    if (i == 0 && b != 0) flags |= 1;
-    if (i == n - 1 && e != nnz) flags |= 1;
-    if (b < 0 || e < b || e > nnz) {
-        flags |= 1;
-    } else {
-        bool diag = false;
-        int prev = -1;
-        for (int64_t p = b; p < e; p++) {
-            int c = col[p];
-            double v = val[p];
-            if (c < 0 || c >= n || c <= prev) flags |= 1;
-            prev = c;
-            if (!isfinite(v)) flags |= 1;
-            if (c == i) {
-                diag = true;
-                if (!(v > 0.0)) flags |= 1;
-            }
-        }
-        if (!diag) flags |= 1;
-    }
-    if (!isfinite(x[i]) || !isfinite(y[i]) || (z && !isfinite(z[i]))) flags |= 2;
+    const int flags = validate_row(i, n, nnz, rowptr, 0, col, 0, val, x, y, z);
     if (flags) atomicOr(err, flags);
 }
 
@@ -103,20 +82,6 @@ __global__ void k_minmax_final(int nb, const double *part, double *bbox) {
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Sec. 4.2 index formula, one coordinate: floor((v - lo) / (hi - lo) * 2^L). Operation order
-// subtract, IEEE round-to-nearest divide, exact multiply by 2^L, floor; the closed upper
-// edge of the box belongs to the last cell and points outside are clamped into it.
-__device__ __forceinline__ int cell_1d(double v, double lo, double hi, int L) {
-    const int w = 1 << L;
-    if (!(hi > lo)) return 0;
-    double q = __ddiv_rn(__dsub_rn(v, lo), __dsub_rn(hi, lo));
-    double s = __dmul_rn(q, (double)w);
-    if (!(s >= 0.0)) return 0;
-    if (s >= (double)w) return w - 1;
-    return (int)floor(s);
-}
-
 // level-L aggregate label of every unknown (eq. agg_L): i = ty * 2^L + tx
 // Cells are indexed t1 + w (t2 + w t3), w = 2^level: t3 = 0 on the quadtree, so the same
 // decoding serves both trees (cell_t1 / cell_t2 / cell_t3 below).
@@ -130,15 +95,6 @@ __global__ void k_bin(int n, const double *__restrict__ x, const double *__restr
     int tz = z ? cell_1d(z[j], bbox[4], bbox[5], L) : 0;
     cell[j] = (tz * (1 << L) + ty) * (1 << L) + tx;
 }
-__device__ __forceinline__ int cell_t1(int c, int w) { return c % w; }
-__device__ __forceinline__ int cell_t2(int c, int w) { return (c / w) % w; }
-__device__ __forceinline__ int cell_t3(int c, int w) { return c / w / w; }
-// parent cell on the grid of width w/2: every coordinate halved (eq. agg_k, both trees)
-__device__ __forceinline__ int parent_cell(int c, int w) {
-    const int h = w >> 1;
-    return ((cell_t3(c, w) >> 1) * h + (cell_t2(c, w) >> 1)) * h + (cell_t1(c, w) >> 1);
-}
-
 // parent cell of a cell of a grid of width w (Sec. 4.2 coarse-level form):
 // ((t2 / 2) * (w / 2) + t1 / 2)
 __global__ void k_parent_cell(int n, const int *__restrict__ cell, int w, int *__restrict__ pc) {
@@ -175,13 +131,6 @@ __global__ void k_scatter_inv(int n, const int *__restrict__ nat, int *__restric
 }
 
 // ---------------------------------------------------------------------------------------
-// span s: the largest |dt1|, |dt2| between the cells of the row and column of an entry
-__device__ __forceinline__ int cell_dist(int a, int b, int w) {
-    int d1 = abs(cell_t1(a, w) - cell_t1(b, w)), d2 = abs(cell_t2(a, w) - cell_t2(b, w));
-    int d3 = abs(cell_t3(a, w) - cell_t3(b, w));
-    return max(max(d1, d2), d3);
-}
-
 __device__ __forceinline__ void block_max_atomic(int v, int *out) {
     __shared__ int sm[kT / 32];
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -229,8 +178,7 @@ __global__ void k_colors(int n, const int *__restrict__ cell, int w, int m,
                          int *__restrict__ color) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int c = cell[i];
-    color[i] = cell_t1(c, w) % m + m * (cell_t2(c, w) % m) + m * m * (cell_t3(c, w) % m);
+    color[i] = cell_color(cell[i], w, m);
 }
 
 // cnt[k] += number of i with key[i] == k, keys in [0, nbins): a shared-memory histogram per
@@ -347,90 +295,10 @@ __global__ void k_rap(int nc, const int *__restrict__ bptr, const int4 *__restri
                       const int *__restrict__ ccell, int cw, int s, const int *__restrict__ csl,
                       int *__restrict__ clen, int *__restrict__ ccol,
                       double *__restrict__ cval, int *err) {
-    constexpr int WMAX = 2 * SMAX + 1;
-    constexpr int NS = DIM == 3 ? WMAX * WMAX * WMAX : WMAX * WMAX;
-    constexpr int NKIDS = DIM == 3 ? 8 : 4;
     int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
-    const int W = 2 * s + 1;
-    double acc[FILL ? NS : 1];
-    int cof[FILL ? NS : 1];
-    unsigned long long bits[(NS + 63) / 64];
-#pragma unroll
-    for (int t = 0; t < (NS + 63) / 64; t++) bits[t] = 0ull;
-    if (FILL) {
-        for (int t = 0; t < NS; t++) acc[t] = 0.0;
-    }
-    const int cP = ccell[P];
-    const int p1 = cell_t1(cP, cw), p2 = cell_t2(cP, cw), p3 = cell_t3(cP, cw);
-    int rbeg, rend;
-    int kids[NKIDS];
-    if (FINE) {
-        rbeg = bptr[P];
-        rend = bptr[P + 1];
-    } else {
-        int4 ch = children[P];
-        kids[0] = ch.x;
-        kids[1] = ch.y;
-        kids[2] = ch.z;
-        kids[3] = ch.w;
-        if constexpr (DIM == 3) {
-            int4 c2 = children2[P];
-            kids[4] = c2.x;
-            kids[5] = c2.y;
-            kids[6] = c2.z;
-            kids[7] = c2.w;
-        }
-        rbeg = 0;
-        rend = NKIDS;
-    }
-    for (int it = rbeg; it < rend; it++) {
-        int i = FINE ? it : kids[it];
-        if (i < 0) continue;
-        const int base = fsl[i >> 5] + (i & 31), width = (fsl[(i >> 5) + 1] - fsl[i >> 5]) >> 5;
-        for (int k = 0; k < width; k++) {
-            int c = fcol[base + 32 * k];
-            if (c < 0) continue;
-            int C = fparent[c];
-            int cC = ccell[C];
-            int d1 = cell_t1(cC, cw) - p1, d2 = cell_t2(cC, cw) - p2, d3 = cell_t3(cC, cw) - p3;
-            if (d1 < -s || d1 > s || d2 < -s || d2 > s || d3 < -s || d3 > s) {
-                atomicOr(err, 4);
-                continue;
-            }
-            // slots in ascending offset order (d3, d2, d1) = ascending coarse cell index
-            int t = ((DIM == 3 ? (d3 + s) * W : 0) + (d2 + s)) * W + (d1 + s);
-            bits[t >> 6] |= 1ull << (t & 63);
-            if (FILL) {
-                acc[t] += fval[base + 32 * k];
-                cof[t] = C;
-            }
-        }
-    }
-    const int center = DIM == 3 ? (s * W + s) * W + s : s * W + s;
-    const int nslot = DIM == 3 ? W * W * W : W * W;
-    if (!FILL) {
-        int cnt = 0;
-#pragma unroll
-        for (int t = 0; t < (NS + 63) / 64; t++) cnt += __popcll(bits[t]);
-        if (!((bits[center >> 6] >> (center & 63)) & 1ull)) cnt++;  // diagonal always stored
-        clen[P] = cnt;
-        return;
-    }
-    const int base = csl[P >> 5] + (P & 31), width = (csl[(P >> 5) + 1] - csl[P >> 5]) >> 5;
-    ccol[base] = P;
-    cval[base] = acc[center];
-    int k = 1;
-    for (int t = 0; t < nslot; t++) {
-        if (t == center || !((bits[t >> 6] >> (t & 63)) & 1ull)) continue;
-        ccol[base + 32 * k] = cof[t];
-        cval[base + 32 * k] = acc[t];
-        k++;
-    }
-    for (; k < width; k++) {
-        ccol[base + 32 * k] = -1;
-        cval[base + 32 * k] = 0.0;
-    }
+    rap_row<SMAX, FINE, FILL, DIM>(P, bptr, children, children2, fsl, fcol, fval, fparent, ccell,
+                                   cw, s, csl, clen, ccol, cval, err);
 }
 
 // stored entries per colour (rows of colour c are the range [cr[c], cr[c+1]))
@@ -490,69 +358,8 @@ __global__ void k_dense_from_sell(int n, const int *__restrict__ sl, const int *
 
 __global__ void k_chol_inverse(int n, double *ga, double *gw, double *ainv, float *ainv32,
                                int *err) {
-    // the factor and the inverse factor live in shared memory when they fit (every access
-    // of the n^3 loops is then a shared-memory access), else in the global scratch
     extern __shared__ double smat[];
-    const bool in_smem = (ga == nullptr);
-    double *a = in_smem ? smat : ga;
-    double *w = in_smem ? smat + (size_t)n * n : gw;
-    __shared__ int bad;
-    const int t = threadIdx.x, T = blockDim.x;
-    if (t == 0) bad = 0;
-    if (in_smem)
-        for (int e = t; e < n * n; e += T) a[e] = ainv[e];  // the dense matrix arrives in ainv
-    __syncthreads();
-    const int lane = t & 31, warp = t >> 5, nwarp = T >> 5;
-    for (int j = 0; j < n; j++) {
-        if (t == 0) {
-            double d = a[(size_t)j * n + j];
-            if (!(d > 0.0) || !isfinite(d)) bad = 1;
-            a[(size_t)j * n + j] = sqrt(fabs(d));
-        }
-        __syncthreads();
-        if (bad) break;
-        double djj = a[(size_t)j * n + j];
-        for (int i = j + 1 + t; i < n; i += T) a[(size_t)i * n + j] /= djj;
-        __syncthreads();
-        // trailing update of the lower triangle, a warp per row (each entry once per j)
-        for (int i = j + 1 + warp; i < n; i += nwarp) {
-            const double lij = a[(size_t)i * n + j];
-            for (int k = j + 1 + lane; k <= i; k += 32) a[(size_t)i * n + k] -= lij * a[(size_t)k * n + j];
-        }
-        __syncthreads();
-    }
-    if (bad) {
-        if (t == 0) atomicOr(err, 8);
-        return;
-    }
-    // W = L^{-1} (lower), one column per thread
-    for (int c = t; c < n; c += T) {
-        for (int i = 0; i < c; i++) w[(size_t)i * n + c] = 0.0;
-        for (int i = c; i < n; i++) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; k++) s -= a[(size_t)i * n + k] * w[(size_t)k * n + c];
-            w[(size_t)i * n + c] = s / a[(size_t)i * n + i];
-        }
-    }
-    __syncthreads();
-    // A^{-1} = W^t W: entry (i, j), i >= j, and its mirror (the same sum: products commute)
-    const int tri = n * (n + 1) / 2;
-    for (int q = t; q < tri; q += T) {
-        int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);  // q = i (i+1) / 2 + j
-        while (i * (i + 1) / 2 > q) i--;
-        while ((i + 1) * (i + 2) / 2 <= q) i++;
-        const int j = q - i * (i + 1) / 2;
-        double s = 0.0;
-        for (int k = i; k < n; k++) s += w[(size_t)k * n + i] * w[(size_t)k * n + j];
-        const float hi = (float)s;  // FP32 cycle: high and low parts, s ~ hi + lo
-        const float lo = (float)(s - (double)hi);
-        for (int m = 0; m < (i == j ? 1 : 2); m++) {
-            const size_t e = m == 0 ? (size_t)i * n + j : (size_t)j * n + i;
-            ainv[e] = s;
-            ainv32[e] = hi;
-            ainv32[(size_t)n * n + e] = lo;
-        }
-    }
+    chol_inverse_block(n, ga, gw, ainv, ainv32, err, smat);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -944,6 +751,8 @@ void coarsest_inverse(amg_hierarchy *h, Level &lv) {
 }
 
 }  // namespace
+
+void build_fine_big_blocks(amg_hierarchy *h) { build_big_blocks(h, h->lev[0]); }
 
 // =======================================================================================
 void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, const double *y,

@@ -1266,8 +1266,8 @@ void annotate_reductions(std::vector<Op> &prog) {
 }
 
 template <class T>
-void fill_tables(amg_hierarchy *h) {
-    std::vector<GLev<T>> tab(h->nlev);
+void table_image(amg_hierarchy *h, std::vector<GLev<T>> &tab) {
+    tab.assign(h->nlev, GLev<T>());
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
         GLev<T> &d = tab[l];
@@ -1302,6 +1302,12 @@ void fill_tables(amg_hierarchy *h) {
         d.sc = lv.sc;
         d.nnext = (l + 1 < h->nlev) ? h->lev[l + 1].n : 0;
     }
+}
+
+template <class T>
+void fill_tables(amg_hierarchy *h) {
+    std::vector<GLev<T>> tab;
+    table_image<T>(h, tab);
     void *&dst = (sizeof(T) == 8) ? h->lev_tab64 : h->lev_tab32;
     if (!dst) dst = halloc<GLev<T>>(h, h->nlev);
     AMG_CUDA(cudaMemcpyAsync(dst, tab.data(), sizeof(GLev<T>) * h->nlev, cudaMemcpyHostToDevice,
@@ -1599,6 +1605,8 @@ void ensure_fp32(amg_hierarchy *h) {
 // one launch of the persistent kernel: z = B^_0 [r] on level 0's table buffers
 template <class T>
 void launch_cycle(amg_hierarchy *h, T *rhs0 = nullptr, T *e0 = nullptr) {
+    // hierarchies of a batched setup get their single-system engine on first use
+    if (!engine_slot<T>(h)) build_engine<T>(h);
     EngineBase *E = engine_slot<T>(h);
     cudaStream_t s = h->stream;
     const bool prof = profiling(h);
@@ -1729,7 +1737,7 @@ void allocate_solve_workspace(amg_hierarchy *h) {
     h->bo = halloc<double>(h, n);
     h->lev[0].v64.rhs = h->ro;
     h->lev[0].v64.e = h->zo;
-    h->osc = halloc<double>(h, OS_ZQ + 2 * (size_t)h->opt.max_iters + 8);
+    h->osc = halloc<double>(h, outer_scalar_count(h->opt.max_iters));
     h->oit = halloc<int>(h, 1);
     h->dP = halloc<double *>(h, h->opt.max_iters);
     h->dQ = halloc<double *>(h, h->opt.max_iters);
@@ -1746,6 +1754,25 @@ void allocate_solve_workspace(amg_hierarchy *h) {
 }
 
 int bounds_flags_solve() { return bounds_flag_read_clear(); }
+
+size_t outer_scalar_count(int max_iters) { return OS_ZQ + 2 * (size_t)max_iters + 8; }
+
+size_t level_table_image(amg_hierarchy *h, bool fp32, std::vector<unsigned char> &out) {
+    auto put = [&](const auto &tab) {
+        const size_t b = sizeof(tab[0]) * tab.size();
+        out.resize(b);
+        std::memcpy(out.data(), tab.data(), b);
+        return b;
+    };
+    if (fp32) {
+        std::vector<GLev<float>> tab;
+        table_image<float>(h, tab);
+        return put(tab);
+    }
+    std::vector<GLev<double>> tab;
+    table_image<double>(h, tab);
+    return put(tab);
+}
 
 void free_engines(amg_hierarchy *h) {
     delete h->eng64;

@@ -231,23 +231,47 @@ def test_full_batch_workload(amg, oracle_mod):
     B.close()
 
 
-def test_batched_setup_matches_single_setups(amg):
-    # amg_batch_setup builds the systems' hierarchies on worker threads, largest first: each
-    # must be the hierarchy the single-system setup builds, bit for bit (levels, operators,
-    # aggregates, colours)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_setup_matches_single_setups(amg, prec):
+    # amg_batch_setup builds every system of more than coarsest_max unknowns with one set of
+    # multi-system kernels (the one-level systems with the single-system setup): each
+    # hierarchy must be the one the single-system setup builds, bit for bit (levels,
+    # operators, aggregates, colours), and so must everything its solves read (reciprocal
+    # diagonals, FP32 copies, big-block schedules, level tables): a fixed-shape batch over the
+    # batched setup's hierarchies and one over single setups give the same bits, and so do
+    # single-system solves of the same system
     probs = [p1_poisson(**s) for s in SPECS] + [p1_poisson(n=129, jitter=0.1, graded=True,
                                                            kappa_blocks=16, seed=11)]
-    B = amg.Batch.from_problems(probs, cycle_prec=amg.FP64)
+    cp = amg.FP32 if prec == "fp32" else amg.FP64
+    B = amg.Batch.from_problems(probs, cycle_prec=cp)
+    singles = [amg.Hierarchy.from_problem(p, cycle_prec=cp) for p in probs]
     for k, p in enumerate(probs):
-        Gb = B.system(k)
-        Gs = amg.Hierarchy.from_problem(p)
+        Gb, Gs = B.system(k), singles[k]
         assert Gb.nlev == Gs.nlev, k
+        assert np.array_equal(Gb.bbox, Gs.bbox) and Gb.L == Gs.L, k
         for l in range(Gs.nlev):
             assert Gb.level_info(l) == Gs.level_info(l), (k, l)
             lb, ls = Gb.level(l), Gs.level(l)
             for key in ls:
                 np.testing.assert_array_equal(lb[key], ls[key], err_msg=f"system {k} level {l} {key}")
-        Gs.close()
+    rhs = [np.random.default_rng(k).standard_normal(p.n) for k, p in enumerate(probs)]
+    views = [B.system(k) for k in range(len(probs))]
+    Bb = amg.Batch.over(views, threads=1024)
+    Bs = amg.Batch.over(singles, threads=1024)
+    xb, itb, rrb, stb = Bb.solve(np.concatenate(rhs), 1e-8)
+    xs, its, rrs, sts = Bs.solve(np.concatenate(rhs), 1e-8)
+    assert (stb == amg.OK).all() and (sts == amg.OK).all()
+    np.testing.assert_array_equal(xb, xs)
+    np.testing.assert_array_equal(itb, its)
+    Bb.close()
+    Bs.close()
+    for k in (1, 5, 6):  # the single-system solver on a batch's system (its engine built then)
+        x1, it1, _, st1 = views[k].solve(rhs[k], 1e-8)
+        x2, it2, _, st2 = singles[k].solve(rhs[k], 1e-8)
+        assert st1 == amg.OK and st2 == amg.OK and it1 == it2, k
+        np.testing.assert_array_equal(x1, x2)
+    for G in singles:
+        G.close()
     B.close()
 
 

@@ -158,3 +158,38 @@ def test_failures_set_the_error_text(lib):
     st = L.amg_csr_to_ell_noalloc(prob.n, prob.rowptr.ctypes.data, prob.col.ctypes.data,
                                   prob.val.ctypes.data, 5, 1, Aj.ctypes.data, Ax.ctypes.data, None)
     assert st == lib.ERR_INVALID_ARG and b"device arrays" in L.amg_last_error()
+
+
+def test_capturing_stream_is_refused_and_the_capture_goes_on(lib):
+    # the call reads its result back and waits on its stream, which a capturing stream does
+    # not allow: it must refuse before any work and leave the caller's capture intact
+    import torch
+
+    L = lib.lib()
+    prob = p1_poisson(17, jitter=0.2, seed=3)
+    width = int(np.diff(prob.rowptr).max())
+    st, _, _ = _pack(lib, L.amg_csr_to_ell_noalloc, prob.rowptr, prob.col, prob.val, width, 1)
+    assert st == lib.OK  # the first call on the device (scratch address) outside any capture
+    d = lambda a: torch.as_tensor(a).cuda()  # noqa: E731
+    rp, cl, vl = d(prob.rowptr), d(prob.col), d(prob.val)
+    Aj = torch.full((prob.n * width,), 7, dtype=torch.int32, device="cuda")
+    Ax = torch.full((prob.n * width,), 7.0, dtype=torch.float64, device="cuda")
+    a = torch.arange(1000, dtype=torch.float64, device="cuda")
+    out = torch.zeros_like(a)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        s = torch.cuda.current_stream()
+        st = L.amg_csr_to_ell_noalloc(prob.n, rp.data_ptr(), cl.data_ptr(), vl.data_ptr(), width,
+                                      1, Aj.data_ptr(), Ax.data_ptr(),
+                                      ctypes.c_void_p(s.cuda_stream))
+        out.copy_(a * 3.0)
+    assert st == lib.ERR_UNSUPPORTED and b"capturing" in L.amg_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), 3.0 * np.arange(1000))
+    assert (Aj.cpu().numpy() == 7).all() and (Ax.cpu().numpy() == 7.0).all()  # no work done
+    st, Aj1, Ax1 = _pack(lib, L.amg_csr_to_ell_noalloc, prob.rowptr, prob.col, prob.val, width, 1)
+    st0, Aj0, Ax0 = _pack(lib, L.amg_csr_to_ell, prob.rowptr, prob.col, prob.val, width, 1)
+    assert st == lib.OK and st0 == lib.OK
+    np.testing.assert_array_equal(Aj1, Aj0)
+    np.testing.assert_array_equal(Ax1, Ax0)
