@@ -167,6 +167,12 @@ typedef struct amg_batch amg_batch;
  *   opt     : options of every system (aux_level 0 = chosen per system); outer must be
  *             AMG_OUTER_FCG. NULL = defaults.
  *   out     : receives the batch (owned by the library until amg_batch_free).
+ * The systems of more than opt->coarsest_max unknowns are set up together: every step of the
+ * setup runs once, as one multi-system kernel launch, for all of them (the others, which are
+ * their own coarsest level, take amg_setup's path). Each hierarchy is bit for bit the one
+ * amg_setup builds from its block. Its arrays are pieces of a few large allocations the batch
+ * owns, so a system's hierarchy lives and dies with the batch (amg_batch_system); its
+ * amg_launch_counts setup figure is the whole batched setup's launches.
  * Errors: as amg_setup (a system's failure fails the call), AMG_ERR_UNSUPPORTED for the
  * FGMRES outer method. On error *out is NULL.
  */

@@ -943,7 +943,7 @@ void build_hierarchy(amg_hierarchy *h, const amg_csr &Ain, const double *x, cons
         int *len = tmp.get<int>(n);
         k_rowlen_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, Ain.rowptr, len);
         AMG_LAUNCH_CHECK();
-        slice_pointers(h, F.A, n, len, false);
+        slice_pointers(h, F.A, n, len, true);  // interior P1 rows: one length
         k_fill_csr<<<nblocks_for(n, kT), kT, 0, s>>>(n, F.nat, F.inv, Ain.rowptr, Ain.col, Ain.val,
                                                      F.A.sl_ptr, F.A.col, F.A.val);
         AMG_LAUNCH_CHECK();

@@ -1160,7 +1160,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             nbig[p] = hbig[p];
         }
         st.reset_readbacks();
-        slice_pointers_multi(st, ar, tmp, all, 0, len, false);
+        slice_pointers_multi(st, ar, tmp, all, 0, len, true);
         Multi<DFill> mf;
         for (int p = 0; p < P; p++) {
             Level &F = hs[p]->lev[0];
