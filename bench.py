@@ -273,6 +273,7 @@ def run_batched(args, world, flush, dev, stream):
     from paper_1209_5421_gb300.meshes import batch_workload
 
     probs = batch_workload(count=args.batch_systems)
+    peak_gbs, _ = measured_peak_hbm()
     rhs = torch.as_tensor(np.concatenate([p.b for p in probs])).to(dev)
     x = torch.empty_like(rhs)
     # the block-diagonal CSR on the device (host-side concatenation in the binding, timed
@@ -307,6 +308,7 @@ def run_batched(args, world, flush, dev, stream):
         t = max_over_ranks(world, sum(lat))
         info = B.info()
         team = B.teams()
+        moved = B.moved_bytes()  # algorithmic bytes of one batch solve (the last one)
         B.close()
         if not (sts == amg.OK).all():
             raise RuntimeError(f"batched {name}: statuses {sorted(set(sts.tolist()))}")
@@ -324,6 +326,14 @@ def run_batched(args, world, flush, dev, stream):
             "teams": {"systems": int((team > 1).sum()), "ctas": int(team[team > 1].sum()),
                       "largest": int(team.max())},
             "device_bytes": info["bytes"],
+            # the batched kernel's roofline: algorithmic bytes of the whole batch solve (every
+            # system's cycles and outer steps) over the batch's time; small systems' levels
+            # stay in L2, so this is not DRAM evidence
+            "roofline": {"bound": "hbm", "kernel": "k_batch (whole batch solve)",
+                         "achieved": round(moved / (t / args.steps / 1e3) / 1e9, 1),
+                         "peak": peak_gbs, "unit": "GB/s",
+                         "frac": round(moved / (t / args.steps / 1e3) / 1e9 / peak_gbs, 4),
+                         "bytes_per_solve": moved},
         }
     # the plain FP64 method, one system at a time (every 16th system, hierarchies resident)
     sample = probs[::16]

@@ -223,6 +223,16 @@ int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_
                    double tuned_ms[4], size_t *bytes);
 
 /*
+ * Algorithmic bytes the last amg_batch_solve moved (0 before a solve), for its roofline: per
+ * system, every outer step's B^_0 application (Alg. 2 over every level, the per-op counts of
+ * the single-system cycle: 4-byte indices, values in the cycle precision) and its FP64 outer
+ * flexible-CG work (conversions, the dots and orthogonalisation against every kept direction,
+ * the SpMV, the update), plus the gather of b and the true residual. Padding and re-reads
+ * are not counted. bytes: host. Errors: AMG_ERR_INVALID_ARG (NULL).
+ */
+int amg_batch_moved_bytes(amg_batch *bt, double *bytes);
+
+/*
  * When each system of the last amg_batch_solve started and finished on the device: host
  * arrays of nprob entries, ns after the earliest start (device clock); each may be NULL.
  * end_ns is each system's latency from the launch of the batch.

@@ -106,6 +106,7 @@ def lib():
         L.amg_batch_teams.restype = C.c_int
         L.amg_batch_system.argtypes = [P, C.c_int32]
         L.amg_batch_system.restype = P
+        L.amg_batch_moved_bytes.argtypes = [P, C.POINTER(C.c_double)]
         L.amg_batch_free.argtypes = [P]
         L.amg_batch_free.restype = None
         for f in ("amg_batch_setup", "amg_batch_solve", "amg_batch_info"):
@@ -495,7 +496,7 @@ class Batch:
 
     def __init__(self, problems=None, aux_level=0, coarsest_max=64, kcycle_n=2, max_iters=200,
                  cycle_prec=FP64, stream=None, device=None, nu_pre=1, nu_post=1,
-                 concatenated=None):
+                 concatenated=None, bbox=None):
         L = lib()
         if concatenated is None:
             concatenated = concatenate(problems, device)
@@ -510,6 +511,10 @@ class Batch:
         o.aux_level, o.coarsest_max, o.kcycle_n, o.max_iters = aux_level, coarsest_max, kcycle_n, max_iters
         o.cycle_prec, o.outer = cycle_prec, OUTER_FCG
         o.nu_pre, o.nu_post = nu_pre, nu_post
+        if bbox is not None:  # one auxiliary box for every system
+            o.has_bbox = 1
+            for k in range(4):
+                o.bbox[k] = bbox[k]
         b = C.c_void_p()
         st = L.amg_batch_setup(self.nprob, row_off.ctypes.data, C.byref(A), _ptr(xx), _ptr(yy),
                                C.byref(o), _stream(stream), C.byref(b))
@@ -599,6 +604,12 @@ class Batch:
                "amg_batch_info")
         return {"nprob": n.value, "threads": t.value, "ctas": c.value,
                 "tuned_ms": list(ms), "bytes": nb.value}
+
+    def moved_bytes(self) -> float:
+        """amg_batch_moved_bytes: algorithmic bytes the last solve moved (its roofline)."""
+        v = C.c_double()
+        _check(lib().amg_batch_moved_bytes(self.b, C.byref(v)), "amg_batch_moved_bytes")
+        return v.value
 
     def timeline(self):
         """(start_ns, end_ns) of every system in the last solve, after the earliest start."""

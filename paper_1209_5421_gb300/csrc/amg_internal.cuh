@@ -346,6 +346,9 @@ void prepare_cycle(amg_hierarchy *h);
 void batch_prepare(amg_hierarchy *h);
 // doubles of the outer iteration's device scalars (h->osc) for max_iters iterations
 size_t outer_scalar_count(int max_iters);
+// algorithmic bytes of one application of B^_0 (Alg. 2 over every level, values of
+// value_bytes bytes; the per-op counts of the cycle's roofline)
+double cycle_application_bytes(amg_hierarchy *h, int value_bytes);
 // host image of h's device level table in the cycle precision fp32 (LevelDev<T, int>[nlev]):
 // what the level table holds once the level arrays exist; returns its size in bytes
 size_t level_table_image(amg_hierarchy *h, bool fp32, std::vector<unsigned char> &out);
@@ -393,6 +396,8 @@ void batch_timeline(const BatchEngine *E, int64_t *start_ns, int64_t *end_ns);
 void batch_set_teams(BatchEngine *E, int max_team);
 // CTAs of each system's team in the chosen launch shape (host array; -1 before a solve)
 void batch_teams(const BatchEngine *E, int *team);
+// algorithmic bytes the last batch_solve moved (every system's cycles and outer steps)
+double batch_moved_bytes(BatchEngine *E);
 // host-set fault of the team barriers for the following solves: limit_ns > 0 replaces the
 // wait limit, extra > 0 makes every team's first barrier wait for that many more arrivals
 // than its members make (so it runs out); 0, 0 restores the defaults

@@ -79,6 +79,8 @@ struct BatchEngine {
     int grid[kNumShapes] = {};
     double tuned_ms[kNumShapes] = {};
     size_t bytes = 0;
+    std::vector<int> last_iters;   // every system's outer steps in the last solve
+    std::vector<double> cyc_bytes; // algorithmic bytes of one B^_0 per system (on demand)
     // the solve's launch sequence, captured once per (b, x, tol) binding
     cudaGraphExec_t graph = nullptr;
     const double *g_b = nullptr;
@@ -404,6 +406,7 @@ int batch_solve(BatchEngine *E, const double *b, double tol, double *x, int *ite
         if (!resume_full(E, st, b, x, tol)) break;
     }
     int first_bad = AMG_OK;
+    E->last_iters = it;
     for (int p = 0; p < E->nprob; p++) {
         if (iters) iters[p] = it[p];
         if (relres) relres[p] = rr[p];
@@ -441,6 +444,38 @@ void batch_barrier_fault(BatchEngine *E, int64_t limit_ns, int extra) {
 }
 
 int bounds_flags_batch() { return bounds_flag_read_clear(); }
+
+// Algorithmic bytes of a system's batched solve of `its` outer steps (solve_one, FP64 outer,
+// 8-byte values, 4-byte indices): per step k (k = 0, 1, ...) one B^_0, the conversions to and
+// from the cycle precision (FP32 cycle), the dots (z, q_j) of the k kept directions (z re-read
+// per group of 4), p_k = z - sum c_j p_j (per chunk of 64: the running p_k read and written),
+// q_k = A p_k with (p_k, q_k) and (r, p_k), and the x / r update; once per solve the gather of
+// b (and bo, ro, xo written) and the true residual.
+double batch_moved_bytes(BatchEngine *E) {
+    if (E->last_iters.empty()) return 0.0;
+    const int vb = E->fp32 ? 4 : 8;
+    if (E->cyc_bytes.empty()) {
+        E->cyc_bytes.resize(E->nprob);
+        for (int p = 0; p < E->nprob; p++)
+            E->cyc_bytes[p] = E->hs[p]->nlev > 1 ? cycle_application_bytes(E->hs[p], vb)
+                                                 : (double)vb * ((double)E->hs[p]->N * E->hs[p]->N + 2.0 * E->hs[p]->N);
+    }
+    double total = 0.0;
+    for (int p = 0; p < E->nprob; p++) {
+        const double n = (double)E->hs[p]->N, nnz = (double)E->hs[p]->lev[0].A.stored;
+        double s = 56.0 * n + 12.0 * nnz + 24.0 * n;  // gather of b; true residual
+        for (int k = 0; k < E->last_iters[p]; k++) {
+            s += E->cyc_bytes[p];
+            if (E->fp32) s += 24.0 * n;
+            s += 8.0 * n * (k + (k + 3) / 4);
+            s += 16.0 * n * std::max(1, (k + 63) / 64) + 8.0 * n * k;
+            s += 12.0 * nnz + 32.0 * n;
+            s += 48.0 * n;
+        }
+        total += s;
+    }
+    return total;
+}
 
 void batch_teams(const BatchEngine *E, int *team) {
     for (int p = 0; p < E->nprob; p++) team[p] = E->shape < 0 ? -1 : E->team[E->shape][p];

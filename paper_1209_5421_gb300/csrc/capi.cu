@@ -588,6 +588,15 @@ int amg_batch_info(const amg_batch *bt, int32_t *nprob, int32_t *threads, int32_
     return AMG_OK;
 }
 
+int amg_batch_moved_bytes(amg_batch *bt, double *bytes) {
+    if (!bt || !bytes) return fail(AMG_ERR_INVALID_ARG, "NULL argument");
+    try {
+        *bytes = amg::batch_moved_bytes(bt->eng);
+        return AMG_OK;
+    }
+    AMG_CATCH
+}
+
 int amg_batch_timeline(const amg_batch *bt, int64_t *start_ns, int64_t *end_ns) {
     if (!bt) return fail(AMG_ERR_INVALID_ARG, "NULL batch");
     try {

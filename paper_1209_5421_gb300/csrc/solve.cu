@@ -751,8 +751,8 @@ __global__ void __launch_bounds__(kRedThreads) k_outer_spmv_dot(GLev<double> L,
     double *q = Q[it];
     double v[2] = {0.0, 0.0};
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < L.n; row += gridDim.x * blockDim.x) {
-        const int s = row >> 5;
-        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+        int base, width;
+        row_span(L, row, base, width);  // computed, not loaded, for uniform slices
         const double acc = row_dot(L, base, 0, width, p);
         q[row] = acc;
         v[0] += p[row] * acc;
@@ -800,8 +800,8 @@ __global__ void k_bump(int *it_ptr) {
 // w = A z
 __global__ void k_spmv(GLev<double> L, const double *__restrict__ z, double *__restrict__ w) {
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < L.n; row += gridDim.x * blockDim.x) {
-        const int s = row >> 5;
-        const int base = L.sl[s] + (row & 31), width = (L.sl[s + 1] - L.sl[s]) >> 5;
+        int base, width;
+        row_span(L, row, base, width);
         w[row] = row_dot(L, base, 0, width, z);
     }
 }
@@ -1323,14 +1323,23 @@ const GLev<T> *dtab(amg_hierarchy *h) {
 // widest slice (slots per row) of each level, from its slice pointers
 std::vector<int> slice_widths(amg_hierarchy *h) {
     std::vector<int> w(h->nlev, 0);
+    std::vector<std::vector<int>> sl(h->nlev);
+    bool read = false;
     for (int l = 0; l < h->nlev; l++) {
         const Sell &A = h->lev[l].A;
-        std::vector<int> sl(A.nslices + 1);
-        AMG_CUDA(cudaMemcpyAsync(sl.data(), A.sl_ptr, sizeof(int) * sl.size(),
+        if (A.uw > 0) {  // one width, known here
+            w[l] = A.uw;
+            continue;
+        }
+        sl[l].resize(A.nslices + 1);
+        AMG_CUDA(cudaMemcpyAsync(sl[l].data(), A.sl_ptr, sizeof(int) * sl[l].size(),
                                  cudaMemcpyDeviceToHost, h->stream));
-        AMG_CUDA(cudaStreamSynchronize(h->stream));
-        for (int k = 0; k < A.nslices; k++) w[l] = std::max(w[l], (sl[k + 1] - sl[k]) / kSliceH);
+        read = true;
     }
+    if (read) AMG_CUDA(cudaStreamSynchronize(h->stream));
+    for (int l = 0; l < h->nlev; l++)
+        for (size_t k = 0; k + 1 < sl[l].size(); k++)
+            w[l] = std::max(w[l], (sl[l][k + 1] - sl[l][k]) / kSliceH);
     return w;
 }
 
@@ -1750,12 +1759,24 @@ void allocate_solve_workspace(amg_hierarchy *h) {
         AMG_LAUNCH_CHECK();
     }
     fill_tables<double>(h);
-    if (h->nlev > 1) build_engine<double>(h);
+    // the FP64 cycle's engine now; an FP32-cycle hierarchy builds its FP32 engine on its first
+    // solve (ensure_fp32), and an FP64 one only if the FP64 cycle is ever launched
+    if (h->nlev > 1 && h->opt.cycle_prec != AMG_FP32) build_engine<double>(h);
 }
 
 int bounds_flags_solve() { return bounds_flag_read_clear(); }
 
 size_t outer_scalar_count(int max_iters) { return OS_ZQ + 2 * (size_t)max_iters + 8; }
+
+double cycle_application_bytes(amg_hierarchy *h, int value_bytes) {
+    std::vector<Op> prog;
+    Builder b{h, &prog, h->nlev + 1};  // every level's ops, down to the coarsest
+    b.bhat(0, V_RHS, V_E);
+    double s = 0.0;
+    for (const Op &op : prog)
+        if (op.kind != OP_NOP) s += op_bytes(h, op, value_bytes);
+    return s;
+}
 
 size_t level_table_image(amg_hierarchy *h, bool fp32, std::vector<unsigned char> &out) {
     auto put = [&](const auto &tab) {

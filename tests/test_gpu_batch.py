@@ -275,6 +275,65 @@ def test_batched_setup_matches_single_setups(amg, prec):
     B.close()
 
 
+@pytest.mark.parametrize("opts", [dict(coarsest_max=16, kcycle_n=3),
+                                  dict(aux_level=5, bbox=(0.0, 1.0, 0.0, 1.0), coarsest_max=8),
+                                  dict(nu_pre=2, nu_post=3, coarsest_max=256)])
+def test_batched_setup_options_match_single_setups(amg, opts):
+    # the options reach every system of the batched setup as they reach amg_setup: a fixed
+    # depth and box (levels of every system from the same auxiliary grid), a small or large
+    # coarsest level (with coarsest_max 256 a 225-unknown system is its own coarsest level, and
+    # the others factor coarsest levels of more than 102 rows in global memory)
+    probs = [p1_poisson(n=n, jitter=0.2, seed=20 + n, rhs="normal") for n in (17, 33, 65, 40)]
+    B = amg.Batch.from_problems(probs, **opts)
+    for k, p in enumerate(probs):
+        Gb, Gs = B.system(k), amg.Hierarchy.from_problem(p, **opts)
+        assert Gb.nlev == Gs.nlev and Gb.L == Gs.L, k
+        assert np.array_equal(Gb.bbox, Gs.bbox), k
+        for l in range(Gs.nlev):
+            assert Gb.level_info(l) == Gs.level_info(l), (k, l)
+            lb, ls = Gb.level(l), Gs.level(l)
+            for key in ls:
+                np.testing.assert_array_equal(lb[key], ls[key], err_msg=f"system {k} level {l} {key}")
+        Gs.close()
+    x, it, rr, st = B.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    assert (st == amg.OK).all() and (rr <= 1e-8).all()
+    B.close()
+
+
+def test_batched_setup_rejects_a_bad_system(amg):
+    # one invalid system fails the whole call with amg_setup's status, and nothing leaks
+    import torch
+
+    probs = [p1_poisson(n=n, jitter=0.2, seed=n, rhs="normal") for n in (33, 17, 45)]
+    B = amg.Batch.from_problems(probs)
+    B.close()
+    torch.cuda.synchronize()
+    base = amg.pool_bytes_in_use(torch.cuda.current_device())
+    sysl = [(p.rowptr, p.col, p.val, p.x, p.y) for p in probs]
+    bad_val = probs[1].val.copy()
+    bad_val[0] = -1.0  # a non-positive diagonal
+    bad_col = probs[2].col.copy()
+    bad_col[[1, 2]] = bad_col[[2, 1]]  # unsorted columns
+    bad_x = probs[1].x.copy()
+    bad_x[3] = np.nan
+    cases = [(1, 2, bad_val, amg.ERR_BAD_MATRIX), (2, 1, bad_col, amg.ERR_BAD_MATRIX),
+             (1, 3, bad_x, amg.ERR_INVALID_ARG)]
+    for k, field, arr, status in cases:
+        probl = list(sysl)
+        t = list(probl[k])
+        t[field] = arr
+        probl[k] = tuple(t)
+        with pytest.raises(amg.AmgError) as e:
+            amg.Batch(probl)
+        assert e.value.status == status, (k, field)
+        torch.cuda.synchronize()
+        assert amg.pool_bytes_in_use(torch.cuda.current_device()) == base
+    B = amg.Batch(sysl)  # the library goes on
+    x, it, rr, st = B.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    assert (st == amg.OK).all()
+    B.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_graded_systems_big_aggregates(amg, oracle_mod, prec):
     # graded meshes: aggregates of up to 484 unknowns on the finest level (462 above 16
@@ -327,3 +386,29 @@ def test_directions_grow_to_max_iters(amg, oracle_mod):
     x2, it2, _, st2 = B.solve(np.concatenate([p.b, q.b]), 1e-8)
     assert np.array_equal(x2, x) and np.array_equal(it2, it) and np.array_equal(st2, st)
     B.close()
+
+
+def test_moved_bytes_of_a_batch(amg):
+    # amg_batch_moved_bytes: 0 before a solve; with a fixed shape each system's solve does not
+    # depend on the others, so the batch's bytes are the sum of its systems' alone; and a
+    # system's bytes exceed its outer steps times one cycle application's stored matrix entries
+    probs = [p1_poisson(n=n, jitter=0.2, seed=30 + n, rhs="normal") for n in (33, 65)]
+    hs = [amg.Hierarchy.from_problem(p, cycle_prec=amg.FP32) for p in probs]
+    both = amg.Batch.over(hs, threads=1024)
+    assert both.moved_bytes() == 0.0
+    _, it2, _, st2 = both.solve(np.concatenate([p.b for p in probs]), 1e-8)
+    b2 = both.moved_bytes()
+    both.close()
+    alone = []
+    for k, h in enumerate(hs):
+        B = amg.Batch.over([h], threads=1024)
+        _, it1, _, st1 = B.solve(probs[k].b, 1e-8)
+        assert st1[0] == amg.OK and it1[0] == it2[k]
+        alone.append(B.moved_bytes())
+        nnz = sum(h.level_info(l)["stored"] for l in range(h.nlev))
+        assert alone[-1] > it1[0] * nnz * 8  # every level's entries (4-byte index, FP32 value)
+        B.close()
+    assert (st2 == amg.OK).all()
+    assert b2 == pytest.approx(alone[0] + alone[1], rel=1e-12)
+    for h in hs:
+        h.close()
