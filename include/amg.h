@@ -170,14 +170,28 @@ typedef struct amg_batch amg_batch;
  * The systems of more than opt->coarsest_max unknowns are set up together: every step of the
  * setup runs once, as one multi-system kernel launch, for all of them (the others, which are
  * their own coarsest level, take amg_setup's path). Each hierarchy is bit for bit the one
- * amg_setup builds from its block. Its arrays are pieces of a few large allocations the batch
- * owns, so a system's hierarchy lives and dies with the batch (amg_batch_system); its
- * amg_launch_counts setup figure is the whole batched setup's launches.
+ * amg_setup builds from its block. Its arrays are pieces of a few large allocations of its own
+ * (about 1 KB per unknown with the batched-solve workspace, charged in full to the
+ * hierarchy); its amg_launch_counts setup figure is the whole batched setup's launches.
  * Errors: as amg_setup (a system's failure fails the call), AMG_ERR_UNSUPPORTED for the
  * FGMRES outer method. On error *out is NULL.
  */
 int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
                     const double *y, const amg_options *opt, void *stream, amg_batch **out);
+
+/*
+ * amg_setup of many systems at once, each hierarchy returned on its own: the systems are given
+ * as for amg_batch_setup (row_off, A, x, y, opt; any outer method) and set up together in the
+ * same way, but out[p] (a host array of nprob pointers) receives system p's hierarchy,
+ * bit for bit the one amg_setup builds from its block, owned by the caller and released by
+ * amg_free like any other, independently of the others. With the flexible-CG outer method
+ * each hierarchy is also ready for batched solves (amg_batch_create). The paper sets up one
+ * system at a time; this entry point serves callers with many new systems at once, such as a
+ * server admitting several matrices.
+ * Errors: as amg_setup (a system's failure fails the call; every out[p] is then NULL).
+ */
+int amg_setup_many(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                   const double *y, const amg_options *opt, void *stream, amg_hierarchy **out);
 
 /*
  * A batch over hierarchies that already exist (built by amg_setup or amg_batch_setup; all

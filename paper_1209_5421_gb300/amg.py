@@ -107,6 +107,7 @@ def lib():
         L.amg_batch_system.argtypes = [P, C.c_int32]
         L.amg_batch_system.restype = P
         L.amg_batch_moved_bytes.argtypes = [P, C.POINTER(C.c_double)]
+        L.amg_setup_many.argtypes = [C.c_int32, P, C.POINTER(Csr), P, P, C.POINTER(Options), P, P]
         L.amg_batch_free.argtypes = [P]
         L.amg_batch_free.restype = None
         for f in ("amg_batch_setup", "amg_batch_solve", "amg_batch_info"):
@@ -483,6 +484,44 @@ def concatenate(problems, device=None):
 
         arrays = [torch.as_tensor(a).to(device) for a in arrays]
     return (row_off, *arrays)
+
+
+def setup_many(problems=None, concatenated=None, stream=None, device=None, **kw):
+    """amg_setup_many: one Hierarchy per system, all set up together (problems or
+    concatenated as for Batch; the options of Hierarchy). Each is freed on its own."""
+    L = lib()
+    if concatenated is None:
+        concatenated = concatenate(problems, device)
+    row_off, rp, cl, vl, xx, yy = concatenated
+    row_off = np.asarray(row_off, np.int64)
+    nprob = len(row_off) - 1
+    A = Csr(int(row_off[-1]), len(cl), _ptr(rp), _ptr(cl), _ptr(vl))
+    o = Options()
+    L.amg_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "bbox":
+            o.has_bbox = 1
+            for j in range(4):
+                o.bbox[j] = v[j]
+        elif k == "outer":
+            o.outer = v
+        elif k in ("aux_level", "coarsest_max", "kcycle_n", "max_iters", "cycle_prec",
+                   "fgmres_restart", "nu_pre", "nu_post"):
+            setattr(o, k, v)
+        else:
+            raise TypeError(f"unknown option {k!r}")
+    out = (C.c_void_p * nprob)()
+    _check(L.amg_setup_many(nprob, row_off.ctypes.data, C.byref(A), _ptr(xx), _ptr(yy),
+                            C.byref(o), _stream(stream), C.cast(out, C.c_void_p)),
+           "amg_setup_many")
+    hs = []
+    for p in range(nprob):
+        h = Hierarchy.__new__(Hierarchy)
+        h.h = C.c_void_p(out[p])
+        h.n = int(row_off[p + 1] - row_off[p])
+        h._keep = None
+        hs.append(h)
+    return hs
 
 
 class Batch:

@@ -147,6 +147,20 @@ struct BatchWs {
     int4 *bigr = nullptr;           // finest level's colours: their big blocks (bb0, bbc, bb1)
 };
 
+// Many small arrays carved from a few large allocations (a bump allocator over chunks): a
+// hierarchy of the batched setup takes its arrays from its own arena, which it frees with
+// itself. Every piece is 256-byte aligned.
+struct Arena {
+    cudaStream_t s = nullptr;
+    std::vector<void *> chunks;
+    char *cur = nullptr;
+    size_t left = 0;
+    size_t bytes = 0;                 // allocated chunk bytes
+    size_t chunk = size_t(1) << 20;   // chunk size (a larger piece gets a chunk of its own)
+    void *get(size_t b);
+    void release();
+};
+
 }  // namespace amg
 
 struct amg_hierarchy {
@@ -162,6 +176,7 @@ struct amg_hierarchy {
     int device = 0;
     // allocations owned by the hierarchy
     std::vector<void *> allocs;
+    amg::Arena arena;                   // the batched setup's arrays of this hierarchy
     size_t bytes = 0;
     // deterministic reduction scratch
     double *red_partials = nullptr;   // [kRedBlocks * kMaxRed]
@@ -175,8 +190,7 @@ struct amg_hierarchy {
     double **dP = nullptr, **dQ = nullptr;
     double *osc = nullptr;             // outer scalars
     int *oit = nullptr;                // device iteration counter
-    double *h_pinned = nullptr;        // pinned host scalars
-    bool pinned_owned = true;          // false: h_pinned is part of a batch's pinned block
+    double *h_pinned = nullptr;        // pinned host scalars (allocated on first use)
     // FGMRES state (FP64 basis)
     double *gm_V = nullptr, *gm_Z = nullptr, *gm_H = nullptr;
     int gm_cap = 0;
@@ -258,40 +272,32 @@ T *halloc(amg_hierarchy *h, size_t count) {
     return (T *)p;
 }
 
-// Many small arrays carved from a few large allocations (a bump allocator over chunks): the
-// batched setup's hierarchies take their arrays from the batch's arena, which owns them and
-// frees them with the batch. Every piece is 256-byte aligned.
-struct Arena {
-    cudaStream_t s = nullptr;
-    std::vector<void *> chunks;
-    char *cur = nullptr;
-    size_t left = 0;
-    size_t bytes = 0;  // allocated chunk bytes
-    size_t chunk = size_t(64) << 20;  // chunk size (a larger piece gets a chunk of its own)
-    void *get(size_t b) {
-        b = (std::max<size_t>(b, 16) + 255) & ~size_t(255);
-        if (b > left) {
-            const size_t c = std::max(b, chunk);
-            void *p = nullptr;
-            device_alloc(&p, c, s);
-            chunks.push_back(p);
-            bytes += c;
-            cur = (char *)p;
-            left = c;
-        }
-        void *r = cur;
-        cur += b;
-        left -= b;
-        return r;
+// Arena::get and Arena::release (declared before amg_hierarchy): a new chunk comes from
+// device_alloc, so the host-set allocation fault reaches it too
+inline void *Arena::get(size_t b) {
+    b = (std::max<size_t>(b, 16) + 255) & ~size_t(255);
+    if (b > left) {
+        const size_t c = std::max(b, chunk);
+        void *p = nullptr;
+        device_alloc(&p, c, s);
+        chunks.push_back(p);
+        bytes += c;
+        cur = (char *)p;
+        left = c;
+        chunk = std::max<size_t>(chunk / 4, size_t(1) << 20);  // the first chunk fell short
     }
-    void release() {
-        for (void *p : chunks) cudaFreeAsync(p, s);
-        chunks.clear();
-        cur = nullptr;
-        left = 0;
-        bytes = 0;
-    }
-};
+    void *r = cur;
+    cur += b;
+    left -= b;
+    return r;
+}
+inline void Arena::release() {
+    for (void *p : chunks) cudaFreeAsync(p, s);
+    chunks.clear();
+    cur = nullptr;
+    left = 0;
+    bytes = 0;
+}
 
 // scratch allocation freed by the owner (RAII)
 struct Scratch {
@@ -357,16 +363,17 @@ void build_fine_big_blocks(amg_hierarchy *h);
 // Batched setup (setup_batch.cu): every hierarchy of hs (created, options and sizes set, no
 // levels yet; system p is rows[p] of the block-diagonal A: rows r0 .. r0 + n, entries
 // nz0 .. nz0 + nnz; x, y device; every system has more than coarsest_max unknowns) is built
-// by one set of multi-system kernels on stream s, with the arrays from `ar` and the pinned
-// scalars of every hierarchy from *pinned (one block, allocated here); then each hierarchy is
-// ready for amg_solve and batched solves like one from amg_setup + batch_prepare. Throws
-// amg::Error.
+// by one set of multi-system kernels on stream s, its arrays in its own arena; then each
+// hierarchy is ready for amg_solve like one from amg_setup, and with batch_ws also for
+// batched solves (as after batch_prepare). Throws amg::Error.
 struct BatchRows {
     int r0, n, nz0, nnz;
 };
 void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const double *x,
-                 const double *y, const std::vector<BatchRows> &rows, cudaStream_t s, Arena &ar,
-                 double **pinned);
+                 const double *y, const std::vector<BatchRows> &rows, cudaStream_t s,
+                 bool batch_ws);
+// the pinned host scalars of the single-system solver (allocated on first use)
+void ensure_pinned(amg_hierarchy *h);
 // outer directions P[j], Q[j] (and the device tables dP, dQ) for j < count at least, in
 // chunks, at most max_iters; returns the number allocated. Synchronises h->stream.
 int ensure_directions(amg_hierarchy *h, int count);

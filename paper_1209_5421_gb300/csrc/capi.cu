@@ -79,8 +79,10 @@ void destroy(amg_hierarchy *h) {
     amg::free_engines(h);
     amg::profiler_free(h);
     for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+    h->arena.s = h->stream;
+    h->arena.release();
     cudaStreamSynchronize(h->stream);
-    if (h->h_pinned && h->pinned_owned) cudaFreeHost(h->h_pinned);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
     if (h->order_ev) cudaEventDestroy(h->order_ev);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -326,8 +328,6 @@ void amg_free(amg_hierarchy *h) { destroy(h); }
 struct amg_batch {
     std::vector<amg_hierarchy *> hs;
     bool owns = true;  // hierarchies built by amg_batch_setup (else borrowed)
-    amg::Arena arena;  // arrays of the hierarchies the batched setup built
-    double *pinned = nullptr;  // their pinned host scalars, one block
     std::vector<int64_t> row_off;
     amg::BatchEngine *eng = nullptr;
     cudaStream_t stream = nullptr;
@@ -343,11 +343,6 @@ void destroy_batch(amg_batch *bt) {
     amg::batch_destroy(bt->eng);
     if (bt->owns)
         for (amg_hierarchy *h : bt->hs) destroy(h);
-    if (bt->stream) {  // after the hierarchies: they hold pieces of the arena
-        bt->arena.release();
-        cudaStreamSynchronize(bt->stream);
-    }
-    if (bt->pinned) cudaFreeHost(bt->pinned);
     if (bt->order_ev) cudaEventDestroy(bt->order_ev);
     if (bt->stream) cudaStreamDestroy(bt->stream);
     delete bt;
@@ -372,10 +367,13 @@ __global__ void k_gather_rowptr(int m, const int *__restrict__ rowptr,
 
 }  // namespace
 
-int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
-                    const double *y, const amg_options *opt, void *stream, amg_batch **out) {
-    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// the argument checks of amg_batch_setup and amg_setup_many
+int check_systems(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                  const double *y) {
     if (nprob < 1 || !row_off || !A || !x || !y || !A->rowptr || !A->col || !A->val)
         return fail(AMG_ERR_INVALID_ARG, "NULL argument or no system");
     if (is_device_ptr(row_off)) return fail(AMG_ERR_INVALID_ARG, "row_off must be host memory");
@@ -385,6 +383,113 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
         if (row_off[p + 1] <= row_off[p]) return fail(AMG_ERR_INVALID_ARG, "every system needs a row");
     if (A->n >= INT32_MAX || A->nnz >= INT32_MAX)
         return fail(AMG_ERR_UNSUPPORTED, "n and nnz must be below 2^31");
+    return AMG_OK;
+}
+
+// One hierarchy per system of the block-diagonal A (arguments checked), into hs (nprob
+// entries; on a throw, hs holds what was built so far, for the caller to destroy). Systems
+// of more than coarsest_max unknowns are set up together by one set of multi-system kernels
+// on stream ws (setup_batch.cu); a system small enough to be its own coarsest level (one
+// level, the exact solve) takes the single-system setup. batch_ws: also prepare every system
+// for batched solves (as batch_prepare).
+void setup_systems(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                   const double *y, const amg_options &o, cudaStream_t us, cudaStream_t ws,
+                   bool batch_ws, std::vector<amg_hierarchy *> &hs) {
+    hs.assign(nprob, nullptr);
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    init_pool_once(dev);
+    Scratch tmp(us);
+    const size_t N = (size_t)A->n;
+    const int *rp = to_device(A->rowptr, N + 1, tmp);
+    const int *cl = to_device(A->col, (size_t)A->nnz, tmp);
+    const double *vl = to_device(A->val, (size_t)A->nnz, tmp);
+    const double *xd = to_device(x, N, tmp);
+    const double *yd = to_device(y, N, tmp);
+    // nonzero offset of every system: rowptr[row_off[p]], gathered and read back at once
+    std::vector<int> nz(nprob + 1);
+    {
+        int64_t *dro = tmp.get<int64_t>((size_t)nprob + 1);
+        int *dnz = tmp.get<int>((size_t)nprob + 1);
+        AMG_CUDA(cudaMemcpyAsync(dro, row_off, sizeof(int64_t) * (nprob + 1),
+                                 cudaMemcpyHostToDevice, us));
+        k_gather_rowptr<<<(nprob + 256) / 256, 256, 0, us>>>(nprob + 1, rp, dro, dnz);
+        AMG_CUDA(cudaGetLastError());
+        AMG_CUDA(cudaMemcpyAsync(nz.data(), dnz, sizeof(int) * (nprob + 1), cudaMemcpyDeviceToHost,
+                                 us));
+        AMG_CUDA(cudaStreamSynchronize(us));
+    }
+    if (nz[0] != 0 || nz[nprob] != A->nnz)
+        throw Error{AMG_ERR_BAD_MATRIX, "rowptr does not run from 0 to nnz"};
+    for (int p = 0; p < nprob; p++)
+        if (nz[p + 1] - nz[p] < (int)(row_off[p + 1] - row_off[p]))
+            throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
+    std::vector<int> multi;
+    for (int p = 0; p < nprob; p++) {
+        const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
+        if (n > o.coarsest_max) {
+            multi.push_back(p);
+            continue;
+        }
+        const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
+        Scratch loc(us);
+        int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
+        k_localize_rows<<<(n + 256) / 256, 256, 0, us>>>(n, rp + r0, z0, lrp);
+        k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
+        AMG_CUDA(cudaGetLastError());
+        amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
+        hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, us);
+        if (batch_ws) amg::batch_prepare(hs[p]);
+    }
+    if (multi.empty()) return;
+    std::vector<amg_hierarchy *> mh;
+    std::vector<amg::BatchRows> rows;
+    cudaEvent_t ready;
+    AMG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaEventRecord(ready, us);  // the staged inputs
+    cudaStreamWaitEvent(ws, ready, 0);
+    cudaEventDestroy(ready);
+    AMG_CUDA(cudaGetLastError());
+    for (int p : multi) {
+        amg_hierarchy *h = new amg_hierarchy();
+        hs[p] = h;
+        h->opt = o;
+        if (h->opt.nu_pre == 0) h->opt.nu_pre = 1;
+        if (h->opt.nu_post == 0) h->opt.nu_post = 1;
+        h->N = row_off[p + 1] - row_off[p];
+        h->dim = 2;
+        h->device = dev;
+        h->stream = ws;  // while the batched setup builds it
+        mh.push_back(h);
+        rows.push_back(amg::BatchRows{(int)row_off[p], (int)h->N, nz[p], nz[p + 1] - nz[p]});
+    }
+    const int64_t l0 = amg::g_launches;
+    try {
+        amg::build_batch(mh, amg_csr{A->n, A->nnz, rp, cl, vl}, xd, yd, rows, ws, batch_ws);
+        for (amg_hierarchy *h : mh) {
+            h->setup_launches = amg::g_launches - l0;  // the whole batched setup's launches
+            h->stream = nullptr;
+            AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+            AMG_CUDA(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
+        }
+        AMG_CUDA(cudaStreamSynchronize(ws));
+    } catch (...) {
+        cudaStreamSynchronize(ws);
+        for (amg_hierarchy *h : mh)
+            if (h->stream == ws) h->stream = nullptr;  // not the hierarchy's own
+        throw;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                    const double *y, const amg_options *opt, void *stream, amg_batch **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (int st = check_systems(nprob, row_off, A, x, y)) return st;
     amg_options o;
     if (opt) o = *opt;
     else amg_options_default(&o);
@@ -395,92 +500,11 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
     try {
         bt = new amg_batch();
         AMG_CUDA(cudaGetDevice(&bt->device));
-        init_pool_once(bt->device);
         AMG_CUDA(cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking));
         AMG_CUDA(cudaEventCreateWithFlags(&bt->order_ev, cudaEventDisableTiming));
         cudaStream_t us = (cudaStream_t)stream;
-        Scratch tmp(us);
-        const size_t N = (size_t)A->n;
-        const int *rp = to_device(A->rowptr, N + 1, tmp);
-        const int *cl = to_device(A->col, (size_t)A->nnz, tmp);
-        const double *vl = to_device(A->val, (size_t)A->nnz, tmp);
-        const double *xd = to_device(x, N, tmp);
-        const double *yd = to_device(y, N, tmp);
-        // nonzero offset of every system: rowptr[row_off[p]], gathered and read back at once
-        std::vector<int> nz(nprob + 1);
-        {
-            int64_t *dro = tmp.get<int64_t>((size_t)nprob + 1);
-            int *dnz = tmp.get<int>((size_t)nprob + 1);
-            AMG_CUDA(cudaMemcpyAsync(dro, row_off, sizeof(int64_t) * (nprob + 1),
-                                     cudaMemcpyHostToDevice, us));
-            k_gather_rowptr<<<(nprob + 256) / 256, 256, 0, us>>>(nprob + 1, rp, dro, dnz);
-            AMG_CUDA(cudaGetLastError());
-            AMG_CUDA(cudaMemcpyAsync(nz.data(), dnz, sizeof(int) * (nprob + 1),
-                                     cudaMemcpyDeviceToHost, us));
-            AMG_CUDA(cudaStreamSynchronize(us));
-        }
-        if (nz[0] != 0 || nz[nprob] != A->nnz)
-            throw Error{AMG_ERR_BAD_MATRIX, "rowptr does not run from 0 to nnz"};
         bt->row_off.assign(row_off, row_off + nprob + 1);
-        for (int p = 0; p < nprob; p++)
-            if (nz[p + 1] - nz[p] < (int)(row_off[p + 1] - row_off[p]))
-                throw Error{AMG_ERR_BAD_MATRIX, "every row needs its diagonal"};
-        // Systems of more than coarsest_max unknowns are set up together, by one set of
-        // multi-system kernels (setup_batch.cu); a system small enough to be its own coarsest
-        // level (one level, the exact solve) takes the single-system setup.
-        bt->hs.assign(nprob, nullptr);
-        std::vector<int> multi;
-        for (int p = 0; p < nprob; p++) {
-            const int r0 = (int)row_off[p], n = (int)(row_off[p + 1] - row_off[p]);
-            if (n > o.coarsest_max) {
-                multi.push_back(p);
-                continue;
-            }
-            const int z0 = nz[p], nnz = nz[p + 1] - nz[p];
-            Scratch loc(us);
-            int *lrp = loc.get<int>((size_t)n + 1), *lcl = loc.get<int>((size_t)nnz);
-            k_localize_rows<<<(n + 256) / 256, 256, 0, us>>>(n, rp + r0, z0, lrp);
-            k_localize_cols<<<(nnz + 255) / 256, 256, 0, us>>>(nnz, cl + z0, r0, lcl);
-            AMG_CUDA(cudaGetLastError());
-            amg_csr Ap{n, nnz, lrp, lcl, vl + z0};
-            bt->hs[p] = setup_device(Ap, xd + r0, yd + r0, nullptr, o, us);
-            amg::batch_prepare(bt->hs[p]);
-        }
-        if (!multi.empty()) {
-            std::vector<amg_hierarchy *> mh;
-            std::vector<amg::BatchRows> rows;
-            AMG_CUDA(cudaEventRecord(bt->order_ev, us));  // the staged inputs
-            AMG_CUDA(cudaStreamWaitEvent(bt->stream, bt->order_ev, 0));
-            for (int p : multi) {
-                amg_hierarchy *h = new amg_hierarchy();
-                bt->hs[p] = h;
-                h->opt = o;
-                if (h->opt.nu_pre == 0) h->opt.nu_pre = 1;
-                if (h->opt.nu_post == 0) h->opt.nu_post = 1;
-                h->N = row_off[p + 1] - row_off[p];
-                h->dim = 2;
-                h->device = bt->device;
-                h->stream = bt->stream;  // while the batch builds it
-                mh.push_back(h);
-                rows.push_back(amg::BatchRows{(int)row_off[p], (int)h->N, nz[p], nz[p + 1] - nz[p]});
-            }
-            bt->arena.s = bt->stream;
-            const int64_t l0 = amg::g_launches;
-            try {
-                amg::build_batch(mh, amg_csr{A->n, A->nnz, rp, cl, vl}, xd, yd, rows, bt->stream,
-                                 bt->arena, &bt->pinned);
-                for (amg_hierarchy *h : mh) {
-                    h->setup_launches = amg::g_launches - l0;  // the whole batch's launches
-                    h->stream = nullptr;
-                    AMG_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
-                    AMG_CUDA(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
-                }
-            } catch (...) {
-                for (amg_hierarchy *h : mh)
-                    if (h->stream == bt->stream) h->stream = nullptr;  // not the hierarchy's own
-                throw;
-            }
-        }
+        setup_systems(nprob, row_off, A, x, y, o, us, bt->stream, true, bt->hs);
         bt->eng = amg::batch_create(bt->hs, bt->row_off, bt->stream, 0);
         AMG_CUDA(cudaStreamSynchronize(us));
         *out = bt;
@@ -495,6 +519,45 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
         destroy_batch(bt);
         return fail(AMG_ERR_CUDA, "unexpected internal exception");
     }
+}
+
+int amg_setup_many(int32_t nprob, const int64_t *row_off, const amg_csr *A, const double *x,
+                   const double *y, const amg_options *opt, void *stream, amg_hierarchy **out) {
+    if (!out) return fail(AMG_ERR_INVALID_ARG, "out is NULL");
+    for (int p = 0; p < nprob; p++) out[p] = nullptr;
+    if (int st = check_systems(nprob, row_off, A, x, y)) return st;
+    amg_options o;
+    if (opt) o = *opt;
+    else amg_options_default(&o);
+    if (int st = check_options(o)) return st;
+    std::vector<amg_hierarchy *> hs;
+    cudaStream_t ws = nullptr;
+    int status = AMG_OK;
+    std::string what;
+    try {
+        AMG_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+        setup_systems(nprob, row_off, A, x, y, o, (cudaStream_t)stream, ws,
+                      o.outer == AMG_OUTER_FCG, hs);
+        AMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    } catch (const Error &e) {
+        status = e.status;
+        what = e.what;
+    } catch (const std::bad_alloc &) {
+        status = AMG_ERR_OOM;
+        what = "host allocation failed";
+    } catch (...) {
+        status = AMG_ERR_CUDA;
+        what = "unexpected internal exception";
+    }
+    if (status != AMG_OK)
+        for (amg_hierarchy *h : hs) destroy(h);
+    if (ws) {
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    }
+    if (status != AMG_OK) return fail(status, what);
+    for (int p = 0; p < nprob; p++) out[p] = hs[p];
+    return AMG_OK;
 }
 
 int amg_batch_create(int32_t nprob, amg_hierarchy *const *hs, int32_t threads, void *stream,

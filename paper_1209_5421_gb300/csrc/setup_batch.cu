@@ -11,8 +11,8 @@
 //
 // What changes is the host side: the setup of one system is a chain of about 240 small
 // launches with a host round trip at every step that sizes the next arrays; here every step
-// is one launch and one round trip for the whole batch, and the many small arrays of every
-// hierarchy come from a few large allocations that the batch owns (Arena).
+// is one launch and one round trip for the whole batch, and the many small arrays of a
+// hierarchy come from a few large allocations of its own (its Arena).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -122,11 +122,10 @@ void launch(Stage &st, const Multi<D> &m, K kern, size_t smem = 0) {
     AMG_LAUNCH_CHECK();
 }
 
+// a piece of h's arena (h is charged the arena's chunks at the end of the setup)
 template <class T>
-T *aget(Arena &ar, amg_hierarchy *h, size_t count) {
-    const size_t b = std::max<size_t>(count * sizeof(T), 16);
-    h->bytes += (b + 255) & ~size_t(255);
-    return (T *)ar.get(b);
+T *aget(amg_hierarchy *h, size_t count) {
+    return (T *)h->arena.get(std::max<size_t>(count * sizeof(T), 16));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -665,7 +664,8 @@ __global__ void kb_convert(const DConvert *__restrict__ D, const int *__restrict
     const DConvert &a = D[k_];
     if (i < a.n) a.dst[i] = (float)a.src[i];
 }
-// byte copies from the upload buffer to every hierarchy's tables (one block per item)
+// byte copies from the upload buffer to every hierarchy's tables, or zeros where the source
+// is null (one block per item)
 struct DCopy {
     const unsigned char *src;
     unsigned char *dst;
@@ -673,7 +673,7 @@ struct DCopy {
 };
 __global__ void kb_copy(const DCopy *__restrict__ D, int m) {
     const DCopy &a = D[blockIdx.x];
-    for (int64_t b = threadIdx.x; b < a.bytes; b += blockDim.x) a.dst[b] = a.src[b];
+    for (int64_t b = threadIdx.x; b < a.bytes; b += blockDim.x) a.dst[b] = a.src ? a.src[b] : 0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -740,7 +740,7 @@ void rap_pass(Stage &st, const std::vector<Sys *> &ps, int lc, bool fill,
 // sliced-ELL slice pointers of level l of the systems ps from their row lengths len[k]
 // (uniform: one slice width where it costs little, as the single-system setup decides);
 // allocates col / val. One host round trip.
-void slice_pointers_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *> &ps, int l,
+void slice_pointers_multi(Stage &st, Scratch &tmp, const std::vector<Sys *> &ps, int l,
                           const std::vector<int *> &len, bool uniform) {
     const int np = (int)ps.size();
     std::vector<int64_t> so(np + 1, 0);
@@ -761,7 +761,7 @@ void slice_pointers_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<
         A.n = lv.n;
         A.nslices = (lv.n + 31) / 32;
         A.uw = 0;
-        A.sl_ptr = aget<int>(ar, h, (size_t)A.nslices + 1);
+        A.sl_ptr = aget<int>(h, (size_t)A.nslices + 1);
         mw.add(DSliceW{lv.n, A.nslices, len[k], sw + so[k], uniform ? small + np + k : nullptr},
                (int64_t)A.nslices * 32);
         mp.add(DSlicePtr{A.nslices, gsl + so[k], A.sl_ptr, small + k}, (int64_t)A.nslices + 1);
@@ -785,8 +785,8 @@ void slice_pointers_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<
                 A.uw = wmax;
             }
         }
-        A.col = aget<int>(ar, h, (size_t)A.padded);
-        A.val = aget<double>(ar, h, (size_t)A.padded);
+        A.col = aget<int>(h, (size_t)A.padded);
+        A.val = aget<double>(h, (size_t)A.padded);
     }
     st.reset_readbacks();
     launch(st, mu, kb_uniform);
@@ -799,7 +799,7 @@ struct NnzRead {
 };
 
 // stored entries of every colour of level l (its colour ranges must be on the host)
-void color_nnz_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *> &ps, int l,
+void color_nnz_multi(Stage &st, Scratch &tmp, const std::vector<Sys *> &ps, int l,
                      const std::vector<int *> &len, std::vector<NnzRead> &reads) {
     std::vector<DColorNnz> items;
     NnzRead rd;
@@ -807,7 +807,7 @@ void color_nnz_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *
         amg_hierarchy *h = ps[k]->h;
         Level &lv = h->lev[l];
         const int nc = (int)lv.color_rows.size() - 1;
-        lv.d_color_nnz = aget<unsigned long long>(ar, h, std::max(1, nc));
+        lv.d_color_nnz = aget<unsigned long long>(h, std::max(1, nc));
         for (int c = 0; c < nc; c++) {
             items.push_back(DColorNnz{lv.color_rows[c], lv.color_rows[c + 1], len[k], lv.d_color_nnz + c});
             rd.lv.push_back(&lv);
@@ -821,19 +821,19 @@ void color_nnz_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *
     reads.push_back(std::move(rd));
 }
 
-void galerkin_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *> &ps, int lc,
+void galerkin_multi(Stage &st, Scratch &tmp, const std::vector<Sys *> &ps, int lc,
                     std::vector<NnzRead> &reads) {
     std::vector<int *> len(ps.size());
     for (size_t k = 0; k < ps.size(); k++) len[k] = tmp.get<int>(ps[k]->h->lev[lc].n);
     rap_pass(st, ps, lc, false, len);
-    slice_pointers_multi(st, ar, tmp, ps, lc, len, true);
-    color_nnz_multi(st, ar, tmp, ps, lc, len, reads);
+    slice_pointers_multi(st, tmp, ps, lc, len, true);
+    color_nnz_multi(st, tmp, ps, lc, len, reads);
     rap_pass(st, ps, lc, true, len);
 }
 
 // colours, stable colour sort (pi order), colour ranges and cells of level l >= 1 of ps
 // (spans set). One host round trip.
-void order_level_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys *> &ps, int l) {
+void order_level_multi(Stage &st, Scratch &tmp, const std::vector<Sys *> &ps, int l) {
     const int np = (int)ps.size();
     std::vector<int64_t> vo(np + 1, 0);
     std::vector<int> kofs(np + 1, 0);
@@ -860,9 +860,9 @@ void order_level_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys
         mc.add(DColors{lv.n, lv.cellw, lv.m, h->cell_nat[l], color}, lv.n);
         mk.add(DColorKeys{lv.n, lv.ncolors, kofs[k], color, keys + vo[k], vals + vo[k], cnt + kofs[k]},
                pad_rows(lv.n));
-        lv.nat = aget<int>(ar, h, lv.n);
-        lv.inv = aget<int>(ar, h, lv.n);
-        lv.cell = aget<int>(ar, h, lv.n);
+        lv.nat = aget<int>(h, lv.n);
+        lv.inv = aget<int>(h, lv.n);
+        lv.cell = aget<int>(h, lv.n);
         mp.add(DPerm{lv.n, vals + vo[k], lv.nat, lv.inv}, lv.n);
         mg.add(DGather{lv.n, lv.nat, h->cell_nat[l], lv.cell}, lv.n);
     }
@@ -884,15 +884,10 @@ void order_level_multi(Stage &st, Arena &ar, Scratch &tmp, const std::vector<Sys
 }  // namespace
 
 void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const double *x,
-                 const double *y, const std::vector<BatchRows> &rows, cudaStream_t s, Arena &ar,
-                 double **pinned) {
+                 const double *y, const std::vector<BatchRows> &rows, cudaStream_t s,
+                 bool batch_ws) {
     const int P = (int)hs.size();
     const amg_options &o = hs[0]->opt;
-    int64_t Ntot = 0;
-    for (const BatchRows &r : rows) Ntot += r.n;
-    // about 700 bytes per unknown end up in the arena (most of it the outer directions)
-    ar.chunk = (size_t)std::min<int64_t>(std::max<int64_t>(Ntot * 256, int64_t(4) << 20),
-                                         int64_t(256) << 20);
     Stage st(s, std::min<size_t>(std::max<size_t>((size_t)P << 13, size_t(1) << 20), size_t(16) << 20),
              ((size_t)P << 14) + (size_t(64) << 10));
     Scratch tmp(s);
@@ -907,18 +902,32 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         S.nz0 = rows[p].nz0;
         S.nnz = rows[p].nnz;
         all[p] = &S;
+        // the arena's first chunk: about 450 bytes per unknown for the levels and the solve
+        // workspace, 540 more for a batched solve's workspace (most of it the 32 outer
+        // directions), 1.2 MB of fixed buffers
+        hs[p]->arena.s = s;
+        hs[p]->arena.chunk = (size_t(5) << 18) + (size_t)S.n * (batch_ws ? 990 : 450);
     }
-    // every hierarchy's error flag, reduction counter and grid-barrier words, zeroed at once
-    constexpr size_t kSmall = 512;  // bytes per system: err (int), counter (uint), bar[32] at 256
-    char *small = (char *)ar.get(kSmall * P);
-    AMG_CUDA(cudaMemsetAsync(small, 0, kSmall * P, s));
+    // every hierarchy's error flag, reduction counter and grid-barrier words (zeroed)
+    constexpr size_t kSmall = 512;  // bytes: err (int), counter (uint), bar[32] at 256
+    std::vector<DCopy> zero(P);
+    std::vector<const int *> errp(P);
     for (int p = 0; p < P; p++) {
         amg_hierarchy *h = hs[p];
-        h->err_flag = (int *)(small + kSmall * p);
-        h->red_counter = (unsigned int *)(small + kSmall * p + 4);
-        h->bar = (unsigned long long *)(small + kSmall * p + 256);
-        h->bytes += kSmall;
+        char *small = (char *)h->arena.get(kSmall);
+        h->err_flag = (int *)small;
+        h->red_counter = (unsigned int *)(small + 4);
+        h->bar = (unsigned long long *)(small + 256);
+        zero[p] = DCopy{nullptr, (unsigned char *)small, (int64_t)kSmall};
+        errp[p] = h->err_flag;
     }
+    {
+        const DCopy *d = st.put(zero.data(), zero.size());
+        kb_copy<<<P, kB, 0, s>>>(d, P);  // a null source writes zeros
+        AMG_LAUNCH_CHECK();
+    }
+    const int *const *d_errp = st.put(errp.data(), errp.size());
+    int *errs = tmp.get<int>((size_t)P);
 
     // ---- validation and auxiliary boxes (eq. ab12); one round trip
     double *box = tmp.get<double>(6 * (size_t)P);
@@ -950,14 +959,14 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             AMG_LAUNCH_CHECK();
         }
         const double *hb = st.get(box, 6 * (size_t)P);
-        const int *ef = st.get((const int *)small, kSmall / sizeof(int) * P);
+        kb_gather_items<<<blocks_of(P), kB, 0, s>>>(d_errp, P, errs);
+        AMG_LAUNCH_CHECK();
+        const int *ef = st.get(errs, (size_t)P);
         st.sync();
         for (int p = 0; p < P; p++) {
-            const int e = ef[kSmall / sizeof(int) * p];
-            if (e & 1) throw Error{AMG_ERR_BAD_MATRIX, "matrix is not valid SPD CSR input"};
-            if (e & 2) throw Error{AMG_ERR_INVALID_ARG, "non-finite coordinate"};
+            if (ef[p] & 1) throw Error{AMG_ERR_BAD_MATRIX, "matrix is not valid SPD CSR input"};
+            if (ef[p] & 2) throw Error{AMG_ERR_INVALID_ARG, "non-finite coordinate"};
         }
-        AMG_CUDA(cudaMemsetAsync(small, 0, kSmall * P, s));  // as the single setup: cleared
         for (int p = 0; p < P; p++) {
             amg_hierarchy *h = hs[p];
             for (int t = 0; t < 6; t++) h->bbox[t] = hb[6 * p + t];
@@ -980,7 +989,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         Multi<DSpanCsr> ms;
         for (Sys *S : all) {
             amg_hierarchy *h = S->h;
-            int *cell = aget<int>(ar, h, S->n);
+            int *cell = aget<int>(h, S->n);
             S->ln.push_back(S->n);
             S->lw.push_back(1 << S->L);
             S->cellnat.push_back(cell);
@@ -1040,8 +1049,8 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             Sys *S = act[k];
             amg_hierarchy *h = S->h;
             const int w = 1 << S->k, ncl = hn[k];
-            int *agg = aget<int>(ar, h, S->ln.back());
-            int *cellof = aget<int>(ar, h, ncl);
+            int *agg = aget<int>(h, S->ln.back());
+            int *cellof = aget<int>(h, ncl);
             ma.add(DAgg{S->ln.back(), co[k], cid + ro[k], num, agg}, S->ln.back());
             mo.add(DCellOf{w * w, co[k], occ, num, cellof}, (int64_t)w * w);
             S->agg.push_back(agg);
@@ -1074,7 +1083,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             lv.cellw = S->lw[l];
             lv.agg_nat = l + 1 < nlev ? S->agg[l] : nullptr;
             h->cell_nat[l] = S->cellnat[l];
-            h->color_nat[l] = aget<int>(ar, h, lv.n);
+            h->color_nat[l] = aget<int>(h, lv.n);
         }
         h->lev[nlev - 1].coarsest = true;
         h->lev[0].span = S->span0;
@@ -1083,7 +1092,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
     }
 
     // ---- level 1 (auxiliary level L): colours with the fine span, pi order
-    order_level_multi(st, ar, tmp, all, 1);
+    order_level_multi(st, tmp, all, 1);
 
     // ---- finest level: colours, pi order (blocks = level-1 pi rows), operator, big blocks
     {
@@ -1107,12 +1116,12 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             mc.add(DColors{F.n, 1 << h->L, F.m, h->cell_nat[0], h->color_nat[0]}, F.n);
             mk.add(DFineKeys{F.n, C1.n, kofs[p], F.agg_nat, C1.inv, keys + vo[p], vals + vo[p]},
                    pad_rows(F.n));
-            F.nat = aget<int>(ar, h, F.n);
-            F.inv = aget<int>(ar, h, F.n);
-            F.parent = aget<int>(ar, h, F.n);
+            F.nat = aget<int>(h, F.n);
+            F.inv = aget<int>(h, F.n);
+            F.parent = aget<int>(h, F.n);
             F.nblocks = C1.n;
-            F.bptr = aget<int>(ar, h, (size_t)C1.n + 1);
-            F.cell = aget<int>(ar, h, F.n);
+            F.bptr = aget<int>(h, (size_t)C1.n + 1);
+            F.cell = aget<int>(h, F.n);
             mu.add(DFineUnpack{F.n, C1.n, kofs[p], keys + vo[p], vals + vo[p], F.nat, F.inv, F.parent,
                                F.bptr},
                    F.n);
@@ -1160,7 +1169,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             nbig[p] = hbig[p];
         }
         st.reset_readbacks();
-        slice_pointers_multi(st, ar, tmp, all, 0, len, true);
+        slice_pointers_multi(st, tmp, all, 0, len, true);
         Multi<DFill> mf;
         for (int p = 0; p < P; p++) {
             Level &F = hs[p]->lev[0];
@@ -1170,7 +1179,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
                    F.n);
         }
         launch(st, mf, kb_fill_csr);
-        color_nnz_multi(st, ar, tmp, all, 0, len, reads);
+        color_nnz_multi(st, tmp, all, 0, len, reads);
         for (int p = 0; p < P; p++) {
             Level &F = hs[p]->lev[0];
             if (nbig[p] > 0) {
@@ -1185,7 +1194,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
     }
 
     // ---- A_1 = P^t A P, then the coarser levels
-    galerkin_multi(st, ar, tmp, all, 1, reads);
+    galerkin_multi(st, tmp, all, 1, reads);
     for (int l = 2; l < maxlev; l++) {
         std::vector<Sys *> ps;
         for (Sys *S : all)
@@ -1202,14 +1211,14 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         st.sync();
         for (int k = 0; k < np; k++) ps[k]->h->lev[l].span = hsp[k];
         st.reset_readbacks();
-        order_level_multi(st, ar, tmp, ps, l);
+        order_level_multi(st, tmp, ps, l);
         Multi<DParentPi> mpp;
         Multi<DChildren> mcc, mch;
         for (int k = 0; k < np; k++) {
             amg_hierarchy *h = ps[k]->h;
             Level &f = h->lev[l - 1], &c = h->lev[l];
-            f.parent = aget<int>(ar, h, f.n);
-            c.children = aget<int4>(ar, h, c.n);
+            f.parent = aget<int>(h, f.n);
+            c.children = aget<int4>(h, c.n);
             mpp.add(DParentPi{f.n, f.nat, f.agg_nat, c.inv, f.parent}, f.n);
             mcc.add(DChildren{c.n, 0, nullptr, nullptr, c.children}, c.n);
             mch.add(DChildren{f.n, f.cellw, f.parent, f.cell, c.children}, f.n);
@@ -1217,7 +1226,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         launch(st, mpp, kb_parent_pi);
         launch(st, mcc, kb_children_clear);
         launch(st, mch, kb_children);
-        galerkin_multi(st, ar, tmp, ps, l, reads);
+        galerkin_multi(st, tmp, ps, l, reads);
     }
 
     // ---- coarsest levels: dense Cholesky and explicit inverse, one CTA per system
@@ -1229,8 +1238,8 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
             amg_hierarchy *h = hs[p];
             Level &lv = h->lev[h->nlev - 1];
             const int n = lv.n;
-            lv.Ainv = aget<double>(ar, h, (size_t)n * n);
-            lv.Ainv32 = aget<float>(ar, h, 2 * (size_t)n * n);
+            lv.Ainv = aget<double>(h, (size_t)n * n);
+            lv.Ainv32 = aget<float>(h, 2 * (size_t)n * n);
             const size_t need = 2 * sizeof(double) * (size_t)n * n;
             double *a = lv.Ainv, *w = nullptr;
             if (need > 160 * 1024) {  // factor and inverse factor in global scratch
@@ -1261,7 +1270,9 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
     {
         std::vector<const unsigned long long *> hr(reads.size());
         for (size_t r = 0; r < reads.size(); r++) hr[r] = st.get(reads[r].mirror, reads[r].lv.size());
-        const int *ef = st.get((const int *)small, kSmall / sizeof(int) * P);
+        kb_gather_items<<<blocks_of(P), kB, 0, s>>>(d_errp, P, errs);
+        AMG_LAUNCH_CHECK();
+        const int *ef = st.get(errs, (size_t)P);
         st.sync();
         for (size_t r = 0; r < reads.size(); r++)
             for (size_t j = 0; j < reads[r].lv.size(); j++)
@@ -1274,9 +1285,8 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
                 for (int64_t c : lv.color_nnz) tot += c;
                 lv.A.stored = tot;
             }
-            const int e = ef[kSmall / sizeof(int) * p];
-            if (e & 8) throw Error{AMG_ERR_BAD_MATRIX, "coarsest operator is not positive definite"};
-            if (e & 4) throw Error{AMG_ERR_CUDA, "internal error: stencil offset beyond the span"};
+            if (ef[p] & 8) throw Error{AMG_ERR_BAD_MATRIX, "coarsest operator is not positive definite"};
+            if (ef[p] & 4) throw Error{AMG_ERR_CUDA, "internal error: stencil offset beyond the span"};
         }
         st.reset_readbacks();
     }
@@ -1284,8 +1294,6 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
     // ---- what amg_setup's solve workspace and a batched solve's preparation hold
     const bool fp32 = (o.cycle_prec == AMG_FP32);
     const int kc = o.kcycle_n, maxit = o.max_iters;
-    const size_t pin_per = 64 + 2 * (size_t)maxit;
-    AMG_CUDA(cudaMallocHost(pinned, sizeof(double) * pin_per * P));
     Multi<DDiag> mdg;
     Multi<DConvert> mcv;
     std::vector<DCopy> copies;
@@ -1304,63 +1312,61 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
     for (int p = 0; p < P; p++) {
         amg_hierarchy *h = hs[p];
         const size_t n = (size_t)h->N;
-        h->red_partials = aget<double>(ar, h, (size_t)kRedBlocks * std::max(8, maxit + 8));
-        h->cyc_partials = aget<double>(ar, h, 2 * 4 * 1024);
-        h->xo = aget<double>(ar, h, n);
-        h->ro = aget<double>(ar, h, n);
-        h->zo = aget<double>(ar, h, n);
-        h->to = aget<double>(ar, h, n);
-        h->bo = aget<double>(ar, h, n);
-        h->osc = aget<double>(ar, h, outer_scalar_count(maxit));
-        h->oit = aget<int>(ar, h, 1);
-        h->dP = aget<double *>(ar, h, maxit);
-        h->dQ = aget<double *>(ar, h, maxit);
-        h->h_pinned = *pinned + pin_per * p;
-        h->pinned_owned = false;
+        h->red_partials = aget<double>(h, (size_t)kRedBlocks * std::max(8, maxit + 8));
+        h->cyc_partials = aget<double>(h, 2 * 4 * 1024);
+        h->xo = aget<double>(h, n);
+        h->ro = aget<double>(h, n);
+        h->zo = aget<double>(h, n);
+        h->to = aget<double>(h, n);
+        h->bo = aget<double>(h, n);
+        h->osc = aget<double>(h, outer_scalar_count(maxit));
+        h->oit = aget<int>(h, 1);
+        h->dP = aget<double *>(h, maxit);
+        h->dQ = aget<double *>(h, maxit);
         for (int l = 0; l < h->nlev; l++) {
             Level &lv = h->lev[l];
             for (int prec = 0; prec < (fp32 ? 2 : 1); prec++) {
                 if (l > 0) {
                     if (prec == 0) {
-                        lv.v64.rhs = aget<double>(ar, h, lv.n);
-                        lv.v64.e = aget<double>(ar, h, lv.n);
+                        lv.v64.rhs = aget<double>(h, lv.n);
+                        lv.v64.e = aget<double>(h, lv.n);
                     } else {
-                        lv.v32.rhs = aget<float>(ar, h, lv.n);
-                        lv.v32.e = aget<float>(ar, h, lv.n);
+                        lv.v32.rhs = aget<float>(h, lv.n);
+                        lv.v32.e = aget<float>(h, lv.n);
                     }
                 }
                 if (l > 0 && !lv.coarsest) {
                     for (int i = -1; i < kc; i++) {
                         if (prec == 0) {
-                            if (i < 0) lv.v64.r = aget<double>(ar, h, lv.n);
+                            if (i < 0) lv.v64.r = aget<double>(h, lv.n);
                             else {
-                                lv.v64.p[i] = aget<double>(ar, h, lv.n);
-                                lv.v64.q[i] = aget<double>(ar, h, lv.n);
+                                lv.v64.p[i] = aget<double>(h, lv.n);
+                                lv.v64.q[i] = aget<double>(h, lv.n);
                             }
                         } else {
-                            if (i < 0) lv.v32.r = aget<float>(ar, h, lv.n);
+                            if (i < 0) lv.v32.r = aget<float>(h, lv.n);
                             else {
-                                lv.v32.p[i] = aget<float>(ar, h, lv.n);
-                                lv.v32.q[i] = aget<float>(ar, h, lv.n);
+                                lv.v32.p[i] = aget<float>(h, lv.n);
+                                lv.v32.q[i] = aget<float>(h, lv.n);
                             }
                         }
                     }
                 }
             }
-            lv.dinv64 = aget<double>(ar, h, lv.n);
+            lv.dinv64 = aget<double>(h, lv.n);
             if (fp32) {
-                lv.dinv32 = aget<float>(ar, h, lv.n);
-                lv.A.val32 = aget<float>(ar, h, (size_t)lv.A.padded);
+                lv.dinv32 = aget<float>(h, lv.n);
+                lv.A.val32 = aget<float>(h, (size_t)lv.A.padded);
                 mcv.add(DConvert{(int)lv.A.padded, lv.A.val, lv.A.val32}, lv.A.padded);
             }
             mdg.add(DDiag{lv.n, lv.A.sl_ptr, lv.A.val, lv.dinv64, fp32 ? lv.dinv32 : nullptr}, lv.n);
-            lv.sc = aget<double>(ar, h, SC_N);
+            lv.sc = aget<double>(h, SC_N);
         }
         h->lev[0].v64.rhs = h->ro;
         h->lev[0].v64.e = h->zo;
         if (fp32) {
-            h->r32 = aget<float>(ar, h, n);
-            h->z32 = aget<float>(ar, h, n);
+            h->r32 = aget<float>(h, n);
+            h->z32 = aget<float>(h, n);
             h->lev[0].v32.rhs = h->r32;
             h->lev[0].v32.e = h->z32;
         }
@@ -1368,43 +1374,44 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         std::vector<unsigned char> img;
         for (int prec = 0; prec < (fp32 ? 2 : 1); prec++) {
             const size_t b = level_table_image(h, prec == 1, img);
-            void *dst = ar.get(b);
-            h->bytes += (b + 255) & ~size_t(255);
+            void *dst = h->arena.get(b);
             (prec == 1 ? h->lev_tab32 : h->lev_tab64) = dst;
             stage(dst, img.data(), b);
         }
-        // outer directions of a batched solve (as ensure_directions: in chunks of 16, each
-        // vector 256-byte aligned) and the batched-solve workspace (as batch_ws)
-        const int target = std::min(maxit, ((std::min(maxit, kBatchDirs) + 15) / 16) * 16);
-        const size_t stride = (n + 31) & ~size_t(31);
-        double *slab = aget<double>(ar, h, 2 * (size_t)target * stride);
-        for (int j = 0; j < target; j++) {
-            h->P.push_back(slab + j * stride);
-            h->Q.push_back(slab + (target + j) * stride);
-        }
-        stage(h->dP, h->P.data(), sizeof(double *) * target);
-        stage(h->dQ, h->Q.data(), sizeof(double *) * target);
-        BatchWs &w = h->bws;
-        w.pq = aget<double>(ar, h, maxit);
-        w.bo = aget<double>(ar, h, n);
-        w.xo = aget<double>(ar, h, n);
-        w.to = aget<double>(ar, h, n);
-        std::vector<int> colors;
-        for (int l = 0; l < h->nlev; l++) {
-            const std::vector<int> &r = (l == 0) ? h->lev[0].color_blocks : h->lev[l].color_rows;
-            w.cofs[l] = (int)colors.size();
-            w.ncol[l] = std::max(0, (int)r.size() - 1);
-            colors.insert(colors.end(), r.begin(), r.end());
-        }
-        w.colors = aget<int>(ar, h, colors.size());
-        stage(w.colors, colors.data(), sizeof(int) * colors.size());
-        const Level &F = h->lev[0];
-        if (F.nbig > 0) {
-            std::vector<int4> bigr;
-            for (size_t c = 0; c + 1 < F.color_big.size(); c++)
-                bigr.push_back(make_int4(F.color_big[c], F.color_bigc[c], F.color_big[c + 1], 0));
-            w.bigr = aget<int4>(ar, h, bigr.size());
-            stage(w.bigr, bigr.data(), sizeof(int4) * bigr.size());
+        if (batch_ws) {
+            // outer directions of a batched solve (as ensure_directions: in chunks of 16, each
+            // vector 256-byte aligned) and the batched-solve workspace (as batch_ws)
+            const int target = std::min(maxit, ((std::min(maxit, kBatchDirs) + 15) / 16) * 16);
+            const size_t stride = (n + 31) & ~size_t(31);
+            double *slab = aget<double>(h, 2 * (size_t)target * stride);
+            for (int j = 0; j < target; j++) {
+                h->P.push_back(slab + j * stride);
+                h->Q.push_back(slab + (target + j) * stride);
+            }
+            stage(h->dP, h->P.data(), sizeof(double *) * target);
+            stage(h->dQ, h->Q.data(), sizeof(double *) * target);
+            BatchWs &w = h->bws;
+            w.pq = aget<double>(h, maxit);
+            w.bo = aget<double>(h, n);
+            w.xo = aget<double>(h, n);
+            w.to = aget<double>(h, n);
+            std::vector<int> colors;
+            for (int l = 0; l < h->nlev; l++) {
+                const std::vector<int> &r = (l == 0) ? h->lev[0].color_blocks : h->lev[l].color_rows;
+                w.cofs[l] = (int)colors.size();
+                w.ncol[l] = std::max(0, (int)r.size() - 1);
+                colors.insert(colors.end(), r.begin(), r.end());
+            }
+            w.colors = aget<int>(h, colors.size());
+            stage(w.colors, colors.data(), sizeof(int) * colors.size());
+            const Level &F = h->lev[0];
+            if (F.nbig > 0) {
+                std::vector<int4> bigr;
+                for (size_t c = 0; c + 1 < F.color_big.size(); c++)
+                    bigr.push_back(make_int4(F.color_big[c], F.color_bigc[c], F.color_big[c + 1], 0));
+                w.bigr = aget<int4>(h, bigr.size());
+                stage(w.bigr, bigr.data(), sizeof(int4) * bigr.size());
+            }
         }
         if (fp32) h->fp32_ready = true;
     }
@@ -1425,6 +1432,7 @@ void build_batch(const std::vector<amg_hierarchy *> &hs, const amg_csr &A, const
         cudaFreeHost(hup);
     }
     st.sync();
+    for (amg_hierarchy *h : hs) h->bytes += h->arena.bytes;  // the hierarchy's chunks
 }
 
 }  // namespace amg

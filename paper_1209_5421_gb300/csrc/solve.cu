@@ -1750,7 +1750,7 @@ void allocate_solve_workspace(amg_hierarchy *h) {
     h->oit = halloc<int>(h, 1);
     h->dP = halloc<double *>(h, h->opt.max_iters);
     h->dQ = halloc<double *>(h, h->opt.max_iters);
-    AMG_CUDA(cudaMallocHost(&h->h_pinned, (64 + 2 * (size_t)h->opt.max_iters) * sizeof(double)));
+    ensure_pinned(h);
     for (int l = 0; l < h->nlev; l++) {
         Level &lv = h->lev[l];
         lv.dinv64 = halloc<double>(h, lv.n);
@@ -1767,6 +1767,11 @@ void allocate_solve_workspace(amg_hierarchy *h) {
 int bounds_flags_solve() { return bounds_flag_read_clear(); }
 
 size_t outer_scalar_count(int max_iters) { return OS_ZQ + 2 * (size_t)max_iters + 8; }
+
+void ensure_pinned(amg_hierarchy *h) {
+    if (!h->h_pinned)
+        AMG_CUDA(cudaMallocHost(&h->h_pinned, (64 + 2 * (size_t)h->opt.max_iters) * sizeof(double)));
+}
 
 double cycle_application_bytes(amg_hierarchy *h, int value_bytes) {
     std::vector<Op> prog;
@@ -1889,6 +1894,7 @@ static int solve_fgmres(amg_hierarchy *h, const double *b_nat, double tol, doubl
 
 int solve(amg_hierarchy *h, const double *b_nat, double tol, double *x_nat, int *iters,
           double *relres) {
+    ensure_pinned(h);  // a hierarchy of the batched setup allocates it here
     if (h->opt.outer == AMG_OUTER_FGMRES) return solve_fgmres(h, b_nat, tol, x_nat, iters, relres);
     cudaStream_t s = h->stream;
     const int n = (int)h->N;

@@ -412,3 +412,46 @@ def test_moved_bytes_of_a_batch(amg):
     assert b2 == pytest.approx(alone[0] + alone[1], rel=1e-12)
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("outer", ["fcg", "fgmres"])
+def test_setup_many_gives_independent_single_hierarchies(amg, outer):
+    # amg_setup_many: the batched setup's hierarchies returned one by one, each the one
+    # amg_setup builds (bit for bit, solves included), each freed on its own
+    import torch
+
+    kw = dict(cycle_prec=amg.FP32, outer=amg.OUTER_FGMRES) if outer == "fgmres" else {}
+    probs = [p1_poisson(**s) for s in SPECS] + [p1_poisson(n=129, jitter=0.1, graded=True,
+                                                           kappa_blocks=16, seed=11, rhs="normal")]
+    torch.cuda.synchronize()
+    base = amg.pool_bytes_in_use(torch.cuda.current_device())
+    many = amg.setup_many([(p.rowptr, p.col, p.val, p.x, p.y) for p in probs], **kw)
+    singles = [amg.Hierarchy.from_problem(p, **kw) for p in probs]
+    for k, (Gm, Gs) in enumerate(zip(many, singles)):
+        assert Gm.nlev == Gs.nlev and Gm.L == Gs.L, k
+        for l in range(Gs.nlev):
+            assert Gm.level_info(l) == Gs.level_info(l), (k, l)
+            lm, ls = Gm.level(l), Gs.level(l)
+            for key in ls:
+                np.testing.assert_array_equal(lm[key], ls[key], err_msg=f"system {k} level {l} {key}")
+    many[0].close()  # one freed: the others are untouched
+    for k in range(1, len(probs)):
+        x1, it1, _, st1 = many[k].solve(probs[k].b, 1e-8)
+        x2, it2, _, st2 = singles[k].solve(probs[k].b, 1e-8)
+        assert st1 == amg.OK and st2 == amg.OK and it1 == it2, k
+        np.testing.assert_array_equal(x1, x2)
+    if outer == "fcg":  # ready for batched solves: the same bits as over single setups
+        rhs = np.concatenate([p.b for p in probs[1:]])
+        Bm = amg.Batch.over(many[1:], threads=1024)
+        Bs = amg.Batch.over(singles[1:], threads=1024)
+        xm, itm, _, stm = Bm.solve(rhs, 1e-8)
+        xs, its, _, sts = Bs.solve(rhs, 1e-8)
+        assert (stm == amg.OK).all()
+        np.testing.assert_array_equal(xm, xs)
+        np.testing.assert_array_equal(itm, its)
+        Bm.close()
+        Bs.close()
+    for G in many[1:] + singles:
+        G.close()
+    torch.cuda.synchronize()
+    assert amg.pool_bytes_in_use(torch.cuda.current_device()) == base
