@@ -19,7 +19,9 @@ Two lanes share the GPU:
   * the large lane: a system above `large_unknowns` is solved by the single-system solver
     (the grid-wide cycle kernel over all SMs). It runs alone: batch workers drain first and
     wait while it runs.
-Setups run on a separate thread (each on the hierarchy's own stream).
+Setups run on a separate thread (each on the hierarchy's own stream). New batch-lane matrices
+that wait at the same time are set up together, by one multi-system setup (amg_setup_many);
+each hierarchy still stands on its own (charged, evicted and freed one by one).
 
 Every system is computed by code whose result does not depend on the other work in flight:
 in the batch lane by one CTA of fixed size, in the large lane by the single-system kernel.
@@ -85,7 +87,7 @@ class _Resident:
 class Server:
     def __init__(self, budget_bytes: int = 150 << 30, cycle_prec: int = amg.FP32,
                  workers: int = 4, max_batch: int = 152, large_unknowns: int = 250_000,
-                 device: int = 0):
+                 device: int = 0, max_group: int = 64):
         import torch
 
         self.torch = torch
@@ -94,6 +96,7 @@ class Server:
         self.prec = cycle_prec
         self.max_batch = max_batch
         self.large = large_unknowns
+        self.max_group = max_group  # new batch-lane matrices set up together, at most
         self.matrices: dict = {}                  # key -> (rowptr, col, val, x, y, z)
         self.res: OrderedDict = OrderedDict()      # key -> _Resident (LRU order)
         self.used = 0
@@ -110,6 +113,8 @@ class Server:
         self.completed: list[Request] = []
         self.evictions = 0
         self.setups = 0
+        self.group_setups = 0  # multi-system setups (amg_setup_many) of several matrices
+        self.suspect: set = set()  # keys of a rejected group: each is set up on its own
         self.setup_failures = 0  # matrices that could not be set up (their requests failed)
         self.batches = 0
         self.errors: list[str] = []
@@ -182,7 +187,8 @@ class Server:
         return {"completed": len(lat), "failed": failed, "solves_per_s": len(lat) / (t1 - t0),
                 "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "setups": self.setups, "setup_failures": self.setup_failures,
+                "setups": self.setups, "group_setups": self.group_setups,
+                "setup_failures": self.setup_failures,
                 "evictions": self.evictions, "batches": self.batches,
                 "max_resident_bytes": self.max_used, "budget_bytes": self.budget,
                 "grown_bytes": self.grown,
@@ -280,6 +286,13 @@ class Server:
                     return
                 if r.key not in self.setting_up:
                     continue
+                group = self._companions(r, m, n)
+            if group:
+                done = self._setup_group(r, est, group)
+                if done is None:  # an unexpected failure: the server stops
+                    return
+                if done:
+                    continue  # else (a matrix of the group was rejected): each on its own
             h = None
             try:
                 with self.grid_lock:
@@ -316,6 +329,73 @@ class Server:
                     self.need_setup.remove(q)
                     self.ready.append(q)
                 self.cv.notify_all()
+
+    def _companions(self, r: Request, m, n: int) -> list:
+        """Other new batch-lane 2D matrices waiting now, admitted at once (their estimates
+        charged, marked as being set up) to be set up with r's matrix in one multi-system
+        setup: [(key, estimate)], empty if none (caller holds cv)."""
+        if m[5] is not None or n > self.large or self.max_group < 2 or r.key in self.suspect:
+            return []
+        out, seen = [], {r.key}
+        for q in self.need_setup:
+            if len(out) + 1 >= self.max_group:
+                break
+            k = q.key
+            if k in seen or k in self.res or k in self.setting_up or k in self.suspect:
+                continue
+            mk = self.matrices.get(k)
+            if mk is None or mk[5] is not None or len(mk[0]) - 1 > self.large:
+                continue
+            est = setup_estimate(len(mk[0]) - 1, len(mk[1]))
+            if not self._admit(est):
+                break
+            seen.add(k)
+            self.setting_up.add(k)
+            self.used += est
+            self.max_used = max(self.max_used, self.used)
+            out.append((k, est))
+        return out
+
+    def _setup_group(self, r: Request, r_est: int, group: list) -> bool:
+        """r's matrix and the group's in one amg_setup_many (each hierarchy then stands on its
+        own: evicted and freed one by one). False if the library rejects the call: the
+        group's charges are returned and r's setup goes on alone (each matrix of the group
+        is set up later on its own, so a bad matrix fails only its own requests)."""
+        keys = [r.key] + [k for k, _ in group]
+        ests = dict(group)
+        ests[r.key] = r_est
+        try:
+            with self.grid_lock:
+                hs = amg.setup_many([self.matrices[k][:5] for k in keys], cycle_prec=self.prec,
+                                    outer=amg.OUTER_FCG)
+            sizes = [h.nbytes for h in hs]
+        except (amg.AmgError, ValueError, TypeError):
+            with self.cv:
+                for k, est in group:
+                    self.setting_up.discard(k)
+                    self.used -= est
+                    self.suspect.add(k)  # set up on its own from now on
+                self.cv.notify_all()
+            return False
+        except Exception as e:  # noqa: BLE001
+            self._fail(f"setup of {keys!r}: {e}")
+            return None
+        with self.cv:
+            for k, h, nbytes in zip(keys, hs, sizes):
+                self.setting_up.discard(k)
+                self.used += nbytes - ests[k]
+                self.res[k] = _Resident(h, nbytes)
+                self.setups += 1
+                if k == r.key:
+                    self.ready.append(r)
+                for q in [q for q in self.need_setup if q.key == k]:
+                    self.need_setup.remove(q)
+                    self.ready.append(q)
+            self.group_setups += 1
+            self.max_used = max(self.max_used, self.used)
+            self._admit(0)  # estimates that fell short: make room again
+            self.cv.notify_all()
+        return True
 
     def _take_ready(self, large: bool):
         """Ready requests of one lane whose hierarchy is idle (caller holds cv)."""

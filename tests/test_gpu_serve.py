@@ -129,3 +129,30 @@ def test_budget_admission_and_eviction(amg):
         A = probs[key].to_scipy()
         assert r.status == amg.OK
         assert np.linalg.norm(b - A @ r.x) / np.linalg.norm(b) <= 1e-8
+
+
+def test_waiting_matrices_set_up_together(amg):
+    # new batch-lane matrices queued at the same time are set up by one amg_setup_many: each
+    # result is still the one a request alone gets (bitwise), and the charged bytes are the
+    # resident hierarchies' own
+    from paper_1209_5421_gb300.serve import Server
+
+    probs = _problems()
+    del probs["m6"]
+    large = 40_000
+    S = Server(workers=2, large_unknowns=large)
+    for k, p in probs.items():
+        S.register(k, p.rowptr, p.col, p.val, p.x, p.y)
+    rng = np.random.default_rng(9)
+    with S.cv:  # all queued before the setup thread looks
+        reqs = [(k, rng.standard_normal(p.n)) for k, p in probs.items()]
+        handles = [S.submit(k, b) for k, b in reqs]
+    S.drain()
+    st = S.stats()
+    assert S.used == sum(e.nbytes for e in S.res.values()) == sum(e.h.nbytes for e in S.res.values())
+    S.close()
+    assert st["group_setups"] == 1 and st["setups"] == len(probs), st
+    for r, (key, b) in zip(handles, reqs):
+        assert r.status == amg.OK and r.lane == "batch", (key, r.status, r.lane)
+        alone = _solo(amg, probs[key], b, large)
+        assert np.array_equal(alone.x, r.x) and alone.iters == r.iters, key

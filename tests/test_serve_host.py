@@ -55,6 +55,7 @@ class Log:
         self.lock = threading.Lock()
         self.intervals = []  # (kind, t0, t1)
         self.closed = []     # sizes of closed hierarchies, in order
+        self.groups = []     # sizes of the multi-system setups (amg.setup_many calls)
         self.running = {}    # kind -> spans in progress
 
     @contextlib.contextmanager
@@ -138,8 +139,16 @@ def server_cls(monkeypatch):
     def make(bytes_per_unknown=BYTES_PER_UNKNOWN, grow_per_solve=0, batch_hold=0.003,
              large_hold=0.003, **kw):
         H, B = make_fakes(torch, log, bytes_per_unknown, grow_per_solve, batch_hold, large_hold)
+
+        def setup_many(problems, cycle_prec=None, outer=None):
+            # as amg_setup_many: one hierarchy per system, or the first rejection for all
+            with log.lock:
+                log.groups.append(len(problems))
+            return [H(*p, cycle_prec=cycle_prec, outer=outer) for p in problems]
+
         monkeypatch.setattr(amg, "Hierarchy", H)
         monkeypatch.setattr(amg, "Batch", B)
+        monkeypatch.setattr(amg, "setup_many", setup_many)
         S = Server(**kw)
         S.dev = torch.device("cpu")  # before the first request: the fakes run on the host
         made.append(S)
@@ -386,3 +395,42 @@ def test_unknown_matrix_fails_its_request(server_cls):
     S.close()
     assert r1.status == amg.ERR_INVALID_ARG and r1.lane == "setup" and r1.x is None
     assert r2.status == amg.OK
+
+
+def test_waiting_matrices_are_set_up_together(server_cls):
+    """New batch-lane matrices that wait at the same time are set up by one multi-system setup
+    (a large-lane matrix still on its own), each charged and resident on its own, with the
+    right results."""
+    make, log = server_cls
+    probs = _problems([9, 12, 15, 11, 30, 10])  # m4 (784 unknowns) takes the large lane
+    S = make(workers=2, large_unknowns=500)
+    _register(S, probs)
+    with S.cv:  # every request queued before the setup thread looks
+        reqs = [(k, S.submit(k, np.ones(probs[k].n))) for k in probs]
+    S.drain(timeout=60)
+    st = S.stats()
+    assert _consistent(S)
+    S.close()
+    assert log.groups == [5], log.groups
+    assert st["setups"] == 6 and st["group_setups"] == 1
+    for key, r in reqs:
+        p = probs[key]
+        assert r.status == amg.OK and r.lane == ("large" if p.n > 500 else "batch")
+        np.testing.assert_allclose(r.x, _solve(p.rowptr, p.col, p.val, r.b), rtol=0, atol=1e-12)
+
+
+def test_group_setup_waits_for_a_large_solve(server_cls):
+    """A multi-system setup, like a single one, does not overlap a large-lane solve."""
+    make, log = server_cls
+    probs = _problems([30, 9, 12, 15])
+    S = make(workers=1, large_unknowns=500, large_hold=0.3)
+    _register(S, probs)
+    S.submit("m0", np.ones(probs["m0"].n))
+    _wait_running(log, "large")
+    with S.cv:
+        rs = [S.submit(k, np.ones(probs[k].n)) for k in ("m1", "m2", "m3")]
+    S.drain(timeout=60)
+    S.close()
+    assert all(r.status == amg.OK for r in rs)
+    assert log.groups == [3], log.groups
+    assert not _overlaps(log, "large", "setup")

@@ -46,6 +46,14 @@ MUTANTS = {
     "setup_outside_grid_lock": (
         "                with self.grid_lock:\n                    h = amg.Hierarchy(",
         "                if True:\n                    h = amg.Hierarchy("),
+    # multi-system setups run beside large-lane solves
+    "group_setup_outside_grid_lock": (
+        "            with self.grid_lock:\n                hs = amg.setup_many(",
+        "            if True:\n                hs = amg.setup_many("),
+    # the matrices set up with the first one are not charged before their setup
+    "group_not_charged": (
+        "            self.setting_up.add(k)\n            self.used += est\n",
+        "            self.setting_up.add(k)\n"),
     # two requests of one matrix in one batch
     "same_system_twice_in_a_batch": (
         "            if ent is None or ent.busy or q.key in seen:",
