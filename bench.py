@@ -139,8 +139,9 @@ def kernel_source_hash():
 
 
 def recorded_traffic(workload, prec):
-    """DRAM bytes per launch of the cycle kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    """DRAM bytes per launch of the cycle kernel (or of the batch kernel: one launch is a
+    whole batch solve) from the committed ncu summary, if it was taken on the current kernel
+    sources (else None)."""
     p = os.path.join(ROOT, "profiles", "cycle_traffic.json")
     try:
         with open(p) as f:
@@ -333,7 +334,10 @@ def run_batched(args, world, flush, dev, stream):
                          "achieved": round(moved / (t / args.steps / 1e3) / 1e9, 1),
                          "peak": peak_gbs, "unit": "GB/s",
                          "frac": round(moved / (t / args.steps / 1e3) / 1e9 / peak_gbs, 4),
-                         "bytes_per_solve": moved},
+                         "bytes_per_solve": moved,
+                         # DRAM bytes of one batch-kernel launch (one whole batch solve) from
+                         # the committed ncu summary, if taken on the current kernel sources
+                         "traffic": recorded_traffic(f"batch_{len(probs)}", name)},
         }
     # the plain FP64 method, one system at a time (every 16th system, hierarchies resident)
     sample = probs[::16]
@@ -604,6 +608,7 @@ def run_served_rate(args, local, mats, rate, nreq, seed):
             "value": round(st["solves_per_s"], 2), "unit": "solves/s",
             "latency_ms": {"p50": round(st["p50_ms"], 2), "p99": round(st["p99_ms"], 2)},
             "requests": nreq, "wall_s": round(wall, 2), "setups": st["setups"],
+            "group_setups": st.get("group_setups", 0),
             "evictions": st["evictions"], "batches": st["batches"],
             "large_lane_solves": st["large_lane"],
             "max_resident_bytes": st["max_resident_bytes"],
