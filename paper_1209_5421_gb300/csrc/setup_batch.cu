@@ -63,18 +63,31 @@ struct Stage {
         AMG_CUDA(cudaMallocHost(&rbuf, rcap));
         device_alloc((void **)&dbuf, cap, s);
     }
+    std::vector<std::pair<void *, void *>> extra;  // one-off buffers of tables above cap
     ~Stage() {
         cudaStreamSynchronize(s);
         if (dbuf) cudaFreeAsync(dbuf, s);
+        for (auto &e : extra)
+            if (e.second) cudaFreeAsync(e.second, s);
         cudaStreamSynchronize(s);
         if (hbuf) cudaFreeHost(hbuf);
         if (rbuf) cudaFreeHost(rbuf);
+        for (auto &e : extra) cudaFreeHost(e.first);
     }
     // device copy of count T's (valid for kernels launched on s afterwards)
     template <class T>
     T *put(const T *src, size_t count) {
         const size_t b = (std::max<size_t>(count * sizeof(T), 1) + 255) & ~size_t(255);
-        if (b > cap) throw Error{AMG_ERR_UNSUPPORTED, "batched setup: launch table too large"};
+        if (b > cap) {  // a table of its own (very large batches)
+            void *h = nullptr, *d = nullptr;
+            AMG_CUDA(cudaMallocHost(&h, b));
+            extra.emplace_back(h, nullptr);
+            device_alloc(&d, b, s);
+            extra.back().second = d;
+            std::memcpy(h, src, count * sizeof(T));
+            AMG_CUDA(cudaMemcpyAsync(d, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+            return (T *)d;
+        }
         if (used + b > cap) {  // every earlier upload has been read once s is idle
             AMG_CUDA(cudaStreamSynchronize(s));
             used = 0;

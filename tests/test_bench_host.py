@@ -64,13 +64,20 @@ def test_recorded_traffic_only_for_the_sources_it_was_taken_on(monkeypatch):
 
 
 def test_kernel_source_hash_follows_the_sources(tmp_path, monkeypatch):
+    # every file the solve kernels are compiled from changes the hash; a setup-only file not
     csrc = tmp_path / "paper_1209_5421_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "a.cu").write_text("x")
+    for f in bench.KERNEL_SOURCES:
+        (csrc / f).write_text("x")
+    (csrc / "setup.cu").write_text("x")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    h1 = bench.kernel_source_hash()
-    (csrc / "a.cu").write_text("y")
-    assert bench.kernel_source_hash() != h1
+    h0 = bench.kernel_source_hash()
+    (csrc / "setup.cu").write_text("y")
+    assert bench.kernel_source_hash() == h0
+    for f in bench.KERNEL_SOURCES:
+        h1 = bench.kernel_source_hash()
+        (csrc / f).write_text("y")
+        assert bench.kernel_source_hash() != h1, f
 
 
 def test_measured_peak_and_fallback(tmp_path, monkeypatch):
