@@ -472,57 +472,6 @@ def time_config(args, world, flush, stream, A, b, x, opts, steps, warmup):
             "iters": its[-1], "relres": float(max(rrs)), "steps": steps}
 
 
-def time_config_one_cta(args, world, flush, stream, A, b, x, opts, steps, warmup):
-    """time_config for the same method executed by the batched kernel on one CTA: the setup is
-    amg_setup_many of the one system (which also prepares it for batched solves) and a batch
-    of one with the fixed 1024-thread shape; the solve is that batch's solve (no grid
-    barriers: one CTA runs every step of the solve)."""
-    import torch
-
-    from paper_1209_5421_gb300 import amg
-
-    n = int(b.numel())
-    cat = (np.array([0, n], np.int64), *A)
-
-    def step(mid=None):
-        (h,) = amg.setup_many(concatenated=cat, **opts)
-        B = amg.Batch.over([h], threads=1024)
-        if mid is not None:
-            mid.record(stream)
-        _, it, rr, st = B.solve(b, args.tol, x=x)
-        B.close()
-        h.close()
-        if st[0] != amg.OK:
-            raise RuntimeError(f"solve failed: status {st[0]}, relres {rr[0]}")
-        return int(it[0]), float(rr[0])
-
-    for _ in range(warmup):
-        flush.fill_(1.0)
-        step()
-    torch.cuda.synchronize()
-    barrier(world)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
-    its, rrs = [], []
-    for k in range(steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        it, rr = step(ev[k][1])
-        ev[k][2].record(stream)
-        its.append(it)
-        rrs.append(rr)
-    torch.cuda.synchronize()
-    barrier(world)
-    lat = [e[0].elapsed_time(e[2]) for e in ev]
-    total = max_over_ranks(world, sum(lat))
-    return {"value": round(world * steps / (total / 1e3), 3), "unit": "solves/s",
-            "ms_per_step": round(total / steps, 3),
-            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
-                           "p99": round(float(np.percentile(lat, 99)), 3)},
-            "setup_ms": round(statistics.median(e[0].elapsed_time(e[1]) for e in ev), 3),
-            "solve_ms": round(statistics.median(e[1].elapsed_time(e[2]) for e in ev), 3),
-            "iters": its[-1], "relres": float(max(rrs)), "steps": steps}
-
-
 def golden_oracle_iters(name, tol):
     """The FP64 oracle's outer iterations for a workload, from the stored golden counts."""
     p = os.path.join(ROOT, "tests", "golden", "oracle_counts.txt")
@@ -555,19 +504,12 @@ def run_small_latency(args, world, flush, dev, stream):
                       dict(aux_level=aux, cycle_prec=amg.FP64, outer=amg.OUTER_FCG),
                       steps=max(20, args.steps), warmup=max(3, args.warmup))
     xg = x.cpu().numpy()
-    one = time_config_one_cta(args, world, flush, stream, A, b, x,
-                              dict(aux_level=aux, cycle_prec=amg.FP64),
-                              steps=max(20, args.steps), warmup=max(3, args.warmup))
-    x1 = x.cpu().numpy()
     oracle.build()
     O = oracle.Hierarchy.from_problem(prob, aux_level=aux)
     xo, ito, _, _ = O.solve(prob.b, args.tol)
-    one.update({"method": "the same plain FP64 method by the batched kernel on one CTA "
-                          "(amg_setup_many, a batch of one, fixed 1024-thread shape)",
-                "err_vs_oracle": rel_err(x1, xo)})
     return {"workload": "quasi_uniform_65", "unknowns": prob.n, "nnz": prob.nnz,
             "aux_level": aux, "method": "FP64 AMLI-cycle, flexible-CG outer (plain method)",
-            **res, "iters_oracle": ito, "err_vs_oracle": rel_err(xg, xo), "one_cta": one}
+            **res, "iters_oracle": ito, "err_vs_oracle": rel_err(xg, xo)}
 
 
 def run_graded(args, world, flush, dev, stream):
