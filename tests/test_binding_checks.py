@@ -111,3 +111,28 @@ def test_ell_packer_checks_rowptr(prob):
         amg.csr_to_ell(rp2, prob.col, prob.val, 9)
     with pytest.raises(ValueError):
         amg.csr_to_ell(rp, prob.col, prob.val[:-1], 9)
+
+
+def test_concatenate_lays_out_the_block_diagonal_matrix():
+    # amg.concatenate (the layout amg_batch_setup and amg_setup_many take): global row
+    # pointers and columns of the block-diagonal matrix, coordinates end to end, row offsets
+    import scipy.sparse as sp
+
+    probs = [p1_poisson(n, jitter=0.2, seed=n, rhs="normal") for n in (5, 9, 4, 12)]
+    ro, rp, cl, vl, xx, yy = amg.concatenate([(p.rowptr, p.col, p.val, p.x, p.y) for p in probs])
+    assert rp.dtype == np.int32 and cl.dtype == np.int32 and vl.dtype == np.float64
+    np.testing.assert_array_equal(ro, np.cumsum([0] + [p.n for p in probs]))
+    A = sp.csr_matrix((vl, cl, rp), shape=(ro[-1], ro[-1]))
+    B = sp.block_diag([p.to_scipy() for p in probs], format="csr")
+    assert abs(A - B).max() == 0.0 and A.nnz == B.nnz
+    np.testing.assert_array_equal(xx, np.concatenate([p.x for p in probs]))
+    np.testing.assert_array_equal(yy, np.concatenate([p.y for p in probs]))
+    bad = [(p.rowptr, p.col, p.val, p.x, p.y) for p in probs]
+    bad[2] = (probs[2].rowptr, probs[2].col, probs[2].val[:-1], probs[2].x, probs[2].y)
+    with pytest.raises(ValueError):
+        amg.concatenate(bad)
+
+
+def test_setup_many_rejects_unknown_options(prob):
+    with pytest.raises(TypeError):
+        amg.setup_many([_args(prob)], outer_method=1)
