@@ -279,8 +279,15 @@ def run_batched(args, world, flush, dev, stream):
     from paper_1209_5421_gb300 import amg
     from paper_1209_5421_gb300.meshes import batch_workload
 
+    from oracle import oracle
+
     probs = batch_workload(count=args.batch_systems)
     peak_gbs, _ = measured_peak_hbm()
+    off = np.concatenate([[0], np.cumsum([p.n for p in probs])])
+    by_size = sorted(range(len(probs)), key=lambda k: probs[k].n)
+    err_sample = sorted(set(by_size[::64] + [by_size[-1]]))
+    oracle_x = {}
+    oracle.build()
     rhs = torch.as_tensor(np.concatenate([p.b for p in probs])).to(dev)
     x = torch.empty_like(rhs)
     # the block-diagonal CSR on the device (host-side concatenation in the binding, timed
@@ -317,6 +324,15 @@ def run_batched(args, world, flush, dev, stream):
         team = B.teams()
         moved = B.moved_bytes()  # algorithmic bytes of one batch solve (the last one)
         B.close()
+        # error against the FP64 oracle's solution, per result, on a sample of the systems
+        # (every 64th in size order, the largest included)
+        xh = x.cpu().numpy()
+        errs = {}
+        for k in err_sample:
+            if k not in oracle_x:
+                O = oracle.Hierarchy.from_problem(probs[k])
+                oracle_x[k] = O.solve(probs[k].b, args.tol)[0]
+            errs[int(probs[k].n)] = rel_err(xh[off[k]:off[k + 1]], oracle_x[k])
         if not (sts == amg.OK).all():
             raise RuntimeError(f"batched {name}: statuses {sorted(set(sts.tolist()))}")
         res[name] = {
@@ -328,14 +344,15 @@ def run_batched(args, world, flush, dev, stream):
             "system_latency_ms": {"p50": round(float(np.percentile(sys_lat, 50)), 3),
                                   "p99": round(float(np.percentile(sys_lat, 99)), 3)},
             "iters": [int(its.min()), int(its.max())], "relres_max": float(rrs.max()),
+            "err_vs_oracle": {"by_unknowns": errs, "max": max(errs.values())},
             "launch_shape": {"threads": info["threads"], "ctas": info["ctas"],
                              "tuned_ms": [round(v, 2) for v in info["tuned_ms"]]},
             "teams": {"systems": int((team > 1).sum()), "ctas": int(team[team > 1].sum()),
                       "largest": int(team.max())},
             "device_bytes": info["bytes"],
             # the batched kernel's roofline: algorithmic bytes of the whole batch solve (every
-            # system's cycles and outer steps) over the batch's time; small systems' levels
-            # stay in L2, so this is not DRAM evidence
+            # system's cycles and outer steps) over the batch's time; ncu counts about as
+            # much DRAM traffic (the recorded `traffic`)
             "roofline": {"bound": "hbm", "kernel": "k_batch (whole batch solve)",
                          "achieved": round(moved / (t / args.steps / 1e3) / 1e9, 1),
                          "peak": peak_gbs, "unit": "GB/s",
