@@ -713,34 +713,14 @@ __device__ bool big_block_smem(const LV &L, const int *lofs, const int *lp, cons
         for (int i = slp[j] + t; i < p1; i += nt) {
             const int o = (int)eo[i] - 1, w = ew[i];
             T acc = 0;
-            if (w - 1 <= kRowBatch) {
-                // one batch (every P1 row): all of the row's shared-memory reads first, then
-                // the products summed in slot order, the zero terms included (row_dot's order)
-                T a[kRowBatch], xv[kRowBatch];
-#pragma unroll
-                for (int q = 0; q < kRowBatch; q++) {
-                    const int kk = 1 + q;
-                    a[q] = T(0);
-                    xv[q] = T(0);
-                    if (kk < w) {
-                        const unsigned short ix = si[o + kk];
-                        a[q] = sa[o + kk];
-                        xv[q] = ix != 0xFFFF ? su[ix] : sx[o + kk];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < kRowBatch; q++) acc += a[q] * xv[q];
-            } else {
-                int kk = 1;
-                for (; kk < w; kk++) {
-                    const unsigned short ix = si[o + kk];
-                    const T xv = ix != 0xFFFF ? su[ix] : sx[o + kk];
-                    acc += sa[o + kk] * xv;
-                }
-                for (const int kend = 1 + (w + kRowBatch - 2) / kRowBatch * kRowBatch; kk < kend;
-                     kk++)
-                    acc += T(0) * T(0);  // row_dot's zero terms to the end of its batch
+            int kk = 1;
+            for (; kk < w; kk++) {
+                const unsigned short ix = si[o + kk];
+                const T xv = ix != 0xFFFF ? su[ix] : sx[o + kk];
+                acc += sa[o + kk] * xv;
             }
+            for (const int kend = 1 + (w + kRowBatch - 2) / kRowBatch * kRowBatch; kk < kend; kk++)
+                acc += T(0) * T(0);  // row_dot's zero terms to the end of its batch
             su[erow[i]] = (ef[i] - acc) * ed[i];
         }
         g.sync();
