@@ -180,9 +180,11 @@ int amg_batch_setup(int32_t nprob, const int64_t *row_off, const amg_csr *A, con
                     const double *y, const amg_options *opt, void *stream, amg_batch **out);
 
 /*
- * amg_setup of many systems at once, each hierarchy returned on its own: the systems are given
- * as for amg_batch_setup (row_off, A, x, y, opt; any outer method) and set up together in the
- * same way, but out[p] (a host array of nprob pointers) receives system p's hierarchy,
+ * amg_setup (the setup of paper Sec. 3.1-4.5: auxiliary grid, quadtree aggregates, colours,
+ * Galerkin operators, exact coarsest inverse) of many systems at once, each hierarchy returned
+ * on its own: the systems are given as for amg_batch_setup (row_off, A, x, y, opt; any outer
+ * method) and set up together in the same way, but out[p] (a host array of nprob pointers,
+ * caller-allocated) receives system p's hierarchy,
  * bit for bit the one amg_setup builds from its block, owned by the caller and released by
  * amg_free like any other, independently of the others. With the flexible-CG outer method
  * each hierarchy is also ready for batched solves (amg_batch_create). The paper sets up one
